@@ -1,0 +1,350 @@
+/*
+ * FP64 CPU oracle for plenoctree luminaire rendering.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the bench's
+ * CPU-baseline leg may load this code.  It shares nothing with the CUDA
+ * library: not a header, not a helper, not a constant.
+ *
+ * What it computes (paper Sec. 4.1):
+ *   L_e(r) = int_0^{t1} T(r,t) sigma(r(t)) Phi(r(t), w) dt      (Eq. 3)
+ *   alpha(r) = 1 - T(r, t1)                                      (Eq. 5)
+ * with either Beer-Lambert transmittance T = exp(-int sigma) or the linear
+ * transmittance T = max(0, 1 - int sigma) (Eq. 4).  In a plenoctree sigma and
+ * the SH coefficients are constant inside each leaf (Sec. 4.2, Sec. 5), so
+ * the integral is an exact sum over the leaf segments the ray crosses: the
+ * oracle enumerates those segments in FP64 (point -> leaf descent, exact
+ * dyadic cell planes) and integrates each one in closed form.
+ *
+ *   exponential: w_i = T_i (1 - exp(-sigma_i dt_i)),  T_{i+1} = exp(-sum sigma dt)
+ *   linear     : T_{i+1} = max(0, 1 - sum sigma dt),   w_i = T_i - T_{i+1}
+ *                (NeRF-style quadrature weights, which sum to alpha)
+ *   linear, literal Eq. 3 with Eq. 4 inside the segment:
+ *                w_i = (T_i^2 - T_{i+1}^2) / 2
+ *   L_e = sum_i w_i Phi_i,  Phi_i = S(sum_k c_{i,k} Y_k(d))          (Eq. 6)
+ *   S = max(0, .) or L_max * sigmoid(.)
+ *
+ * SH basis: real, orthonormal, index k = l(l+1)+m, m < 0 <-> sin(|m| phi),
+ * no Condon-Shortley phase, built from the associated-Legendre recursion and
+ * the normalisation constants (Sec. 4.2 names the basis, not a convention).
+ *
+ * Conventions (readings of the paper):
+ *   - the ray is r(t) = o + t d with the caller's march direction d; SH is
+ *     evaluated at d (normalised in FP64);
+ *   - lookup tie rule: a point exactly on a mid-plane goes to the upper child
+ *     when the direction component is >= 0 (or when there is no direction);
+ *     the root box is closed;
+ *   - after a segment, the exit coordinate(s) are snapped to the exact plane;
+ *   - early stop: after a segment, stop if T < t_stop or T <= 0;
+ *   - sigma < sigma_min is treated as zero density (Sec. 6.2 heuristic).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int32_t depth, sh_degree;
+    int64_t n_nodes, n_leaves;
+    const int32_t* child;  /* [n_nodes][8] */
+    const float* sigma;    /* [n_leaves] */
+    const float* sh;       /* [n_leaves][3][K] */
+    double bbox_min[3], bbox_max[3];
+} oracle_tree;
+
+typedef struct {
+    int32_t transmittance; /* 0 exponential, 1 linear (dT weights), 2 linear literal */
+    int32_t activation;    /* 0 max(0,.), 1 l_max * sigmoid(.) */
+    double l_max;
+    double t_stop;
+    double sigma_min;
+} oracle_params;
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------ */
+/* Real spherical harmonics from the associated Legendre functions.     */
+
+static double factorial(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+/* P_l^m(x), m >= 0, without the Condon-Shortley phase. */
+static double assoc_legendre(int l, int m, double x) {
+    double pmm = 1.0;
+    if (m > 0) {
+        double s = sqrt((1.0 - x) * (1.0 + x));
+        double f = 1.0;
+        for (int i = 1; i <= m; ++i) {
+            pmm *= f * s;
+            f += 2.0;
+        }
+    }
+    if (l == m) return pmm;
+    double pmm1 = x * (2.0 * m + 1.0) * pmm;
+    if (l == m + 1) return pmm1;
+    double pll = 0.0;
+    for (int ll = m + 2; ll <= l; ++ll) {
+        pll = ((2.0 * ll - 1.0) * x * pmm1 - (ll + m - 1.0) * pmm) / (ll - m);
+        pmm = pmm1;
+        pmm1 = pll;
+    }
+    return pll;
+}
+
+/* Y[k], k = l(l+1)+m, for the direction (dx,dy,dz) (normalised here). */
+void oracle_sh_basis(int degree, double dx, double dy, double dz, double* Y) {
+    double n = sqrt(dx * dx + dy * dy + dz * dz);
+    double x = dx / n, y = dy / n, z = dz / n;
+    double phi = atan2(y, x);
+    for (int l = 0; l <= degree; ++l) {
+        for (int m = -l; m <= l; ++m) {
+            int am = m < 0 ? -m : m;
+            double K = sqrt((2.0 * l + 1.0) / (4.0 * OR_PI) * factorial(l - am) / factorial(l + am));
+            double P = assoc_legendre(l, am, z);
+            double v;
+            if (m == 0) v = K * P;
+            else if (m > 0) v = sqrt(2.0) * K * P * cos(am * phi);
+            else v = sqrt(2.0) * K * P * sin(am * phi);
+            Y[l * (l + 1) + m] = v;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Point -> leaf.  Returns the leaf id (>= 0), -1 for an empty octant, -2
+ * when p is outside the unit cube or the tree is malformed.  Writes the
+ * cell's lower corner and edge length. */
+static int64_t locate(const oracle_tree* t, const double p[3], const double* dir, double lo[3], double* size,
+                      int* level) {
+    for (int a = 0; a < 3; ++a)
+        if (!(p[a] >= 0.0 && p[a] <= 1.0)) return -2;
+    lo[0] = lo[1] = lo[2] = 0.0;
+    *size = 1.0;
+    *level = 0;
+    if (t->n_nodes == 0) return t->n_leaves == 1 ? 0 : -2; /* depth-0 tree: the root is a leaf */
+    int64_t node = 0;
+    for (int l = 0; l <= t->depth; ++l) {
+        int slot = 0;
+        double half = *size * 0.5;
+        for (int a = 0; a < 3; ++a) {
+            double mid = lo[a] + half;
+            int up = p[a] > mid || (p[a] == mid && (dir == NULL || dir[a] >= 0.0));
+            if (up) lo[a] = mid;
+            slot |= up << a;
+        }
+        *size = half;
+        *level = l + 1;
+        int32_t e = t->child[node * 8 + slot];
+        if (e >= 0) {
+            if (e >= t->n_nodes) return -2;
+            node = e;
+            continue;
+        }
+        if (e == -1) return -1;
+        int64_t leaf = -(int64_t)e - 2;
+        return leaf < t->n_leaves ? leaf : -2;
+    }
+    return -2; /* deeper than the declared depth */
+}
+
+void oracle_lookup(const oracle_tree* t, const float* pts, const float* dirs, int64_t n, int64_t* leaf_out,
+                   int32_t* level_out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double p[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+        double d[3];
+        if (dirs) {
+            d[0] = dirs[3 * i];
+            d[1] = dirs[3 * i + 1];
+            d[2] = dirs[3 * i + 2];
+        }
+        double lo[3], size;
+        int level;
+        leaf_out[i] = locate(t, p, dirs ? d : NULL, lo, &size, &level);
+        if (level_out) level_out[i] = level;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* One ray.  Outputs radiance, transmittance, the per-channel error scale
+ * sum_i w_i sum_k |c_k Y_k| (or sum_i w_i Phi_i for the sigmoid), the number
+ * of leaf segments and of segments whose SH record is read, and an optional
+ * trace of (leaf id or -1, t_in, t_out). */
+typedef struct {
+    double rgb[3], T, bound[3];
+    int32_t n_leaf, n_sh, n_cell, status;
+} ray_result;
+
+static void render_one(const oracle_tree* t, const oracle_params* prm, const float* ray, ray_result* res,
+                       int64_t* tr_leaf, double* tr_t, int32_t tr_max, int32_t* tr_n) {
+    const int K = (t->sh_degree + 1) * (t->sh_degree + 1);
+    double ext[3], o[3], d[3], dw[3];
+    for (int a = 0; a < 3; ++a) {
+        ext[a] = t->bbox_max[a] - t->bbox_min[a];
+        o[a] = ((double)ray[a] - t->bbox_min[a]) / ext[a];
+        dw[a] = ray[3 + a];
+        d[a] = dw[a] / ext[a];
+    }
+    memset(res, 0, sizeof(*res));
+    res->T = 1.0;
+    if (tr_n) *tr_n = 0;
+
+    /* proxy clip: slab test against the unit cube */
+    double tn = -INFINITY, tf = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) {
+            if (o[a] < 0.0 || o[a] > 1.0) return;
+            continue;
+        }
+        double t0 = (0.0 - o[a]) / d[a], t1 = (1.0 - o[a]) / d[a];
+        if (t0 > t1) { double s = t0; t0 = t1; t1 = s; }
+        if (t0 > tn) tn = t0;
+        if (t1 < tf) tf = t1;
+    }
+    if (!(tn < tf) || !(tf > 0.0)) return;
+
+    double Y[16];
+    oracle_sh_basis(t->sh_degree, dw[0], dw[1], dw[2], Y);
+
+    double tcur = tn > 0.0 ? tn : 0.0;
+    double p[3];
+    for (int a = 0; a < 3; ++a) p[a] = o[a] + tcur * d[a];
+    if (tn > 0.0) {
+        /* snap the entry face(s) */
+        for (int a = 0; a < 3; ++a) {
+            if (d[a] == 0.0) continue;
+            double t0 = (0.0 - o[a]) / d[a], t1 = (1.0 - o[a]) / d[a];
+            double near = t0 < t1 ? t0 : t1;
+            if (near == tn) p[a] = d[a] > 0.0 ? 0.0 : 1.0;
+        }
+    }
+
+    double T = 1.0, od = 0.0;
+    const int64_t max_iter = 3 * ((int64_t)1 << t->depth) + 16;
+    int64_t iter = 0;
+    for (;;) {
+        if (++iter > max_iter) { res->status = 1; break; }
+        for (int a = 0; a < 3; ++a) { /* FP64 rounding guard for non-snapped coordinates */
+            if (p[a] < 0.0) p[a] = 0.0;
+            if (p[a] > 1.0) p[a] = 1.0;
+        }
+        double lo[3], size;
+        int level;
+        int64_t leaf = locate(t, p, d, lo, &size, &level);
+        if (leaf == -2) { res->status = 2; break; }
+        double tx[3], tnext = tf;
+        for (int a = 0; a < 3; ++a) {
+            if (d[a] > 0.0) tx[a] = (lo[a] + size - o[a]) / d[a];
+            else if (d[a] < 0.0) tx[a] = (lo[a] - o[a]) / d[a];
+            else tx[a] = INFINITY;
+            if (tx[a] < tnext) tnext = tx[a];
+        }
+        double dt = tnext - tcur;
+        if (dt < 0.0) dt = 0.0;
+        res->n_cell++;
+        if (tr_n && *tr_n < tr_max) {
+            tr_leaf[*tr_n] = leaf;
+            tr_t[2 * *tr_n] = tcur;
+            tr_t[2 * *tr_n + 1] = tnext;
+            ++*tr_n;
+        }
+        if (leaf >= 0) {
+            res->n_leaf++;
+            double sg = t->sigma[leaf];
+            if (sg < prm->sigma_min) sg = 0.0;
+            if (sg > 0.0) {
+                const float* rec = t->sh + (size_t)leaf * 3 * K;
+                int emits = 0;
+                for (int k = 0; k < 3 * K; ++k) emits |= rec[k] != 0.0f;
+                double a_seg = sg * dt, w, Tn;
+                if (prm->transmittance == 0) {
+                    w = T * (-expm1(-a_seg));
+                    od += a_seg;
+                    Tn = exp(-od);
+                } else {
+                    od += a_seg;
+                    Tn = 1.0 - od;
+                    if (Tn < 0.0) Tn = 0.0;
+                    w = prm->transmittance == 1 ? T - Tn : 0.5 * (T * T - Tn * Tn);
+                }
+                if (emits) res->n_sh++;
+                if (emits || prm->activation == 1) {
+                    for (int ch = 0; ch < 3; ++ch) {
+                        double s = 0.0, sa = 0.0;
+                        for (int k = 0; k < K; ++k) {
+                            s += rec[ch * K + k] * Y[k];
+                            sa += fabs(rec[ch * K + k] * Y[k]);
+                        }
+                        double c;
+                        if (prm->activation == 0) {
+                            c = s > 0.0 ? s : 0.0;
+                            res->bound[ch] += w * sa;
+                        } else {
+                            c = prm->l_max / (1.0 + exp(-s));
+                            res->bound[ch] += w * c;
+                        }
+                        res->rgb[ch] += w * c;
+                    }
+                }
+                T = Tn;
+            }
+        }
+        if (tnext >= tf) break;
+        if (T < prm->t_stop || T <= 0.0) break;
+        tcur = tnext;
+        for (int a = 0; a < 3; ++a) p[a] = o[a] + tcur * d[a];
+        for (int a = 0; a < 3; ++a)
+            if (tx[a] == tnext) p[a] = d[a] > 0.0 ? lo[a] + size : lo[a];
+    }
+    res->T = T;
+}
+
+/* Render n rays (float[n][6]: origin, direction).  Any output pointer may be
+ * NULL.  n_threads <= 0 uses the OpenMP default.  Returns the number of rays
+ * whose status is non-zero. */
+int64_t oracle_render(const oracle_tree* t, const float* rays, int64_t n, const oracle_params* prm, double* rgb,
+                      double* T, double* bound, int32_t* n_leaf, int32_t* n_sh, int32_t* n_cell, int32_t* status,
+                      int n_threads) {
+    int64_t bad = 0;
+#ifdef _OPENMP
+    if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 64) num_threads(n_threads) reduction(+ : bad)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        ray_result r;
+        render_one(t, prm, rays + 6 * i, &r, NULL, NULL, 0, NULL);
+        if (rgb) for (int c = 0; c < 3; ++c) rgb[3 * i + c] = r.rgb[c];
+        if (T) T[i] = r.T;
+        if (bound) for (int c = 0; c < 3; ++c) bound[3 * i + c] = r.bound[c];
+        if (n_leaf) n_leaf[i] = r.n_leaf;
+        if (n_sh) n_sh[i] = r.n_sh;
+        if (n_cell) n_cell[i] = r.n_cell;
+        if (status) status[i] = r.status;
+        bad += r.status != 0;
+    }
+    return bad;
+}
+
+/* The ordered cells one ray crosses: leaf id (or -1 for an empty octant) and
+ * [t_in, t_out].  Returns the number written (<= max). */
+int32_t oracle_trace(const oracle_tree* t, const oracle_params* prm, const float* ray, int32_t max, int64_t* leaf,
+                     double* t_in_out) {
+    ray_result r;
+    int32_t n = 0;
+    render_one(t, prm, ray, &r, leaf, t_in_out, max, &n);
+    return n;
+}
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
