@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Throughput of the plenoctree luminaire render on GB300.
+
+Workload (the at-scale configuration): a procedural luminaire octree of max
+depth 10 (1024^3 finest cells, ~32M leaves, SH degree 3 = 16 coefficients x
+RGB + sigma, 196 B per FP32 leaf) and a wavefront of 16,777,216 rays with
+origins uniform in a 10 x 10 x 3 room and cosine-weighted directions, kept
+only when they meet the luminaire's proxy box.  One step renders the whole
+wavefront (proxy clip, octree walk, SH emission, compositing) with one
+persistent kernel launch; inputs are resident in HBM and larger than L2.
+
+Prints one JSON line (rank 0).  `value` is Mrays/s with FP32 leaves; the
+`fp16` / `bf16` objects time the same rays with 16-bit leaves.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s plenoctree render (FP32 vs FP16 leaves) and % of HBM roofline"
+UNIT = "Mrays/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rays", type=int, default=1 << 24)
+    ap.add_argument("--depth", type=int, default=10)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 20, help="rays in the oracle's timed sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(depth: int, n_rays: int, seed: int):
+    import plogen
+    rec = plogen.LUMINAIRE_D10.with_(depth=depth)
+    t0 = time.time()
+    tree = plogen.luminaire_tree(rec)
+    rays = plogen.rays_room(n_rays, seed=seed)
+    return rec, tree, rays, time.time() - t0
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed regions run."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.reader.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("render.cu", "plo_internal.h"):
+        with open(os.path.join(ROOT, "paper_2207_05009_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(precision: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "render_d10_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch", {}).get(precision)
+
+
+def rel_errors(rgb, T, ref):
+    scale = np.maximum(ref["bound"], 1e-30)
+    e_c = np.abs(np.asarray(rgb, np.float64) - ref["rgb"]) / scale
+    e_c[(ref["bound"] == 0) & (np.asarray(rgb) == 0)] = 0.0
+    e_T = np.abs(np.asarray(T, np.float64) - ref["T"]) / np.maximum(ref["T"], 1e-3)
+    return float(e_c.max()), float(e_T.max())
+
+
+def run_reference(args, world, rank):
+    """FP64 oracle on the host cores, on bounded samples of the workload."""
+    if rank != 0:
+        return 0
+    import oracle
+    rec, tree, rays, gen_s = workload(args.depth, args.rays, seed=11)
+    cores = len(os.sched_getaffinity(0))
+    per_step = min(args.cpu_sample // 4 if args.cpu_sample >= 4 else 1, len(rays))
+    for w in range(args.warmup):
+        oracle.render(tree, rays[(w * 997) % max(1, len(rays) - 4096):][:4096], n_threads=cores)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(args.steps):
+        off = (k * per_step) % max(1, len(rays) - per_step + 1)
+        oracle.render(tree, rays[off:off + per_step], n_threads=cores)
+        done += per_step
+    dt = time.perf_counter() - t0
+    v = done / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"luminaire octree depth {args.depth}, SH degree 3, {args.rays} room rays",
+                       "rays_per_step_sampled": per_step, "leaves": int(tree.n_leaves)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} rays of the {args.rays}-ray wavefront per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import paper_2207_05009_gb300 as plo
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    K, W = args.steps, args.warmup
+    assert W >= 3, "at least 3 warm-up steps"
+
+    rec, tree, rays_np, gen_s = workload(args.depth, args.rays, seed=11 + rank)
+    n = len(rays_np)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    trees = {"fp32": plo.Tree(tree, plo.PREC_FP32), "fp16": plo.Tree(tree, plo.PREC_FP16),
+             "bf16": plo.Tree(tree, plo.PREC_BF16)}
+    build_s = time.time() - t0
+    rays = torch.from_numpy(rays_np).cuda()
+    rgb = torch.empty((n, 3), device="cuda")
+    T = torch.empty(n, device="cuda")
+    params = plo.RenderParams()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def timed(tr):
+        for _ in range(W):
+            plo.render(tr, rays, params, rgb=rgb, T=T)
+        barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for a, b in evs:
+            a.record(stream)
+            plo.render(tr, rays, params, rgb=rgb, T=T)
+            b.record(stream)
+        end.record(stream)
+        barrier()
+        total = start.elapsed_time(end)
+        per_launch = [a.elapsed_time(b) for a, b in evs]
+        tr.check()
+        if dist is not None:
+            tt = torch.tensor([total], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            total = float(tt.item())
+        return total, sum(per_launch) / len(per_launch)
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    res = {}
+    for name in ("fp32", "fp16", "bf16"):
+        res[name] = timed(trees[name])
+    e2e = None
+    if not args.no_e2e:
+        rays_h = torch.from_numpy(rays_np).pin_memory()
+        rgb_h = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+        T_h = torch.empty(n, dtype=torch.float32).pin_memory()
+        for _ in range(W):
+            plo.render_host(trees["fp32"], rays_h, params, rgb=rgb_h, T=T_h)
+        barrier()
+        t1 = time.perf_counter()
+        for _ in range(K):
+            plo.render_host(trees["fp32"], rays_h, params, rgb=rgb_h, T=T_h)
+        barrier()
+        e2e_s = time.perf_counter() - t1
+        if dist is not None:
+            tt = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * n * K / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": n * 24,
+               "d2h_bytes_per_step": n * 16, "ms_per_step": e2e_s / K * 1e3}
+    clocks = sampler.stop()
+
+    # FP32 outputs of the last timed pass, for the parity spot check below
+    plo.render(trees["fp32"], rays, params, rgb=rgb, T=T)
+    out32 = (rgb[: args.cpu_sample].cpu().numpy(), T[: args.cpu_sample].cpu().numpy())
+    plo.render(trees["fp16"], rays, params, rgb=rgb, T=T)
+    out16 = (rgb[: args.cpu_sample].cpu().numpy(), T[: args.cpu_sample].cpu().numpy())
+    torch.cuda.synchronize()
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    # FP64 oracle on a bounded sample: CPU baseline, per-ray algorithmic
+    # bytes, and a parity spot check of the timed launch configuration.
+    cpu = None
+    K16 = tree.K
+    sample = min(args.cpu_sample, n)
+    if not args.no_cpu:
+        import oracle
+        cores = len(os.sched_getaffinity(0))
+        tc = time.perf_counter()
+        ref = oracle.render(tree, rays_np[:sample], n_threads=cores)
+        cpu_s = time.perf_counter() - tc
+        cpu = {"value": sample / cpu_s / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {sample} rays of the {n}-ray wavefront ({cpu_s:.1f} s)"}
+        leaf_visits = float(ref["n_leaf"].mean())
+        sh_visits = float(ref["n_sh"].mean())
+        cells = float(ref["n_cell"].mean())
+        parity = {"sample_rays": sample, "fp32_max_rel_err": rel_errors(*out32, ref),
+                  "fp16_max_rel_err": rel_errors(*out16, ref)}
+    else:
+        leaf_visits = sh_visits = cells = float("nan")
+        parity = None
+
+    peak, peak_kind = measured_peak()
+    bytes_ray = {"fp32": 40 + 4 * leaf_visits + 12 * K16 * sh_visits,
+                 "fp16": 40 + 4 * leaf_visits + (6 * K16 + 4) * sh_visits}
+    bytes_ray["bf16"] = bytes_ray["fp16"]
+    lines = {}
+    for name, (total, per_launch) in res.items():
+        mrays = world * n * K / (total / 1e3) / 1e6
+        ach = bytes_ray[name] * n / (per_launch / 1e3) / 1e9
+        traffic = ncu_traffic(name)
+        lines[name] = {"value": mrays, "ms_per_step": total / K, "kernel_ms": per_launch,
+                       "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                    "frac": ach / peak, "traffic": traffic,
+                                    "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                                    "frac_of_8TBs": ach / 8000.0,
+                                    "algorithmic_bytes_per_ray": bytes_ray[name]}}
+    info = trees["fp32"].info()
+    line = {
+        "metric": METRIC, "value": lines["fp32"]["value"], "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": lines["fp32"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"luminaire octree depth {args.depth} ({tree.n_leaves} leaves, SH degree 3, "
+                               f"K=16), {n} room rays per GPU meeting the proxy box",
+                   "rays_per_gpu": n, "leaves": int(tree.n_leaves), "nodes": int(tree.n_nodes),
+                   "emissive_leaves": int(info["n_sh_records"]),
+                   "tree_bytes_fp32": int(info["node_bytes"] + info["sh_bytes"]),
+                   "l2": "inputs larger than L2 (tree and rays each exceed 129 MB); no flush",
+                   "parallelism": f"replicas x{world} (rays shard, no collective)",
+                   "mean_cells_per_ray": cells, "mean_leaf_visits_per_ray": leaf_visits,
+                   "mean_sh_reads_per_ray": sh_visits, "host_setup_s": round(gen_s + build_s, 1)},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": K,
+        "roofline": lines["fp32"]["roofline"],
+        "cpu_baseline": cpu,
+        "fp16": {k: v for k, v in lines["fp16"].items()},
+        "bf16": {k: v for k, v in lines["bf16"].items()},
+        "fp16_speedup_vs_fp32": lines["fp16"]["value"] / lines["fp32"]["value"],
+        "parity": parity,
+    }
+    line["fp16"]["roofline"]["frac"] = line["fp16"]["roofline"]["achieved"] / peak
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

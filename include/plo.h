@@ -1,0 +1,191 @@
+/*
+ * plo.h — C ABI of libplo, a GB300 (sm_103a) library that renders complex
+ * luminaires stored as plenoctrees and trains / distils the NeRF-SH network
+ * they come from.
+ *
+ * Method: Condor & Jarabo, "A Learned Radiance-Field Representation for
+ * Complex Luminaires" (EGSR 2022, arXiv 2207.05009).  A luminaire is a
+ * radiance field inside a proxy box (Sec. 3); along a ray r(t) the library
+ * returns the emitted radiance L_e (Eq. 3) and the transmittance T(r, t1) so
+ * that the caller forms L_o = L_e + T * L_i (Eq. 2, read with the pass-through
+ * factor T; alpha = 1 - T is Eq. 5).  The field is stored as a sparse octree
+ * of leaves holding a density sigma and real SH coefficients of the emission
+ * (Sec. 4.2, Sec. 5).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are caller-owned DEVICE memory (for example PyTorch
+ *     tensors on the current device); h_* are caller-owned HOST memory.  The
+ *     library never frees caller memory and keeps no pointer to it after the
+ *     call returns (asynchronous calls read/write it in stream order).
+ *   - Handles (plo_tree) are owned by the library and freed by *_free.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Calls marked "async" enqueue work and return without
+ *     synchronising; errors found on the host are returned immediately.
+ *   - On a non-OK status, plo_last_error() returns a message for the calling
+ *     thread.  No call aborts the process.
+ *   - All arrays are C-contiguous, little-endian, float32 unless stated.
+ */
+#ifndef PLO_H
+#define PLO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PLO_OK = 0,
+    PLO_ERR_INVALID_ARG = -1,     /* bad pointer, size, enum or parameter value      */
+    PLO_ERR_BAD_TREE = -2,        /* canonical tree failed validation                 */
+    PLO_ERR_OOM = -3,             /* device or host allocation failed                 */
+    PLO_ERR_CUDA = -4,            /* a CUDA runtime call failed                       */
+    PLO_ERR_TRAVERSAL_LIMIT = -5, /* some ray hit the per-ray step cap (device-found) */
+    PLO_ERR_TIMEOUT = -6,         /* a bounded device wait gave up (device-found)     */
+    PLO_ERR_UNSUPPORTED = -7      /* valid request this build does not implement      */
+} plo_status;
+
+/* Leaf storage precision (Sec. 5 leaves, stored in FP32 or in 16-bit floats
+ * with a per-leaf power-of-two FP32 scale for the SH coefficients). */
+enum { PLO_PREC_FP32 = 0, PLO_PREC_FP16 = 1, PLO_PREC_BF16 = 2 };
+/* Transmittance model: Beer-Lambert, or the linear model of Eq. 4 with
+ * weights w_i = T_i - T_{i+1}, or Eq. 4 integrated literally inside each
+ * segment, w_i = (T_i^2 - T_{i+1}^2) / 2. */
+enum { PLO_TRANS_EXP = 0, PLO_TRANS_LINEAR = 1, PLO_TRANS_LINEAR_LITERAL = 2 };
+/* Emission activation S of Eq. 6: max(0, x), or l_max * sigmoid(x). */
+enum { PLO_ACT_RELU = 0, PLO_ACT_SIGMOID = 1 };
+
+/* Per-ray status codes written to the optional d_status arrays. */
+enum { PLO_RAY_OK = 0, PLO_RAY_STEP_LIMIT = 1, PLO_RAY_INVALID = 3 };
+
+typedef struct plo_tree plo_tree;
+
+/* Canonical host tree (Sec. 5 plenoctree), read-only during the call.
+ *   depth      maximum leaf level, 0..16 (level 0 = the root cell).
+ *   sh_degree  l_max, 0..3; K = (l_max + 1)^2 coefficients per channel.
+ *   child      int32 [n_nodes][8]: >= 0 internal node id, -1 empty octant,
+ *              <= -2 leaf with id -c-2.  Node 0 is the root; the child slot is
+ *              bx | by << 1 | bz << 2 with b = 1 for the upper half.
+ *              n_nodes == 0 means the root itself is leaf 0 (n_leaves == 1) or
+ *              the tree is empty (n_leaves == 0).
+ *   sigma      float [n_leaves], finite, >= 0 (density per unit length).
+ *   sh         float [n_leaves][3][K] channel-major SH coefficients.
+ *   bbox_min/max  proxy box in world space the unit cube maps onto. */
+typedef struct {
+    int32_t depth;
+    int32_t sh_degree;
+    int64_t n_nodes;
+    int64_t n_leaves;
+    const int32_t* child;
+    const float* sigma;
+    const float* sh;
+    float bbox_min[3];
+    float bbox_max[3];
+} plo_tree_desc;
+
+/* Render parameters.
+ *   transmittance  PLO_TRANS_*          activation  PLO_ACT_*
+ *   l_max          scale of the sigmoid activation (Eq. 6); ignored for RELU
+ *   t_stop         stop a ray once T < t_stop after a leaf (0 = never early;
+ *                  alpha_max of Sec. 6.2 is t_stop = 1 - alpha_max)
+ *   sigma_min      leaves with sigma < sigma_min count as empty (Sec. 6.2)
+ *   max_steps      per-ray cap on cells visited; 0 = 4 * 2^depth + 64 */
+typedef struct {
+    int32_t transmittance;
+    int32_t activation;
+    float l_max;
+    float t_stop;
+    float sigma_min;
+    int32_t max_steps;
+} plo_render_params;
+
+typedef struct {
+    int32_t depth, sh_degree, precision;
+    int32_t top_levels;        /* levels staged in shared memory by the render kernel */
+    int64_t n_nodes, n_leaves;
+    int64_t n_sh_records;      /* leaves with at least one non-zero SH coefficient   */
+    int64_t node_bytes;        /* device bytes of the node table                     */
+    int64_t sh_bytes;          /* device bytes of the SH record table                */
+    int32_t sh_record_stride;  /* bytes between SH records                           */
+    int32_t device;            /* CUDA device that holds the tree                    */
+} plo_tree_info;
+
+/* Checks a canonical tree on the host without touching a GPU: index ranges,
+ * each node and leaf referenced at most once (no cycles or sharing), node
+ * levels below `depth`, finite non-negative sigma, finite SH, box extents.
+ * Returns PLO_OK, PLO_ERR_INVALID_ARG or PLO_ERR_BAD_TREE. */
+plo_status plo_validate_tree(const plo_tree_desc* desc);
+
+/* Validates `desc`, packs it into the device layout at `precision`
+ * (PLO_PREC_*) and uploads it to the current CUDA device.  Synchronous.
+ * FP16 stores sigma as binary16 (sigma must be <= 65504) and each leaf's SH
+ * coefficients as binary16 times a per-leaf power-of-two FP32 scale; BF16 the
+ * same in bfloat16.  On success *out owns the device copy; free it with
+ * plo_tree_free.  The host arrays may be released after the call. */
+plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out);
+
+/* Frees a tree (NULL is a no-op).  Synchronises the device first. */
+void plo_tree_free(plo_tree* tree);
+
+plo_status plo_tree_get_info(const plo_tree* tree, plo_tree_info* out);
+
+/* Renders n rays (async).  Per ray, paper Eq. 3-5: clip to the proxy box,
+ * walk the octree front to back over exact per-leaf segments, evaluate the
+ * leaf's SH emission in the ray direction, composite emission/absorption.
+ *   d_rays    float [n][6]: origin xyz, direction xyz (world space; the
+ *             direction should be unit length: t is measured in its units).
+ *   d_rgb     float [n][3] emitted radiance L_e.
+ *   d_T       float [n] transmittance T(r, t1); alpha = 1 - T.
+ *   d_status  int32 [n] per-ray PLO_RAY_* code, or NULL.
+ * A ray with a NaN/Inf component or a zero direction gets NaN outputs and
+ * PLO_RAY_INVALID.  A ray that exceeds max_steps keeps its partial result,
+ * gets PLO_RAY_STEP_LIMIT and raises the tree's device error flag (read by
+ * plo_tree_check).  n == 0 is a no-op. */
+plo_status plo_render_rays(const plo_tree* tree, const float* d_rays, int64_t n, const plo_render_params* params,
+                           float* d_rgb, float* d_T, int32_t* d_status, void* stream);
+
+/* Same computation as plo_render_rays for rays in HOST memory: copies
+ * h_rays to the device, renders, copies h_rgb / h_T back, in chunks that
+ * overlap copies with rendering on internal streams ordered after `stream`.
+ * Synchronous (returns after h_rgb / h_T are written).  Pinned host memory
+ * gives full copy bandwidth; pageable memory works but is slower. */
+plo_status plo_render_rays_host(const plo_tree* tree, const float* h_rays, int64_t n,
+                                const plo_render_params* params, float* h_rgb, float* h_T, void* stream);
+
+/* Point -> leaf lookup (async), the descent step of the render.
+ *   d_points  float [n][3] in the tree's unit-cube coordinates.
+ *   d_dirs    float [n][3] or NULL: on a cell plane a point belongs to the
+ *             upper cell when the direction component is >= 0 (always, when
+ *             NULL); the faces of the root cube are closed.
+ *   d_leaf    int64 [n] canonical leaf id, -1 for an empty octant, -2 outside
+ *             the unit cube.
+ *   d_level   int32 [n] level of the cell found, or NULL. */
+plo_status plo_lookup_points(const plo_tree* tree, const float* d_points, const float* d_dirs, int64_t n,
+                             int64_t* d_leaf, int32_t* d_level, void* stream);
+
+/* Diagnostic trace (async): the first `max_cells` cells each ray crosses, in
+ * order, exactly as plo_render_rays walks them.
+ *   d_leaf   int64 [n][max_cells] canonical leaf id, -1 for an empty octant
+ *            (unused slots -3).
+ *   d_t      float [n][max_cells][2] segment [t_in, t_out] along the ray.
+ *   d_count  int32 [n] number of cells crossed (may exceed max_cells). */
+plo_status plo_trace_rays(const plo_tree* tree, const float* d_rays, int64_t n, const plo_render_params* params,
+                          int32_t max_cells, int64_t* d_leaf, float* d_t, int32_t* d_count, void* stream);
+
+/* Synchronises `stream` and reports device-detected errors of earlier
+ * renders of this tree: PLO_ERR_TRAVERSAL_LIMIT if some ray hit its step cap.
+ * Clears the flag. */
+plo_status plo_tree_check(const plo_tree* tree, void* stream);
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+const char* plo_last_error(void);
+
+/* Library version string. */
+const char* plo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLO_H */

@@ -124,7 +124,8 @@ def render(tree, rays, transmittance=EXPONENTIAL, activation=RELU, l_max=1.0, t_
            n_threads: int = 0) -> dict:
     """Exact FP64 render of float32 rays [n,6].  Returns a dict of arrays:
     rgb [n,3], T [n], bound [n,3] (per-channel error scale), n_leaf, n_sh,
-    n_cell, status (0 ok, 1 iteration cap, 2 lookup failure)."""
+    n_cell, status (0 ok, 1 iteration cap, 2 lookup failure, 3 invalid ray:
+    NaN/Inf component or zero direction, with NaN outputs)."""
     lib = _load()
     b = _Bound(tree)
     rays = np.ascontiguousarray(rays, np.float32)

@@ -175,7 +175,8 @@ void oracle_lookup(const oracle_tree* t, const float* pts, const float* dirs, in
 /* One ray.  Outputs radiance, transmittance, the per-channel error scale
  * sum_i w_i sum_k |c_k Y_k| (or sum_i w_i Phi_i for the sigmoid), the number
  * of leaf segments and of segments whose SH record is read, and an optional
- * trace of (leaf id or -1, t_in, t_out). */
+ * trace of (leaf id or -1, t_in, t_out).  Status: 0 ok, 1 iteration cap,
+ * 2 lookup failure, 3 invalid ray (NaN/Inf component or zero direction). */
 typedef struct {
     double rgb[3], T, bound[3];
     int32_t n_leaf, n_sh, n_cell, status;
@@ -194,6 +195,14 @@ static void render_one(const oracle_tree* t, const oracle_params* prm, const flo
     memset(res, 0, sizeof(*res));
     res->T = 1.0;
     if (tr_n) *tr_n = 0;
+    /* a ray with a non-finite component or a zero direction is invalid */
+    int bad = dw[0] == 0.0 && dw[1] == 0.0 && dw[2] == 0.0;
+    for (int a = 0; a < 6; ++a) bad |= !isfinite((double)ray[a]);
+    if (bad) {
+        res->status = 3;
+        res->rgb[0] = res->rgb[1] = res->rgb[2] = res->T = NAN;
+        return;
+    }
 
     /* proxy clip: slab test against the unit cube */
     double tn = -INFINITY, tf = INFINITY;

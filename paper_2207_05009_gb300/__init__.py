@@ -1,0 +1,239 @@
+"""Python binding of libplo (include/plo.h): plenoctree luminaire rendering on
+GB300.  Argument marshalling only: every step of the path runs in the
+library's CUDA kernels; PyTorch supplies device memory and the current stream.
+
+There is no CPU fallback.  If libplo.so cannot be built or loaded, or no CUDA
+device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["PloError", "Tree", "RenderParams", "load", "render", "render_host", "lookup", "trace",
+           "PREC_FP32", "PREC_FP16", "PREC_BF16", "TRANS_EXP", "TRANS_LINEAR", "TRANS_LINEAR_LITERAL",
+           "ACT_RELU", "ACT_SIGMOID"]
+
+PREC_FP32, PREC_FP16, PREC_BF16 = 0, 1, 2
+TRANS_EXP, TRANS_LINEAR, TRANS_LINEAR_LITERAL = 0, 1, 2
+ACT_RELU, ACT_SIGMOID = 0, 1
+RAY_OK, RAY_STEP_LIMIT, RAY_INVALID = 0, 1, 3
+
+STATUS_NAMES = {0: "PLO_OK", -1: "PLO_ERR_INVALID_ARG", -2: "PLO_ERR_BAD_TREE", -3: "PLO_ERR_OOM",
+                -4: "PLO_ERR_CUDA", -5: "PLO_ERR_TRAVERSAL_LIMIT", -6: "PLO_ERR_TIMEOUT",
+                -7: "PLO_ERR_UNSUPPORTED"}
+
+
+class PloError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class TreeDesc(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
+                ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("child", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("sh", ctypes.c_void_p),
+                ("bbox_min", ctypes.c_float * 3), ("bbox_max", ctypes.c_float * 3)]
+
+
+class _RenderParams(ctypes.Structure):
+    _fields_ = [("transmittance", ctypes.c_int32), ("activation", ctypes.c_int32),
+                ("l_max", ctypes.c_float), ("t_stop", ctypes.c_float), ("sigma_min", ctypes.c_float),
+                ("max_steps", ctypes.c_int32)]
+
+
+class TreeInfo(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("top_levels", ctypes.c_int32), ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("n_sh_records", ctypes.c_int64), ("node_bytes", ctypes.c_int64), ("sh_bytes", ctypes.c_int64),
+                ("sh_record_stride", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+@dataclass
+class RenderParams:
+    transmittance: int = TRANS_EXP
+    activation: int = ACT_RELU
+    l_max: float = 1.0
+    t_stop: float = 0.0
+    sigma_min: float = 0.0
+    max_steps: int = 0
+
+    def _c(self) -> _RenderParams:
+        p = _RenderParams()
+        p.transmittance, p.activation = self.transmittance, self.activation
+        p.l_max, p.t_stop, p.sigma_min, p.max_steps = self.l_max, self.t_stop, self.sigma_min, self.max_steps
+        return p
+
+
+_lib = None
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Loads libplo.so (building it first when sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libplo.so not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sigs = {
+        "plo_validate_tree": (I32, [P]),
+        "plo_build_tree": (I32, [P, I32, P]),
+        "plo_tree_free": (None, [P]),
+        "plo_tree_get_info": (I32, [P, P]),
+        "plo_render_rays": (I32, [P, P, I64, P, P, P, P, P]),
+        "plo_render_rays_host": (I32, [P, P, I64, P, P, P, P]),
+        "plo_lookup_points": (I32, [P, P, P, I64, P, P, P]),
+        "plo_trace_rays": (I32, [P, P, I64, P, I32, P, P, P, P]),
+        "plo_tree_check": (I32, [P, P]),
+        "plo_last_error": (ctypes.c_char_p, []),
+        "plo_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise PloError(status, load().plo_last_error().decode())
+
+
+def _desc(host_tree):
+    """ctypes descriptor for a canonical host tree (keeps arrays alive)."""
+    child = np.ascontiguousarray(host_tree.child, np.int32)
+    sigma = np.ascontiguousarray(host_tree.sigma, np.float32)
+    sh = np.ascontiguousarray(host_tree.sh, np.float32)
+    d = TreeDesc()
+    d.depth, d.sh_degree = int(host_tree.depth), int(host_tree.sh_degree)
+    d.n_nodes, d.n_leaves = child.shape[0], sigma.shape[0]
+    d.child = child.ctypes.data if child.size else None
+    d.sigma = sigma.ctypes.data if sigma.size else None
+    d.sh = sh.ctypes.data if sh.size else None
+    d.bbox_min[:] = tuple(getattr(host_tree, "bbox_min", (0.0, 0.0, 0.0)))
+    d.bbox_max[:] = tuple(getattr(host_tree, "bbox_max", (1.0, 1.0, 1.0)))
+    return d, (child, sigma, sh)
+
+
+def validate(host_tree) -> None:
+    """Host-only validation of a canonical tree (raises PloError)."""
+    d, keep = _desc(host_tree)
+    _check(load().plo_validate_tree(ctypes.byref(d)))
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Tree:
+    """A packed plenoctree on the current CUDA device (plo_build_tree)."""
+
+    def __init__(self, host_tree, precision: int = PREC_FP32):
+        lib = load()
+        d, keep = _desc(host_tree)
+        h = ctypes.c_void_p()
+        _check(lib.plo_build_tree(ctypes.byref(d), precision, ctypes.byref(h)))
+        self._h = h
+        self.precision = precision
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = TreeInfo()
+        _check(load().plo_tree_get_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in TreeInfo._fields_}
+
+    def check(self, stream=None) -> None:
+        _check(load().plo_tree_check(self._h, _stream(stream)))
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().plo_tree_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def render(tree: Tree, rays, params: RenderParams | None = None, rgb=None, T=None, status=None, stream=None):
+    """plo_render_rays on CUDA tensors: rays float32 [n, 6] -> (rgb [n,3], T [n], status [n] or None)."""
+    import torch
+    params = params or RenderParams()
+    if not (rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous() and rays.shape[-1] == 6):
+        raise ValueError("rays must be a contiguous float32 CUDA tensor of shape [n, 6]")
+    n = rays.shape[0]
+    rgb = rgb if rgb is not None else torch.empty((n, 3), device=rays.device, dtype=torch.float32)
+    T = T if T is not None else torch.empty(n, device=rays.device, dtype=torch.float32)
+    p = params._c()
+    _check(load().plo_render_rays(tree.handle, _ptr(rays), n, ctypes.byref(p), _ptr(rgb), _ptr(T), _ptr(status),
+                                  _stream(stream)))
+    return rgb, T, status
+
+
+def render_host(tree: Tree, rays: np.ndarray, params: RenderParams | None = None, rgb=None, T=None, stream=None):
+    """plo_render_rays_host: rays in host memory (numpy or pinned CPU tensor)."""
+    params = params or RenderParams()
+    import torch
+    if isinstance(rays, torch.Tensor):
+        n = rays.shape[0]
+        rp = rays.data_ptr()
+        rgb = rgb if rgb is not None else torch.empty((n, 3), dtype=torch.float32, pin_memory=rays.is_pinned())
+        T = T if T is not None else torch.empty(n, dtype=torch.float32, pin_memory=rays.is_pinned())
+        op, tp = rgb.data_ptr(), T.data_ptr()
+    else:
+        rays = np.ascontiguousarray(rays, np.float32)
+        n = rays.shape[0]
+        rp = rays.ctypes.data
+        rgb = rgb if rgb is not None else np.empty((n, 3), np.float32)
+        T = T if T is not None else np.empty(n, np.float32)
+        op, tp = rgb.ctypes.data, T.ctypes.data
+    p = params._c()
+    _check(load().plo_render_rays_host(tree.handle, ctypes.c_void_p(rp), n, ctypes.byref(p), ctypes.c_void_p(op),
+                                       ctypes.c_void_p(tp), _stream(stream)))
+    return rgb, T
+
+
+def lookup(tree: Tree, points, dirs=None, stream=None):
+    """plo_lookup_points: points float32 [n,3] CUDA -> (leaf int64 [n], level int32 [n])."""
+    import torch
+    n = points.shape[0]
+    leaf = torch.empty(n, device=points.device, dtype=torch.int64)
+    level = torch.empty(n, device=points.device, dtype=torch.int32)
+    _check(load().plo_lookup_points(tree.handle, _ptr(points), _ptr(dirs), n, _ptr(leaf), _ptr(level),
+                                    _stream(stream)))
+    return leaf, level
+
+
+def trace(tree: Tree, rays, max_cells: int, params: RenderParams | None = None, stream=None):
+    """plo_trace_rays: -> (leaf int64 [n, max_cells], t float32 [n, max_cells, 2], count int32 [n])."""
+    import torch
+    params = params or RenderParams()
+    n = rays.shape[0]
+    leaf = torch.full((n, max_cells), -3, device=rays.device, dtype=torch.int64)
+    t = torch.zeros((n, max_cells, 2), device=rays.device, dtype=torch.float32)
+    cnt = torch.zeros(n, device=rays.device, dtype=torch.int32)
+    p = params._c()
+    _check(load().plo_trace_rays(tree.handle, _ptr(rays), n, ctypes.byref(p), max_cells, _ptr(leaf), _ptr(t),
+                                 _ptr(cnt), _stream(stream)))
+    return leaf, t, cnt

@@ -1,0 +1,68 @@
+// Internal definitions shared by the library's translation units.
+//
+// Device layout of a packed tree (built by tree.cpp from the canonical host
+// format of include/plo.h):
+//
+//   nodes   uint2 [n_nodes][8]   one 8-byte entry per child slot
+//             .x == ENTRY_EMPTY             empty octant
+//             .x <  LEAF_BIT                internal node id
+//             .x &  LEAF_BIT                leaf; low 31 bits = SH record id,
+//                                           or NO_SH_RECORD when all of the
+//                                           leaf's coefficients are zero
+//             .y  (leaves only)  FP32 trees: sigma as float bits
+//                               FP16/BF16:  bits 0..15 sigma (binary16 or
+//                               bfloat16), bits 16..23 biased exponent of the
+//                               leaf's power-of-two SH scale
+//           A leaf's density travels with its parent's child entry, so a
+//           non-emissive leaf costs no load beyond the descent itself.
+//           Nodes of the top `top_levels` levels come first (breadth-first),
+//           the rest follow in depth-first (Morton) order.
+//   leaf_ids int32 [n_nodes][8]  canonical leaf id per entry (-1 otherwise);
+//           read only by the lookup and trace diagnostics.
+//   sh      records of 3*K coefficients, channel-major, one per emissive
+//           leaf, in depth-first order, `sh_stride` bytes apart (16-byte
+//           aligned): FP32 12K bytes rounded up to 16; FP16/BF16 6K rounded
+//           up to 16 (K=9: 64 B, K=16: 96 B).
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/plo.h"
+
+namespace plo {
+
+constexpr uint32_t ENTRY_EMPTY = 0xFFFFFFFFu;
+constexpr uint32_t LEAF_BIT = 0x80000000u;
+constexpr uint32_t NO_SH_RECORD = 0x7FFFFFFEu;
+constexpr int MAX_DEPTH = 16;
+constexpr int MAX_TOP_NODES = 585;  // levels 0..3 of a full octree
+
+inline int sh_K(int degree) { return (degree + 1) * (degree + 1); }
+inline int sh_stride_bytes(int K, int precision) {
+    int raw = precision == PLO_PREC_FP32 ? 12 * K : 6 * K;
+    return (raw + 15) / 16 * 16;
+}
+
+// Thread-local error message, returned by plo_last_error().
+plo_status set_error(plo_status s, const std::string& msg);
+plo_status cuda_error(int err, const char* what);
+
+}  // namespace plo
+
+struct plo_tree {
+    int32_t depth;       // depth of the packed tree (>= 1; a root leaf is re-rooted one level down)
+    int32_t sh_degree, K, precision;
+    int32_t top_levels;  // levels whose nodes are staged in shared memory
+    int32_t n_top;       // number of nodes in those levels (ids 0..n_top-1)
+    int64_t n_nodes, n_leaves, n_sh;
+    int32_t sh_stride;
+    int32_t device;
+    float bbox_min[3], inv_ext[3];
+    void* d_nodes;       // uint2 [n_nodes][8]
+    int32_t* d_leaf_ids; // [n_nodes][8]
+    void* d_sh;
+    unsigned int* d_flags;  // device error flags (bit 0: step limit)
+    int64_t node_bytes, sh_bytes;
+    int32_t sm_count;
+};

@@ -1,0 +1,661 @@
+// Fused plenoctree render kernel for sm_103a: proxy clip -> octree walk ->
+// per-leaf SH emission -> front-to-back emission/absorption compositing
+// (paper Sec. 4.1, Eq. 3-5; plenoctree of Sec. 4.2 / Sec. 5).
+//
+// One thread renders one ray at a time.  The grid is persistent: each warp
+// owns a contiguous chunk of rays and a lane that finishes its ray takes the
+// next one of the chunk, so a warp does not idle behind its longest ray.
+//
+// Numerics (all FP32, no FP64 on the device):
+//   * The ray position is kept as an unevaluated sum hi + lo of two floats
+//     per axis ("double-float").  Segment lengths come from exact dyadic cell
+//     planes minus that position, so every segment length has ~1e-7 relative
+//     error however far the ray origin is, and the cell sequence matches an
+//     FP64 walk except for rays passing within ~1e-13 of a cell edge.
+//   * The exit coordinate is snapped onto the exact plane; the next cell is
+//     found by re-descending from the deepest common ancestor (kept on a
+//     per-ray stack) with the tie rule "on a plane, go where the direction
+//     points", so progress is guaranteed.
+//   * Optical depth is accumulated as a compensated (two-float) sum;
+//     T = exp(-OD) or max(0, 1 - OD) is recomputed from it after each leaf.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "plo_internal.h"
+
+namespace plo {
+namespace {
+
+constexpr int BLOCK = 256;
+constexpr int WARPS = BLOCK / 32;
+constexpr int STACK = MAX_DEPTH + 1;
+
+struct KParams {
+    const uint2* nodes;
+    const int32_t* leaf_ids;
+    const uint8_t* sh;
+    int32_t sh_stride;
+    int32_t depth;
+    int32_t n_top;
+    float bmin[3], inv_ext[3];
+    int32_t transmittance, activation;
+    float l_max, t_stop, sigma_min;
+    int32_t max_steps;
+    const float* rays;
+    int64_t n;
+    int64_t chunk;  // rays per warp
+    float* rgb;
+    float* T;
+    int32_t* status;
+    unsigned int* flags;
+    // trace mode
+    int32_t trace_max;
+    int64_t* tr_leaf;
+    float* tr_t;
+    int32_t* tr_count;
+};
+
+// ---------------------------------------------------------------- double-float
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// (a_hi + a_lo) * (r_hi + r_lo) with r = 1/d in double-float.
+__device__ __forceinline__ DF df_mul(DF a, float rh, float rl) {
+    float p = __fmul_rn(a.hi, rh);
+    float e = __fmaf_rn(a.hi, rh, -p);
+    e = __fmaf_rn(a.hi, rl, e);
+    e = __fmaf_rn(a.lo, rh, e);
+    return fast_two_sum(p, e);
+}
+// double-float reciprocal of d (d finite, non-zero)
+__device__ __forceinline__ void df_recip(float d, float& rh, float& rl) {
+    rh = __frcp_rn(d);
+    float r = __fmaf_rn(-rh, d, 1.0f);  // exact residual
+    rl = __fmul_rn(r, rh);
+}
+// p + t * d, all double-float except d
+__device__ __forceinline__ DF df_axpy(DF p, DF t, float d) {
+    float m = __fmul_rn(t.hi, d);
+    float me = __fmaf_rn(t.hi, d, -m);
+    me = __fmaf_rn(t.lo, d, me);
+    DF s = two_sum(p.hi, m);
+    float lo = __fadd_rn(__fadd_rn(s.lo, p.lo), me);
+    return fast_two_sum(s.hi, lo);
+}
+// (P - p) for an exact float plane P
+__device__ __forceinline__ DF df_from_plane(float P, DF p) {
+    DF n = two_sum(P, -p.hi);
+    return two_sum(n.hi, __fsub_rn(n.lo, p.lo));
+}
+__device__ __forceinline__ bool df_less(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool df_eq(DF a, DF b) { return a.hi == b.hi && a.lo == b.lo; }
+// tie rule: p above the plane m, or on it with a non-negative direction
+__device__ __forceinline__ int above(DF p, float m, float d) {
+    return p.hi > m || (p.hi == m && (p.lo > 0.0f || (p.lo == 0.0f && d >= 0.0f)));
+}
+__device__ __forceinline__ float pow2i(int e) { return __int_as_float((127 + e) << 23); }  // e in [-126, 127]
+
+// ---------------------------------------------------------------- SH basis
+// Real orthonormal SH, k = l(l+1)+m, m < 0 <-> sin(|m| phi), no Condon-
+// Shortley phase, as Cartesian polynomials of the unit direction.
+template <int K>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+    Y[0] = 0.28209479177387814f;
+    if (K > 1) {
+        Y[1] = 0.4886025119029199f * y;
+        Y[2] = 0.4886025119029199f * z;
+        Y[3] = 0.4886025119029199f * x;
+    }
+    if (K > 4) {
+        float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 1.0925484305920792f * x * y;
+        Y[5] = 1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (3.0f * zz - 1.0f);
+        Y[7] = 1.0925484305920792f * x * z;
+        Y[8] = 0.5462742152960396f * (xx - yy);
+        if (K > 9) {
+            Y[9] = 0.5900435899266435f * y * (3.0f * xx - yy);
+            Y[10] = 2.890611442640554f * x * y * z;
+            Y[11] = 0.4570457994644658f * y * (5.0f * zz - 1.0f);
+            Y[12] = 0.3731763325901154f * z * (5.0f * zz - 3.0f);
+            Y[13] = 0.4570457994644658f * x * (5.0f * zz - 1.0f);
+            Y[14] = 1.445305721320277f * z * (xx - yy);
+            Y[15] = 0.5900435899266435f * x * (xx - 3.0f * yy);
+        }
+    }
+}
+
+// Loads one SH record and returns sum_k c_{ch,k} Y_k for the three channels.
+template <int K, int PREC>
+__device__ __forceinline__ void sh_eval(const uint8_t* rec, uint32_t yword, const float* Y, float& r, float& g,
+                                        float& b) {
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    if (PREC == PLO_PREC_FP32) {
+        constexpr int NV = (3 * K + 3) / 4;
+        const float4* v = reinterpret_cast<const float4*>(rec);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            float4 q = __ldg(v + j);
+            float e[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int gi = 4 * j + u;
+                if (gi < 3 * K) acc[gi / K] = __fmaf_rn(e[u], Y[gi % K], acc[gi / K]);
+            }
+        }
+    } else {
+        constexpr int NV = (3 * K + 7) / 8;
+        const uint4* v = reinterpret_cast<const uint4*>(rec);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            uint4 q = __ldg(v + j);
+            uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                int gi = 8 * j + u;
+                if (gi < 3 * K) {
+                    uint16_t bits = (uint16_t)(w[u >> 1] >> (16 * (u & 1)));
+                    float f = PREC == PLO_PREC_FP16 ? __half2float(__ushort_as_half(bits))
+                                                    : __uint_as_float((uint32_t)bits << 16);
+                    acc[gi / K] = __fmaf_rn(f, Y[gi % K], acc[gi / K]);
+                }
+            }
+        }
+        float s = pow2i((int)((yword >> 16) & 0xFFu) - 127);
+        acc[0] *= s;
+        acc[1] *= s;
+        acc[2] *= s;
+    }
+    r = acc[0];
+    g = acc[1];
+    b = acc[2];
+}
+
+template <int PREC>
+__device__ __forceinline__ float decode_sigma(uint32_t y) {
+    if (PREC == PLO_PREC_FP32) return __uint_as_float(y);
+    if (PREC == PLO_PREC_FP16) return __half2float(__ushort_as_half((uint16_t)(y & 0xFFFFu)));
+    return __uint_as_float((y & 0xFFFFu) << 16);
+}
+
+__device__ __forceinline__ float act_fn(float s, int act, float l_max) {
+    return act == PLO_ACT_RELU ? fmaxf(s, 0.0f) : l_max / (1.0f + expf(-s));
+}
+
+// ---------------------------------------------------------------- per-ray state
+struct Ray {
+    DF p[3];
+    float d[3];
+    float dirn[3];  // normalised world direction for the SH basis
+    float T, r, g, b;
+    DF od;
+    DF t;           // ray parameter at the current cell entry (trace only)
+    int level;
+    int steps;
+    uint32_t c[3];  // integer cell coordinates at `level`
+    uint32_t entry_x, entry_y;
+    int32_t leaf_id;  // canonical id of the current cell (trace only)
+    int status;
+    bool live;
+};
+
+__device__ __forceinline__ uint2 load_entry(const uint2* nodes, const uint2* s_nodes, int n_top, uint32_t node,
+                                            int slot) {
+    if (node < (uint32_t)n_top) return s_nodes[node * 8 + slot];
+    return __ldg(nodes + (size_t)node * 8 + slot);
+}
+
+// Descends from `stack[lev]` (cell coords c at level lev) to the leaf or
+// empty octant containing the ray position, recording the path.
+template <bool TRACE>
+__device__ __forceinline__ void descend(const KParams& kp, const uint2* s_nodes, Ray& R, uint32_t* stack, int lev) {
+    uint32_t node = stack[lev];
+    uint32_t cx = R.c[0], cy = R.c[1], cz = R.c[2];
+    int slot = 0;
+    uint2 e = make_uint2(ENTRY_EMPTY, 0);
+    for (int guard = 0; guard <= MAX_DEPTH; ++guard) {
+        float sc = pow2i(-(lev + 1));
+        int bx = above(R.p[0], (float)(2u * cx + 1u) * sc, R.d[0]);
+        int by = above(R.p[1], (float)(2u * cy + 1u) * sc, R.d[1]);
+        int bz = above(R.p[2], (float)(2u * cz + 1u) * sc, R.d[2]);
+        cx = 2u * cx + bx;
+        cy = 2u * cy + by;
+        cz = 2u * cz + bz;
+        slot = bx | (by << 1) | (bz << 2);
+        e = load_entry(kp.nodes, s_nodes, kp.n_top, node, slot);
+        ++lev;
+        if (e.x & LEAF_BIT) break;  // leaf or empty
+        node = e.x;
+        stack[lev] = node;
+        if (lev >= kp.depth) {  // malformed table: treat as empty
+            e = make_uint2(ENTRY_EMPTY, 0);
+            break;
+        }
+    }
+    R.level = lev;
+    R.c[0] = cx;
+    R.c[1] = cy;
+    R.c[2] = cz;
+    R.entry_x = e.x;
+    R.entry_y = e.y;
+    if (TRACE) R.leaf_id = e.x == ENTRY_EMPTY ? -1 : __ldg(kp.leaf_ids + (size_t)stack[lev - 1] * 8 + slot);
+}
+
+// Proxy clip and first descent.  Returns false for a miss or an invalid ray
+// (outputs already set).
+template <bool TRACE>
+__device__ bool ray_begin(const KParams& kp, const uint2* s_nodes, int64_t i, Ray& R, uint32_t* stack) {
+    const float* q = kp.rays + 6 * i;
+    float o[3], dw[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = __ldg(q + a);
+        dw[a] = __ldg(q + 3 + a);
+    }
+    R.T = 1.0f;
+    R.r = R.g = R.b = 0.0f;
+    R.od = {0.0f, 0.0f};
+    R.t = {0.0f, 0.0f};
+    R.status = PLO_RAY_OK;
+    R.steps = 0;
+    bool bad = dw[0] == 0.0f && dw[1] == 0.0f && dw[2] == 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bad |= !isfinite(o[a]) || !isfinite(dw[a]);
+    if (bad) {
+        R.status = PLO_RAY_INVALID;
+        R.r = R.g = R.b = R.T = __int_as_float(0x7fc00000);
+        return false;
+    }
+    float inv_n = rsqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
+    float ou[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R.dirn[a] = dw[a] * inv_n;
+        ou[a] = __fmul_rn(__fsub_rn(o[a], kp.bmin[a]), kp.inv_ext[a]);
+        R.d[a] = __fmul_rn(dw[a], kp.inv_ext[a]);
+    }
+    // slab test in double-float
+    DF tn = {-INFINITY, 0.0f}, tf = {INFINITY, 0.0f};
+    DF near_a[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        near_a[a] = {-INFINITY, 0.0f};
+        if (R.d[a] == 0.0f) {
+            if (ou[a] < 0.0f || ou[a] > 1.0f) return false;
+            continue;
+        }
+        float rh, rl;
+        df_recip(R.d[a], rh, rl);
+        DF pa = {ou[a], 0.0f};
+        DF t0 = df_mul(df_from_plane(0.0f, pa), rh, rl);
+        DF t1 = df_mul(df_from_plane(1.0f, pa), rh, rl);
+        if (df_less(t1, t0)) {
+            DF s = t0;
+            t0 = t1;
+            t1 = s;
+        }
+        near_a[a] = t0;
+        if (df_less(tn, t0)) tn = t0;
+        if (df_less(t1, tf)) tf = t1;
+    }
+    if (!df_less(tn, tf) || !(tf.hi > 0.0f || (tf.hi == 0.0f && tf.lo > 0.0f))) return false;
+    bool outside = tn.hi > 0.0f || (tn.hi == 0.0f && tn.lo > 0.0f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        DF oa = {ou[a], 0.0f};
+        R.p[a] = outside ? df_axpy(oa, tn, R.d[a]) : oa;
+        if (outside && R.d[a] != 0.0f && df_eq(near_a[a], tn)) R.p[a] = {R.d[a] > 0.0f ? 0.0f : 1.0f, 0.0f};
+        if (R.p[a].hi < 0.0f) R.p[a] = {0.0f, 0.0f};  // rounding guard
+        if (R.p[a].hi > 1.0f || (R.p[a].hi == 1.0f && R.p[a].lo > 0.0f)) R.p[a] = {1.0f, 0.0f};
+    }
+    if (TRACE) R.t = outside ? tn : DF{0.0f, 0.0f};
+    stack[0] = 0;
+    R.c[0] = R.c[1] = R.c[2] = 0;
+    descend<TRACE>(kp, s_nodes, R, stack, 0);
+    return true;
+}
+
+// One cell: segment length, compositing, advance.  Returns false when the
+// ray is finished.
+template <int K, int PREC, bool TRACE>
+__device__ bool ray_step(const KParams& kp, const uint2* s_nodes, int64_t i, Ray& R, uint32_t* stack) {
+    // segment: exit parameter of the current cell along each axis
+    const int L = R.level;
+    const float size = pow2i(-L);
+    DF dt = {INFINITY, 0.0f};
+    DF dts[3];
+    float planes[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        dts[a] = {INFINITY, 0.0f};
+        planes[a] = 0.0f;
+        if (R.d[a] == 0.0f) continue;
+        float P = (float)(R.c[a] + (R.d[a] > 0.0f ? 1u : 0u)) * size;
+        planes[a] = P;
+        float rh, rl;
+        df_recip(R.d[a], rh, rl);
+        DF v = df_mul(df_from_plane(P, R.p[a]), rh, rl);
+        if (v.hi < 0.0f) v = {0.0f, 0.0f};
+        dts[a] = v;
+        if (df_less(v, dt)) dt = v;
+    }
+    const float seg = dt.hi;
+    ++R.steps;
+
+    if (TRACE) {
+        int k = R.steps - 1;
+        if (k < kp.trace_max) {
+            size_t o = (size_t)i * kp.trace_max + k;
+            kp.tr_leaf[o] = R.leaf_id;
+            DF t1 = two_sum(R.t.hi, dt.hi);
+            t1 = fast_two_sum(t1.hi, __fadd_rn(t1.lo, __fadd_rn(R.t.lo, dt.lo)));
+            kp.tr_t[2 * o] = R.t.hi;
+            kp.tr_t[2 * o + 1] = t1.hi;
+            R.t = t1;
+        }
+    }
+
+    // composite the leaf (Eq. 3-5)
+    if (R.entry_x != ENTRY_EMPTY) {
+        float sigma = decode_sigma<PREC>(R.entry_y);
+        if (sigma < kp.sigma_min) sigma = 0.0f;
+        if (sigma > 0.0f) {
+            float a = sigma * seg;
+            float Tin = R.T;
+            DF s = two_sum(R.od.hi, a);
+            R.od = fast_two_sum(s.hi, __fadd_rn(s.lo, R.od.lo));
+            float od = R.od.hi + R.od.lo;
+            float w, Tout;
+            if (kp.transmittance == PLO_TRANS_EXP) {
+                w = Tin * (-expm1f(-a));
+                Tout = expf(-od);
+            } else {
+                Tout = fmaxf(0.0f, 1.0f - od);
+                float dT = fminf(Tin, a);
+                w = kp.transmittance == PLO_TRANS_LINEAR ? dT : 0.5f * dT * (Tin + Tout);
+            }
+            uint32_t rec = R.entry_x & ~LEAF_BIT;
+            float cr = 0.0f, cg = 0.0f, cb = 0.0f;
+            bool emits = rec != NO_SH_RECORD;
+            if (emits) {
+                float Y[K];
+                sh_basis<K>(R.dirn[0], R.dirn[1], R.dirn[2], Y);
+                sh_eval<K, PREC>(kp.sh + (size_t)rec * kp.sh_stride, R.entry_y, Y, cr, cg, cb);
+            }
+            if (emits || kp.activation != PLO_ACT_RELU) {
+                R.r = __fmaf_rn(w, act_fn(cr, kp.activation, kp.l_max), R.r);
+                R.g = __fmaf_rn(w, act_fn(cg, kp.activation, kp.l_max), R.g);
+                R.b = __fmaf_rn(w, act_fn(cb, kp.activation, kp.l_max), R.b);
+            }
+            R.T = Tout;
+            if (R.T < kp.t_stop || R.T <= 0.0f) return false;
+        }
+    }
+    if (R.steps >= kp.max_steps) {
+        R.status = PLO_RAY_STEP_LIMIT;
+        atomicOr(kp.flags, 1u);
+        return false;
+    }
+
+    // advance to the exit point; snap the exit axes onto their planes
+    int l_anc = L;
+    uint32_t nc[3] = {R.c[0], R.c[1], R.c[2]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (R.d[a] != 0.0f && df_eq(dts[a], dt)) {
+            R.p[a] = {planes[a], 0.0f};
+            uint32_t cn = R.d[a] > 0.0f ? R.c[a] + 1u : R.c[a] - 1u;
+            if (cn >> L) return false;  // left the root cube (also catches 0 - 1)
+            nc[a] = cn;
+            int diff = 32 - __clz(cn ^ R.c[a]);
+            if (L - diff < l_anc) l_anc = L - diff;
+        } else {
+            R.p[a] = df_axpy(R.p[a], dt, R.d[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) R.c[a] = nc[a] >> (L - l_anc);
+    descend<TRACE>(kp, s_nodes, R, stack, l_anc);
+    return true;
+}
+
+__device__ __forceinline__ void ray_store(const KParams& kp, int64_t i, const Ray& R) {
+    kp.rgb[3 * i + 0] = R.r;
+    kp.rgb[3 * i + 1] = R.g;
+    kp.rgb[3 * i + 2] = R.b;
+    kp.T[i] = R.T;
+    if (kp.status) kp.status[i] = R.status;
+    if (kp.tr_count) kp.tr_count[i] = R.steps;
+}
+
+template <int K, int PREC, bool TRACE>
+__global__ void __launch_bounds__(BLOCK) k_render(KParams kp) {
+    // nodes of the top levels, staged once per (persistent) block
+    extern __shared__ uint2 s_nodes[];
+    for (int j = threadIdx.x; j < kp.n_top * 8; j += BLOCK) s_nodes[j] = kp.nodes[j];
+    __syncthreads();
+
+    uint32_t stack[STACK];  // node id per level of the current cell's path
+    const int lane = threadIdx.x & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    const int64_t warp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    const int64_t beg = warp * kp.chunk;
+    if (beg >= kp.n) return;  // whole warp exits together
+    const int64_t end = min(beg + kp.chunk, kp.n);
+
+    Ray R;
+    int64_t my = 0;
+    int64_t next = beg;  // warp-uniform cursor into the chunk
+    bool live = false;
+    for (;;) {
+        // lanes without a ray take the next ones of the chunk; rays that miss
+        // the proxy finish at once, so repeat until no lane is idle
+        for (;;) {
+            unsigned idle = __ballot_sync(0xffffffffu, !live);
+            if (idle == 0u || next >= end) break;
+            int64_t cand = next + __popc(idle & lanes_below);
+            next += __popc(idle);
+            if (!live && cand < end) {
+                my = cand;
+                live = ray_begin<TRACE>(kp, s_nodes, my, R, stack);
+                if (!live) ray_store(kp, my, R);
+            }
+        }
+        if (__ballot_sync(0xffffffffu, live) == 0u) break;
+        if (live) {
+            live = ray_step<K, PREC, TRACE>(kp, s_nodes, my, R, stack);
+            if (!live) ray_store(kp, my, R);
+        }
+    }
+}
+
+// Point -> leaf lookup: descent from the root with the same tie rule.
+__global__ void k_lookup(const uint2* nodes, const int32_t* leaf_ids, int depth, const float* pts, const float* dirs,
+                         int64_t n, int64_t* out_leaf, int32_t* out_level) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float p[3], d[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        p[a] = pts[3 * i + a];
+        if (dirs) d[a] = dirs[3 * i + a];
+    }
+    int64_t res = -2;
+    int lev = 0;
+    if (p[0] >= 0.0f && p[0] <= 1.0f && p[1] >= 0.0f && p[1] <= 1.0f && p[2] >= 0.0f && p[2] <= 1.0f) {
+        uint32_t node = 0, c[3] = {0, 0, 0};
+        for (lev = 0; lev < depth;) {
+            float sc = pow2i(-(lev + 1));
+            int slot = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float m = (float)(2u * c[a] + 1u) * sc;
+                int up = p[a] > m || (p[a] == m && d[a] >= 0.0f);
+                c[a] = 2u * c[a] + up;
+                slot |= up << a;
+            }
+            uint2 e = __ldg(nodes + (size_t)node * 8 + slot);
+            ++lev;
+            if (e.x == ENTRY_EMPTY) {
+                res = -1;
+                break;
+            }
+            if (e.x & LEAF_BIT) {
+                res = __ldg(leaf_ids + (size_t)node * 8 + slot);
+                break;
+            }
+            node = e.x;
+        }
+    }
+    out_leaf[i] = res;
+    if (out_level) out_level[i] = lev;
+}
+
+// Persistent grid: as many blocks as fit on the device at once (occupancy
+// API), each warp owning a contiguous chunk of the rays.
+template <int K, int PREC, bool TRACE>
+cudaError_t launch_k(KParams kp, int sm_count, size_t smem, cudaStream_t s) {
+    auto fn = k_render<K, PREC, TRACE>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BLOCK, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t warps_needed = (kp.n + 31) / 32;
+    int64_t grid = (warps_needed + WARPS - 1) / WARPS;
+    int64_t max_grid = (int64_t)sm_count * per_sm;
+    if (grid > max_grid) grid = max_grid;
+    int64_t total_warps = grid * WARPS;
+    kp.chunk = (kp.n + total_warps - 1) / total_warps;
+    fn<<<(unsigned)grid, BLOCK, smem, s>>>(kp);
+    return cudaGetLastError();
+}
+
+template <bool TRACE>
+cudaError_t dispatch(const plo_tree* t, const KParams& kp, size_t smem, cudaStream_t s) {
+#define PLO_CASE(KK, PP)                                                   \
+    if (t->K == KK && t->precision == PP) return launch_k<KK, PP, TRACE>(kp, t->sm_count, smem, s);
+    PLO_CASE(1, PLO_PREC_FP32) PLO_CASE(4, PLO_PREC_FP32) PLO_CASE(9, PLO_PREC_FP32) PLO_CASE(16, PLO_PREC_FP32)
+    PLO_CASE(1, PLO_PREC_FP16) PLO_CASE(4, PLO_PREC_FP16) PLO_CASE(9, PLO_PREC_FP16) PLO_CASE(16, PLO_PREC_FP16)
+    PLO_CASE(1, PLO_PREC_BF16) PLO_CASE(4, PLO_PREC_BF16) PLO_CASE(9, PLO_PREC_BF16) PLO_CASE(16, PLO_PREC_BF16)
+#undef PLO_CASE
+    return cudaErrorInvalidValue;
+}
+
+plo_status check_params(const plo_render_params* p) {
+    if (!p) return set_error(PLO_ERR_INVALID_ARG, "params is NULL");
+    if (p->transmittance < PLO_TRANS_EXP || p->transmittance > PLO_TRANS_LINEAR_LITERAL)
+        return set_error(PLO_ERR_INVALID_ARG, "unknown transmittance model");
+    if (p->activation != PLO_ACT_RELU && p->activation != PLO_ACT_SIGMOID)
+        return set_error(PLO_ERR_INVALID_ARG, "unknown activation");
+    if (!(p->t_stop >= 0.0f && p->t_stop <= 1.0f)) return set_error(PLO_ERR_INVALID_ARG, "t_stop must be in [0, 1]");
+    if (!(p->sigma_min >= 0.0f) || !std::isfinite(p->sigma_min))
+        return set_error(PLO_ERR_INVALID_ARG, "sigma_min must be finite and >= 0");
+    if (p->activation == PLO_ACT_SIGMOID && !std::isfinite(p->l_max))
+        return set_error(PLO_ERR_INVALID_ARG, "l_max must be finite");
+    if (p->max_steps < 0) return set_error(PLO_ERR_INVALID_ARG, "max_steps must be >= 0");
+    return PLO_OK;
+}
+
+template <bool TRACE>
+plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, const plo_render_params* p,
+                         float* d_rgb, float* d_T, int32_t* d_status, int32_t trace_max, int64_t* tr_leaf,
+                         float* tr_t, int32_t* tr_count, void* stream) {
+    if (!t) return set_error(PLO_ERR_INVALID_ARG, "tree is NULL");
+    plo_status st = check_params(p);
+    if (st != PLO_OK) return st;
+    if (n < 0) return set_error(PLO_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return PLO_OK;
+    if (!d_rays || !d_rgb || !d_T) return set_error(PLO_ERR_INVALID_ARG, "rays, rgb or T is NULL");
+    if (TRACE && (trace_max <= 0 || !tr_leaf || !tr_t || !tr_count))
+        return set_error(PLO_ERR_INVALID_ARG, "trace buffers are NULL or max_cells <= 0");
+    KParams kp{};
+    kp.nodes = static_cast<const uint2*>(t->d_nodes);
+    kp.leaf_ids = t->d_leaf_ids;
+    kp.sh = static_cast<const uint8_t*>(t->d_sh);
+    kp.sh_stride = t->sh_stride;
+    kp.depth = t->depth;
+    kp.n_top = t->n_top;
+    for (int a = 0; a < 3; ++a) {
+        kp.bmin[a] = t->bbox_min[a];
+        kp.inv_ext[a] = t->inv_ext[a];
+    }
+    kp.transmittance = p->transmittance;
+    kp.activation = p->activation;
+    kp.l_max = p->l_max;
+    kp.t_stop = p->t_stop;
+    kp.sigma_min = p->sigma_min;
+    kp.max_steps = p->max_steps > 0 ? p->max_steps : 4 * (1 << t->depth) + 64;
+    kp.rays = d_rays;
+    kp.n = n;
+    kp.rgb = d_rgb;
+    kp.T = d_T;
+    kp.status = d_status;
+    kp.flags = t->d_flags;
+    kp.trace_max = trace_max;
+    kp.tr_leaf = tr_leaf;
+    kp.tr_t = tr_t;
+    kp.tr_count = tr_count;
+    size_t smem = (size_t)t->n_top * 8 * sizeof(uint2);
+    cudaError_t e = dispatch<TRACE>(t, kp, smem, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_error(e, "render kernel launch");
+    return PLO_OK;
+}
+
+}  // namespace
+}  // namespace plo
+
+using namespace plo;
+
+extern "C" plo_status plo_render_rays(const plo_tree* tree, const float* d_rays, int64_t n,
+                                      const plo_render_params* params, float* d_rgb, float* d_T, int32_t* d_status,
+                                      void* stream) {
+    return render_common<false>(tree, d_rays, n, params, d_rgb, d_T, d_status, 0, nullptr, nullptr, nullptr,
+                                stream);
+}
+
+extern "C" plo_status plo_trace_rays(const plo_tree* tree, const float* d_rays, int64_t n,
+                                     const plo_render_params* params, int32_t max_cells, int64_t* d_leaf,
+                                     float* d_t, int32_t* d_count, void* stream) {
+    // The trace runs the render kernel itself (trace instantiation); its
+    // radiance goes to a stream-ordered temporary and is discarded.
+    if (!tree) return set_error(PLO_ERR_INVALID_ARG, "tree is NULL");
+    if (n < 0) return set_error(PLO_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return PLO_OK;
+    float* rgbT = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&rgbT, (size_t)n * 4 * sizeof(float), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_error(e, "trace scratch allocation");
+    plo_status st = render_common<true>(tree, d_rays, n, params, rgbT, rgbT + 3 * n, nullptr, max_cells, d_leaf,
+                                        d_t, d_count, stream);
+    cudaFreeAsync(rgbT, (cudaStream_t)stream);
+    return st;
+}
+
+extern "C" plo_status plo_lookup_points(const plo_tree* t, const float* d_points, const float* d_dirs, int64_t n,
+                                        int64_t* d_leaf, int32_t* d_level, void* stream) {
+    if (!t) return set_error(PLO_ERR_INVALID_ARG, "tree is NULL");
+    if (n < 0) return set_error(PLO_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return PLO_OK;
+    if (!d_points || !d_leaf) return set_error(PLO_ERR_INVALID_ARG, "points or leaf output is NULL");
+    int64_t grid = (n + 255) / 256;
+    k_lookup<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(static_cast<const uint2*>(t->d_nodes), t->d_leaf_ids,
+                                                               t->depth, d_points, d_dirs, n, d_leaf, d_level);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "lookup kernel launch");
+    return PLO_OK;
+}

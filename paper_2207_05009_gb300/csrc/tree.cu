@@ -1,0 +1,354 @@
+// plo_validate_tree / plo_build_tree / plo_tree_free / plo_tree_get_info /
+// plo_tree_check: validation of the canonical plenoctree (Sec. 5) and its
+// packing into the device layout described in plo_internal.h.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "plo_internal.h"
+
+using namespace plo;
+
+namespace {
+
+plo_status validate(const plo_tree_desc* t) {
+    if (!t) return set_error(PLO_ERR_INVALID_ARG, "tree descriptor is NULL");
+    if (t->depth < 0 || t->depth > MAX_DEPTH)
+        return set_error(PLO_ERR_INVALID_ARG, "depth must be in [0, 16], got " + std::to_string(t->depth));
+    if (t->sh_degree < 0 || t->sh_degree > 3)
+        return set_error(PLO_ERR_INVALID_ARG, "sh_degree must be in [0, 3], got " + std::to_string(t->sh_degree));
+    if (t->n_nodes < 0 || t->n_leaves < 0) return set_error(PLO_ERR_INVALID_ARG, "negative node or leaf count");
+    if (t->n_nodes >= (int64_t)LEAF_BIT - 1) return set_error(PLO_ERR_INVALID_ARG, "too many nodes (>= 2^31 - 1)");
+    if (t->n_leaves >= (int64_t)NO_SH_RECORD) return set_error(PLO_ERR_INVALID_ARG, "too many leaves");
+    if (t->n_nodes > 0 && !t->child) return set_error(PLO_ERR_INVALID_ARG, "child table is NULL");
+    if (t->n_leaves > 0 && (!t->sigma || !t->sh)) return set_error(PLO_ERR_INVALID_ARG, "sigma or sh is NULL");
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(t->bbox_min[a]) || !std::isfinite(t->bbox_max[a]) || !(t->bbox_max[a] > t->bbox_min[a]))
+            return set_error(PLO_ERR_INVALID_ARG, "bounding box must be finite with max > min on every axis");
+    }
+    if (t->n_nodes == 0) {
+        if (t->n_leaves > 1)
+            return set_error(PLO_ERR_BAD_TREE, "a tree without nodes holds at most one leaf (the root)");
+    } else {
+        if (t->depth < 1) return set_error(PLO_ERR_BAD_TREE, "a tree with nodes needs depth >= 1");
+        std::vector<uint8_t> seen_node(t->n_nodes, 0), seen_leaf(t->n_leaves, 0);
+        std::vector<std::pair<int64_t, int>> stack;
+        stack.push_back({0, 0});
+        seen_node[0] = 1;
+        while (!stack.empty()) {
+            auto [nid, lev] = stack.back();
+            stack.pop_back();
+            for (int s = 0; s < 8; ++s) {
+                int32_t e = t->child[nid * 8 + s];
+                if (e >= 0) {
+                    if (e >= t->n_nodes)
+                        return set_error(PLO_ERR_BAD_TREE, "node " + std::to_string(nid) + " slot " +
+                                                               std::to_string(s) + ": child index out of range");
+                    if (lev + 1 >= t->depth)
+                        return set_error(PLO_ERR_BAD_TREE, "node " + std::to_string(e) + " sits at level " +
+                                                               std::to_string(lev + 1) +
+                                                               ", its children would exceed depth " +
+                                                               std::to_string(t->depth));
+                    if (seen_node[e])
+                        return set_error(PLO_ERR_BAD_TREE, "node " + std::to_string(e) +
+                                                               " is referenced twice (cycle or shared subtree)");
+                    seen_node[e] = 1;
+                    stack.push_back({e, lev + 1});
+                } else if (e <= -2) {
+                    int64_t leaf = -(int64_t)e - 2;
+                    if (leaf >= t->n_leaves)
+                        return set_error(PLO_ERR_BAD_TREE, "leaf index " + std::to_string(leaf) + " out of range");
+                    if (seen_leaf[leaf])
+                        return set_error(PLO_ERR_BAD_TREE, "leaf " + std::to_string(leaf) + " is referenced twice");
+                    seen_leaf[leaf] = 1;
+                }
+            }
+        }
+    }
+    const int K = sh_K(t->sh_degree);
+    for (int64_t i = 0; i < t->n_leaves; ++i) {
+        float s = t->sigma[i];
+        if (!std::isfinite(s) || s < 0.0f)
+            return set_error(PLO_ERR_BAD_TREE, "sigma of leaf " + std::to_string(i) + " is negative or not finite");
+    }
+    for (int64_t i = 0; i < t->n_leaves * 3 * K; ++i) {
+        if (!std::isfinite(t->sh[i]))
+            return set_error(PLO_ERR_BAD_TREE, "SH coefficient of leaf " + std::to_string(i / (3 * K)) +
+                                                   " is not finite");
+    }
+    return PLO_OK;
+}
+
+uint16_t half_bits(float v) {
+    __half h = __float2half_rn(v);
+    uint16_t b;
+    std::memcpy(&b, &h, 2);
+    return b;
+}
+uint16_t bf16_bits(float v) {
+    __nv_bfloat16 h = __float2bfloat16_rn(v);
+    uint16_t b;
+    std::memcpy(&b, &h, 2);
+    return b;
+}
+
+}  // namespace
+
+extern "C" plo_status plo_validate_tree(const plo_tree_desc* desc) { return validate(desc); }
+
+extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out) {
+    if (!out) return set_error(PLO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (precision < PLO_PREC_FP32 || precision > PLO_PREC_BF16)
+        return set_error(PLO_ERR_INVALID_ARG, "precision must be PLO_PREC_FP32, _FP16 or _BF16");
+    plo_status st = validate(desc);
+    if (st != PLO_OK) return st;
+    const int K = sh_K(desc->sh_degree);
+    if (precision == PLO_PREC_FP16) {
+        for (int64_t i = 0; i < desc->n_leaves; ++i)
+            if (desc->sigma[i] > 65504.0f)
+                return set_error(PLO_ERR_INVALID_ARG, "FP16 leaves: sigma of leaf " + std::to_string(i) +
+                                                          " exceeds the binary16 range (65504)");
+    }
+
+    // Canonical child table; a tree without nodes is re-rooted one level down
+    // (eight slots that all hold the root leaf, or all empty).
+    std::vector<int32_t> synth;
+    const int32_t* child = desc->child;
+    int64_t n_nodes = desc->n_nodes;
+    int depth = desc->depth;
+    if (n_nodes == 0) {
+        synth.assign(8, desc->n_leaves == 1 ? -2 : -1);
+        child = synth.data();
+        n_nodes = 1;
+        depth = 1;
+    }
+
+    // Levels by breadth-first search; the first `top` levels keep BFS order.
+    std::vector<int32_t> bfs;
+    std::vector<int8_t> level(n_nodes, -1);
+    bfs.reserve(n_nodes);
+    bfs.push_back(0);
+    level[0] = 0;
+    for (size_t i = 0; i < bfs.size(); ++i) {
+        int32_t nid = bfs[i];
+        for (int s = 0; s < 8; ++s) {
+            int32_t e = child[(int64_t)nid * 8 + s];
+            if (e >= 0) {
+                level[e] = level[nid] + 1;
+                bfs.push_back(e);
+            }
+        }
+    }
+    const int top = depth < 4 ? depth : 4;
+    std::vector<int32_t> order;  // new id -> canonical id
+    order.reserve(bfs.size());
+    std::vector<int32_t> new_id(n_nodes, -1);
+    for (int32_t nid : bfs)
+        if (level[nid] < top) {
+            new_id[nid] = (int32_t)order.size();
+            order.push_back(nid);
+        }
+    const int32_t n_top = (int32_t)order.size();
+    // depth-first pre-order of the subtrees below the top levels
+    std::vector<int32_t> stack;
+    for (int32_t nid : bfs) {
+        if (level[nid] != top) continue;
+        stack.push_back(nid);
+        while (!stack.empty()) {
+            int32_t v = stack.back();
+            stack.pop_back();
+            new_id[v] = (int32_t)order.size();
+            order.push_back(v);
+            for (int s = 7; s >= 0; --s) {
+                int32_t e = child[(int64_t)v * 8 + s];
+                if (e >= 0) stack.push_back(e);
+            }
+        }
+    }
+    const int64_t n_packed = (int64_t)order.size();
+
+    // SH records in depth-first (Morton) order of the leaves.
+    std::vector<uint32_t> rec_of_leaf(desc->n_leaves > 0 ? desc->n_leaves : 1, NO_SH_RECORD);
+    int64_t n_sh = 0;
+    {
+        std::vector<int32_t> st{0};
+        while (!st.empty()) {
+            int32_t v = st.back();
+            st.pop_back();
+            for (int s = 7; s >= 0; --s) {
+                int32_t e = child[(int64_t)v * 8 + s];
+                if (e >= 0) st.push_back(e);
+            }
+            for (int s = 0; s < 8; ++s) {
+                int32_t e = child[(int64_t)v * 8 + s];
+                if (e <= -2) {
+                    int64_t leaf = -(int64_t)e - 2;
+                    if (rec_of_leaf[leaf] != NO_SH_RECORD) continue;  // root leaf repeated in 8 slots
+                    const float* c = desc->sh + leaf * 3 * K;
+                    bool emits = false;
+                    for (int k = 0; k < 3 * K; ++k) emits |= c[k] != 0.0f;
+                    if (emits) rec_of_leaf[leaf] = (uint32_t)n_sh++;
+                }
+            }
+        }
+    }
+    // Note: the depth-first walk above visits a node's leaves after pushing its
+    // children, so records follow pre-order of nodes; within a node, slot order.
+
+    const int stride = sh_stride_bytes(K, precision);
+    std::vector<uint32_t> nodes;
+    std::vector<int32_t> leaf_ids;
+    std::vector<uint8_t> sh;
+    try {
+        nodes.assign(n_packed * 16, 0);
+        leaf_ids.assign(n_packed * 8, -1);
+        sh.assign((size_t)(n_sh > 0 ? n_sh : 1) * stride, 0);
+    } catch (const std::bad_alloc&) {
+        return set_error(PLO_ERR_OOM, "host allocation for the packed tree failed");
+    }
+    std::vector<int8_t> scale_exp(desc->n_leaves > 0 ? desc->n_leaves : 1, 0);
+    for (int64_t leaf = 0; leaf < desc->n_leaves; ++leaf) {
+        uint32_t r = rec_of_leaf[leaf];
+        if (r == NO_SH_RECORD) continue;
+        const float* c = desc->sh + leaf * 3 * K;
+        uint8_t* dst = sh.data() + (size_t)r * stride;
+        if (precision == PLO_PREC_FP32) {
+            std::memcpy(dst, c, sizeof(float) * 3 * K);
+            continue;
+        }
+        float m = 0.0f;
+        for (int k = 0; k < 3 * K; ++k) m = std::fmax(m, std::fabs(c[k]));
+        int e;
+        std::frexp(m, &e);  // m = f * 2^e, f in [0.5, 1): m / 2^e <= 1
+        if (e < -126) e = -126;
+        if (e > 127) e = 127;
+        scale_exp[leaf] = (int8_t)0;  // placeholder, stored below
+        float inv = std::ldexp(1.0f, -e);
+        uint16_t* h = reinterpret_cast<uint16_t*>(dst);
+        for (int k = 0; k < 3 * K; ++k) {
+            float v = c[k] * inv;
+            h[k] = precision == PLO_PREC_FP16 ? half_bits(v) : bf16_bits(v);
+        }
+        scale_exp[leaf] = (int8_t)e;
+    }
+    for (int64_t i = 0; i < n_packed; ++i) {
+        int32_t v = order[i];
+        for (int s = 0; s < 8; ++s) {
+            int32_t e = child[(int64_t)v * 8 + s];
+            uint32_t x = ENTRY_EMPTY, y = 0;
+            if (e >= 0) {
+                x = (uint32_t)new_id[e];
+            } else if (e <= -2) {
+                int64_t leaf = -(int64_t)e - 2;
+                leaf_ids[i * 8 + s] = (int32_t)leaf;
+                x = LEAF_BIT | rec_of_leaf[leaf];
+                float sg = desc->sigma[leaf];
+                if (precision == PLO_PREC_FP32) {
+                    std::memcpy(&y, &sg, 4);
+                } else {
+                    uint32_t sb = precision == PLO_PREC_FP16 ? half_bits(sg) : bf16_bits(sg);
+                    uint32_t eb = rec_of_leaf[leaf] == NO_SH_RECORD ? 0u : (uint32_t)(scale_exp[leaf] + 127);
+                    y = sb | (eb << 16);
+                }
+            }
+            nodes[i * 16 + 2 * s] = x;
+            nodes[i * 16 + 2 * s + 1] = y;
+        }
+    }
+
+    plo_tree* t = new (std::nothrow) plo_tree();
+    if (!t) return set_error(PLO_ERR_OOM, "host allocation failed");
+    t->depth = depth;
+    t->sh_degree = desc->sh_degree;
+    t->K = K;
+    t->precision = precision;
+    t->top_levels = top;
+    t->n_top = n_top;
+    t->n_nodes = n_packed;
+    t->n_leaves = desc->n_leaves;
+    t->n_sh = n_sh;
+    t->sh_stride = stride;
+    for (int a = 0; a < 3; ++a) {
+        t->bbox_min[a] = desc->bbox_min[a];
+        t->inv_ext[a] = 1.0f / (desc->bbox_max[a] - desc->bbox_min[a]);
+    }
+    t->node_bytes = n_packed * 64;
+    t->sh_bytes = (int64_t)n_sh * stride;
+    cudaError_t err = cudaGetDevice(&t->device);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->device);
+    if (err != cudaSuccess) {
+        delete t;
+        return cuda_error(err, "cudaGetDevice");
+    }
+    size_t sh_alloc = (size_t)(n_sh > 0 ? n_sh : 1) * stride;
+    if ((err = cudaMalloc(&t->d_nodes, (size_t)t->node_bytes)) != cudaSuccess ||
+        (err = cudaMalloc((void**)&t->d_leaf_ids, (size_t)n_packed * 8 * sizeof(int32_t))) != cudaSuccess ||
+        (err = cudaMalloc(&t->d_sh, sh_alloc)) != cudaSuccess ||
+        (err = cudaMalloc((void**)&t->d_flags, 256)) != cudaSuccess) {
+        plo_tree_free(t);
+        cudaGetLastError();
+        return err == cudaErrorMemoryAllocation ? set_error(PLO_ERR_OOM, "device allocation for the tree failed")
+                                                : cuda_error(err, "cudaMalloc");
+    }
+    if ((err = cudaMemcpy(t->d_nodes, nodes.data(), (size_t)t->node_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (err = cudaMemcpy(t->d_leaf_ids, leaf_ids.data(), (size_t)n_packed * 8 * sizeof(int32_t),
+                          cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (err = cudaMemcpy(t->d_sh, sh.data(), sh_alloc, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (err = cudaMemset(t->d_flags, 0, 256)) != cudaSuccess) {
+        plo_tree_free(t);
+        return cuda_error(err, "upload of the packed tree");
+    }
+    *out = t;
+    return PLO_OK;
+}
+
+extern "C" void plo_tree_free(plo_tree* t) {
+    if (!t) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(t->device);
+    cudaDeviceSynchronize();
+    cudaFree(t->d_nodes);
+    cudaFree(t->d_leaf_ids);
+    cudaFree(t->d_sh);
+    cudaFree(t->d_flags);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete t;
+}
+
+extern "C" plo_status plo_tree_get_info(const plo_tree* t, plo_tree_info* out) {
+    if (!t || !out) return set_error(PLO_ERR_INVALID_ARG, "tree or out is NULL");
+    out->depth = t->depth;
+    out->sh_degree = t->sh_degree;
+    out->precision = t->precision;
+    out->top_levels = t->top_levels;
+    out->n_nodes = t->n_nodes;
+    out->n_leaves = t->n_leaves;
+    out->n_sh_records = t->n_sh;
+    out->node_bytes = t->node_bytes;
+    out->sh_bytes = t->sh_bytes;
+    out->sh_record_stride = t->sh_stride;
+    out->device = t->device;
+    return PLO_OK;
+}
+
+extern "C" plo_status plo_tree_check(const plo_tree* t, void* stream) {
+    if (!t) return set_error(PLO_ERR_INVALID_ARG, "tree is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int flags = 0;
+    cudaError_t err = cudaMemcpyAsync(&flags, t->d_flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return cuda_error(err, "plo_tree_check");
+    if (flags) {
+        cudaMemsetAsync(t->d_flags, 0, sizeof(unsigned int), s);
+        cudaStreamSynchronize(s);
+        if (flags & 1u) return set_error(PLO_ERR_TRAVERSAL_LIMIT, "a ray exceeded its step cap (max_steps)");
+    }
+    return PLO_OK;
+}
