@@ -306,10 +306,19 @@ static void render_one(const oracle_tree* t, const oracle_params* prm, const flo
         }
         if (tnext >= tf) break;
         if (T < prm->t_stop || T <= 0.0) break;
+        /* the exit point lies on the closed box of the cell just left: exit
+         * axes on their plane, the others clamped into the box (FP64 rounding
+         * of o + t d may put them a hair inside the old cell otherwise) */
         tcur = tnext;
-        for (int a = 0; a < 3; ++a) p[a] = o[a] + tcur * d[a];
-        for (int a = 0; a < 3; ++a)
-            if (tx[a] == tnext) p[a] = d[a] > 0.0 ? lo[a] + size : lo[a];
+        for (int a = 0; a < 3; ++a) {
+            if (tx[a] == tnext) {
+                p[a] = d[a] > 0.0 ? lo[a] + size : lo[a];
+            } else {
+                p[a] = o[a] + tcur * d[a];
+                if (p[a] < lo[a]) p[a] = lo[a];
+                if (p[a] > lo[a] + size) p[a] = lo[a] + size;
+            }
+        }
     }
     res->T = T;
 }

@@ -224,3 +224,56 @@ def test_trace_is_ordered_and_contiguous():
         ch = chord(r[:3], r[3:])
         assert t[0, 0] == pytest.approx(ch[0], abs=1e-12)
         assert t[-1, 1] == pytest.approx(ch[1], abs=1e-12)
+
+
+def corner_rays(rng, n, grid=64):
+    """Diagonal rays from grid points: they cross many cells exactly through
+    shared corners and edges."""
+    g = np.arange(grid + 1) / grid
+    out = []
+    for _ in range(n):
+        o = rng.choice(g, 3) - 2.0
+        s = rng.choice([-1.0, 1.0], 3)
+        o = np.where(s > 0, o, 3.0 - (o + 2.0))
+        out.append(np.concatenate([o, s / np.sqrt(3)]))
+    return np.array(out, np.float32)
+
+
+def test_corner_rays_progress_and_closed_form():
+    rng = np.random.default_rng(21)
+    rays = corner_rays(rng, 400)
+    c = coeffs9(rng)
+    sig = float(np.float32(2.5))
+    tree = uniform_tree(4, sig, c)
+    out = oracle.render(tree, rays)
+    assert np.all(out["status"] == 0)
+    for i, r in enumerate(rays):
+        ch = chord(r[:3], r[3:])
+        L = 0.0 if ch is None else ch[1] - ch[0]
+        T = math.exp(-sig * L)
+        assert out["T"][i] == pytest.approx(T, rel=1e-12, abs=1e-15)
+        np.testing.assert_allclose(out["rgb"][i], emission(c, r[3:]) * (1 - T), rtol=1e-11, atol=1e-13)
+    # sparse luminaire tree: every corner ray terminates, and its segments tile the chord
+    d6 = plogen.luminaire_tree(plogen.LUMINAIRE_D6)
+    out = oracle.render(d6, rays)
+    assert np.all(out["status"] == 0)
+    for r in rays[:100]:
+        leaf, t = oracle.trace(d6, r)
+        ch = chord(r[:3], r[3:])
+        if ch is None:
+            assert len(leaf) == 0
+            continue
+        np.testing.assert_array_equal(t[1:, 0], t[:-1, 1])
+        assert t[0, 0] == pytest.approx(ch[0], abs=1e-12) and t[-1, 1] == pytest.approx(ch[1], abs=1e-12)
+
+
+def test_corner_rays_match_midpoint_quadrature():
+    rng = np.random.default_rng(22)
+    tree = random_tree(3, rng, emissive=0.8, sigma_range=(0.1, 4.0))
+    rays = corner_rays(rng, 6, grid=8)
+    out = oracle.render(tree, rays)
+    assert np.all(out["status"] == 0)
+    for i, r in enumerate(rays):
+        rgb, T = midpoint_quadrature(tree, r, 2.5e-4)
+        scale = max(np.abs(out["rgb"][i]).max(), 1e-3)
+        assert np.abs(rgb - out["rgb"][i]).max() / scale < 3e-3
