@@ -119,9 +119,9 @@ plo_status plo_validate_tree(const plo_tree_desc* desc);
 
 /* Validates `desc`, packs it into the device layout at `precision`
  * (PLO_PREC_*) and uploads it to the current CUDA device.  Synchronous.
- * FP16 stores sigma as binary16 (sigma must be <= 65504) and each leaf's SH
- * coefficients as binary16 times a per-leaf power-of-two FP32 scale; BF16 the
- * same in bfloat16.  On success *out owns the device copy; free it with
+ * FP16 / BF16 store each leaf's SH coefficients as binary16 / bfloat16 times a
+ * per-leaf power-of-two FP32 scale, and sigma as a 24-bit float (8-bit
+ * exponent, 16-bit mantissa, round-to-nearest-even).  On success *out owns the device copy; free it with
  * plo_tree_free.  The host arrays may be released after the call. */
 plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out);
 

@@ -62,7 +62,7 @@ def _load():
         lib.oracle_lookup.restype = None
         lib.oracle_lookup.argtypes = [P, P, P, ctypes.c_int64, P, P]
         lib.oracle_render.restype = ctypes.c_int64
-        lib.oracle_render.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P, P, P, P, ctypes.c_int]
+        lib.oracle_render.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P, P, P, P, P, ctypes.c_int]
         lib.oracle_trace.restype = ctypes.c_int32
         lib.oracle_trace.argtypes = [P, P, P, ctypes.c_int32, P, P]
         lib.oracle_max_threads.restype = ctypes.c_int
@@ -123,19 +123,21 @@ def lookup(tree, pts, dirs=None):
 def render(tree, rays, transmittance=EXPONENTIAL, activation=RELU, l_max=1.0, t_stop=0.0, sigma_min=0.0,
            n_threads: int = 0) -> dict:
     """Exact FP64 render of float32 rays [n,6].  Returns a dict of arrays:
-    rgb [n,3], T [n], bound [n,3] (per-channel error scale), n_leaf, n_sh,
+    rgb [n,3], T [n], bound [n,3] (per-channel error scale), cond [n,3]
+    (sensitivity to optical-depth errors), n_leaf, n_sh,
     n_cell, status (0 ok, 1 iteration cap, 2 lookup failure, 3 invalid ray:
     NaN/Inf component or zero direction, with NaN outputs)."""
     lib = _load()
     b = _Bound(tree)
     rays = np.ascontiguousarray(rays, np.float32)
     n = rays.shape[0]
-    out = {"rgb": np.zeros((n, 3)), "T": np.ones(n), "bound": np.zeros((n, 3)),
+    out = {"rgb": np.zeros((n, 3)), "T": np.ones(n), "bound": np.zeros((n, 3)), "cond": np.zeros((n, 3)),
            "n_leaf": np.zeros(n, np.int32), "n_sh": np.zeros(n, np.int32), "n_cell": np.zeros(n, np.int32),
            "status": np.zeros(n, np.int32)}
     p = _params(transmittance, activation, l_max, t_stop, sigma_min)
     lib.oracle_render(ctypes.byref(b.struct), rays.ctypes.data, n, ctypes.byref(p),
-                      *(out[k].ctypes.data for k in ("rgb", "T", "bound", "n_leaf", "n_sh", "n_cell", "status")),
+                      *(out[k].ctypes.data for k in ("rgb", "T", "bound", "cond", "n_leaf", "n_sh", "n_cell",
+                                                      "status")),
                       int(n_threads))
     return out
 

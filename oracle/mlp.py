@@ -1,0 +1,257 @@
+"""FP64 oracle for the learned part: NeRF-SH network, quadrature render, the
+paper's loss, its gradients, Adam, and the distillation into an octree.
+
+TEST INFRASTRUCTURE ONLY (tests, smoke, the bench's CPU leg).  Plain numpy;
+matrix products are the only library primitive.  Follows:
+  - network (Sec. 4.2, "Network architecture"): Fourier positional encoding
+    of the position, 8 fully connected layers of 256 with ReLU, a linear head
+    to sigma and 3 (l_max+1)^2 SH coefficients; sigma = ReLU(raw);
+  - emission (Eq. 6): Phi = L_max * sigmoid(sum_k c_k Y_k(d));
+  - render (Sec. 4.1, Eq. 3-5): deterministic ray marching with stratified
+    samples; exponential or linear (Eq. 4) transmittance; alpha = 1 - T;
+  - loss (Sec. 4.3, Eq. 7-9): L = mean_r [ sum_ch ((C^ - C)/(lambda C^ + eps))^2
+    + (alpha^ - alpha)^2 ] with eps = 0.01, computed on values divided by L_max
+    (lambda = 1), the denominator held constant (no gradient through it);
+  - Adam with the learning rate decaying exponentially from 5e-4 to 5e-6
+    (Sec. 4.4);
+  - distillation (Sec. 5, "Creating the plenoctree"): centre sample of each
+    voxel, prune sigma < threshold, average jittered samples in kept voxels.
+
+The SH basis is the oracle's own (``oracle.sh_basis``, Legendre recursion).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle as _oracle
+
+WIDTH = 256
+DEPTH = 8
+N_FREQ = 10
+PE_DIM = 3 + 6 * N_FREQ  # 63
+
+
+def n_out(l_max: int = 3) -> int:
+    return 1 + 3 * (l_max + 1) ** 2
+
+
+def layer_shapes(l_max: int = 3):
+    """[(out, in)] for the 8 hidden layers and the head."""
+    shapes = [(WIDTH, PE_DIM)] + [(WIDTH, WIDTH)] * (DEPTH - 1) + [(n_out(l_max), WIDTH)]
+    return shapes
+
+
+def init_params(rng: np.random.Generator, l_max: int = 3):
+    """He-uniform weights, zero biases (FP64)."""
+    Ws, bs = [], []
+    for (o, i) in layer_shapes(l_max):
+        lim = math.sqrt(6.0 / i)
+        Ws.append(rng.uniform(-lim, lim, (o, i)))
+        bs.append(np.zeros(o))
+    return Ws, bs
+
+
+def positional_encoding(x: np.ndarray) -> np.ndarray:
+    """gamma(x) = [x, sin(2^j pi x), cos(2^j pi x)]_{j=0..9}, per component:
+    x [M,3] -> [M,63] in the order x, then for each j sin (3), cos (3)."""
+    feats = [x]
+    for j in range(N_FREQ):
+        f = (2.0 ** j) * math.pi * x
+        feats.append(np.sin(f))
+        feats.append(np.cos(f))
+    return np.concatenate(feats, axis=1)
+
+
+def forward(Ws, bs, X):
+    """MLP forward.  Returns (raw outputs [M, n_out], hidden activations)."""
+    H = [X]
+    h = X
+    for l in range(DEPTH):
+        h = np.maximum(h @ Ws[l].T + bs[l], 0.0)
+        H.append(h)
+    raw = h @ Ws[DEPTH].T + bs[DEPTH]
+    return raw, H
+
+
+def backward(Ws, H, draw):
+    """Gradients of the MLP parameters given d loss / d raw."""
+    dWs = [None] * (DEPTH + 1)
+    dbs = [None] * (DEPTH + 1)
+    dWs[DEPTH] = draw.T @ H[DEPTH]
+    dbs[DEPTH] = draw.sum(0)
+    g = draw @ Ws[DEPTH]
+    for l in range(DEPTH - 1, -1, -1):
+        g = g * (H[l + 1] > 0)
+        dWs[l] = g.T @ H[l]
+        dbs[l] = g.sum(0)
+        g = g @ Ws[l]
+    return dWs, dbs
+
+
+def clip_unit_cube(o, d):
+    """[t0, t1] of each ray inside the unit cube (t0 clamped at 0), and a hit
+    mask (positive-length intersection in front of the origin)."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / d
+        ta = (0.0 - o) * inv
+        tb = (1.0 - o) * inv
+    tlo = np.where(d == 0, np.where((o >= 0) & (o <= 1), -np.inf, np.inf), np.minimum(ta, tb))
+    thi = np.where(d == 0, np.where((o >= 0) & (o <= 1), np.inf, -np.inf), np.maximum(ta, tb))
+    t0 = tlo.max(1)
+    t1 = thi.min(1)
+    hit = (t0 < t1) & (t1 > 0)
+    return np.maximum(t0, 0.0), t1, hit
+
+
+def stratified_samples(rays, jitter):
+    """Sample parameters per ray: t_j = t0 + (j + u_j)(t1 - t0)/N, segment
+    lengths delta_j = t_{j+1} - t_j (the last one ends at t1), positions
+    x_j = o + t_j d.  jitter u [R, N] in [0, 1).  Misses get zero lengths."""
+    o, d = rays[:, :3].astype(np.float64), rays[:, 3:].astype(np.float64)
+    R, N = jitter.shape
+    t0, t1, hit = clip_unit_cube(o, d)
+    t0 = np.where(hit, t0, 0.0)
+    t1 = np.where(hit, t1, 0.0)
+    span = (t1 - t0)[:, None]
+    t = t0[:, None] + (np.arange(N)[None, :] + jitter) * span / N
+    nxt = np.concatenate([t[:, 1:], t1[:, None]], axis=1)
+    delta = np.where(hit[:, None], nxt - t, 0.0)
+    x = o[:, None, :] + t[..., None] * d[:, None, :]
+    return t, delta, x, hit
+
+
+def sh_matrix(dirs, l_max):
+    return np.stack([_oracle.sh_basis(l_max, v) for v in dirs])
+
+
+def composite(raw, delta, Y, l_max_scale, transmittance="exp"):
+    """Quadrature render of Eq. 3 for raw outputs [R, N, n_out].
+    Returns (C [R,3], alpha [R], cache for backward)."""
+    R, N, _ = raw.shape
+    K = Y.shape[1]
+    sigma = np.maximum(raw[..., 0], 0.0)
+    coef = raw[..., 1:].reshape(R, N, 3, K)
+    s = np.einsum("rnck,rk->rnc", coef, Y)
+    sig = 1.0 / (1.0 + np.exp(-s))
+    c = l_max_scale * sig
+    a = sigma * delta
+    cum = np.concatenate([np.zeros((R, 1)), np.cumsum(a, axis=1)], axis=1)  # [R, N+1]
+    if transmittance == "exp":
+        T = np.exp(-cum)
+    else:
+        T = np.maximum(0.0, 1.0 - cum)
+    w = T[:, :-1] - T[:, 1:]
+    C = np.einsum("rn,rnc->rc", w, c)
+    alpha = w.sum(1)
+    return C, alpha, dict(sigma=sigma, a=a, T=T, w=w, c=c, sig=sig, Y=Y, raw=raw, delta=delta,
+                          transmittance=transmittance, l_max_scale=l_max_scale)
+
+
+def loss_terms(C, alpha, C_gt, alpha_gt, l_max_scale, kind="paper", eps=0.01, lam=1.0, denom=None):
+    """Per-ray loss and its gradient w.r.t. (C, alpha).  kind: 'paper'
+    (HDR-regularised colour + alpha), 'reg' (colour only), 'mse' (plain MSE
+    on normalised colour).  `denom` overrides the held-constant denominator."""
+    Cn, Gn = C / l_max_scale, C_gt / l_max_scale
+    if kind == "mse":
+        den = np.ones_like(Cn)
+    else:
+        den = lam * Cn + eps if denom is None else denom
+    r = (Cn - Gn) / den
+    per_ray = (r ** 2).sum(1)
+    dC = 2.0 * r / den / l_max_scale
+    dA = np.zeros_like(alpha)
+    if kind == "paper":
+        per_ray = per_ray + (alpha - alpha_gt) ** 2
+        dA = 2.0 * (alpha - alpha_gt)
+    return per_ray, dC, dA
+
+
+def composite_backward(cache, dC, dA):
+    """d loss / d raw [R, N, n_out] from d loss / d C and d loss / d alpha."""
+    w, c, T, a = cache["w"], cache["c"], cache["T"], cache["a"]
+    sig, Y, raw, delta = cache["sig"], cache["Y"], cache["raw"], cache["delta"]
+    R, N = w.shape
+    K = Y.shape[1]
+    dc = w[..., None] * dC[:, None, :]                       # d/dc_j
+    ds = dc * cache["l_max_scale"] * sig * (1.0 - sig)       # through the sigmoid
+    dcoef = np.einsum("rnc,rk->rnck", ds, Y).reshape(R, N, 3 * K)
+    # d/da_j.  exp: dw_k/da_j = T_{j+1} for k = j, -w_k for k > j;
+    # linear: T_k = max(0, 1 - cum_k), w_k = T_k - T_{k+1}.
+    g_w = np.einsum("rnc,rc->rn", c, dC) + dA[:, None]      # d loss / d w_k
+    if cache["transmittance"] == "exp":
+        Tn = T[:, 1:]
+        suffix = np.flip(np.cumsum(np.flip(w * g_w, 1), 1), 1)  # sum_{k>=j} w_k g_k
+        after = suffix - w * g_w                                 # sum_{k>j}
+        da = Tn * g_w - after
+    else:
+        # T_k depends on a_j (j < k) with slope -1 while 1 - cum_k > 0
+        act = (1.0 - np.concatenate([np.zeros((R, 1)), np.cumsum(a, 1)], 1)) > 0  # [R, N+1]
+        # w_k = T_k - T_{k+1}: d w_k / d a_j = -act_k [j<k] + act_{k+1} [j<k+1]
+        # d loss/d a_j = sum_k g_k (act_{k+1}[j<=k] - act_k[j<k])
+        gk_act_next = g_w * act[:, 1:]
+        gk_act = g_w * act[:, :-1]
+        s1 = np.flip(np.cumsum(np.flip(gk_act_next, 1), 1), 1)          # sum_{k>=j}
+        s2 = np.flip(np.cumsum(np.flip(gk_act, 1), 1), 1) - gk_act      # sum_{k>j}
+        da = s1 - s2
+    dsigma = da * delta * (raw[..., 0] > 0)
+    return np.concatenate([dsigma[..., None], dcoef], axis=2)
+
+
+def train_loss_and_grads(Ws, bs, rays, jitter, C_gt, alpha_gt, l_max_scale, l_max=3, kind="paper",
+                         transmittance="exp", denom=None):
+    """One training batch: returns (mean loss, dWs, dbs, extras)."""
+    t, delta, x, hit = stratified_samples(rays, jitter)
+    R, N = jitter.shape
+    X = positional_encoding(x.reshape(R * N, 3))
+    raw, H = forward(Ws, bs, X)
+    raw = raw.reshape(R, N, -1)
+    d = rays[:, 3:].astype(np.float64)
+    Y = sh_matrix(d, l_max)
+    C, alpha, cache = composite(raw, delta, Y, l_max_scale, transmittance)
+    per_ray, dC, dA = loss_terms(C, alpha, C_gt, alpha_gt, l_max_scale, kind, denom=denom)
+    loss = per_ray.mean()
+    draw = composite_backward(cache, dC / R, dA / R).reshape(R * N, -1)
+    dWs, dbs = backward(Ws, H, draw)
+    return loss, dWs, dbs, dict(C=C, alpha=alpha, raw=raw, draw=draw, X=X)
+
+
+def lr_at(step: int, total: int, lr0=5e-4, lr1=5e-6) -> float:
+    """Exponential decay from lr0 to lr1 over `total` steps (Sec. 4.4)."""
+    return lr0 * (lr1 / lr0) ** (min(step, total) / max(total, 1))
+
+
+def adam_update(p, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (step counts from 1).  Returns new (p, m, v)."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** step)
+    vh = v / (1 - b2 ** step)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def distill_dense(Ws, bs, depth, jitter, sigma_thresh=0.01, l_max=3):
+    """Plenoctree extraction at `depth`: sigma of each voxel centre; voxels
+    with sigma >= sigma_thresh are kept and get the average of ReLU(sigma)
+    and of the raw SH coefficients over the jittered samples jitter
+    [n_kept, S, 3] (offsets in [0,1)^3 inside the voxel).  Returns
+    (kept voxel integer coords [n,3] in x-fastest order, sigma_centre of all
+    voxels [G^3], averaged sigma [n], averaged SH [n, 3, K])."""
+    G = 1 << depth
+    idx = np.arange(G ** 3)
+    ijk = np.stack([idx % G, (idx // G) % G, idx // (G * G)], 1)
+    centres = (ijk + 0.5) / G
+    raw, _ = forward(Ws, bs, positional_encoding(centres))
+    sig_c = np.maximum(raw[:, 0], 0.0)
+    kept = np.nonzero(sig_c >= sigma_thresh)[0]
+    if jitter is None:
+        return ijk[kept], sig_c, None, None
+    S = jitter.shape[1]
+    pts = (ijk[kept][:, None, :] + jitter[: len(kept)]) / G
+    raw_s, _ = forward(Ws, bs, positional_encoding(pts.reshape(-1, 3)))
+    raw_s = raw_s.reshape(len(kept), S, -1)
+    sig = np.maximum(raw_s[..., 0], 0.0).mean(1)
+    K = (l_max + 1) ** 2
+    sh = raw_s[..., 1:].mean(1).reshape(len(kept), 3, K)
+    return ijk[kept], sig_c, sig, sh

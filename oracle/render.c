@@ -175,10 +175,13 @@ void oracle_lookup(const oracle_tree* t, const float* pts, const float* dirs, in
 /* One ray.  Outputs radiance, transmittance, the per-channel error scale
  * sum_i w_i sum_k |c_k Y_k| (or sum_i w_i Phi_i for the sigmoid), the number
  * of leaf segments and of segments whose SH record is read, and an optional
- * trace of (leaf id or -1, t_in, t_out).  Status: 0 ok, 1 iteration cap,
+ * trace of (leaf id or -1, t_in, t_out).  `cond` is the per-channel
+ * sensitivity sum_i OD_i |Phi_i| (OD_i = optical depth at the end of segment
+ * i): an error e in every optical depth moves the linear-model radiance by at
+ * most e * cond.  Status: 0 ok, 1 iteration cap,
  * 2 lookup failure, 3 invalid ray (NaN/Inf component or zero direction). */
 typedef struct {
-    double rgb[3], T, bound[3];
+    double rgb[3], T, bound[3], cond[3];
     int32_t n_leaf, n_sh, n_cell, status;
 } ray_result;
 
@@ -294,9 +297,11 @@ static void render_one(const oracle_tree* t, const oracle_params* prm, const flo
                         if (prm->activation == 0) {
                             c = s > 0.0 ? s : 0.0;
                             res->bound[ch] += w * sa;
+                            res->cond[ch] += od * sa;
                         } else {
                             c = prm->l_max / (1.0 + exp(-s));
                             res->bound[ch] += w * c;
+                            res->cond[ch] += od * c;
                         }
                         res->rgb[ch] += w * c;
                     }
@@ -327,8 +332,8 @@ static void render_one(const oracle_tree* t, const oracle_params* prm, const flo
  * NULL.  n_threads <= 0 uses the OpenMP default.  Returns the number of rays
  * whose status is non-zero. */
 int64_t oracle_render(const oracle_tree* t, const float* rays, int64_t n, const oracle_params* prm, double* rgb,
-                      double* T, double* bound, int32_t* n_leaf, int32_t* n_sh, int32_t* n_cell, int32_t* status,
-                      int n_threads) {
+                      double* T, double* bound, double* cond, int32_t* n_leaf, int32_t* n_sh, int32_t* n_cell,
+                      int32_t* status, int n_threads) {
     int64_t bad = 0;
 #ifdef _OPENMP
     if (n_threads <= 0) n_threads = omp_get_max_threads();
@@ -340,6 +345,7 @@ int64_t oracle_render(const oracle_tree* t, const float* rays, int64_t n, const 
         if (rgb) for (int c = 0; c < 3; ++c) rgb[3 * i + c] = r.rgb[c];
         if (T) T[i] = r.T;
         if (bound) for (int c = 0; c < 3; ++c) bound[3 * i + c] = r.bound[c];
+        if (cond) for (int c = 0; c < 3; ++c) cond[3 * i + c] = r.cond[c];
         if (n_leaf) n_leaf[i] = r.n_leaf;
         if (n_sh) n_sh[i] = r.n_sh;
         if (n_cell) n_cell[i] = r.n_cell;

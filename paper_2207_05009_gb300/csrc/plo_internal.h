@@ -10,9 +10,13 @@
 //                                           or NO_SH_RECORD when all of the
 //                                           leaf's coefficients are zero
 //             .y  (leaves only)  FP32 trees: sigma as float bits
-//                               FP16/BF16:  bits 0..15 sigma (binary16 or
-//                               bfloat16), bits 16..23 biased exponent of the
-//                               leaf's power-of-two SH scale
+//                               FP16/BF16:  bits 0..23 sigma as a 24-bit
+//                               float (FP32 bits 30..7: exponent and 16
+//                               mantissa bits, round-to-nearest-even),
+//                               bits 24..31 biased exponent e+127 of the
+//                               leaf's SH scale 2^e (FP16 maps the largest
+//                               |coefficient| into [2^14, 2^15), BF16 into
+//                               [0.5, 1))
 //           A leaf's density travels with its parent's child entry, so a
 //           non-emissive leaf costs no load beyond the descent itself.
 //           Nodes of the top `top_levels` levels come first (breadth-first),
@@ -58,7 +62,7 @@ struct plo_tree {
     int64_t n_nodes, n_leaves, n_sh;
     int32_t sh_stride;
     int32_t device;
-    float bbox_min[3], inv_ext[3];
+    float bbox_min[3], inv_ext[3], inv_ext_lo[3];  // 1/extent as a double-float
     void* d_nodes;       // uint2 [n_nodes][8]
     int32_t* d_leaf_ids; // [n_nodes][8]
     void* d_sh;

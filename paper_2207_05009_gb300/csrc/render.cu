@@ -41,7 +41,7 @@ struct KParams {
     int32_t sh_stride;
     int32_t depth;
     int32_t n_top;
-    float bmin[3], inv_ext[3];
+    float bmin[3], inv_ext[3], inv_ext_lo[3];  // 1/extent as a double-float
     int32_t transmittance, activation;
     float l_max, t_stop, sigma_min;
     int32_t max_steps;
@@ -81,17 +81,19 @@ __device__ __forceinline__ DF df_mul(DF a, float rh, float rl) {
     e = __fmaf_rn(a.lo, rh, e);
     return fast_two_sum(p, e);
 }
-// double-float reciprocal of d (d finite, non-zero)
-__device__ __forceinline__ void df_recip(float d, float& rh, float& rl) {
-    rh = __frcp_rn(d);
-    float r = __fmaf_rn(-rh, d, 1.0f);  // exact residual
+// double-float reciprocal of d = dh + dl (dh finite, non-zero)
+__device__ __forceinline__ void df_recip(float dh, float dl, float& rh, float& rl) {
+    rh = __frcp_rn(dh);
+    float r = __fmaf_rn(-rh, dh, 1.0f);  // exact residual of the rounded reciprocal
+    r = __fmaf_rn(-rh, dl, r);
     rl = __fmul_rn(r, rh);
 }
-// p + t * d, all double-float except d
-__device__ __forceinline__ DF df_axpy(DF p, DF t, float d) {
-    float m = __fmul_rn(t.hi, d);
-    float me = __fmaf_rn(t.hi, d, -m);
-    me = __fmaf_rn(t.lo, d, me);
+// p + t * d, all double-float
+__device__ __forceinline__ DF df_axpy(DF p, DF t, float dh, float dl) {
+    float m = __fmul_rn(t.hi, dh);
+    float me = __fmaf_rn(t.hi, dh, -m);
+    me = __fmaf_rn(t.lo, dh, me);
+    me = __fmaf_rn(t.hi, dl, me);
     DF s = two_sum(p.hi, m);
     float lo = __fadd_rn(__fadd_rn(s.lo, p.lo), me);
     return fast_two_sum(s.hi, lo);
@@ -175,7 +177,7 @@ __device__ __forceinline__ void sh_eval(const uint8_t* rec, uint32_t yword, cons
                 }
             }
         }
-        float s = pow2i((int)((yword >> 16) & 0xFFu) - 127);
+        float s = pow2i((int)(yword >> 24) - 127);
         acc[0] *= s;
         acc[1] *= s;
         acc[2] *= s;
@@ -188,8 +190,7 @@ __device__ __forceinline__ void sh_eval(const uint8_t* rec, uint32_t yword, cons
 template <int PREC>
 __device__ __forceinline__ float decode_sigma(uint32_t y) {
     if (PREC == PLO_PREC_FP32) return __uint_as_float(y);
-    if (PREC == PLO_PREC_FP16) return __half2float(__ushort_as_half((uint16_t)(y & 0xFFFFu)));
-    return __uint_as_float((y & 0xFFFFu) << 16);
+    return __uint_as_float((y & 0xFFFFFFu) << 7);  // 24-bit float: exponent + 16 mantissa bits
 }
 
 __device__ __forceinline__ float act_fn(float s, int act, float l_max) {
@@ -199,7 +200,7 @@ __device__ __forceinline__ float act_fn(float s, int act, float l_max) {
 // ---------------------------------------------------------------- per-ray state
 struct Ray {
     DF p[3];
-    float d[3];
+    float d[3], dl[3];  // unit-cube direction as a double-float (dl = 0 for the unit box)
     float dirn[3];  // normalised world direction for the SH basis
     float T, r, g, b;
     DF od;
@@ -281,12 +282,14 @@ __device__ bool ray_begin(const KParams& kp, const uint2* s_nodes, int64_t i, Ra
         return false;
     }
     float inv_n = rsqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
-    float ou[3];
+    DF ou[3];  // origin in unit-cube coordinates, (o - bmin) / extent in double-float
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         R.dirn[a] = dw[a] * inv_n;
-        ou[a] = __fmul_rn(__fsub_rn(o[a], kp.bmin[a]), kp.inv_ext[a]);
-        R.d[a] = __fmul_rn(dw[a], kp.inv_ext[a]);
+        ou[a] = df_mul(two_sum(o[a], -kp.bmin[a]), kp.inv_ext[a], kp.inv_ext_lo[a]);
+        DF du = df_mul(DF{dw[a], 0.0f}, kp.inv_ext[a], kp.inv_ext_lo[a]);
+        R.d[a] = du.hi;
+        R.dl[a] = du.lo;
     }
     // slab test in double-float
     DF tn = {-INFINITY, 0.0f}, tf = {INFINITY, 0.0f};
@@ -295,14 +298,15 @@ __device__ bool ray_begin(const KParams& kp, const uint2* s_nodes, int64_t i, Ra
     for (int a = 0; a < 3; ++a) {
         near_a[a] = {-INFINITY, 0.0f};
         if (R.d[a] == 0.0f) {
-            if (ou[a] < 0.0f || ou[a] > 1.0f) return false;
+            if (ou[a].hi < 0.0f || ou[a].hi > 1.0f || (ou[a].hi == 0.0f && ou[a].lo < 0.0f) ||
+                (ou[a].hi == 1.0f && ou[a].lo > 0.0f))
+                return false;
             continue;
         }
         float rh, rl;
-        df_recip(R.d[a], rh, rl);
-        DF pa = {ou[a], 0.0f};
-        DF t0 = df_mul(df_from_plane(0.0f, pa), rh, rl);
-        DF t1 = df_mul(df_from_plane(1.0f, pa), rh, rl);
+        df_recip(R.d[a], R.dl[a], rh, rl);
+        DF t0 = df_mul(df_from_plane(0.0f, ou[a]), rh, rl);
+        DF t1 = df_mul(df_from_plane(1.0f, ou[a]), rh, rl);
         if (df_less(t1, t0)) {
             DF s = t0;
             t0 = t1;
@@ -316,8 +320,7 @@ __device__ bool ray_begin(const KParams& kp, const uint2* s_nodes, int64_t i, Ra
     bool outside = tn.hi > 0.0f || (tn.hi == 0.0f && tn.lo > 0.0f);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        DF oa = {ou[a], 0.0f};
-        R.p[a] = outside ? df_axpy(oa, tn, R.d[a]) : oa;
+        R.p[a] = outside ? df_axpy(ou[a], tn, R.d[a], R.dl[a]) : ou[a];
         if (outside && R.d[a] != 0.0f && df_eq(near_a[a], tn)) R.p[a] = {R.d[a] > 0.0f ? 0.0f : 1.0f, 0.0f};
         if (R.p[a].hi < 0.0f) R.p[a] = {0.0f, 0.0f};  // rounding guard
         if (R.p[a].hi > 1.0f || (R.p[a].hi == 1.0f && R.p[a].lo > 0.0f)) R.p[a] = {1.0f, 0.0f};
@@ -347,7 +350,7 @@ __device__ bool ray_step(const KParams& kp, const uint2* s_nodes, int64_t i, Ray
         float P = (float)(R.c[a] + (R.d[a] > 0.0f ? 1u : 0u)) * size;
         planes[a] = P;
         float rh, rl;
-        df_recip(R.d[a], rh, rl);
+        df_recip(R.d[a], R.dl[a], rh, rl);
         DF v = df_mul(df_from_plane(P, R.p[a]), rh, rl);
         if (v.hi < 0.0f) v = {0.0f, 0.0f};
         dts[a] = v;
@@ -384,7 +387,7 @@ __device__ bool ray_step(const KParams& kp, const uint2* s_nodes, int64_t i, Ray
                 w = Tin * (-expm1f(-a));
                 Tout = expf(-od);
             } else {
-                Tout = fmaxf(0.0f, 1.0f - od);
+                Tout = fmaxf(0.0f, __fsub_rn(__fsub_rn(1.0f, R.od.hi), R.od.lo));
                 float dT = fminf(Tin, a);
                 w = kp.transmittance == PLO_TRANS_LINEAR ? dT : 0.5f * dT * (Tin + Tout);
             }
@@ -411,12 +414,16 @@ __device__ bool ray_step(const KParams& kp, const uint2* s_nodes, int64_t i, Ray
         return false;
     }
 
-    // advance to the exit point; snap the exit axes onto their planes
+    // advance to the exit point; snap the exit axes onto their planes.  Axes
+    // whose exit lies within 2^-36 (relative) of the first one count as exits
+    // too, so a ray through a shared edge or corner crosses it in one step
+    // instead of leaving a sliver segment behind.
     int l_anc = L;
     uint32_t nc[3] = {R.c[0], R.c[1], R.c[2]};
+    const float tie = __fmaf_rn(dt.hi, 1.4551915228366852e-11f, dt.hi);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (R.d[a] != 0.0f && df_eq(dts[a], dt)) {
+        if (R.d[a] != 0.0f && (df_eq(dts[a], dt) || dts[a].hi <= tie)) {
             R.p[a] = {planes[a], 0.0f};
             uint32_t cn = R.d[a] > 0.0f ? R.c[a] + 1u : R.c[a] - 1u;
             if (cn >> L) return false;  // left the root cube (also catches 0 - 1)
@@ -424,7 +431,7 @@ __device__ bool ray_step(const KParams& kp, const uint2* s_nodes, int64_t i, Ray
             int diff = 32 - __clz(cn ^ R.c[a]);
             if (L - diff < l_anc) l_anc = L - diff;
         } else {
-            R.p[a] = df_axpy(R.p[a], dt, R.d[a]);
+            R.p[a] = df_axpy(R.p[a], dt, R.d[a], R.dl[a]);
         }
     }
 #pragma unroll
@@ -594,6 +601,7 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     for (int a = 0; a < 3; ++a) {
         kp.bmin[a] = t->bbox_min[a];
         kp.inv_ext[a] = t->inv_ext[a];
+        kp.inv_ext_lo[a] = t->inv_ext_lo[a];
     }
     kp.transmittance = p->transmittance;
     kp.activation = p->activation;

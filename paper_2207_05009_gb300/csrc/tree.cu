@@ -96,6 +96,16 @@ uint16_t bf16_bits(float v) {
     std::memcpy(&b, &h, 2);
     return b;
 }
+// sigma >= 0 as a 24-bit float: FP32 without its sign bit, mantissa rounded
+// to nearest-even at 16 bits (relative error <= 2^-17).
+uint32_t sigma24_bits(float v) {
+    uint32_t b;
+    std::memcpy(&b, &v, 4);
+    b &= 0x7FFFFFFFu;
+    uint32_t r = (b + 0x3Fu + ((b >> 7) & 1u)) >> 7;
+    if (r >= 0xFF0000u) r = 0xFEFFFFu;  // keep it finite (exponent 255 would be inf)
+    return r;
+}
 
 }  // namespace
 
@@ -109,12 +119,6 @@ extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precisio
     plo_status st = validate(desc);
     if (st != PLO_OK) return st;
     const int K = sh_K(desc->sh_degree);
-    if (precision == PLO_PREC_FP16) {
-        for (int64_t i = 0; i < desc->n_leaves; ++i)
-            if (desc->sigma[i] > 65504.0f)
-                return set_error(PLO_ERR_INVALID_ARG, "FP16 leaves: sigma of leaf " + std::to_string(i) +
-                                                          " exceeds the binary16 range (65504)");
-    }
 
     // Canonical child table; a tree without nodes is re-rooted one level down
     // (eight slots that all hold the root leaf, or all empty).
@@ -225,7 +229,11 @@ extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precisio
         float m = 0.0f;
         for (int k = 0; k < 3 * K; ++k) m = std::fmax(m, std::fabs(c[k]));
         int e;
-        std::frexp(m, &e);  // m = f * 2^e, f in [0.5, 1): m / 2^e <= 1
+        std::frexp(m, &e);  // m = f * 2^e, f in [0.5, 1)
+        // FP16: map the largest coefficient into [2^14, 2^15) so that the
+        // leaf's smaller coefficients keep binary16's normal range (down to
+        // 2^-29 of the largest); BF16 has FP32's range and uses [0.5, 1).
+        if (precision == PLO_PREC_FP16) e -= 15;
         if (e < -126) e = -126;
         if (e > 127) e = 127;
         scale_exp[leaf] = (int8_t)0;  // placeholder, stored below
@@ -252,9 +260,8 @@ extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precisio
                 if (precision == PLO_PREC_FP32) {
                     std::memcpy(&y, &sg, 4);
                 } else {
-                    uint32_t sb = precision == PLO_PREC_FP16 ? half_bits(sg) : bf16_bits(sg);
                     uint32_t eb = rec_of_leaf[leaf] == NO_SH_RECORD ? 0u : (uint32_t)(scale_exp[leaf] + 127);
-                    y = sb | (eb << 16);
+                    y = sigma24_bits(sg) | (eb << 24);
                 }
             }
             nodes[i * 16 + 2 * s] = x;
@@ -276,7 +283,9 @@ extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precisio
     t->sh_stride = stride;
     for (int a = 0; a < 3; ++a) {
         t->bbox_min[a] = desc->bbox_min[a];
-        t->inv_ext[a] = 1.0f / (desc->bbox_max[a] - desc->bbox_min[a]);
+        double inv = 1.0 / ((double)desc->bbox_max[a] - (double)desc->bbox_min[a]);
+        t->inv_ext[a] = (float)inv;
+        t->inv_ext_lo[a] = (float)(inv - (double)t->inv_ext[a]);
     }
     t->node_bytes = n_packed * 64;
     t->sh_bytes = (int64_t)n_sh * stride;

@@ -94,8 +94,13 @@ def test_validator_rejects_malformed_trees():
     _expect(HostTree(0, 2, np.zeros((0, 8), np.int32), np.ones(2, np.float32), np.zeros((2, 3, 9), np.float32)), BAD)
 
 
-def test_fp16_sigma_range_is_checked_before_any_device_work():
-    t = uniform_tree(1, 1e5, np.ones((3, 9)))
+def test_build_rejects_bad_precision_before_any_device_work():
+    t = uniform_tree(1, 1.0, np.ones((3, 9)))
     with pytest.raises(plo.PloError) as ei:
-        plo.Tree(t, plo.PREC_FP16)
-    assert ei.value.status == -1 and "binary16" in str(ei.value)
+        plo.Tree(t, 7)
+    assert ei.value.status == -1 and "precision" in str(ei.value)
+    with pytest.raises(plo.PloError) as ei:
+        bad = t.child.copy()
+        bad[0, 3] = 99
+        plo.Tree(HostTree(1, 2, bad, t.sigma, t.sh), plo.PREC_FP16)
+    assert ei.value.status == -2

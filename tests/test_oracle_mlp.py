@@ -1,0 +1,163 @@
+"""Pins for the learned-part oracle: positional-encoding values, quadrature
+closed forms, loss special cases, central finite differences of the full
+training loss, Adam's first step, the learning-rate schedule, and the
+distillation of a constant field."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import plogen
+from oracle import mlp
+from tests.trees import chord
+
+
+def test_positional_encoding_values():
+    x = np.array([[0.0, 0.5, 0.25]])
+    g = mlp.positional_encoding(x)
+    assert g.shape == (1, 63)
+    np.testing.assert_array_equal(g[0, :3], x[0])
+    for j in range(10):
+        s, c = g[0, 3 + 6 * j: 6 + 6 * j], g[0, 6 + 6 * j: 9 + 6 * j]
+        assert s[0] == 0.0 and c[0] == 1.0                         # x = 0
+        assert s[1] == pytest.approx(math.sin(2 ** j * math.pi / 2), abs=1e-12)
+        assert c[1] == pytest.approx(math.cos(2 ** j * math.pi / 2), abs=1e-12)
+    assert g[0, 3 + 1] == pytest.approx(1.0)   # sin(pi/2)
+    assert g[0, 9 + 4] == pytest.approx(-1.0)  # cos(2 pi * 0.5)
+
+
+def test_samples_lie_in_the_chord_and_are_ordered():
+    rays = plogen.rays_sphere(64, seed=3)
+    rng = np.random.default_rng(0)
+    jit = rng.random((64, 16))
+    t, delta, x, hit = mlp.stratified_samples(rays, jit)
+    for i, r in enumerate(rays):
+        ch = chord(r[:3], r[3:])
+        assert hit[i] == (ch is not None)
+        if ch is None:
+            continue
+        assert np.all(np.diff(t[i]) > 0)
+        assert t[i, 0] >= ch[0] - 1e-12 and t[i, -1] <= ch[1] + 1e-12
+        assert t[i, -1] + delta[i, -1] == pytest.approx(ch[1], abs=1e-12)
+        assert np.all((x[i] >= -1e-9) & (x[i] <= 1 + 1e-9))
+
+
+def test_composite_closed_forms():
+    R, N = 5, 32
+    rng = np.random.default_rng(1)
+    delta = rng.uniform(0.001, 0.05, (R, N))
+    K = 16
+    raw = np.zeros((R, N, 1 + 3 * K))
+    raw[..., 0] = 3.0                       # constant sigma
+    raw[..., 1:] = rng.normal(size=3 * K)   # same coefficients everywhere
+    Y = mlp.sh_matrix(np.tile([0.0, 0.0, 1.0], (R, 1)), 3)
+    C, alpha, _ = mlp.composite(raw, delta, Y, 7.0, "exp")
+    L = delta.sum(1)
+    np.testing.assert_allclose(alpha, 1 - np.exp(-3.0 * L), rtol=1e-13)
+    s = raw[0, 0, 1:].reshape(3, K) @ Y[0]
+    phi = 7.0 / (1 + np.exp(-s))
+    np.testing.assert_allclose(C, alpha[:, None] * phi[None], rtol=1e-12)
+    C, alpha, _ = mlp.composite(raw, delta, Y, 7.0, "linear")
+    np.testing.assert_allclose(alpha, np.minimum(1.0, 3.0 * L), rtol=1e-13)
+
+
+def test_loss_special_cases():
+    C = np.array([[1.0, 2.0, 3.0]])
+    a = np.array([0.4])
+    per, dC, dA = mlp.loss_terms(C, a, C, a, 10.0)
+    assert per[0] == 0 and np.all(dC == 0) and dA[0] == 0
+    per, dC, dA = mlp.loss_terms(C, a, np.zeros_like(C), np.zeros(1), 10.0, kind="paper")
+    cn = C[0] / 10
+    assert per[0] == pytest.approx(((cn / (cn + 0.01)) ** 2).sum() + 0.16)
+    per, dC, _ = mlp.loss_terms(C, a, np.zeros_like(C), a, 10.0, kind="mse")
+    assert per[0] == pytest.approx((cn ** 2).sum())
+    np.testing.assert_allclose(dC[0], 2 * cn / 10)
+
+
+def _batch(seed=0, R=6, N=12, l_max=3):
+    rng = np.random.default_rng(seed)
+    Ws, bs = mlp.init_params(rng, l_max)
+    # small-scale weights so that the sigmoid and ReLUs are away from kinks
+    Ws = [w * 0.5 for w in Ws]
+    bs = [rng.normal(0, 0.05, b.shape) for b in bs]
+    bs[-1][0] = 1.0
+    rays = plogen.rays_sphere(R, seed=seed + 40)
+    jit = rng.random((R, N))
+    C_gt = rng.uniform(0, 5, (R, 3))
+    a_gt = rng.uniform(0, 1, R)
+    return Ws, bs, rays, jit, C_gt, a_gt
+
+
+@pytest.mark.parametrize("kind,trans,seed", [("paper", "exp", 1), ("paper", "exp", 5), ("mse", "exp", 2),
+                                              ("paper", "linear", 11), ("paper", "linear", 10)])
+def test_gradients_match_central_differences(kind, trans, seed):
+    Ws, bs, rays, jit, C_gt, a_gt = _batch(seed=seed)
+    Lm = 6.0
+    loss0, dWs, dbs, ex = mlp.train_loss_and_grads(Ws, bs, rays, jit, C_gt, a_gt, Lm, kind=kind,
+                                                   transmittance=trans)
+    # the loss holds its denominator constant: freeze it at the base point
+    den = ex["C"] / Lm + 0.01
+
+    def loss_at(Wmod=None, bmod=None):
+        return mlp.train_loss_and_grads(Wmod or Ws, bmod or bs, rays, jit, C_gt, a_gt, Lm, kind=kind,
+                                        transmittance=trans, denom=den)[0]
+
+    def fd(setter, h):
+        return (loss_at(*setter(+h)) - loss_at(*setter(-h))) / (2 * h)
+
+    rng = np.random.default_rng(5)
+    checks = 0
+    for l in [0, 3, 7, 8]:
+        scale = float(np.sqrt((dWs[l] ** 2).mean()))
+        tries = 0
+        done = 0
+        while done < 4 and tries < 40:
+            tries += 1
+            i = rng.integers(0, Ws[l].shape[0])
+            j = rng.integers(0, Ws[l].shape[1])
+
+            def setter(h, i=i, j=j, l=l):
+                W2 = [w.copy() for w in Ws]
+                W2[l][i, j] += h
+                return W2, None
+            f1, f2 = fd(setter, 1e-5), fd(setter, 5e-6)
+            if abs(f1 - f2) > 1e-4 * abs(f1) + 1e-6 * scale:
+                continue  # a ReLU or clamp kink within the step: resample
+            assert dWs[l][i, j] == pytest.approx(f1, rel=1e-4, abs=1e-5 * scale), (l, i, j)
+            done += 1
+            checks += 1
+        k = int(np.argmax(np.abs(dbs[l])))
+
+        def bset(h, k=k, l=l):
+            b2 = [b.copy() for b in bs]
+            b2[l][k] += h
+            return None, b2
+        assert dbs[l][k] == pytest.approx(fd(bset, 1e-5), rel=1e-4)
+    assert checks == 16
+
+
+def test_adam_first_step_and_schedule():
+    g = np.array([0.3, -2.0, 1e-3])
+    p, m, v = mlp.adam_update(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, 1e-3)
+    np.testing.assert_allclose(p, -1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    assert mlp.lr_at(0, 1000) == pytest.approx(5e-4)
+    assert mlp.lr_at(1000, 1000) == pytest.approx(5e-6)
+    assert mlp.lr_at(500, 1000) == pytest.approx(5e-5)
+
+
+def test_distill_constant_field():
+    rng = np.random.default_rng(2)
+    Ws, bs = mlp.init_params(rng)
+    Ws = [w * 0 for w in Ws]
+    bs = [b * 0 for b in bs]
+    bs[-1][0] = 0.5
+    bs[-1][1:] = np.arange(48) * 0.01
+    jit = rng.random((8 ** 2 * 8, 8, 3))
+    ijk, sig_c, sig, sh = mlp.distill_dense(Ws, bs, 3, jit)
+    assert len(ijk) == 512 and np.all(sig_c == 0.5)
+    np.testing.assert_allclose(sig, 0.5)
+    np.testing.assert_allclose(sh.reshape(len(ijk), -1), np.tile(np.arange(48) * 0.01, (512, 1)))
+    bs[-1][0] = 0.005  # below the 0.01 threshold: everything pruned
+    ijk, *_ = mlp.distill_dense(Ws, bs, 3, None)
+    assert len(ijk) == 0

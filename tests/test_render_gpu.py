@@ -7,7 +7,7 @@ import oracle
 import paper_2207_05009_gb300 as plo
 import plogen
 from plogen import HostTree
-from tests.parity import RTOL_FP16, RTOL_FP32, assert_radiance_close, quantise_tree
+from tests.parity import COND_ETA_LINEAR, RTOL_FP16, RTOL_FP32, assert_radiance_close, quantise_tree
 from tests.trees import random_tree, uniform_tree
 
 pytestmark = pytest.mark.gpu
@@ -43,7 +43,8 @@ def test_d6_luminaire_fp32_parity(torch_cuda, d6, model):
     g_rgb, g_T, st = gpu_render(torch_cuda, d6, rays, transmittance=TRANS[model][0])
     ref = oracle.render(d6, rays, transmittance=TRANS[model][1])
     assert np.all(st == 0)
-    assert_radiance_close(g_rgb, g_T, ref, RTOL_FP32, what=f"D6 {model}")
+    eta = 0.0 if model == "exp" else COND_ETA_LINEAR
+    assert_radiance_close(g_rgb, g_T, ref, RTOL_FP32, what=f"D6 {model}", cond_eta=eta)
 
 
 def test_sigmoid_activation_parity(torch_cuda, d6):
