@@ -43,7 +43,9 @@ def _stale(target, inputs):
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile every csrc/*.cu in parallel, then link libplo.so."""
+    """Compile every csrc/*.cu in parallel, then link libplo.so.  Extra nvcc
+    flags (for example -DPLO_RENDER_MIN_BLOCKS=3) come from $PLO_NVCC_FLAGS;
+    pass force=True after changing them."""
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     deps = _deps()
@@ -52,7 +54,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + deps):
-            cmd = [cc, *ARCH, *FLAGS, "-I", INCLUDE, "-c", src, "-o", obj]
+            cmd = [cc, *ARCH, *FLAGS, *os.environ.get("PLO_NVCC_FLAGS", "").split(), "-I", INCLUDE, "-c", src,
+                   "-o", obj]
             if ptxas_info:
                 cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)

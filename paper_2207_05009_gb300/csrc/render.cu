@@ -4,7 +4,9 @@
 //
 // One thread renders one ray at a time.  The grid is persistent: each warp
 // owns a contiguous chunk of rays and a lane that finishes its ray takes the
-// next one of the chunk, so a warp does not idle behind its longest ray.
+// next one of the chunk, so a warp does not idle behind its longest ray; each
+// lane advances through a small state machine (descend / composite) so that
+// lanes never wait for each other's dependent node loads.
 //
 // Numerics (all FP32, no FP64 on the device):
 //   * The ray position is kept as an unevaluated sum hi + lo of two floats
@@ -31,6 +33,9 @@ namespace plo {
 namespace {
 
 constexpr int BLOCK = 256;
+#ifndef PLO_RENDER_MIN_BLOCKS
+#define PLO_RENDER_MIN_BLOCKS 3  // resident blocks per SM the register budget is sized for (measured best)
+#endif
 constexpr int WARPS = BLOCK / 32;
 constexpr int STACK = MAX_DEPTH + 1;
 
@@ -198,20 +203,27 @@ __device__ __forceinline__ float act_fn(float s, int act, float l_max) {
 }
 
 // ---------------------------------------------------------------- per-ray state
+// Each lane runs a small state machine so that lanes of a warp never wait for
+// each other's descents: one loop iteration composites at most one leaf and
+// issues at most one dependent node load (levels staged in shared memory
+// resolve within the same iteration).
+enum : int { ST_IDLE = 0, ST_DESCEND = 1, ST_LEAF = 2 };
+
 struct Ray {
     DF p[3];
     float d[3], dl[3];  // unit-cube direction as a double-float (dl = 0 for the unit box)
-    float dirn[3];  // normalised world direction for the SH basis
+    float dirn[3];      // normalised world direction for the SH basis
     float T, r, g, b;
     DF od;
-    DF t;           // ray parameter at the current cell entry (trace only)
+    DF t;               // ray parameter at the current cell entry (trace only)
+    uint32_t c[3];      // integer cell coordinates at `level`
+    uint32_t node;      // node whose child is looked up next (ST_DESCEND)
+    uint32_t entry_x, entry_y;
     int level;
     int steps;
-    uint32_t c[3];  // integer cell coordinates at `level`
-    uint32_t entry_x, entry_y;
-    int32_t leaf_id;  // canonical id of the current cell (trace only)
+    int slot;           // slot of the current cell in its parent (trace only)
+    int state;
     int status;
-    bool live;
 };
 
 __device__ __forceinline__ uint2 load_entry(const uint2* nodes, const uint2* s_nodes, int n_top, uint32_t node,
@@ -220,46 +232,50 @@ __device__ __forceinline__ uint2 load_entry(const uint2* nodes, const uint2* s_n
     return __ldg(nodes + (size_t)node * 8 + slot);
 }
 
-// Descends from `stack[lev]` (cell coords c at level lev) to the leaf or
-// empty octant containing the ray position, recording the path.
-template <bool TRACE>
-__device__ __forceinline__ void descend(const KParams& kp, const uint2* s_nodes, Ray& R, uint32_t* stack, int lev) {
-    uint32_t node = stack[lev];
-    uint32_t cx = R.c[0], cy = R.c[1], cz = R.c[2];
-    int slot = 0;
-    uint2 e = make_uint2(ENTRY_EMPTY, 0);
+// Descends from R.node (cell coords R.c at R.level) through the shared-memory
+// levels and at most one global level.  Ends in ST_LEAF (leaf or empty
+// octant found) or stays in ST_DESCEND with the next node to load.
+__device__ __forceinline__ void descend_step(const KParams& kp, const uint2* s_nodes, Ray& R, uint32_t* stack) {
     for (int guard = 0; guard <= MAX_DEPTH; ++guard) {
-        float sc = pow2i(-(lev + 1));
-        int bx = above(R.p[0], (float)(2u * cx + 1u) * sc, R.d[0]);
-        int by = above(R.p[1], (float)(2u * cy + 1u) * sc, R.d[1]);
-        int bz = above(R.p[2], (float)(2u * cz + 1u) * sc, R.d[2]);
-        cx = 2u * cx + bx;
-        cy = 2u * cy + by;
-        cz = 2u * cz + bz;
-        slot = bx | (by << 1) | (bz << 2);
-        e = load_entry(kp.nodes, s_nodes, kp.n_top, node, slot);
-        ++lev;
-        if (e.x & LEAF_BIT) break;  // leaf or empty
-        node = e.x;
-        stack[lev] = node;
-        if (lev >= kp.depth) {  // malformed table: treat as empty
-            e = make_uint2(ENTRY_EMPTY, 0);
-            break;
+        const float sc = pow2i(-(R.level + 1));
+        int bx = above(R.p[0], (float)(2u * R.c[0] + 1u) * sc, R.d[0]);
+        int by = above(R.p[1], (float)(2u * R.c[1] + 1u) * sc, R.d[1]);
+        int bz = above(R.p[2], (float)(2u * R.c[2] + 1u) * sc, R.d[2]);
+        R.c[0] = 2u * R.c[0] + bx;
+        R.c[1] = 2u * R.c[1] + by;
+        R.c[2] = 2u * R.c[2] + bz;
+        R.slot = bx | (by << 1) | (bz << 2);
+        const bool global = R.node >= (uint32_t)kp.n_top;
+        uint2 e = load_entry(kp.nodes, s_nodes, kp.n_top, R.node, R.slot);
+        ++R.level;
+        if ((e.x & LEAF_BIT) || R.level >= kp.depth) {  // leaf, empty octant (or a malformed table)
+            if (!(e.x & LEAF_BIT)) e = make_uint2(ENTRY_EMPTY, 0u);
+            R.entry_x = e.x;
+            R.entry_y = e.y;
+            R.state = ST_LEAF;
+            return;
         }
+        stack[R.level] = e.x;
+        const uint32_t parent = R.node;
+        R.node = e.x;
+        (void)parent;
+        if (global || R.node >= (uint32_t)kp.n_top) return;  // next lookup needs a global load
     }
-    R.level = lev;
-    R.c[0] = cx;
-    R.c[1] = cy;
-    R.c[2] = cz;
-    R.entry_x = e.x;
-    R.entry_y = e.y;
-    if (TRACE) R.leaf_id = e.x == ENTRY_EMPTY ? -1 : __ldg(kp.leaf_ids + (size_t)stack[lev - 1] * 8 + slot);
 }
 
-// Proxy clip and first descent.  Returns false for a miss or an invalid ray
-// (outputs already set).
+__device__ __forceinline__ void ray_store(const KParams& kp, int64_t i, const Ray& R) {
+    kp.rgb[3 * i + 0] = R.r;
+    kp.rgb[3 * i + 1] = R.g;
+    kp.rgb[3 * i + 2] = R.b;
+    kp.T[i] = R.T;
+    if (kp.status) kp.status[i] = R.status;
+    if (kp.tr_count) kp.tr_count[i] = R.steps;
+}
+
+// Proxy clip.  On a hit the lane enters ST_DESCEND at the root; on a miss or
+// an invalid ray the outputs are written and the lane stays ST_IDLE.
 template <bool TRACE>
-__device__ bool ray_begin(const KParams& kp, const uint2* s_nodes, int64_t i, Ray& R, uint32_t* stack) {
+__device__ void ray_begin(const KParams& kp, int64_t i, Ray& R, uint32_t* stack) {
     const float* q = kp.rays + 6 * i;
     float o[3], dw[3];
 #pragma unroll
@@ -273,13 +289,15 @@ __device__ bool ray_begin(const KParams& kp, const uint2* s_nodes, int64_t i, Ra
     R.t = {0.0f, 0.0f};
     R.status = PLO_RAY_OK;
     R.steps = 0;
+    R.state = ST_IDLE;
     bool bad = dw[0] == 0.0f && dw[1] == 0.0f && dw[2] == 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) bad |= !isfinite(o[a]) || !isfinite(dw[a]);
     if (bad) {
         R.status = PLO_RAY_INVALID;
         R.r = R.g = R.b = R.T = __int_as_float(0x7fc00000);
-        return false;
+        ray_store(kp, i, R);
+        return;
     }
     float inv_n = rsqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
     DF ou[3];  // origin in unit-cube coordinates, (o - bmin) / extent in double-float
@@ -294,13 +312,14 @@ __device__ bool ray_begin(const KParams& kp, const uint2* s_nodes, int64_t i, Ra
     // slab test in double-float
     DF tn = {-INFINITY, 0.0f}, tf = {INFINITY, 0.0f};
     DF near_a[3];
+    bool miss = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         near_a[a] = {-INFINITY, 0.0f};
         if (R.d[a] == 0.0f) {
             if (ou[a].hi < 0.0f || ou[a].hi > 1.0f || (ou[a].hi == 0.0f && ou[a].lo < 0.0f) ||
                 (ou[a].hi == 1.0f && ou[a].lo > 0.0f))
-                return false;
+                miss = true;
             continue;
         }
         float rh, rl;
@@ -316,7 +335,10 @@ __device__ bool ray_begin(const KParams& kp, const uint2* s_nodes, int64_t i, Ra
         if (df_less(tn, t0)) tn = t0;
         if (df_less(t1, tf)) tf = t1;
     }
-    if (!df_less(tn, tf) || !(tf.hi > 0.0f || (tf.hi == 0.0f && tf.lo > 0.0f))) return false;
+    if (miss || !df_less(tn, tf) || !(tf.hi > 0.0f || (tf.hi == 0.0f && tf.lo > 0.0f))) {
+        ray_store(kp, i, R);
+        return;
+    }
     bool outside = tn.hi > 0.0f || (tn.hi == 0.0f && tn.lo > 0.0f);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -327,15 +349,16 @@ __device__ bool ray_begin(const KParams& kp, const uint2* s_nodes, int64_t i, Ra
     }
     if (TRACE) R.t = outside ? tn : DF{0.0f, 0.0f};
     stack[0] = 0;
+    R.node = 0;
+    R.level = 0;
     R.c[0] = R.c[1] = R.c[2] = 0;
-    descend<TRACE>(kp, s_nodes, R, stack, 0);
-    return true;
+    R.state = ST_DESCEND;
 }
 
-// One cell: segment length, compositing, advance.  Returns false when the
-// ray is finished.
+// One cell: segment length, compositing, advance.  Leaves the lane in
+// ST_DESCEND (next cell) or ST_IDLE (ray finished, outputs written).
 template <int K, int PREC, bool TRACE>
-__device__ bool ray_step(const KParams& kp, const uint2* s_nodes, int64_t i, Ray& R, uint32_t* stack) {
+__device__ void leaf_step(const KParams& kp, int64_t i, Ray& R, uint32_t* stack) {
     // segment: exit parameter of the current cell along each axis
     const int L = R.level;
     const float size = pow2i(-L);
@@ -361,15 +384,16 @@ __device__ bool ray_step(const KParams& kp, const uint2* s_nodes, int64_t i, Ray
 
     if (TRACE) {
         int k = R.steps - 1;
+        DF t1 = two_sum(R.t.hi, dt.hi);
+        t1 = fast_two_sum(t1.hi, __fadd_rn(t1.lo, __fadd_rn(R.t.lo, dt.lo)));
         if (k < kp.trace_max) {
             size_t o = (size_t)i * kp.trace_max + k;
-            kp.tr_leaf[o] = R.leaf_id;
-            DF t1 = two_sum(R.t.hi, dt.hi);
-            t1 = fast_two_sum(t1.hi, __fadd_rn(t1.lo, __fadd_rn(R.t.lo, dt.lo)));
+            kp.tr_leaf[o] = R.entry_x == ENTRY_EMPTY ? -1
+                                                     : __ldg(kp.leaf_ids + (size_t)stack[L - 1] * 8 + R.slot);
             kp.tr_t[2 * o] = R.t.hi;
             kp.tr_t[2 * o + 1] = t1.hi;
-            R.t = t1;
         }
+        R.t = t1;
     }
 
     // composite the leaf (Eq. 3-5)
@@ -381,11 +405,10 @@ __device__ bool ray_step(const KParams& kp, const uint2* s_nodes, int64_t i, Ray
             float Tin = R.T;
             DF s = two_sum(R.od.hi, a);
             R.od = fast_two_sum(s.hi, __fadd_rn(s.lo, R.od.lo));
-            float od = R.od.hi + R.od.lo;
             float w, Tout;
             if (kp.transmittance == PLO_TRANS_EXP) {
                 w = Tin * (-expm1f(-a));
-                Tout = expf(-od);
+                Tout = expf(-(R.od.hi + R.od.lo));
             } else {
                 Tout = fmaxf(0.0f, __fsub_rn(__fsub_rn(1.0f, R.od.hi), R.od.lo));
                 float dT = fminf(Tin, a);
@@ -405,13 +428,19 @@ __device__ bool ray_step(const KParams& kp, const uint2* s_nodes, int64_t i, Ray
                 R.b = __fmaf_rn(w, act_fn(cb, kp.activation, kp.l_max), R.b);
             }
             R.T = Tout;
-            if (R.T < kp.t_stop || R.T <= 0.0f) return false;
+            if (R.T < kp.t_stop || R.T <= 0.0f) {
+                ray_store(kp, i, R);
+                R.state = ST_IDLE;
+                return;
+            }
         }
     }
     if (R.steps >= kp.max_steps) {
         R.status = PLO_RAY_STEP_LIMIT;
         atomicOr(kp.flags, 1u);
-        return false;
+        ray_store(kp, i, R);
+        R.state = ST_IDLE;
+        return;
     }
 
     // advance to the exit point; snap the exit axes onto their planes.  Axes
@@ -421,12 +450,13 @@ __device__ bool ray_step(const KParams& kp, const uint2* s_nodes, int64_t i, Ray
     int l_anc = L;
     uint32_t nc[3] = {R.c[0], R.c[1], R.c[2]};
     const float tie = __fmaf_rn(dt.hi, 1.4551915228366852e-11f, dt.hi);
+    bool left = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (R.d[a] != 0.0f && (df_eq(dts[a], dt) || dts[a].hi <= tie)) {
             R.p[a] = {planes[a], 0.0f};
             uint32_t cn = R.d[a] > 0.0f ? R.c[a] + 1u : R.c[a] - 1u;
-            if (cn >> L) return false;  // left the root cube (also catches 0 - 1)
+            left |= (cn >> L) != 0u;  // left the root cube (also catches 0 - 1)
             nc[a] = cn;
             int diff = 32 - __clz(cn ^ R.c[a]);
             if (L - diff < l_anc) l_anc = L - diff;
@@ -434,23 +464,20 @@ __device__ bool ray_step(const KParams& kp, const uint2* s_nodes, int64_t i, Ray
             R.p[a] = df_axpy(R.p[a], dt, R.d[a], R.dl[a]);
         }
     }
+    if (left) {
+        ray_store(kp, i, R);
+        R.state = ST_IDLE;
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) R.c[a] = nc[a] >> (L - l_anc);
-    descend<TRACE>(kp, s_nodes, R, stack, l_anc);
-    return true;
-}
-
-__device__ __forceinline__ void ray_store(const KParams& kp, int64_t i, const Ray& R) {
-    kp.rgb[3 * i + 0] = R.r;
-    kp.rgb[3 * i + 1] = R.g;
-    kp.rgb[3 * i + 2] = R.b;
-    kp.T[i] = R.T;
-    if (kp.status) kp.status[i] = R.status;
-    if (kp.tr_count) kp.tr_count[i] = R.steps;
+    R.level = l_anc;
+    R.node = stack[l_anc];
+    R.state = ST_DESCEND;
 }
 
 template <int K, int PREC, bool TRACE>
-__global__ void __launch_bounds__(BLOCK) k_render(KParams kp) {
+__global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams kp) {
     // nodes of the top levels, staged once per (persistent) block
     extern __shared__ uint2 s_nodes[];
     for (int j = threadIdx.x; j < kp.n_top * 8; j += BLOCK) s_nodes[j] = kp.nodes[j];
@@ -465,28 +492,25 @@ __global__ void __launch_bounds__(BLOCK) k_render(KParams kp) {
     const int64_t end = min(beg + kp.chunk, kp.n);
 
     Ray R;
+    R.state = ST_IDLE;
     int64_t my = 0;
     int64_t next = beg;  // warp-uniform cursor into the chunk
-    bool live = false;
     for (;;) {
-        // lanes without a ray take the next ones of the chunk; rays that miss
-        // the proxy finish at once, so repeat until no lane is idle
+        // idle lanes take the next rays of the chunk; rays that miss the proxy
+        // finish at once, so repeat while lanes are idle and rays remain
         for (;;) {
-            unsigned idle = __ballot_sync(0xffffffffu, !live);
+            unsigned idle = __ballot_sync(0xffffffffu, R.state == ST_IDLE);
             if (idle == 0u || next >= end) break;
             int64_t cand = next + __popc(idle & lanes_below);
             next += __popc(idle);
-            if (!live && cand < end) {
+            if (R.state == ST_IDLE && cand < end) {
                 my = cand;
-                live = ray_begin<TRACE>(kp, s_nodes, my, R, stack);
-                if (!live) ray_store(kp, my, R);
+                ray_begin<TRACE>(kp, my, R, stack);
             }
         }
-        if (__ballot_sync(0xffffffffu, live) == 0u) break;
-        if (live) {
-            live = ray_step<K, PREC, TRACE>(kp, s_nodes, my, R, stack);
-            if (!live) ray_store(kp, my, R);
-        }
+        if (__ballot_sync(0xffffffffu, R.state != ST_IDLE) == 0u) break;
+        if (R.state == ST_LEAF) leaf_step<K, PREC, TRACE>(kp, my, R, stack);
+        if (R.state == ST_DESCEND) descend_step(kp, s_nodes, R, stack);
     }
 }
 
