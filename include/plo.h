@@ -153,6 +153,24 @@ plo_status plo_render_rays(const plo_tree* tree, const float* d_rays, int64_t n,
 plo_status plo_render_rays_host(const plo_tree* tree, const float* h_rays, int64_t n,
                                 const plo_render_params* params, float* h_rgb, float* h_T, void* stream);
 
+/* Allocation-free variant of plo_render_rays_host, for callers that cannot
+ * allocate device memory while they render: for example a CPU path tracer
+ * that queries the luminaire from its emitter code inside the frame loop, or
+ * a host process whose device memory is fixed at start-up.  Same inputs,
+ * outputs and results as plo_render_rays_host; the paper has no counterpart.
+ *   - Rays and results are staged in a fixed device array inside the library
+ *     (10 MiB, held by every GPU that loads the library until exit), so at
+ *     most 262,144 rays per call; larger n returns PLO_ERR_INVALID_ARG.
+ *   - The call makes no device allocation and no allocating library call.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device); make that first call before capturing any stream.
+ *   - All calls share the array: calls whose work overlaps on the GPU (other
+ *     streams, other host threads) race and corrupt each other's results.
+ *   - Copies and the render run on `stream`; the call returns after h_rgb and
+ *     h_T are written.  The tree must live on the current device. */
+plo_status plo_render_rays_host_noalloc(const plo_tree* tree, const float* h_rays, int64_t n,
+                                        const plo_render_params* params, float* h_rgb, float* h_T, void* stream);
+
 /* Point -> leaf lookup (async), the descent step of the render.
  *   d_points  float [n][3] in the tree's unit-cube coordinates.
  *   d_dirs    float [n][3] or NULL: on a cell plane a point belongs to the

@@ -91,6 +91,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "plo_tree_get_info": (I32, [P, P]),
         "plo_render_rays": (I32, [P, P, I64, P, P, P, P, P]),
         "plo_render_rays_host": (I32, [P, P, I64, P, P, P, P]),
+        "plo_render_rays_host_noalloc": (I32, [P, P, I64, P, P, P, P]),
         "plo_lookup_points": (I32, [P, P, P, I64, P, P, P]),
         "plo_trace_rays": (I32, [P, P, I64, P, I32, P, P, P, P]),
         "plo_tree_check": (I32, [P, P]),
@@ -211,6 +212,25 @@ def render_host(tree: Tree, rays: np.ndarray, params: RenderParams | None = None
     p = params._c()
     _check(load().plo_render_rays_host(tree.handle, ctypes.c_void_p(rp), n, ctypes.byref(p), ctypes.c_void_p(op),
                                        ctypes.c_void_p(tp), _stream(stream)))
+    return rgb, T
+
+
+NOALLOC_MAX_RAYS = 262144
+
+
+def render_host_noalloc(tree: Tree, rays: np.ndarray, params: RenderParams | None = None, stream=None):
+    """plo_render_rays_host_noalloc: host rays (numpy, at most NOALLOC_MAX_RAYS)
+    staged through the library's fixed device array; allocates no device
+    memory.  Returns (rgb [n,3], T [n]) as numpy arrays."""
+    params = params or RenderParams()
+    rays = np.ascontiguousarray(rays, np.float32)
+    n = rays.shape[0]
+    rgb = np.empty((n, 3), np.float32)
+    T = np.empty(n, np.float32)
+    p = params._c()
+    _check(load().plo_render_rays_host_noalloc(tree.handle, ctypes.c_void_p(rays.ctypes.data), n, ctypes.byref(p),
+                                               ctypes.c_void_p(rgb.ctypes.data), ctypes.c_void_p(T.ctypes.data),
+                                               _stream(stream)))
     return rgb, T
 
 

@@ -26,6 +26,8 @@
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
+#include <string>
 
 #include "plo_internal.h"
 
@@ -689,5 +691,74 @@ extern "C" plo_status plo_lookup_points(const plo_tree* t, const float* d_points
                                                                t->depth, d_points, d_dirs, n, d_leaf, d_level);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "lookup kernel launch");
+    return PLO_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free host path
+// plo_render_rays_host_noalloc: the host-buffer render for callers that must
+// not allocate device memory (see include/plo.h).  Its device staging for
+// rays and results is the file-scope array below, so the call itself makes
+// no cudaMalloc/cudaFree and no allocating library call.
+namespace {
+
+constexpr int64_t kNoAllocMaxRays = 262144;  // 10 floats per ray: 10 MiB in all
+// rays [max][6], then rgb [max][3], then T [max].  Every GPU that loads the
+// library holds this array until the process exits.  All calls share it.
+__device__ __align__(256) float g_noalloc_stage[kNoAllocMaxRays * 10];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the staging array on the current device (`dev`),
+// looked up once per device.  In host code g_noalloc_stage names a host-side
+// stand-in, never the device memory, so only this address may be used.
+plo_status noalloc_stage(int dev, float** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_stage);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress of the no-allocation staging array");
+        g_noalloc_ptr[dev] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return PLO_OK;
+}
+
+}  // namespace
+
+extern "C" plo_status plo_render_rays_host_noalloc(const plo_tree* tree, const float* h_rays, int64_t n,
+                                                   const plo_render_params* params, float* h_rgb, float* h_T,
+                                                   void* stream) {
+    if (!tree) return set_error(PLO_ERR_INVALID_ARG, "tree is NULL");
+    if (n < 0) return set_error(PLO_ERR_INVALID_ARG, "n must be >= 0");
+    if (n > kNoAllocMaxRays)
+        return set_error(PLO_ERR_INVALID_ARG, "n = " + std::to_string(n) +
+                                                  " exceeds the allocation-free path's maximum of " +
+                                                  std::to_string(kNoAllocMaxRays) + " rays per call");
+    if (n == 0) return PLO_OK;
+    if (!h_rays || !h_rgb || !h_T) return set_error(PLO_ERR_INVALID_ARG, "rays, rgb or T is NULL");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return set_error(PLO_ERR_UNSUPPORTED, "device index beyond the allocation-free path's table");
+    if (dev != tree->device)
+        return set_error(PLO_ERR_INVALID_ARG, "the tree lives on another device than the current one");
+    float* base = nullptr;
+    plo_status st = noalloc_stage(dev, &base);
+    if (st != PLO_OK) return st;
+    float* d_rays = base;
+    float* d_rgb = base + 6 * kNoAllocMaxRays;
+    float* d_T = base + 9 * kNoAllocMaxRays;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(d_rays, h_rays, (size_t)n * 6 * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "host-to-device ray copy");
+    st = plo_render_rays(tree, d_rays, n, params, d_rgb, d_T, nullptr, stream);
+    if (st != PLO_OK) return st;
+    e = cudaMemcpyAsync(h_rgb, d_rgb, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_T, d_T, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "plo_render_rays_host_noalloc");
     return PLO_OK;
 }
