@@ -196,6 +196,88 @@ plo_status plo_trace_rays(const plo_tree* tree, const float* d_rays, int64_t n, 
  * Clears the flag. */
 plo_status plo_tree_check(const plo_tree* tree, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned part (Sec. 4.2-4.4): the NeRF-SH network and its training.
+ *
+ * Network: positional encoding of the sample position x in the unit cube,
+ * gamma(x) = [x, sin(2^j pi x), cos(2^j pi x)]_{j<10} (63 features), eight
+ * fully connected layers of 256 with ReLU, and a linear head to sigma_raw
+ * and 3 (l_max+1)^2 SH coefficients (channel-major).  sigma = ReLU(raw);
+ * emission = l_max * sigmoid(sum_k c_k Y_k(d)) (Eq. 6).  BF16 weights and
+ * activations, FP32 accumulation on the tensor cores, FP32 master weights.
+ * Parameters are exchanged in the canonical FP32 order: for each layer
+ * W [out][in] then b [out], layers 1..9 (in: 63, 256 x 7, 256; out: 256 x 8,
+ * 1 + 3K).  Rays for training are given in the unit cube (the proxy box). */
+typedef struct plo_mlp plo_mlp;
+
+/* Loss of Sec. 4.3 on values divided by l_max: PAPER = sum over channels of
+ * ((C^ - C) / (C^ + eps))^2 (denominator held constant) + (alpha^ - alpha)^2
+ * (Eq. 7-9); REG = the colour term only; MSE = plain squared error. */
+enum { PLO_LOSS_PAPER = 0, PLO_LOSS_REG = 1, PLO_LOSS_MSE = 2 };
+
+typedef struct {
+    int32_t sh_degree;      /* must be 3 (48 SH coefficients)                      */
+    int32_t transmittance;  /* PLO_TRANS_EXP or PLO_TRANS_LINEAR                   */
+    int32_t loss;           /* PLO_LOSS_*                                          */
+    int32_t total_steps;    /* learning-rate decay horizon                         */
+    float l_max;            /* maximum radiance: sigmoid scale and loss unit       */
+    float eps;              /* loss regulariser, 0.01 in the paper                 */
+    float lr0, lr1;         /* exponential decay lr0 -> lr1 (5e-4 -> 5e-6)         */
+    uint64_t seed;          /* stream of the stratified-sampling jitter            */
+} plo_mlp_desc;
+
+/* Number of parameters of the network for SH degree `sh_degree`. */
+int64_t plo_mlp_param_count(int32_t sh_degree);
+
+/* Creates the network on the current device with He-uniform weights drawn
+ * from `seed` and zero biases. */
+plo_status plo_mlp_create(const plo_mlp_desc* desc, uint64_t seed, plo_mlp** out);
+void plo_mlp_free(plo_mlp* mlp);
+
+/* Host <-> device parameter exchange in the canonical order (n must equal
+ * plo_mlp_param_count).  Synchronous.  get_grads returns the gradient of the
+ * last training step (the one its Adam update used). */
+plo_status plo_mlp_set_params(plo_mlp* mlp, const float* h_params, int64_t n);
+plo_status plo_mlp_get_params(const plo_mlp* mlp, float* h_params, int64_t n);
+plo_status plo_mlp_get_grads(const plo_mlp* mlp, float* h_grads, int64_t n);
+
+/* Raw network outputs at n points (async).  d_points float [n][3] in the
+ * unit cube; d_raw float [n][1 + 3K] (sigma_raw, then SH coefficients). */
+plo_status plo_mlp_forward(plo_mlp* mlp, const float* d_points, int64_t n, float* d_raw, void* stream);
+
+/* One training step (async): stratified samples along each ray (Sec. 4.1),
+ * network forward, quadrature render (Eq. 3-5), the loss, backward, Adam
+ * with the decayed learning rate (Sec. 4.4).
+ *   d_rays      float [n_rays][6] origin, direction (unit-cube coordinates)
+ *   d_rgb_gt    float [n_rays][3] target L_e;  d_alpha_gt float [n_rays]
+ *   n_samples   32, 64, 128 or 256; n_rays * n_samples a multiple of 128
+ *   d_jitter    float [n_rays][n_samples] in [0,1), or NULL to draw it from
+ *               the desc's seed and the step number (SplitMix64)
+ *   d_loss_out  float [1]: the batch's mean loss before the update. */
+plo_status plo_mlp_train_step(plo_mlp* mlp, const float* d_rays, const float* d_rgb_gt, const float* d_alpha_gt,
+                              int32_t n_rays, int32_t n_samples, const float* d_jitter, float* d_loss_out,
+                              void* stream);
+
+/* Synchronises `stream`; PLO_ERR_TIMEOUT if a tensor-core kernel gave up on
+ * a bounded pipeline wait since the last check (the flag is cleared). */
+plo_status plo_mlp_check(const plo_mlp* mlp, void* stream);
+
+/* Number of training steps taken. */
+int64_t plo_mlp_step(const plo_mlp* mlp);
+
+/* The tensor-core building blocks (async), exposed for testing.
+ * plo_gemm_bf16: C[M][N] = A[M][K] B[N][K]^T, A and B bf16 row-major,
+ *   (N, K) in {(256, 64), (256, 256), (64, 256)}; epilogue 0: bf16
+ *   ReLU(C + bias), 1: fp32 C + bias, 2: bf16 C * (mask > 0) with mask bf16
+ *   [M][N]; d_out row-major [M][N].
+ * plo_wgrad_bf16: dW[n_out][n_in] += dZ^T H over M rows (dZ bf16 [M][n_out],
+ *   H bf16 [M][n_in], n_out, n_in in {64, 256}, M a multiple of 64).
+ * d_err: device word, bit 1 set if a pipeline wait gave up. */
+plo_status plo_gemm_bf16(const void* d_A, const void* d_B, int32_t M, int32_t N, int32_t K, int32_t epilogue,
+                         const float* d_bias, const void* d_mask, void* d_out, unsigned int* d_err, void* stream);
+plo_status plo_wgrad_bf16(const void* d_dZ, int32_t n_out, const void* d_H, int32_t n_in, int32_t M, float* d_dW,
+                          unsigned int* d_err, void* stream);
+
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* plo_last_error(void);
 

@@ -257,3 +257,129 @@ def trace(tree: Tree, rays, max_cells: int, params: RenderParams | None = None, 
     _check(load().plo_trace_rays(tree.handle, _ptr(rays), n, ctypes.byref(p), max_cells, _ptr(leaf), _ptr(t),
                                  _ptr(cnt), _stream(stream)))
     return leaf, t, cnt
+
+
+# ---------------------------------------------------------------- learned part
+LOSS_PAPER, LOSS_REG, LOSS_MSE = 0, 1, 2
+
+
+class MlpDesc(ctypes.Structure):
+    _fields_ = [("sh_degree", ctypes.c_int32), ("transmittance", ctypes.c_int32), ("loss", ctypes.c_int32),
+                ("total_steps", ctypes.c_int32), ("l_max", ctypes.c_float), ("eps", ctypes.c_float),
+                ("lr0", ctypes.c_float), ("lr1", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+def _load_mlp_sigs(lib):
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sigs = {
+        "plo_mlp_param_count": (I64, [I32]),
+        "plo_mlp_create": (I32, [P, ctypes.c_uint64, P]),
+        "plo_mlp_free": (None, [P]),
+        "plo_mlp_set_params": (I32, [P, P, I64]),
+        "plo_mlp_get_params": (I32, [P, P, I64]),
+        "plo_mlp_get_grads": (I32, [P, P, I64]),
+        "plo_mlp_forward": (I32, [P, P, I64, P, P]),
+        "plo_mlp_train_step": (I32, [P, P, P, P, I32, I32, P, P, P]),
+        "plo_mlp_check": (I32, [P, P]),
+        "plo_mlp_step": (I64, [P]),
+        "plo_gemm_bf16": (I32, [P, P, I32, I32, I32, I32, P, P, P, P, P]),
+        "plo_wgrad_bf16": (I32, [P, I32, P, I32, I32, P, P, P]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+
+
+def mlp_lib():
+    lib = load()
+    if not getattr(lib, "_mlp_sigs", False):
+        _load_mlp_sigs(lib)
+        lib._mlp_sigs = True
+    return lib
+
+
+class Mlp:
+    """The NeRF-SH network on the current device (plo_mlp_*)."""
+
+    def __init__(self, l_max: float, loss: int = LOSS_PAPER, transmittance: int = TRANS_EXP, total_steps: int = 1000,
+                 lr0: float = 5e-4, lr1: float = 5e-6, eps: float = 0.01, seed: int = 1, jitter_seed: int = 2):
+        lib = mlp_lib()
+        d = MlpDesc()
+        d.sh_degree, d.transmittance, d.loss, d.total_steps = 3, transmittance, loss, total_steps
+        d.l_max, d.eps, d.lr0, d.lr1, d.seed = l_max, eps, lr0, lr1, jitter_seed
+        h = ctypes.c_void_p()
+        _check(lib.plo_mlp_create(ctypes.byref(d), seed, ctypes.byref(h)))
+        self._h = h
+        self.n_params = int(lib.plo_mlp_param_count(3))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_params(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, np.float32)
+        _check(mlp_lib().plo_mlp_set_params(self._h, ctypes.c_void_p(flat.ctypes.data), flat.size))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _check(mlp_lib().plo_mlp_get_params(self._h, ctypes.c_void_p(out.ctypes.data), out.size))
+        return out
+
+    def get_grads(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _check(mlp_lib().plo_mlp_get_grads(self._h, ctypes.c_void_p(out.ctypes.data), out.size))
+        return out
+
+    def forward(self, points, stream=None):
+        import torch
+        n = points.shape[0]
+        raw = torch.empty((n, 49), device=points.device, dtype=torch.float32)
+        _check(mlp_lib().plo_mlp_forward(self._h, _ptr(points), n, _ptr(raw), _stream(stream)))
+        return raw
+
+    def train_step(self, rays, rgb_gt, alpha_gt, n_samples: int = 128, jitter=None, loss_out=None, stream=None):
+        import torch
+        loss_out = loss_out if loss_out is not None else torch.empty(1, device=rays.device, dtype=torch.float32)
+        _check(mlp_lib().plo_mlp_train_step(self._h, _ptr(rays), _ptr(rgb_gt), _ptr(alpha_gt), rays.shape[0],
+                                            n_samples, _ptr(jitter), _ptr(loss_out), _stream(stream)))
+        return loss_out
+
+    def check(self, stream=None):
+        _check(mlp_lib().plo_mlp_check(self._h, _stream(stream)))
+
+    @property
+    def step(self) -> int:
+        return int(mlp_lib().plo_mlp_step(self._h))
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            mlp_lib().plo_mlp_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def gemm_bf16(A, B, epilogue: int, bias=None, mask=None, out=None, err=None, stream=None):
+    """plo_gemm_bf16 on CUDA tensors (A [M][K], B [N][K] bf16)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if out is None:
+        out = torch.empty((M, N), device=A.device, dtype=torch.float32 if epilogue == 1 else torch.bfloat16)
+    err = err if err is not None else torch.zeros(1, device=A.device, dtype=torch.int32)
+    _check(mlp_lib().plo_gemm_bf16(_ptr(A), _ptr(B), M, N, K, epilogue, _ptr(bias), _ptr(mask), _ptr(out), _ptr(err),
+                                   _stream(stream)))
+    return out, err
+
+
+def wgrad_bf16(dZ, H, dW, err=None, stream=None):
+    """plo_wgrad_bf16: dW [n_out][n_in] (fp32) += dZ^T H."""
+    import torch
+    err = err if err is not None else torch.zeros(1, device=dZ.device, dtype=torch.int32)
+    _check(mlp_lib().plo_wgrad_bf16(_ptr(dZ), dZ.shape[1], _ptr(H), H.shape[1], dZ.shape[0], _ptr(dW), _ptr(err),
+                                    _stream(stream)))
+    return dW, err

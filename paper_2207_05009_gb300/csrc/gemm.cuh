@@ -1,0 +1,398 @@
+// BF16 tensor-core GEMMs for the NeRF-SH network (Sec. 4.2) on sm_103a:
+// tcgen05.mma with FP32 accumulators in TMEM, operands staged by TMA into
+// 128-byte-swizzled shared memory.
+//
+// k_gemm:  C[M][N] = A[M][K] * B[N][K]^T  (both K-major), fused epilogue:
+//          bias + ReLU -> bf16, bias -> fp32, or (x mask>0) -> bf16.
+//          Persistent CTAs; B (the weights, N*K*2 <= 128 KB) stays resident
+//          in shared memory; A streams through a 4-stage ring of 128x64
+//          tiles; two TMEM accumulators let the epilogue of one 128-row tile
+//          overlap the MMAs of the next.
+// k_wgrad: dW[o][i] += sum_m dZ[m][o] * H[m][i] over a chunk of rows m
+//          (both operands MN-major, read straight from the row-major
+//          activations), split over CTAs and reduced with vector atomics.
+//
+// Warp roles (192 threads): warp 0 lane 0 issues TMA, warp 1 owns TMEM and
+// lane 0 issues MMAs, warps 2-5 run the epilogue (warp w reads TMEM lanes
+// 32*(w%4) .. +31).  All mbarrier waits are bounded; a wait that gives up
+// raises an abort flag in shared memory and a bit in the caller's error word,
+// every role then drains what it has in flight and the CTA frees its TMEM.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sm100.cuh"
+
+namespace plo {
+namespace gemm {
+
+constexpr int THREADS = 192;
+constexpr int BM = 128;
+constexpr int BK = 64;  // one 128-byte swizzle row of bf16
+constexpr int STAGES = 4;
+constexpr int A_STAGE_BYTES = BM * BK * 2;  // 16 KB
+
+enum Epi : int { EPI_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK_BF16 = 2 };
+
+struct EpiArgs {
+    const float* bias;            // [N] (EPI_RELU_BF16, EPI_BIAS_F32)
+    __nv_bfloat16* out_bf16;      // [M][ldo]
+    float* out_f32;               // [M][ldo]
+    int ldo;
+    const __nv_bfloat16* mask;    // [M][ldm] (EPI_MASK_BF16)
+    int ldm;
+    unsigned int* err;            // device error word (bit 1: GEMM wait timeout)
+};
+
+__host__ __device__ constexpr int tmem_cols_for(int n) {
+    return n * 2 <= 32 ? 32 : (n * 2 <= 64 ? 64 : (n * 2 <= 128 ? 128 : (n * 2 <= 256 ? 256 : 512)));
+}
+__host__ __device__ constexpr size_t gemm_smem_bytes(int N, int K) {
+    return 1024 /*align*/ + (size_t)N * K * 2 + (size_t)STAGES * A_STAGE_BYTES + 256 /*barriers*/;
+}
+
+struct Ctl {
+    uint64_t full[STAGES], empty[STAGES], bfull, tfull[2], tempty[2], drain;
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t ph, Ctl* ctl, unsigned int* err) {
+    const uint32_t a = sm100::smem_addr(bar);
+    for (uint32_t it = 0; it < sm100::WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(ph)
+            : "memory");
+        if (done) return true;
+        if ((it & 1023u) == 1023u && *(volatile int*)&ctl->abort) return false;
+    }
+    *(volatile int*)&ctl->abort = 1;
+    atomicOr(err, 2u);
+    return false;
+}
+
+template <int N>
+__device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int row, int M, int col, const float* v) {
+    if (row >= M) return;
+    if (epi == EPI_BIAS_F32) {
+        float4* dst = reinterpret_cast<float4*>(ep.out_f32 + (size_t)row * ep.ldo + col);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float4 b = *reinterpret_cast<const float4*>(ep.bias + col + 4 * j);
+            dst[j] = make_float4(v[4 * j] + b.x, v[4 * j + 1] + b.y, v[4 * j + 2] + b.z, v[4 * j + 3] + b.w);
+        }
+        return;
+    }
+    uint32_t packed[16];
+    if (epi == EPI_RELU_BF16) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float a = fmaxf(v[2 * j] + __ldg(ep.bias + col + 2 * j), 0.0f);
+            float b = fmaxf(v[2 * j + 1] + __ldg(ep.bias + col + 2 * j + 1), 0.0f);
+            __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            packed[j] = *reinterpret_cast<uint32_t*>(&h);
+        }
+    } else {  // EPI_MASK_BF16
+        const uint4* m4 = reinterpret_cast<const uint4*>(ep.mask + (size_t)row * ep.ldm + col);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint4 mw = __ldg(m4 + q);
+            uint32_t w[4] = {mw.x, mw.y, mw.z, mw.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                // bf16 pair (lo, hi): positive iff sign clear and not zero
+                uint32_t lo = w[u] & 0xFFFFu, hi = w[u] >> 16;
+                float a = (lo != 0u && !(lo & 0x8000u)) ? v[8 * q + 2 * u] : 0.0f;
+                float b = (hi != 0u && !(hi & 0x8000u)) ? v[8 * q + 2 * u + 1] : 0.0f;
+                __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                packed[4 * q + u] = *reinterpret_cast<uint32_t*>(&h);
+            }
+        }
+    }
+    uint4* dst = reinterpret_cast<uint4*>(ep.out_bf16 + (size_t)row * ep.ldo + col);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+}
+
+template <int N, int K>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiArgs ep, int epi, int M) {
+    static_assert(K % BK == 0 && N % 32 == 0 && N <= 256, "tile shape");
+    constexpr int KB = K / BK;
+    constexpr int TMEM_COLS = tmem_cols_for(N);
+    constexpr uint32_t IDESC = sm100::idesc_bf16(BM, N, 0, 0);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* sB = smem;                    // KB blocks of [N rows][128 B]
+    uint8_t* sA = sB + (size_t)N * K * 2;  // STAGES x [128 rows][128 B]
+    Ctl* ctl = reinterpret_cast<Ctl*>(sA + STAGES * A_STAGE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            sm100::mbar_init(&ctl->full[s], 1);
+            sm100::mbar_init(&ctl->empty[s], 1);
+        }
+        sm100::mbar_init(&ctl->bfull, 1);
+        for (int j = 0; j < 2; ++j) {
+            sm100::mbar_init(&ctl->tfull[j], 1);
+            sm100::mbar_init(&ctl->tempty[j], 128);
+        }
+        sm100::mbar_init(&ctl->drain, 1);
+        ctl->abort = 0;
+        sm100::fence_mbar_init();
+    }
+    if (warp == 1) sm100::tmem_alloc(&ctl->tmem, TMEM_COLS);
+    sm100::tc_fence_before();
+    __syncthreads();
+    sm100::tc_fence_after();
+    const uint32_t tmem = ctl->tmem;
+    const int n_tiles = (M + BM - 1) / BM;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        sm100::prefetch_tmap(&tmA);
+        sm100::prefetch_tmap(&tmB);
+        sm100::mbar_arrive_expect_tx(&ctl->bfull, (uint32_t)(N * K * 2));
+        for (int kb = 0; kb < KB; ++kb) sm100::tma_load_2d(sB + (size_t)kb * N * 128, &tmB, kb * BK, 0, &ctl->bfull);
+        int stage = 0;
+        uint32_t ph = 0;
+        uint32_t armed = 0, armed_ph = 0;  // stages with a load issued, and its parity
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+            for (int kb = 0; kb < KB; ++kb) {
+                if (!wait_or_abort(&ctl->empty[stage], ph ^ 1u, ctl, ep.err)) {
+                    ok = false;
+                    break;
+                }
+                sm100::mbar_arrive_expect_tx(&ctl->full[stage], A_STAGE_BYTES);
+                sm100::tma_load_2d(sA + stage * A_STAGE_BYTES, &tmA, kb * BK, tile * BM, &ctl->full[stage]);
+                armed |= 1u << stage;
+                armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
+                if (++stage == STAGES) {
+                    stage = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+        if (!ok) {  // drain the loads still in flight before the CTA exits
+            for (int s = 0; s < STAGES; ++s)
+                if (armed & (1u << s)) sm100::mbar_wait(&ctl->full[s], (armed_ph >> s) & 1u);
+            sm100::mbar_wait(&ctl->bfull, 0);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        bool ok = wait_or_abort(&ctl->bfull, 0, ctl, ep.err);
+        int stage = 0, acc = 0;
+        uint32_t ph = 0, aph = 0;
+        bool issued = false;
+        for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+            if (!wait_or_abort(&ctl->tempty[acc], aph ^ 1u, ctl, ep.err)) {
+                ok = false;
+                break;
+            }
+            sm100::tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(acc * N);
+            for (int kb = 0; kb < KB; ++kb) {
+                if (!wait_or_abort(&ctl->full[stage], ph, ctl, ep.err)) {
+                    ok = false;
+                    break;
+                }
+                sm100::tc_fence_after();
+                const uint32_t a0 = sm100::smem_addr(sA + stage * A_STAGE_BYTES);
+                const uint32_t b0 = sm100::smem_addr(sB + (size_t)kb * N * 128);
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k) {
+                    uint64_t adesc = sm100::smem_desc_sw128(a0 + 32 * k, 16, 1024);
+                    uint64_t bdesc = sm100::smem_desc_sw128(b0 + 32 * k, 16, 1024);
+                    sm100::mma_bf16(d, adesc, bdesc, IDESC, (kb | k) != 0);
+                }
+                issued = true;
+                sm100::mma_commit(&ctl->empty[stage]);
+                if (++stage == STAGES) {
+                    stage = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (!ok) break;
+            sm100::mma_commit(&ctl->tfull[acc]);
+            if (++acc == 2) {
+                acc = 0;
+                aph ^= 1u;
+            }
+        }
+        if (!ok && issued) {  // let issued MMAs finish before TMEM is freed
+            sm100::mma_commit(&ctl->drain);
+            sm100::mbar_wait(&ctl->drain, 0);
+        }
+    } else if (warp >= 2) {
+        // ---------------- epilogue
+        const int q = warp & 3;
+        int acc = 0;
+        uint32_t aph = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            if (!wait_or_abort(&ctl->tfull[acc], aph, ctl, ep.err)) break;
+            sm100::tc_fence_after();
+            const int row = tile * BM + q * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < N / 32; ++c) {
+                float v[32];
+                sm100::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * N + c * 32), v);
+                epilogue_chunk<N>(ep, epi, row, M, c * 32, v);
+            }
+            sm100::tc_fence_before();
+            sm100::mbar_arrive(&ctl->tempty[acc]);
+            if (++acc == 2) {
+                acc = 0;
+                aph ^= 1u;
+            }
+        }
+    }
+    sm100::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        sm100::tc_fence_after();
+        sm100::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- weight gradient
+// dW[o][i] += sum_{m in chunk} dZ[m][o] * H[m][i]; o in [out_base, out_base+128).
+// A' = dZ^T tile: two TMA boxes of 64 (o) x 64 (m) -> MN-major, LBO = 8 KB
+// between the 64-wide o blocks, SBO = 1 KB between 8-row m groups.  B' = H^T
+// tile: NIN/64 boxes of 64 (i) x 64 (m), same strides.
+template <int NIN>
+__host__ __device__ constexpr size_t wgrad_stage_bytes() {
+    return (size_t)(2 + NIN / 64) * 64 * 128;
+}
+template <int NIN>
+__host__ __device__ constexpr size_t wgrad_smem_bytes() {
+    return 1024 + STAGES * wgrad_stage_bytes<NIN>() + 256;
+}
+
+template <int NIN>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_wgrad(const __grid_constant__ CUtensorMap tmDZ, const __grid_constant__ CUtensorMap tmH, float* dW, int n_out,
+            int M, int chunk, unsigned int* err) {
+    constexpr int TMEM_COLS = NIN < 32 ? 32 : NIN;
+    constexpr uint32_t IDESC = sm100::idesc_bf16(BM, NIN, 1, 1);
+    constexpr uint32_t STAGE = (uint32_t)wgrad_stage_bytes<NIN>();
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    Ctl* ctl = reinterpret_cast<Ctl*>(smem + STAGES * STAGE);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int out_base = blockIdx.y * BM;
+    const int m_beg = blockIdx.x * chunk;
+    const int m_end = min(m_beg + chunk, M);
+    const int n_kb = m_end > m_beg ? (m_end - m_beg + 63) / 64 : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            sm100::mbar_init(&ctl->full[s], 1);
+            sm100::mbar_init(&ctl->empty[s], 1);
+        }
+        sm100::mbar_init(&ctl->tfull[0], 1);
+        sm100::mbar_init(&ctl->drain, 1);
+        ctl->abort = 0;
+        sm100::fence_mbar_init();
+    }
+    if (warp == 1) sm100::tmem_alloc(&ctl->tmem, TMEM_COLS);
+    sm100::tc_fence_before();
+    __syncthreads();
+    sm100::tc_fence_after();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp == 0 && lane == 0) {
+        sm100::prefetch_tmap(&tmDZ);
+        sm100::prefetch_tmap(&tmH);
+        int stage = 0;
+        uint32_t ph = 0, armed = 0, armed_ph = 0;
+        bool ok = true;
+        for (int kb = 0; kb < n_kb; ++kb) {
+            if (!wait_or_abort(&ctl->empty[stage], ph ^ 1u, ctl, err)) {
+                ok = false;
+                break;
+            }
+            uint8_t* st = smem + stage * STAGE;
+            const int m0 = m_beg + kb * 64;
+            sm100::mbar_arrive_expect_tx(&ctl->full[stage], STAGE);
+            sm100::tma_load_2d(st, &tmDZ, out_base, m0, &ctl->full[stage]);
+            sm100::tma_load_2d(st + 8192, &tmDZ, out_base + 64, m0, &ctl->full[stage]);
+#pragma unroll
+            for (int j = 0; j < NIN / 64; ++j)
+                sm100::tma_load_2d(st + 16384 + j * 8192, &tmH, j * 64, m0, &ctl->full[stage]);
+            armed |= 1u << stage;
+            armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
+            if (++stage == STAGES) {
+                stage = 0;
+                ph ^= 1u;
+            }
+        }
+        if (!ok)
+            for (int s = 0; s < STAGES; ++s)
+                if (armed & (1u << s)) sm100::mbar_wait(&ctl->full[s], (armed_ph >> s) & 1u);
+    } else if (warp == 1 && lane == 0) {
+        int stage = 0;
+        uint32_t ph = 0;
+        bool ok = true, issued = false;
+        for (int kb = 0; kb < n_kb; ++kb) {
+            if (!wait_or_abort(&ctl->full[stage], ph, ctl, err)) {
+                ok = false;
+                break;
+            }
+            sm100::tc_fence_after();
+            const uint32_t a0 = sm100::smem_addr(smem + stage * STAGE);
+            const uint32_t b0 = a0 + 16384;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint64_t adesc = sm100::smem_desc_sw128(a0 + 2048 * k, 8192, 1024);
+                uint64_t bdesc = sm100::smem_desc_sw128(b0 + 2048 * k, 8192, 1024);
+                sm100::mma_bf16(tmem, adesc, bdesc, IDESC, (kb | k) != 0);
+            }
+            issued = true;
+            sm100::mma_commit(&ctl->empty[stage]);
+            if (++stage == STAGES) {
+                stage = 0;
+                ph ^= 1u;
+            }
+        }
+        if (ok && issued) sm100::mma_commit(&ctl->tfull[0]);
+        if (!ok && issued) {
+            sm100::mma_commit(&ctl->drain);
+            sm100::mbar_wait(&ctl->drain, 0);
+        }
+    } else if (warp >= 2 && n_kb > 0) {
+        const int q = warp & 3;
+        if (wait_or_abort(&ctl->tfull[0], 0, ctl, err)) {
+            sm100::tc_fence_after();
+            const int o = out_base + q * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < NIN / 32; ++c) {
+                float v[32];
+                sm100::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
+                if (o < n_out) {
+                    float4* dst = reinterpret_cast<float4*>(dW + (size_t)o * NIN + c * 32);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        atomicAdd(dst + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+                }
+            }
+        }
+    }
+    sm100::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        sm100::tc_fence_after();
+        sm100::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+}  // namespace gemm
+}  // namespace plo

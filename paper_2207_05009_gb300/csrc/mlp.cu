@@ -1,0 +1,952 @@
+// Learned part (paper Sec. 4.2-4.4): the NeRF-SH network trained by the
+// library's own kernels on rays rendered from a ground-truth octree.
+//
+//   sampling + positional encoding  k_pe        (Sec. 4.1 ray marching, Sec. 4.2 PE)
+//   8 x 256 ReLU layers + SH head   k_gemm      (tcgen05, gemm.cuh)
+//   quadrature, loss, d loss/d raw  k_quad      (Eq. 3-6, Eq. 7-9)
+//   weight / bias gradients         k_wgrad, k_colsum
+//   data gradients through ReLU     k_gemm (mask epilogue)
+//   Adam + exponential lr decay     k_adam      (Sec. 4.4)
+//
+// Activations are bf16 [samples][features] row-major; weights are kept as
+// FP32 masters plus bf16 copies W [out][in] (forward B operand) and W^T
+// [in][out] (data-gradient B operand), zero-padded to the GEMM tile shapes:
+// layer 1 input 63 -> 64 columns, head output 1 + 3K -> 64 rows.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gemm.cuh"
+#include "plo_internal.h"
+#include "sh.cuh"
+
+using namespace plo;
+
+namespace plo {
+namespace {
+
+constexpr int WIDTH = 256;
+constexpr int DEPTH = 8;
+constexpr int N_FREQ = 10;
+constexpr int PE_DIM = 3 + 6 * N_FREQ;  // 63
+constexpr int PE_PAD = 64;
+constexpr int OUT_PAD = 64;
+constexpr int N_LAYERS = DEPTH + 1;
+
+// ---------------------------------------------------------------- TMA maps
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder() {
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    });
+    return fn;
+}
+
+// bf16 matrix [rows][cols] (cols contiguous) read in boxes of 64 columns x
+// box_rows rows with the 128-byte swizzle.
+plo_status make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+    EncodeFn fn = encoder();
+    if (!fn) return set_error(PLO_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 2};
+    cuuint32_t box[2] = {64, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(PLO_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+    return PLO_OK;
+}
+
+int sm_count_of_current() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// ---------------------------------------------------------------- GEMM launchers
+template <int N, int K>
+cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, const gemm::EpiArgs& ep, int epi, int M,
+                        int sms, cudaStream_t s) {
+    const size_t smem = gemm::gemm_smem_bytes(N, K);
+    cudaError_t e = cudaFuncSetAttribute(gemm::k_gemm<N, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int tiles = (M + gemm::BM - 1) / gemm::BM;
+    int grid = tiles < sms ? tiles : sms;
+    if (grid < 1) return cudaSuccess;
+    gemm::k_gemm<N, K><<<grid, gemm::THREADS, smem, s>>>(A, B, ep, epi, M);
+    return cudaGetLastError();
+}
+
+template <int NIN>
+cudaError_t launch_wgrad(const CUtensorMap& dZ, const CUtensorMap& H, float* dW, int n_out, int M, int sms,
+                         unsigned int* err, cudaStream_t s) {
+    const size_t smem = gemm::wgrad_smem_bytes<NIN>();
+    cudaError_t e = cudaFuncSetAttribute(gemm::k_wgrad<NIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int out_tiles = (n_out + gemm::BM - 1) / gemm::BM;
+    int n_chunks = (2 * sms) / out_tiles;
+    const int blocks64 = M / 64;
+    if (n_chunks > blocks64) n_chunks = blocks64;
+    if (n_chunks < 1) n_chunks = 1;
+    const int chunk = ((blocks64 + n_chunks - 1) / n_chunks) * 64;
+    n_chunks = (M + chunk - 1) / chunk;
+    dim3 grid(n_chunks, out_tiles);
+    gemm::k_wgrad<NIN><<<grid, gemm::THREADS, smem, s>>>(dZ, H, dW, n_out, M, chunk, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- small kernels
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+// Stratification jitter in [0,1): SplitMix64 (Steele, Lea, Flood 2014)
+// finaliser applied to a key of (seed, step, ray, sample).
+__device__ __forceinline__ float jitter_u(uint64_t seed, uint64_t step, uint64_t ray, uint64_t j) {
+    uint64_t k = mix64(seed ^ mix64(step + 0x51ED2701ULL));
+    k = mix64(k ^ (ray * 0x9E3779B97F4A7C15ULL + j));
+    return (float)(k >> 40) * (1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ void unit_cube_clip(const float* o, const float* d, float& t0, float& t1, bool& hit) {
+    float tn = -INFINITY, tf = INFINITY;
+    bool miss = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0f) {
+            miss |= o[a] < 0.0f || o[a] > 1.0f;
+            continue;
+        }
+        float inv = 1.0f / d[a];
+        float ta = (0.0f - o[a]) * inv, tb = (1.0f - o[a]) * inv;
+        tn = fmaxf(tn, fminf(ta, tb));
+        tf = fminf(tf, fmaxf(ta, tb));
+    }
+    hit = !miss && tn < tf && tf > 0.0f;
+    t0 = hit ? fmaxf(tn, 0.0f) : 0.0f;
+    t1 = hit ? tf : 0.0f;
+}
+
+// Stratified samples t_j = t0 + (j + u_j)(t1 - t0)/N along each ray, segment
+// lengths delta_j = t_{j+1} - t_j (the last ends at t1), and the positional
+// encoding of x_j = o + t_j d -> X[ray*N + j][0..63] (column 63 is zero).
+__global__ void k_pe(const float* rays, int n_rays, int N, const float* jitter, uint64_t seed, uint64_t step,
+                     __nv_bfloat16* X, float* delta) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_rays * N) return;
+    const int r = (int)(idx / N), j = (int)(idx % N);
+    float o[3], d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = __ldg(rays + 6 * (int64_t)r + a);
+        d[a] = __ldg(rays + 6 * (int64_t)r + 3 + a);
+    }
+    float t0, t1;
+    bool hit;
+    unit_cube_clip(o, d, t0, t1, hit);
+    const float span = t1 - t0;
+    const float u = jitter ? __ldg(jitter + idx) : jitter_u(seed, step, r, j);
+    const float t = t0 + ((float)j + u) * span / (float)N;
+    float tn = t1;
+    if (j + 1 < N) {
+        const float un = jitter ? __ldg(jitter + idx + 1) : jitter_u(seed, step, r, j + 1);
+        tn = t0 + ((float)(j + 1) + un) * span / (float)N;
+    }
+    delta[idx] = hit ? tn - t : 0.0f;
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = fminf(fmaxf(o[a] + t * d[a], 0.0f), 1.0f);
+    __nv_bfloat16* row = X + idx * PE_PAD;
+    float f[PE_PAD];
+    f[0] = x[0];
+    f[1] = x[1];
+    f[2] = x[2];
+#pragma unroll
+    for (int k = 0; k < N_FREQ; ++k) {
+        const float sc = (float)(1 << k);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float sv, cv;
+            sincospif(sc * x[a], &sv, &cv);
+            f[3 + 6 * k + a] = sv;
+            f[6 + 6 * k + a] = cv;
+        }
+    }
+    f[63] = 0.0f;
+    uint4* dst = reinterpret_cast<uint4*>(row);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int u2 = 0; u2 < 4; ++u2) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(f[8 * q + 2 * u2], f[8 * q + 2 * u2 + 1]);
+            w[u2] = *reinterpret_cast<uint32_t*>(&h);
+        }
+        dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Positional encoding of given points (unit-cube coordinates) -> X.
+__global__ void k_pe_points(const float* pts, int64_t n, __nv_bfloat16* X) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = __ldg(pts + 3 * idx + a);
+    float f[PE_PAD];
+    f[0] = x[0];
+    f[1] = x[1];
+    f[2] = x[2];
+#pragma unroll
+    for (int k = 0; k < N_FREQ; ++k) {
+        const float sc = (float)(1 << k);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float sv, cv;
+            sincospif(sc * x[a], &sv, &cv);
+            f[3 + 6 * k + a] = sv;
+            f[6 + 6 * k + a] = cv;
+        }
+    }
+    f[63] = 0.0f;
+    uint4* dst = reinterpret_cast<uint4*>(X + idx * PE_PAD);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int u2 = 0; u2 < 4; ++u2) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(f[8 * q + 2 * u2], f[8 * q + 2 * u2 + 1]);
+            w[u2] = *reinterpret_cast<uint32_t*>(&h);
+        }
+        dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Quadrature render of Eq. 3 from the head outputs, the loss of Eq. 7-9 and
+// its gradient w.r.t. the head outputs.  One warp per ray; lane l owns the
+// samples [l*S, (l+1)*S).  raw: fp32 [ray*N + j][64] (0: sigma, 1 + ch*K + k:
+// SH); dO: bf16, same layout; ray_loss [n_rays].
+template <int K, int S>
+__global__ void k_quad(const float* raw, const float* delta, const float* rays, const float* rgb_gt,
+                       const float* alpha_gt, int n_rays, float l_max, float eps, int transmittance, int loss_kind,
+                       float inv_rays, __nv_bfloat16* dO, float* ray_loss) {
+    const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n_rays) return;
+    constexpr int N = 32 * S;
+    float dn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dn[a] = __ldg(rays + 6 * (int64_t)r + 3 + a);
+    const float inv_len = rsqrtf(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2]);
+    float Y[K];
+    sh_basis<K>(dn[0] * inv_len, dn[1] * inv_len, dn[2] * inv_len, Y);
+
+    float sig[S][3], c[S][3], a[S], dl[S];
+    bool pos[S];
+    float local = 0.0f;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t row = (int64_t)r * N + lane * S + s;
+        const float* q = raw + row * OUT_PAD;
+        const float sr = __ldg(q);
+        pos[s] = sr > 0.0f;
+        dl[s] = __ldg(delta + row);
+        a[s] = fmaxf(sr, 0.0f) * dl[s];
+        local += a[s];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = __fmaf_rn(__ldg(q + 1 + ch * K + k), Y[k], acc);
+            const float sg = 1.0f / (1.0f + expf(-acc));
+            sig[s][ch] = sg;
+            c[s][ch] = l_max * sg;
+        }
+    }
+    // exclusive prefix of optical depth across lanes
+    float incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        float v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    float cum = incl - local;
+    float T[S + 1], w[S];
+    const bool lin = transmittance != PLO_TRANS_EXP;
+    T[0] = lin ? fmaxf(0.0f, 1.0f - cum) : expf(-cum);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        cum += a[s];
+        T[s + 1] = lin ? fmaxf(0.0f, 1.0f - cum) : expf(-cum);
+        w[s] = T[s] - T[s + 1];
+    }
+    float C[3] = {0.0f, 0.0f, 0.0f}, alpha = 0.0f;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        alpha += w[s];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) C[ch] = __fmaf_rn(w[s], c[s][ch], C[ch]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        alpha += __shfl_xor_sync(0xffffffffu, alpha, off);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) C[ch] += __shfl_xor_sync(0xffffffffu, C[ch], off);
+    }
+    // loss (values divided by l_max; the denominator is held constant)
+    float dC[3], loss = 0.0f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float cn = C[ch] / l_max, gn = __ldg(rgb_gt + 3 * (int64_t)r + ch) / l_max;
+        const float den = loss_kind == 2 ? 1.0f : cn + eps;
+        const float res = (cn - gn) / den;
+        loss += res * res;
+        dC[ch] = 2.0f * res / den / l_max * inv_rays;
+    }
+    float dA = 0.0f;
+    if (loss_kind == 0) {
+        const float da = alpha - __ldg(alpha_gt + r);
+        loss += da * da;
+        dA = 2.0f * da * inv_rays;
+    }
+    if (lane == 0) ray_loss[r] = loss;
+    // d loss / d w_j, then d loss / d a_j
+    float g[S], wg_local = 0.0f, actg_local = 0.0f, actnext_local = 0.0f;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        g[s] = dA;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) g[s] = __fmaf_rn(c[s][ch], dC[ch], g[s]);
+        wg_local += w[s] * g[s];
+        actg_local += (T[s] > 0.0f ? g[s] : 0.0f);
+        actnext_local += (T[s + 1] > 0.0f ? g[s] : 0.0f);
+    }
+    // suffix sums over later lanes (exclusive of this lane)
+    float suf_wg = wg_local, suf_actg = actg_local, suf_actnext = actnext_local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        float v1 = __shfl_down_sync(0xffffffffu, suf_wg, off);
+        float v2 = __shfl_down_sync(0xffffffffu, suf_actg, off);
+        float v3 = __shfl_down_sync(0xffffffffu, suf_actnext, off);
+        if (lane + off < 32) {
+            suf_wg += v1;
+            suf_actg += v2;
+            suf_actnext += v3;
+        }
+    }
+    float after_wg = suf_wg - wg_local;          // sum over later lanes
+    float after_actg = suf_actg - actg_local;
+    float after_actnext = suf_actnext - actnext_local;
+    float da[S];
+#pragma unroll
+    for (int s = S - 1; s >= 0; --s) {
+        if (!lin) {
+            // da_j = T_{j+1} g_j - sum_{k>j} w_k g_k
+            da[s] = T[s + 1] * g[s] - after_wg;
+            after_wg += w[s] * g[s];
+        } else {
+            // da_j = sum_{k>=j} g_k [T_{k+1} > 0] - sum_{k>j} g_k [T_k > 0]
+            after_actnext += (T[s + 1] > 0.0f ? g[s] : 0.0f);
+            da[s] = after_actnext - after_actg;
+            after_actg += (T[s] > 0.0f ? g[s] : 0.0f);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t row = (int64_t)r * N + lane * S + s;
+        float out[OUT_PAD];
+#pragma unroll
+        for (int k = 0; k < OUT_PAD; ++k) out[k] = 0.0f;
+        out[0] = pos[s] ? da[s] * dl[s] : 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float ds = w[s] * dC[ch] * l_max * sig[s][ch] * (1.0f - sig[s][ch]);
+#pragma unroll
+            for (int k = 0; k < K; ++k) out[1 + ch * K + k] = ds * Y[k];
+        }
+        uint4* dst = reinterpret_cast<uint4*>(dO + row * OUT_PAD);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            uint32_t wv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                __nv_bfloat162 h = __floats2bfloat162_rn(out[8 * q + 2 * u], out[8 * q + 2 * u + 1]);
+                wv[u] = *reinterpret_cast<uint32_t*>(&h);
+            }
+            dst[q] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+    }
+}
+
+// db[n] += sum_m dZ[m][n], n < ncols (bf16 input, fp32 sums).
+__global__ void k_colsum(const __nv_bfloat16* dZ, int64_t M, int ncols, int rows_per_block, float* db) {
+    const int pairs = ncols / 2;
+    const int p = threadIdx.x % pairs;
+    const int rg = threadIdx.x / pairs;
+    const int groups = blockDim.x / pairs;
+    const int64_t m0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t m1 = min(m0 + rows_per_block, M);
+    float sx = 0.0f, sy = 0.0f;
+    for (int64_t m = m0 + rg; m < m1; m += groups) {
+        __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(dZ + m * ncols + 2 * p);
+        float2 f = __bfloat1622float2(v);
+        sx += f.x;
+        sy += f.y;
+    }
+    __shared__ float red[2][256];
+    red[0][threadIdx.x] = sx;
+    red[1][threadIdx.x] = sy;
+    __syncthreads();
+    if (rg == 0) {
+        for (int g = 1; g < groups; ++g) {
+            sx += red[0][g * pairs + p];
+            sy += red[1][g * pairs + p];
+        }
+        atomicAdd(db + 2 * p, sx);
+        atomicAdd(db + 2 * p + 1, sy);
+    }
+}
+
+struct LayerGeom {
+    int64_t off[N_LAYERS + 1];  // offset of layer l's W in the padded flat array; bias follows W
+    int out_real[N_LAYERS], in_real[N_LAYERS], out_pad[N_LAYERS], in_pad[N_LAYERS];
+};
+
+__device__ __forceinline__ int find_layer(const LayerGeom& g, int64_t i) {
+    int l = 0;
+#pragma unroll
+    for (int k = 1; k < N_LAYERS; ++k)
+        if (i >= g.off[k]) l = k;
+    return l;
+}
+
+// Adam (Kingma & Ba) with bias correction on the FP32 masters, then the bf16
+// copies W [out][in] and W^T [in][out].  Padding entries stay zero.
+__global__ void k_adam(LayerGeom g, float* master, float* m, float* v, const float* grad, int64_t n, float lr,
+                       float b1, float b2, float eps, float bc1, float bc2, int update, __nv_bfloat16* const* W,
+                       __nv_bfloat16* const* WT) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int l = find_layer(g, i);
+    const int64_t loc = i - g.off[l];
+    const int64_t wsz = (int64_t)g.out_pad[l] * g.in_pad[l];
+    const bool is_w = loc < wsz;
+    const int o = is_w ? (int)(loc / g.in_pad[l]) : (int)(loc - wsz);
+    const int in = is_w ? (int)(loc % g.in_pad[l]) : 0;
+    const bool real = o < g.out_real[l] && (!is_w || in < g.in_real[l]);
+    float p = master[i];
+    if (update && real) {
+        const float gi = grad[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        master[i] = p;
+    }
+    if (!real) p = 0.0f;
+    if (is_w) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(p);
+        W[l][(int64_t)o * g.in_pad[l] + in] = h;
+        if (WT[l]) WT[l][(int64_t)in * g.out_pad[l] + o] = h;
+    }
+}
+
+__global__ void k_mean(const float* x, int n, float* out) {
+    __shared__ float red[256];
+    float s = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] / (float)n;
+}
+
+}  // namespace
+}  // namespace plo
+
+// ---------------------------------------------------------------- the handle
+struct plo_mlp {
+    plo_mlp_desc desc;
+    int K, n_out;
+    int device, sms;
+    LayerGeom geom;
+    int64_t n_params_pad;
+    float *master = nullptr, *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
+    __nv_bfloat16* W[N_LAYERS] = {};
+    __nv_bfloat16* WT[N_LAYERS] = {};
+    __nv_bfloat16** d_W = nullptr;
+    __nv_bfloat16** d_WT = nullptr;
+    CUtensorMap mapW[N_LAYERS], mapWT[N_LAYERS];
+    int64_t step = 0;
+    unsigned int* d_err = nullptr;
+    // workspace (samples capacity)
+    int64_t cap = 0;
+    int cap_rays = 0;
+    __nv_bfloat16* H[N_LAYERS] = {};  // H[0] = X [cap][64], H[1..8] [cap][256]
+    float* raw = nullptr;             // [cap][64]
+    __nv_bfloat16* dO = nullptr;      // [cap][64]
+    __nv_bfloat16* dZ[2] = {};        // [cap][256]
+    float* delta = nullptr;
+    float* ray_loss = nullptr;
+    CUtensorMap mapA_H[N_LAYERS], mapA_dO, mapA_dZ[2];   // A operand boxes (128 rows)
+    CUtensorMap mapW_H[N_LAYERS], mapW_dO, mapW_dZ[2];   // wgrad boxes (64 rows)
+};
+
+namespace {
+
+void free_workspace(plo_mlp* m) {
+    for (int l = 0; l < N_LAYERS; ++l) cudaFree(m->H[l]), m->H[l] = nullptr;
+    cudaFree(m->raw);
+    cudaFree(m->dO);
+    cudaFree(m->dZ[0]);
+    cudaFree(m->dZ[1]);
+    cudaFree(m->delta);
+    cudaFree(m->ray_loss);
+    m->raw = m->delta = m->ray_loss = nullptr;
+    m->dO = m->dZ[0] = m->dZ[1] = nullptr;
+    m->cap = 0;
+    m->cap_rays = 0;
+}
+
+plo_status ensure_workspace(plo_mlp* m, int64_t samples, int rays) {
+    if (samples <= m->cap && rays <= m->cap_rays) return PLO_OK;
+    cudaDeviceSynchronize();
+    free_workspace(m);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc((void**)&m->H[0], (size_t)samples * PE_PAD * 2);
+    for (int l = 1; l < N_LAYERS; ++l) alloc((void**)&m->H[l], (size_t)samples * WIDTH * 2);
+    alloc((void**)&m->raw, (size_t)samples * OUT_PAD * 4);
+    alloc((void**)&m->dO, (size_t)samples * OUT_PAD * 2);
+    alloc((void**)&m->dZ[0], (size_t)samples * WIDTH * 2);
+    alloc((void**)&m->dZ[1], (size_t)samples * WIDTH * 2);
+    alloc((void**)&m->delta, (size_t)samples * 4);
+    alloc((void**)&m->ray_loss, (size_t)(rays > 0 ? rays : 1) * 4);
+    if (e != cudaSuccess) {
+        free_workspace(m);
+        cudaGetLastError();
+        return set_error(PLO_ERR_OOM, "device allocation of the training workspace failed");
+    }
+    m->cap = samples;
+    m->cap_rays = rays;
+    plo_status st = PLO_OK;
+    for (int l = 0; l < N_LAYERS && st == PLO_OK; ++l) {
+        const int cols = l == 0 ? PE_PAD : WIDTH;
+        st = make_map(&m->mapA_H[l], m->H[l], samples, cols, 128);
+        if (st == PLO_OK) st = make_map(&m->mapW_H[l], m->H[l], samples, cols, 64);
+    }
+    if (st == PLO_OK) st = make_map(&m->mapA_dO, m->dO, samples, OUT_PAD, 128);
+    if (st == PLO_OK) st = make_map(&m->mapW_dO, m->dO, samples, OUT_PAD, 64);
+    for (int k = 0; k < 2 && st == PLO_OK; ++k) {
+        st = make_map(&m->mapA_dZ[k], m->dZ[k], samples, WIDTH, 128);
+        if (st == PLO_OK) st = make_map(&m->mapW_dZ[k], m->dZ[k], samples, WIDTH, 64);
+    }
+    return st;
+}
+
+void init_geom(plo_mlp* m) {
+    int64_t off = 0;
+    for (int l = 0; l < N_LAYERS; ++l) {
+        m->geom.in_real[l] = l == 0 ? PE_DIM : WIDTH;
+        m->geom.in_pad[l] = l == 0 ? PE_PAD : WIDTH;
+        m->geom.out_real[l] = l == DEPTH ? m->n_out : WIDTH;
+        m->geom.out_pad[l] = l == DEPTH ? OUT_PAD : WIDTH;
+        m->geom.off[l] = off;
+        off += (int64_t)m->geom.out_pad[l] * m->geom.in_pad[l] + m->geom.out_pad[l];
+    }
+    m->geom.off[N_LAYERS] = off;
+    m->n_params_pad = off;
+}
+
+float* bias_ptr(plo_mlp* m, float* base, int l) {
+    return base + m->geom.off[l] + (int64_t)m->geom.out_pad[l] * m->geom.in_pad[l];
+}
+
+plo_status refresh_bf16(plo_mlp* m, cudaStream_t s) {
+    const int64_t n = m->n_params_pad;
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->geom, m->master, m->adam_m, m->adam_v, m->grad, n, 0.0f,
+                                                       0.9f, 0.999f, 1e-8f, 1.0f, 1.0f, 0, m->d_W, m->d_WT);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "weight cast kernel");
+}
+
+// canonical flat order of the oracle: W_l [out][in] then b_l, l = 1..9
+int64_t canonical_count(int n_out) {
+    return (int64_t)WIDTH * PE_DIM + WIDTH + (int64_t)(DEPTH - 1) * (WIDTH * WIDTH + WIDTH) + (int64_t)n_out * WIDTH +
+           n_out;
+}
+
+void canonical_to_padded(const plo_mlp* m, const float* c, std::vector<float>& p) {
+    p.assign(m->n_params_pad, 0.0f);
+    int64_t ci = 0;
+    for (int l = 0; l < N_LAYERS; ++l) {
+        const LayerGeom& g = m->geom;
+        for (int o = 0; o < g.out_real[l]; ++o)
+            for (int i = 0; i < g.in_real[l]; ++i) p[g.off[l] + (int64_t)o * g.in_pad[l] + i] = c[ci++];
+        for (int o = 0; o < g.out_real[l]; ++o) p[g.off[l] + (int64_t)g.out_pad[l] * g.in_pad[l] + o] = c[ci++];
+    }
+}
+void padded_to_canonical(const plo_mlp* m, const std::vector<float>& p, float* c) {
+    int64_t ci = 0;
+    for (int l = 0; l < N_LAYERS; ++l) {
+        const LayerGeom& g = m->geom;
+        for (int o = 0; o < g.out_real[l]; ++o)
+            for (int i = 0; i < g.in_real[l]; ++i) c[ci++] = p[g.off[l] + (int64_t)o * g.in_pad[l] + i];
+        for (int o = 0; o < g.out_real[l]; ++o) c[ci++] = p[g.off[l] + (int64_t)g.out_pad[l] * g.in_pad[l] + o];
+    }
+}
+
+// Forward of the MLP over H[0] (already encoded) for `samples` rows; the head
+// writes fp32 raw outputs.
+plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s) {
+    gemm::EpiArgs ep{};
+    ep.err = m->d_err;
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < DEPTH && e == cudaSuccess; ++l) {
+        ep.bias = bias_ptr(m, m->master, l);
+        ep.out_bf16 = m->H[l + 1];
+        ep.ldo = WIDTH;
+        if (l == 0)
+            e = launch_gemm<WIDTH, PE_PAD>(m->mapA_H[0], m->mapW[0], ep, gemm::EPI_RELU_BF16, (int)samples, m->sms, s);
+        else
+            e = launch_gemm<WIDTH, WIDTH>(m->mapA_H[l], m->mapW[l], ep, gemm::EPI_RELU_BF16, (int)samples, m->sms, s);
+    }
+    if (e == cudaSuccess) {
+        ep.bias = bias_ptr(m, m->master, DEPTH);
+        ep.out_f32 = m->raw;
+        ep.ldo = OUT_PAD;
+        e = launch_gemm<OUT_PAD, WIDTH>(m->mapA_H[DEPTH], m->mapW[DEPTH], ep, gemm::EPI_BIAS_F32, (int)samples, m->sms,
+                                        s);
+    }
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "MLP forward GEMM launch");
+}
+
+plo_status check_mlp_desc(const plo_mlp_desc* d) {
+    if (!d) return set_error(PLO_ERR_INVALID_ARG, "desc is NULL");
+    if (d->sh_degree != 3) return set_error(PLO_ERR_UNSUPPORTED, "the network is built for SH degree 3 (48 coefficients)");
+    if (d->transmittance < PLO_TRANS_EXP || d->transmittance > PLO_TRANS_LINEAR)
+        return set_error(PLO_ERR_INVALID_ARG, "transmittance must be PLO_TRANS_EXP or PLO_TRANS_LINEAR");
+    if (d->loss < PLO_LOSS_PAPER || d->loss > PLO_LOSS_MSE) return set_error(PLO_ERR_INVALID_ARG, "unknown loss");
+    if (!(d->l_max > 0.0f) || !(d->lr0 > 0.0f) || !(d->lr1 > 0.0f) || d->total_steps < 1 || !(d->eps > 0.0f))
+        return set_error(PLO_ERR_INVALID_ARG, "l_max, lr0, lr1, eps must be > 0 and total_steps >= 1");
+    return PLO_OK;
+}
+
+}  // namespace
+
+extern "C" int64_t plo_mlp_param_count(int32_t sh_degree) {
+    return canonical_count(1 + 3 * (sh_degree + 1) * (sh_degree + 1));
+}
+
+extern "C" plo_status plo_mlp_create(const plo_mlp_desc* desc, uint64_t seed, plo_mlp** out) {
+    if (!out) return set_error(PLO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    plo_status st = check_mlp_desc(desc);
+    if (st != PLO_OK) return st;
+    plo_mlp* m = new (std::nothrow) plo_mlp();
+    if (!m) return set_error(PLO_ERR_OOM, "host allocation failed");
+    m->desc = *desc;
+    m->K = (desc->sh_degree + 1) * (desc->sh_degree + 1);
+    m->n_out = 1 + 3 * m->K;
+    cudaGetDevice(&m->device);
+    m->sms = sm_count_of_current();
+    init_geom(m);
+    const size_t pbytes = (size_t)m->n_params_pad * 4;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc((void**)&m->master, pbytes);
+    alloc((void**)&m->adam_m, pbytes);
+    alloc((void**)&m->adam_v, pbytes);
+    alloc((void**)&m->grad, pbytes);
+    alloc((void**)&m->d_err, 256);
+    for (int l = 0; l < N_LAYERS; ++l) {
+        alloc((void**)&m->W[l], (size_t)m->geom.out_pad[l] * m->geom.in_pad[l] * 2);
+        if (l >= 1) alloc((void**)&m->WT[l], (size_t)m->geom.out_pad[l] * m->geom.in_pad[l] * 2);
+    }
+    alloc((void**)&m->d_W, sizeof(void*) * N_LAYERS);
+    alloc((void**)&m->d_WT, sizeof(void*) * N_LAYERS);
+    if (e != cudaSuccess) {
+        plo_mlp_free(m);
+        cudaGetLastError();
+        return set_error(PLO_ERR_OOM, "device allocation of the network failed");
+    }
+    cudaMemcpy(m->d_W, m->W, sizeof(void*) * N_LAYERS, cudaMemcpyHostToDevice);
+    cudaMemcpy(m->d_WT, m->WT, sizeof(void*) * N_LAYERS, cudaMemcpyHostToDevice);
+    cudaMemset(m->adam_m, 0, pbytes);
+    cudaMemset(m->adam_v, 0, pbytes);
+    cudaMemset(m->grad, 0, pbytes);
+    cudaMemset(m->d_err, 0, 256);
+    for (int l = 0; l < N_LAYERS && st == PLO_OK; ++l) {
+        st = make_map(&m->mapW[l], m->W[l], m->geom.out_pad[l], m->geom.in_pad[l], (uint32_t)m->geom.out_pad[l]);
+        if (st == PLO_OK && l >= 1)
+            st = make_map(&m->mapWT[l], m->WT[l], m->geom.in_pad[l], m->geom.out_pad[l], (uint32_t)m->geom.in_pad[l]);
+    }
+    if (st != PLO_OK) {
+        plo_mlp_free(m);
+        return st;
+    }
+    // He-uniform initial weights, zero biases; counter-based (SplitMix64).
+    std::vector<float> canon(canonical_count(m->n_out));
+    int64_t ci = 0;
+    uint64_t ctr = 0;
+    auto unif = [&]() {
+        uint64_t z = seed + 0x9E3779B97F4A7C15ULL * (++ctr);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int l = 0; l < N_LAYERS; ++l) {
+        const double lim = std::sqrt(6.0 / m->geom.in_real[l]);
+        for (int k = 0; k < m->geom.out_real[l] * m->geom.in_real[l]; ++k) canon[ci++] = (float)((2 * unif() - 1) * lim);
+        for (int k = 0; k < m->geom.out_real[l]; ++k) canon[ci++] = 0.0f;
+    }
+    *out = m;
+    st = plo_mlp_set_params(m, canon.data(), (int64_t)canon.size());
+    if (st != PLO_OK) {
+        plo_mlp_free(m);
+        *out = nullptr;
+    }
+    return st;
+}
+
+extern "C" void plo_mlp_free(plo_mlp* m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    free_workspace(m);
+    cudaFree(m->master);
+    cudaFree(m->adam_m);
+    cudaFree(m->adam_v);
+    cudaFree(m->grad);
+    cudaFree(m->d_err);
+    for (int l = 0; l < N_LAYERS; ++l) {
+        cudaFree(m->W[l]);
+        cudaFree(m->WT[l]);
+    }
+    cudaFree(m->d_W);
+    cudaFree(m->d_WT);
+    delete m;
+}
+
+extern "C" plo_status plo_mlp_set_params(plo_mlp* m, const float* h_params, int64_t n) {
+    if (!m || !h_params) return set_error(PLO_ERR_INVALID_ARG, "mlp or params is NULL");
+    if (n != canonical_count(m->n_out)) return set_error(PLO_ERR_INVALID_ARG, "wrong parameter count");
+    std::vector<float> pad;
+    canonical_to_padded(m, h_params, pad);
+    cudaError_t e = cudaMemcpy(m->master, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "parameter upload");
+    plo_status st = refresh_bf16(m, nullptr);
+    if (st != PLO_OK) return st;
+    e = cudaDeviceSynchronize();
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "plo_mlp_set_params");
+}
+
+static plo_status download_canonical(const plo_mlp* m, const float* dev, float* h, int64_t n) {
+    if (!m || !h) return set_error(PLO_ERR_INVALID_ARG, "mlp or output is NULL");
+    if (n != canonical_count(m->n_out)) return set_error(PLO_ERR_INVALID_ARG, "wrong parameter count");
+    std::vector<float> pad(m->n_params_pad);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(pad.data(), dev, pad.size() * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "parameter download");
+    padded_to_canonical(m, pad, h);
+    return PLO_OK;
+}
+
+extern "C" plo_status plo_mlp_get_params(const plo_mlp* m, float* h_params, int64_t n) {
+    return download_canonical(m, m ? m->master : nullptr, h_params, n);
+}
+extern "C" plo_status plo_mlp_get_grads(const plo_mlp* m, float* h_grads, int64_t n) {
+    return download_canonical(m, m ? m->grad : nullptr, h_grads, n);
+}
+
+extern "C" plo_status plo_mlp_forward(plo_mlp* m, const float* d_points, int64_t n, float* d_raw, void* stream) {
+    if (!m) return set_error(PLO_ERR_INVALID_ARG, "mlp is NULL");
+    if (n < 0) return set_error(PLO_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return PLO_OK;
+    if (!d_points || !d_raw) return set_error(PLO_ERR_INVALID_ARG, "points or raw output is NULL");
+    if (n > (int64_t)1 << 30) return set_error(PLO_ERR_INVALID_ARG, "n too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    plo_status st = ensure_workspace(m, n, m->cap_rays);
+    if (st != PLO_OK) return st;
+    k_pe_points<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_points, n, m->H[0]);
+    st = forward_layers(m, n, s);
+    if (st != PLO_OK) return st;
+    cudaError_t e = cudaMemcpy2DAsync(d_raw, (size_t)m->n_out * 4, m->raw, OUT_PAD * 4, (size_t)m->n_out * 4, (size_t)n,
+                                      cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "raw output copy");
+}
+
+extern "C" plo_status plo_mlp_train_step(plo_mlp* m, const float* d_rays, const float* d_rgb_gt,
+                                         const float* d_alpha_gt, int32_t n_rays, int32_t n_samples,
+                                         const float* d_jitter, float* d_loss_out, void* stream) {
+    if (!m) return set_error(PLO_ERR_INVALID_ARG, "mlp is NULL");
+    if (!d_rays || !d_rgb_gt || !d_alpha_gt || !d_loss_out)
+        return set_error(PLO_ERR_INVALID_ARG, "rays, targets or loss output is NULL");
+    if (n_rays <= 0 || n_samples <= 0) return set_error(PLO_ERR_INVALID_ARG, "n_rays and n_samples must be > 0");
+    if (n_samples != 32 && n_samples != 64 && n_samples != 128 && n_samples != 256)
+        return set_error(PLO_ERR_UNSUPPORTED, "n_samples must be 32, 64, 128 or 256");
+    const int64_t M = (int64_t)n_rays * n_samples;
+    if (M % 128 != 0) return set_error(PLO_ERR_INVALID_ARG, "n_rays * n_samples must be a multiple of 128");
+    if (M > ((int64_t)1 << 28)) return set_error(PLO_ERR_INVALID_ARG, "batch too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    plo_status st = ensure_workspace(m, M, n_rays);
+    if (st != PLO_OK) return st;
+    const plo_mlp_desc& D = m->desc;
+    ++m->step;
+    cudaError_t e = cudaMemsetAsync(m->grad, 0, (size_t)m->n_params_pad * 4, s);
+    if (e != cudaSuccess) return cuda_error(e, "gradient clear");
+    k_pe<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(d_rays, n_rays, n_samples, d_jitter, D.seed, (uint64_t)m->step,
+                                                     m->H[0], m->delta);
+    st = forward_layers(m, M, s);
+    if (st != PLO_OK) return st;
+    const float inv_rays = 1.0f / (float)n_rays;
+    const unsigned qblocks = (unsigned)((n_rays + 3) / 4);
+#define PLO_QUAD(SS)                                                                                               \
+    k_quad<16, SS><<<qblocks, 128, 0, s>>>(m->raw, m->delta, d_rays, d_rgb_gt, d_alpha_gt, n_rays, D.l_max, D.eps, \
+                                           D.transmittance, D.loss, inv_rays, m->dO, m->ray_loss)
+    if (n_samples == 32) PLO_QUAD(1);
+    else if (n_samples == 64) PLO_QUAD(2);
+    else if (n_samples == 128) PLO_QUAD(4);
+    else PLO_QUAD(8);
+#undef PLO_QUAD
+    // backward: head
+    gemm::EpiArgs ep{};
+    ep.err = m->d_err;
+    auto colsum = [&](const __nv_bfloat16* dz, int ncols, float* db) {
+        const int rows = 4096;
+        k_colsum<<<(unsigned)((M + rows - 1) / rows), 256, 0, s>>>(dz, M, ncols, rows, db);
+    };
+    e = launch_wgrad<WIDTH>(m->mapW_dO, m->mapW_H[DEPTH], m->grad + m->geom.off[DEPTH], OUT_PAD, (int)M, m->sms,
+                            m->d_err, s);
+    colsum(m->dO, OUT_PAD, bias_ptr(m, m->grad, DEPTH));
+    ep.out_bf16 = m->dZ[0];
+    ep.ldo = WIDTH;
+    ep.mask = m->H[DEPTH];
+    ep.ldm = WIDTH;
+    if (e == cudaSuccess)
+        e = launch_gemm<WIDTH, OUT_PAD>(m->mapA_dO, m->mapWT[DEPTH], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+    // hidden layers l = 8 .. 2 (index l-1 = 7 .. 1), then layer 1
+    int cur = 0;
+    for (int l = DEPTH - 1; l >= 0 && e == cudaSuccess; --l) {
+        // dZ[cur] is d loss / d pre-activation of layer l (0-based), input H[l]
+        if (l == 0)
+            e = launch_wgrad<PE_PAD>(m->mapW_dZ[cur], m->mapW_H[0], m->grad + m->geom.off[0], WIDTH, (int)M, m->sms,
+                                     m->d_err, s);
+        else
+            e = launch_wgrad<WIDTH>(m->mapW_dZ[cur], m->mapW_H[l], m->grad + m->geom.off[l], WIDTH, (int)M, m->sms,
+                                    m->d_err, s);
+        colsum(m->dZ[cur], WIDTH, bias_ptr(m, m->grad, l));
+        if (l == 0 || e != cudaSuccess) break;
+        ep.out_bf16 = m->dZ[cur ^ 1];
+        ep.mask = m->H[l];
+        e = launch_gemm<WIDTH, WIDTH>(m->mapA_dZ[cur], m->mapWT[l], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+        cur ^= 1;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "MLP backward launch");
+    // Adam with exponential decay lr0 -> lr1 over total_steps
+    const double frac = std::fmin((double)(m->step - 1), (double)D.total_steps) / (double)D.total_steps;
+    const float lr = (float)(D.lr0 * std::pow((double)D.lr1 / D.lr0, frac));
+    const float bc1 = (float)(1.0 - std::pow(0.9, (double)m->step));
+    const float bc2 = (float)(1.0 - std::pow(0.999, (double)m->step));
+    const int64_t n = m->n_params_pad;
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->geom, m->master, m->adam_m, m->adam_v, m->grad, n, lr, 0.9f,
+                                                       0.999f, 1e-8f, bc1, bc2, 1, m->d_W, m->d_WT);
+    k_mean<<<1, 256, 0, s>>>(m->ray_loss, n_rays, d_loss_out);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "MLP update launch");
+}
+
+extern "C" plo_status plo_mlp_check(const plo_mlp* m, void* stream) {
+    if (!m) return set_error(PLO_ERR_INVALID_ARG, "mlp is NULL");
+    unsigned int flags = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&flags, m->d_err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "plo_mlp_check");
+    if (flags) {
+        cudaMemsetAsync(m->d_err, 0, 4, s);
+        cudaStreamSynchronize(s);
+        return set_error(PLO_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on a pipeline barrier");
+    }
+    return PLO_OK;
+}
+
+extern "C" int64_t plo_mlp_step(const plo_mlp* m) { return m ? m->step : -1; }
+
+// ---------------------------------------------------------------- raw GEMM entry points
+extern "C" plo_status plo_gemm_bf16(const void* d_A, const void* d_B, int32_t M, int32_t N, int32_t K,
+                                    int32_t epilogue, const float* d_bias, const void* d_mask, void* d_out,
+                                    unsigned int* d_err, void* stream) {
+    if (!d_A || !d_B || !d_out || !d_err) return set_error(PLO_ERR_INVALID_ARG, "A, B, out or err is NULL");
+    if (M <= 0) return set_error(PLO_ERR_INVALID_ARG, "M must be > 0");
+    const bool shape_ok = (N == 256 && (K == 64 || K == 256)) || (N == 64 && K == 256);
+    if (!shape_ok) return set_error(PLO_ERR_UNSUPPORTED, "(N, K) must be (256, 64), (256, 256) or (64, 256)");
+    if (epilogue < 0 || epilogue > 2) return set_error(PLO_ERR_INVALID_ARG, "unknown epilogue");
+    if ((epilogue != gemm::EPI_MASK_BF16 && !d_bias) || (epilogue == gemm::EPI_MASK_BF16 && !d_mask))
+        return set_error(PLO_ERR_INVALID_ARG, "bias (epilogues 0, 1) or mask (epilogue 2) is NULL");
+    CUtensorMap mA, mB;
+    plo_status st = make_map(&mA, d_A, (uint64_t)M, (uint64_t)K, 128);
+    if (st == PLO_OK) st = make_map(&mB, d_B, (uint64_t)N, (uint64_t)K, (uint32_t)N);
+    if (st != PLO_OK) return st;
+    gemm::EpiArgs ep{};
+    ep.bias = d_bias;
+    ep.out_bf16 = static_cast<__nv_bfloat16*>(d_out);
+    ep.out_f32 = static_cast<float*>(d_out);
+    ep.ldo = N;
+    ep.mask = static_cast<const __nv_bfloat16*>(d_mask);
+    ep.ldm = N;
+    ep.err = d_err;
+    const int sms = sm_count_of_current();
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (N == 256 && K == 64) e = launch_gemm<256, 64>(mA, mB, ep, epilogue, M, sms, s);
+    else if (N == 256) e = launch_gemm<256, 256>(mA, mB, ep, epilogue, M, sms, s);
+    else e = launch_gemm<64, 256>(mA, mB, ep, epilogue, M, sms, s);
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "GEMM launch");
+}
+
+extern "C" plo_status plo_wgrad_bf16(const void* d_dZ, int32_t n_out, const void* d_H, int32_t n_in, int32_t M,
+                                     float* d_dW, unsigned int* d_err, void* stream) {
+    if (!d_dZ || !d_H || !d_dW || !d_err) return set_error(PLO_ERR_INVALID_ARG, "dZ, H, dW or err is NULL");
+    if (M <= 0 || M % 64) return set_error(PLO_ERR_INVALID_ARG, "M must be a positive multiple of 64");
+    if (!((n_out == 64 || n_out == 256) && (n_in == 64 || n_in == 256)))
+        return set_error(PLO_ERR_UNSUPPORTED, "n_out and n_in must be 64 or 256");
+    CUtensorMap mZ, mH;
+    plo_status st = make_map(&mZ, d_dZ, (uint64_t)M, (uint64_t)n_out, 64);
+    if (st == PLO_OK) st = make_map(&mH, d_H, (uint64_t)M, (uint64_t)n_in, 64);
+    if (st != PLO_OK) return st;
+    const int sms = sm_count_of_current();
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = n_in == 256 ? launch_wgrad<256>(mZ, mH, d_dW, n_out, M, sms, d_err, s)
+                                : launch_wgrad<64>(mZ, mH, d_dW, n_out, M, sms, d_err, s);
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "weight-gradient GEMM launch");
+}

@@ -10,9 +10,9 @@
 namespace plo {
 namespace sm100 {
 
-// ~2^26 polls of try_wait (each may suspend for a while): far beyond any
+// ~2^24 polls of try_wait (each may suspend for a while): far beyond any
 // legitimate wait, short enough to return in seconds.
-constexpr uint32_t WAIT_LIMIT = 1u << 26;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
