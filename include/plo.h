@@ -171,6 +171,50 @@ plo_status plo_render_rays_host(const plo_tree* tree, const float* h_rays, int64
 plo_status plo_render_rays_host_noalloc(const plo_tree* tree, const float* h_rays, int64_t n,
                                         const plo_render_params* params, float* h_rgb, float* h_T, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched render of several luminaires (one launch for all of them).
+ * Rays of tree t are d_rays[ray_offsets[t] .. ray_offsets[t+1]) of one
+ * concatenated array (outputs likewise).  A persistent kernel drains one
+ * queue of ray claims over all trees, so uneven ray counts balance
+ * themselves; trees may differ in depth, SH degree and leaf precision.
+ * The batch keeps pointers to the trees: they must outlive it. */
+typedef struct plo_batch plo_batch;
+
+/* Launch shape of the batch kernel.
+ *   claim_rays     rays a warp takes from the queue at a time (multiple of 32)
+ *   blocks_per_sm  resident blocks per SM (0: as many as fit)
+ *   top_nodes      nodes per tree staged in shared memory (0..73) */
+typedef struct {
+    int32_t claim_rays;
+    int32_t blocks_per_sm;
+    int32_t top_nodes;
+} plo_batch_config;
+
+/* n_trees in [1, 16]; ray_offsets: host int64 [n_trees + 1], starting at 0. */
+plo_status plo_batch_create(const plo_tree* const* trees, int32_t n_trees, const int64_t* ray_offsets,
+                            const plo_render_params* params, plo_batch** out);
+void plo_batch_free(plo_batch* batch);
+plo_status plo_batch_set_config(plo_batch* batch, const plo_batch_config* cfg);
+plo_status plo_batch_get_config(const plo_batch* batch, plo_batch_config* cfg);
+
+/* Renders the whole batch (async): d_rays float [n][6], d_rgb float [n][3],
+ * d_T float [n], d_status int32 [n] or NULL, n = ray_offsets[n_trees]. */
+plo_status plo_batch_render(plo_batch* batch, const float* d_rays, float* d_rgb, float* d_T, int32_t* d_status,
+                            void* stream);
+
+/* Captures one batch render on these buffers into a CUDA graph (queue reset
+ * + kernel); plo_batch_replay launches it on `stream` (async).  Changing the
+ * config drops the graph. */
+plo_status plo_batch_capture(plo_batch* batch, const float* d_rays, float* d_rgb, float* d_T, int32_t* d_status,
+                             void* stream);
+plo_status plo_batch_replay(plo_batch* batch, void* stream);
+
+/* Times every launch shape of a small grid (claim 32..1024, blocks per SM,
+ * shared-memory staging on/off) on these buffers, `reps` launches each, and
+ * keeps the fastest; returns it and its time per launch.  Synchronous. */
+plo_status plo_batch_autotune(plo_batch* batch, const float* d_rays, float* d_rgb, float* d_T, int32_t reps,
+                              void* stream, plo_batch_config* best, float* best_ms);
+
 /* Point -> leaf lookup (async), the descent step of the render.
  *   d_points  float [n][3] in the tree's unit-cube coordinates.
  *   d_dirs    float [n][3] or NULL: on a cell plane a point belongs to the
@@ -223,14 +267,22 @@ typedef struct {
     float l_max;            /* maximum radiance: sigmoid scale and loss unit       */
     float eps;              /* loss regulariser, 0.01 in the paper                 */
     float lr0, lr1;         /* exponential decay lr0 -> lr1 (5e-4 -> 5e-6)         */
-    uint64_t seed;          /* stream of the stratified-sampling jitter            */
+    float init_radiance;    /* emission the network starts from (0: l_max / 2)     */
+    int32_t reserved;       /* must be 0                                           */
+    uint64_t seed;          /* stream of the stratified-sampling and distillation
+                               jitter                                              */
 } plo_mlp_desc;
 
 /* Number of parameters of the network for SH degree `sh_degree`. */
 int64_t plo_mlp_param_count(int32_t sh_degree);
 
-/* Creates the network on the current device with He-uniform weights drawn
- * from `seed` and zero biases. */
+/* Creates the network on the current device.  Initial parameters (drawn
+ * from `seed`): He-uniform hidden weights and zero hidden biases; the head's
+ * weights He-uniform scaled by 0.1, sigma bias 0.5 (every sample starts with
+ * positive density), and the DC SH bias of each channel set so that the
+ * emission starts at init_radiance.  Starting at l_max / 2 against HDR
+ * targets far below l_max, the first updates drive sigma below zero
+ * everywhere and the ReLU keeps it there. */
 plo_status plo_mlp_create(const plo_mlp_desc* desc, uint64_t seed, plo_mlp** out);
 void plo_mlp_free(plo_mlp* mlp);
 
@@ -257,6 +309,17 @@ plo_status plo_mlp_forward(plo_mlp* mlp, const float* d_points, int64_t n, float
 plo_status plo_mlp_train_step(plo_mlp* mlp, const float* d_rays, const float* d_rgb_gt, const float* d_alpha_gt,
                               int32_t n_rays, int32_t n_samples, const float* d_jitter, float* d_loss_out,
                               void* stream);
+
+/* Distils the network into a plenoctree (Sec. 5, "Creating the plenoctree";
+ * synchronous).  Every voxel of the 2^depth grid (depth 1..10) is evaluated
+ * at its centre; voxels with sigma >= sigma_thresh (0.01 in the paper) are
+ * kept, each as a leaf holding the mean of ReLU(sigma_raw) and of the raw SH
+ * coefficients over `samples` (1..256) jittered positions inside it (offsets
+ * from SplitMix64 keyed by the desc's seed and the voxel's Morton code).  The
+ * tree is packed at `precision` and owned by *out; render it with
+ * PLO_ACT_SIGMOID and the network's l_max. */
+plo_status plo_distill(plo_mlp* mlp, int32_t depth, int32_t samples, float sigma_thresh, int32_t precision,
+                       plo_tree** out, void* stream);
 
 /* Synchronises `stream`; PLO_ERR_TIMEOUT if a tensor-core kernel gave up on
  * a bounded pipeline wait since the last check (the flag is cleared). */

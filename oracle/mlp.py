@@ -255,3 +255,46 @@ def distill_dense(Ws, bs, depth, jitter, sigma_thresh=0.01, l_max=3):
     K = (l_max + 1) ** 2
     sh = raw_s[..., 1:].mean(1).reshape(len(kept), 3, K)
     return ijk[kept], sig_c, sig, sh
+
+
+# ---------------------------------------------------------------- distillation sampling
+# Voxels are addressed by their Morton code at depth D: the child slot
+# (bx | by << 1 | bz << 2) of every level from the root, most significant
+# first.  The jittered sample offsets inside a voxel come from the SplitMix64
+# generator (Steele, Lea, Flood, "Fast splittable pseudorandom number
+# generators", OOPSLA 2014), written here from its definition:
+#   mix(z): z += 0x9E3779B97F4A7C15; z = (z ^ z>>30) * 0xBF58476D1CE4E5B9;
+#           z = (z ^ z>>27) * 0x94D049BB133111EB; return z ^ z>>31
+#   key = mix(mix(seed ^ 0xD15711) ^ (code * 0x9E3779B97F4A7C15 + 3 s + a))
+#   u   = (key >> 40) / 2^24            (sample s, axis a)
+_M64 = (1 << 64) - 1
+
+
+def _mix64(z):
+    z = (z + 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def morton_code(ijk, depth):
+    """Morton code of integer voxel coords [n,3] at `depth`."""
+    code = np.zeros(len(ijk), dtype=object)
+    for l in range(depth):
+        bit = depth - 1 - l
+        slot = ((ijk[:, 0] >> bit) & 1) | (((ijk[:, 1] >> bit) & 1) << 1) | (((ijk[:, 2] >> bit) & 1) << 2)
+        code = code * 8 + slot.astype(object)
+    return code
+
+
+def distill_jitter(seed, codes, S):
+    """Offsets in [0,1)^3 of S samples in each voxel, [n, S, 3]."""
+    k0 = _mix64(seed ^ 0xD15711)
+    out = np.empty((len(codes), S, 3))
+    for i, c in enumerate(codes):
+        base = (int(c) * 0x9E3779B97F4A7C15) & _M64
+        for s in range(S):
+            for a in range(3):
+                key = _mix64(k0 ^ ((base + 3 * s + a) & _M64))
+                out[i, s, a] = (key >> 40) / 16777216.0
+    return out

@@ -266,7 +266,8 @@ LOSS_PAPER, LOSS_REG, LOSS_MSE = 0, 1, 2
 class MlpDesc(ctypes.Structure):
     _fields_ = [("sh_degree", ctypes.c_int32), ("transmittance", ctypes.c_int32), ("loss", ctypes.c_int32),
                 ("total_steps", ctypes.c_int32), ("l_max", ctypes.c_float), ("eps", ctypes.c_float),
-                ("lr0", ctypes.c_float), ("lr1", ctypes.c_float), ("seed", ctypes.c_uint64)]
+                ("lr0", ctypes.c_float), ("lr1", ctypes.c_float), ("init_radiance", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 def _load_mlp_sigs(lib):
@@ -284,6 +285,7 @@ def _load_mlp_sigs(lib):
         "plo_mlp_step": (I64, [P]),
         "plo_gemm_bf16": (I32, [P, P, I32, I32, I32, I32, P, P, P, P, P]),
         "plo_wgrad_bf16": (I32, [P, I32, P, I32, I32, P, P, P]),
+        "plo_distill": (I32, [P, I32, I32, ctypes.c_float, I32, P, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -302,11 +304,13 @@ class Mlp:
     """The NeRF-SH network on the current device (plo_mlp_*)."""
 
     def __init__(self, l_max: float, loss: int = LOSS_PAPER, transmittance: int = TRANS_EXP, total_steps: int = 1000,
-                 lr0: float = 5e-4, lr1: float = 5e-6, eps: float = 0.01, seed: int = 1, jitter_seed: int = 2):
+                 lr0: float = 5e-4, lr1: float = 5e-6, eps: float = 0.01, seed: int = 1, jitter_seed: int = 2,
+                 init_radiance: float = 0.0):
         lib = mlp_lib()
         d = MlpDesc()
         d.sh_degree, d.transmittance, d.loss, d.total_steps = 3, transmittance, loss, total_steps
         d.l_max, d.eps, d.lr0, d.lr1, d.seed = l_max, eps, lr0, lr1, jitter_seed
+        d.init_radiance, d.reserved = init_radiance, 0
         h = ctypes.c_void_p()
         _check(lib.plo_mlp_create(ctypes.byref(d), seed, ctypes.byref(h)))
         self._h = h
@@ -347,6 +351,17 @@ class Mlp:
     def check(self, stream=None):
         _check(mlp_lib().plo_mlp_check(self._h, _stream(stream)))
 
+    def distill(self, depth: int, samples: int = 8, sigma_thresh: float = 0.01, precision: int = PREC_FP32,
+                stream=None) -> "Tree":
+        """plo_distill: the network as a plenoctree of the given depth."""
+        h = ctypes.c_void_p()
+        _check(mlp_lib().plo_distill(self._h, depth, samples, sigma_thresh, precision, ctypes.byref(h),
+                                     _stream(stream)))
+        t = Tree.__new__(Tree)
+        t._h = h
+        t.precision = precision
+        return t
+
     @property
     def step(self) -> int:
         return int(mlp_lib().plo_mlp_step(self._h))
@@ -383,3 +398,111 @@ def wgrad_bf16(dZ, H, dW, err=None, stream=None):
     _check(mlp_lib().plo_wgrad_bf16(_ptr(dZ), dZ.shape[1], _ptr(H), H.shape[1], dZ.shape[0], _ptr(dW), _ptr(err),
                                     _stream(stream)))
     return dW, err
+
+
+# ---------------------------------------------------------------- batched render
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("claim_rays", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("top_nodes", ctypes.c_int32)]
+
+
+def _batch_lib():
+    lib = load()
+    if not getattr(lib, "_batch_sigs", False):
+        P, I32 = ctypes.c_void_p, ctypes.c_int32
+        sigs = {
+            "plo_batch_create": (I32, [P, I32, P, P, P]),
+            "plo_batch_free": (None, [P]),
+            "plo_batch_set_config": (I32, [P, P]),
+            "plo_batch_get_config": (I32, [P, P]),
+            "plo_batch_render": (I32, [P, P, P, P, P, P]),
+            "plo_batch_capture": (I32, [P, P, P, P, P, P]),
+            "plo_batch_replay": (I32, [P, P]),
+            "plo_batch_autotune": (I32, [P, P, P, P, I32, P, P, P]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype, fn.argtypes = res, args
+        lib._batch_sigs = True
+    return lib
+
+
+class Batch:
+    """Several trees rendered by one persistent launch (plo_batch_*).  Rays of
+    tree t are rows offsets[t]:offsets[t+1] of one concatenated array."""
+
+    def __init__(self, trees, offsets, params: RenderParams | None = None):
+        lib = _batch_lib()
+        self._trees = list(trees)  # keep the trees alive
+        arr = (ctypes.c_void_p * len(trees))(*[t.handle.value for t in trees])
+        offs = np.ascontiguousarray(offsets, np.int64)
+        self.n_rays = int(offs[-1])
+        p = (params or RenderParams())._c()
+        h = ctypes.c_void_p()
+        _check(lib.plo_batch_create(arr, len(trees), ctypes.c_void_p(offs.ctypes.data), ctypes.byref(p),
+                                    ctypes.byref(h)))
+        self._h = h
+
+    def config(self) -> dict:
+        c = BatchConfig()
+        _check(_batch_lib().plo_batch_get_config(self._h, ctypes.byref(c)))
+        return {"claim_rays": c.claim_rays, "blocks_per_sm": c.blocks_per_sm, "top_nodes": c.top_nodes}
+
+    def set_config(self, claim_rays: int, blocks_per_sm: int, top_nodes: int):
+        c = BatchConfig(claim_rays, blocks_per_sm, top_nodes)
+        _check(_batch_lib().plo_batch_set_config(self._h, ctypes.byref(c)))
+
+    def render(self, rays, rgb, T, status=None, stream=None):
+        _check(_batch_lib().plo_batch_render(self._h, _ptr(rays), _ptr(rgb), _ptr(T), _ptr(status), _stream(stream)))
+
+    def capture(self, rays, rgb, T, status=None, stream=None):
+        _check(_batch_lib().plo_batch_capture(self._h, _ptr(rays), _ptr(rgb), _ptr(T), _ptr(status),
+                                              _stream(stream)))
+
+    def replay(self, stream=None):
+        _check(_batch_lib().plo_batch_replay(self._h, _stream(stream)))
+
+    def autotune(self, rays, rgb, T, reps: int = 2, stream=None):
+        c = BatchConfig()
+        ms = ctypes.c_float()
+        _check(_batch_lib().plo_batch_autotune(self._h, _ptr(rays), _ptr(rgb), _ptr(T), reps, _stream(stream),
+                                               ctypes.byref(c), ctypes.byref(ms)))
+        return {"claim_rays": c.claim_rays, "blocks_per_sm": c.blocks_per_sm, "top_nodes": c.top_nodes}, ms.value
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _batch_lib().plo_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def autotune_cached(batch: "Batch", key: str, rays, rgb, T, reps: int = 2, path: str | None = None):
+    """Applies the launch shape cached for (this GPU, key) in a JSON file
+    (default ~/.cache/plo/autotune.json), autotuning and recording it when
+    absent.  Returns (config, source) with source 'cache' or 'tuned'."""
+    import json
+    import torch
+    path = path or os.path.join(os.path.expanduser("~"), ".cache", "plo", "autotune.json")
+    gpu = torch.cuda.get_device_name()
+    full = f"{gpu}|{key}"
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    if full in cache:
+        c = cache[full]
+        batch.set_config(c["claim_rays"], c["blocks_per_sm"], c["top_nodes"])
+        return c, "cache"
+    cfg, ms = batch.autotune(rays, rgb, T, reps=reps)
+    cache[full] = dict(cfg, ms=ms)
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, path)
+    return cfg, "tuned"

@@ -207,13 +207,8 @@ __global__ void k_pe(const float* rays, int n_rays, int N, const float* jitter, 
     }
 }
 
-// Positional encoding of given points (unit-cube coordinates) -> X.
-__global__ void k_pe_points(const float* pts, int64_t n, __nv_bfloat16* X) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n) return;
-    float x[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] = __ldg(pts + 3 * idx + a);
+// Positional encoding of one point (unit-cube coordinates) into a bf16 row.
+__device__ __forceinline__ void encode_point(const float* x, __nv_bfloat16* row) {
     float f[PE_PAD];
     f[0] = x[0];
     f[1] = x[1];
@@ -230,7 +225,7 @@ __global__ void k_pe_points(const float* pts, int64_t n, __nv_bfloat16* X) {
         }
     }
     f[63] = 0.0f;
-    uint4* dst = reinterpret_cast<uint4*>(X + idx * PE_PAD);
+    uint4* dst = reinterpret_cast<uint4*>(row);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         uint32_t w[4];
@@ -241,6 +236,85 @@ __global__ void k_pe_points(const float* pts, int64_t n, __nv_bfloat16* X) {
         }
         dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
     }
+}
+
+// Positional encoding of given points (unit-cube coordinates) -> X.
+__global__ void k_pe_points(const float* pts, int64_t n, __nv_bfloat16* X) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = __ldg(pts + 3 * idx + a);
+    encode_point(x, X + idx * PE_PAD);
+}
+
+// ---- distillation (Sec. 5, "Creating the plenoctree") ----
+// Voxels at depth D are addressed by their Morton code: the child slot
+// (bx | by << 1 | bz << 2) of every level from the root, most significant
+// first.
+__device__ __forceinline__ void morton_decode(uint64_t m, int D, uint32_t* c) {
+    c[0] = c[1] = c[2] = 0;
+    for (int l = 0; l < D; ++l) {
+        const uint32_t slot = (uint32_t)(m >> (3 * (D - 1 - l))) & 7u;
+        c[0] = 2u * c[0] + (slot & 1u);
+        c[1] = 2u * c[1] + ((slot >> 1) & 1u);
+        c[2] = 2u * c[2] + (slot >> 2);
+    }
+}
+
+// Centre of voxels base .. base+n-1 (Morton order) -> X.
+__global__ void k_pe_centres(uint64_t base, int64_t n, int D, __nv_bfloat16* X) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    uint32_t c[3];
+    morton_decode(base + (uint64_t)idx, D, c);
+    const float inv_g = 1.0f / (float)(1u << D);
+    float x[3] = {((float)c[0] + 0.5f) * inv_g, ((float)c[1] + 0.5f) * inv_g, ((float)c[2] + 0.5f) * inv_g};
+    encode_point(x, X + idx * PE_PAD);
+}
+
+// S jittered samples in each listed voxel -> X (row i*S + s).  Offsets come
+// from SplitMix64 (Steele, Lea, Flood 2014): key = mix(mix(seed ^ 0xD15711)
+// ^ (code * 0x9E3779B97F4A7C15 + 3 s + a)), u = (key >> 40) / 2^24.
+__global__ void k_pe_jitter(const uint64_t* codes, int64_t nv, int S, int D, uint64_t seed, __nv_bfloat16* X) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nv * S) return;
+    const int64_t i = idx / S;
+    const int s = (int)(idx % S);
+    const uint64_t code = __ldg(reinterpret_cast<const unsigned long long*>(codes) + i);
+    uint32_t c[3];
+    morton_decode(code, D, c);
+    const uint64_t k0 = mix64(seed ^ 0xD15711ULL);
+    const uint64_t base = code * 0x9E3779B97F4A7C15ULL;
+    const float inv_g = 1.0f / (float)(1u << D);
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const uint64_t key = mix64(k0 ^ (base + (uint64_t)(3 * s + a)));
+        const float u = (float)(key >> 40) * (1.0f / 16777216.0f);
+        x[a] = ((float)c[a] + u) * inv_g;
+    }
+    encode_point(x, X + idx * PE_PAD);
+}
+
+__global__ void k_keep(const float* raw, int64_t n, float thresh, uint8_t* flags) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    flags[idx] = fmaxf(__ldg(raw + idx * OUT_PAD), 0.0f) >= thresh ? 1 : 0;
+}
+
+// out[i] = mean over the S samples of voxel i: ReLU(sigma_raw), raw SH.
+__global__ void k_average(const float* raw, int64_t nv, int S, int n_out, float* out) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nv * n_out) return;
+    const int64_t i = idx / n_out;
+    const int k = (int)(idx % n_out);
+    float acc = 0.0f;
+    for (int s = 0; s < S; ++s) {
+        const float v = __ldg(raw + (i * S + s) * OUT_PAD + k);
+        acc += k == 0 ? fmaxf(v, 0.0f) : v;
+    }
+    out[idx] = acc / (float)S;
 }
 
 // Quadrature render of Eq. 3 from the head outputs, the loss of Eq. 7-9 and
@@ -656,6 +730,8 @@ plo_status check_mlp_desc(const plo_mlp_desc* d) {
     if (d->loss < PLO_LOSS_PAPER || d->loss > PLO_LOSS_MSE) return set_error(PLO_ERR_INVALID_ARG, "unknown loss");
     if (!(d->l_max > 0.0f) || !(d->lr0 > 0.0f) || !(d->lr1 > 0.0f) || d->total_steps < 1 || !(d->eps > 0.0f))
         return set_error(PLO_ERR_INVALID_ARG, "l_max, lr0, lr1, eps must be > 0 and total_steps >= 1");
+    if (!(d->init_radiance >= 0.0f) || d->reserved != 0)
+        return set_error(PLO_ERR_INVALID_ARG, "init_radiance must be >= 0 and reserved 0");
     return PLO_OK;
 }
 
@@ -726,10 +802,17 @@ extern "C" plo_status plo_mlp_create(const plo_mlp_desc* desc, uint64_t seed, pl
         return (double)(z >> 11) * (1.0 / 9007199254740992.0);
     };
     for (int l = 0; l < N_LAYERS; ++l) {
-        const double lim = std::sqrt(6.0 / m->geom.in_real[l]);
+        const double lim = std::sqrt(6.0 / m->geom.in_real[l]) * (l == DEPTH ? 0.1 : 1.0);
         for (int k = 0; k < m->geom.out_real[l] * m->geom.in_real[l]; ++k) canon[ci++] = (float)((2 * unif() - 1) * lim);
         for (int k = 0; k < m->geom.out_real[l]; ++k) canon[ci++] = 0.0f;
     }
+    // head biases: sigma starts positive, the DC coefficient sets the emission
+    float* head_b = canon.data() + canon.size() - m->n_out;
+    head_b[0] = 0.5f;
+    const double p0 = desc->init_radiance > 0.0f ? std::fmin(std::fmax(desc->init_radiance / desc->l_max, 1e-6), 0.5)
+                                                 : 0.5;
+    const double dc = std::log(p0 / (1.0 - p0)) / 0.28209479177387814;  // logit / Y_0^0
+    for (int ch = 0; ch < 3; ++ch) head_b[1 + ch * m->K] = (float)dc;
     *out = m;
     st = plo_mlp_set_params(m, canon.data(), (int64_t)canon.size());
     if (st != PLO_OK) {
@@ -949,4 +1032,108 @@ extern "C" plo_status plo_wgrad_bf16(const void* d_dZ, int32_t n_out, const void
     cudaError_t e = n_in == 256 ? launch_wgrad<256>(mZ, mH, d_dW, n_out, M, sms, d_err, s)
                                 : launch_wgrad<64>(mZ, mH, d_dW, n_out, M, sms, d_err, s);
     return e == cudaSuccess ? PLO_OK : cuda_error(e, "weight-gradient GEMM launch");
+}
+
+// ---------------------------------------------------------------- distillation
+// plo_distill (Sec. 5, "Creating the plenoctree"): the network's sigma at the
+// centre of every voxel at `depth` decides which voxels are kept (sigma >=
+// sigma_thresh); each kept voxel gets the mean of ReLU(sigma_raw) and of the
+// raw SH coefficients over `samples` jittered positions inside it.  Voxels
+// are visited in Morton order, so the kept list is sorted and the octree is
+// assembled on the host in one pass, then packed by plo_build_tree.
+extern "C" plo_status plo_distill(plo_mlp* m, int32_t depth, int32_t samples, float sigma_thresh,
+                                  int32_t precision, plo_tree** out, void* stream) {
+    if (!m || !out) return set_error(PLO_ERR_INVALID_ARG, "mlp or out is NULL");
+    *out = nullptr;
+    if (depth < 1 || depth > 10) return set_error(PLO_ERR_INVALID_ARG, "depth must be in [1, 10]");
+    if (samples < 1 || samples > 256) return set_error(PLO_ERR_INVALID_ARG, "samples must be in [1, 256]");
+    if (!(sigma_thresh >= 0.0f)) return set_error(PLO_ERR_INVALID_ARG, "sigma_thresh must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t total = (int64_t)1 << (3 * depth);
+    const int64_t C = total < ((int64_t)1 << 19) ? total : ((int64_t)1 << 19);
+    plo_status st = ensure_workspace(m, C < 128 ? 128 : C, m->cap_rays);
+    if (st != PLO_OK) return st;
+    const int n_out = m->n_out;
+    uint8_t* d_flags = nullptr;
+    unsigned long long* d_codes = nullptr;
+    float* d_avg = nullptr;
+    const int64_t vmax = C / samples > 0 ? C / samples : 1;
+    cudaError_t e = cudaMalloc((void**)&d_flags, (size_t)C);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_codes, (size_t)vmax * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_avg, (size_t)vmax * n_out * 4);
+    std::vector<uint8_t> flags(C);
+    std::vector<unsigned long long> codes;
+    std::vector<float> vals;
+    std::vector<unsigned long long> sub;
+    for (int64_t base = 0; e == cudaSuccess && st == PLO_OK && base < total; base += C) {
+        const int64_t n = total - base < C ? total - base : C;
+        k_pe_centres<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((uint64_t)base, n, depth, m->H[0]);
+        st = forward_layers(m, n, s);
+        if (st != PLO_OK) break;
+        k_keep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->raw, n, sigma_thresh, d_flags);
+        e = cudaMemcpyAsync(flags.data(), d_flags, (size_t)n, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        sub.clear();
+        for (int64_t i = 0; i < n; ++i)
+            if (flags[i]) sub.push_back((unsigned long long)(base + i));
+        for (size_t off = 0; off < sub.size() && e == cudaSuccess && st == PLO_OK; off += (size_t)vmax) {
+            const int64_t nv = (int64_t)std::min(sub.size() - off, (size_t)vmax);
+            e = cudaMemcpyAsync(d_codes, sub.data() + off, (size_t)nv * 8, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) break;
+            k_pe_jitter<<<(unsigned)((nv * samples + 255) / 256), 256, 0, s>>>(
+                reinterpret_cast<const uint64_t*>(d_codes), nv, samples, depth, m->desc.seed, m->H[0]);
+            st = forward_layers(m, nv * samples, s);
+            if (st != PLO_OK) break;
+            k_average<<<(unsigned)((nv * n_out + 255) / 256), 256, 0, s>>>(m->raw, nv, samples, n_out, d_avg);
+            const size_t old = vals.size();
+            vals.resize(old + (size_t)nv * n_out);
+            e = cudaMemcpyAsync(vals.data() + old, d_avg, (size_t)nv * n_out * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        codes.insert(codes.end(), sub.begin(), sub.end());
+    }
+    cudaFree(d_flags);
+    cudaFree(d_codes);
+    cudaFree(d_avg);
+    if (st != PLO_OK) return st;
+    if (e != cudaSuccess) return cuda_error(e, "plo_distill");
+    st = plo_mlp_check(m, stream);
+    if (st != PLO_OK) return st;
+    // octree over the kept voxels (Morton-sorted leaves at level `depth`)
+    const int64_t nl = (int64_t)codes.size();
+    const int K = m->K;
+    std::vector<int32_t> child;
+    child.assign(8, -1);
+    int32_t n_nodes = 1;
+    std::vector<float> sigma(nl), sh((size_t)nl * 3 * K);
+    for (int64_t i = 0; i < nl; ++i) {
+        const unsigned long long c = codes[i];
+        int32_t node = 0;
+        for (int l = 0; l < depth - 1; ++l) {
+            const int slot = (int)((c >> (3 * (depth - 1 - l))) & 7ull);
+            int32_t& e2 = child[(size_t)node * 8 + slot];
+            if (e2 == -1) {
+                e2 = n_nodes++;
+                child.resize((size_t)n_nodes * 8, -1);
+            }
+            node = child[(size_t)node * 8 + slot];
+        }
+        child[(size_t)node * 8 + (int)(c & 7ull)] = (int32_t)(-i - 2);
+        sigma[i] = vals[(size_t)i * n_out];
+        for (int k = 0; k < 3 * K; ++k) sh[(size_t)i * 3 * K + k] = vals[(size_t)i * n_out + 1 + k];
+    }
+    plo_tree_desc d{};
+    d.depth = depth;
+    d.sh_degree = m->desc.sh_degree;
+    d.n_nodes = n_nodes;
+    d.n_leaves = nl;
+    d.child = child.data();
+    d.sigma = sigma.data();
+    d.sh = sh.data();
+    for (int a = 0; a < 3; ++a) {
+        d.bbox_min[a] = 0.0f;
+        d.bbox_max[a] = 1.0f;
+    }
+    return plo_build_tree(&d, precision, out);
 }

@@ -42,24 +42,31 @@ constexpr int BLOCK = 256;
 constexpr int WARPS = BLOCK / 32;
 constexpr int STACK = MAX_DEPTH + 1;
 
-struct KParams {
+// One packed tree as the kernels see it.
+struct TreeParams {
     const uint2* nodes;
     const int32_t* leaf_ids;
     const uint8_t* sh;
+    unsigned int* flags;
     int32_t sh_stride;
     int32_t depth;
-    int32_t n_top;
+    int32_t n_top;   // nodes staged in shared memory (ids 0 .. n_top-1)
+    int32_t s_off;   // their offset in the block's shared node table (entries)
+    int32_t K, prec;
+    int32_t max_steps;
     float bmin[3], inv_ext[3], inv_ext_lo[3];  // 1/extent as a double-float
+};
+
+struct KParams {
+    TreeParams tree;
     int32_t transmittance, activation;
     float l_max, t_stop, sigma_min;
-    int32_t max_steps;
     const float* rays;
     int64_t n;
     int64_t chunk;  // rays per warp
     float* rgb;
     float* T;
     int32_t* status;
-    unsigned int* flags;
     // trace mode
     int32_t trace_max;
     int64_t* tr_leaf;
@@ -166,9 +173,33 @@ __device__ __forceinline__ void sh_eval(const uint8_t* rec, uint32_t yword, cons
 }
 
 template <int PREC>
-__device__ __forceinline__ float decode_sigma(uint32_t y) {
-    if (PREC == PLO_PREC_FP32) return __uint_as_float(y);
+__device__ __forceinline__ float decode_sigma(uint32_t y, int prec) {
+    if (PREC == PLO_PREC_FP32 || (PREC < 0 && prec == PLO_PREC_FP32)) return __uint_as_float(y);
     return __uint_as_float((y & 0xFFFFFFu) << 7);  // 24-bit float: exponent + 16 mantissa bits
+}
+
+// SH emission of one record; K / PREC given at compile time, or read from
+// the tree when K == 0 (the batch kernel mixes trees).
+template <int K, int PREC>
+__device__ __forceinline__ void sh_emission(const TreeParams& tp, uint32_t rec, uint32_t yword, const float* dirn,
+                                            float& r, float& g, float& b) {
+    const uint8_t* p = tp.sh + (size_t)rec * tp.sh_stride;
+    if (K > 0) {
+        float Y[K > 0 ? K : 1];
+        sh_basis<(K > 0 ? K : 1)>(dirn[0], dirn[1], dirn[2], Y);
+        sh_eval<(K > 0 ? K : 1), PREC>(p, yword, Y, r, g, b);
+        return;
+    }
+    float Y[16];
+    sh_basis<16>(dirn[0], dirn[1], dirn[2], Y);
+#define PLO_SH_CASE(KK, PP) \
+    if (tp.K == KK && tp.prec == PP) return sh_eval<KK, PP>(p, yword, Y, r, g, b);
+    PLO_SH_CASE(16, PLO_PREC_FP32) PLO_SH_CASE(9, PLO_PREC_FP32) PLO_SH_CASE(16, PLO_PREC_FP16)
+    PLO_SH_CASE(9, PLO_PREC_FP16) PLO_SH_CASE(16, PLO_PREC_BF16) PLO_SH_CASE(9, PLO_PREC_BF16)
+    PLO_SH_CASE(4, PLO_PREC_FP32) PLO_SH_CASE(4, PLO_PREC_FP16) PLO_SH_CASE(4, PLO_PREC_BF16)
+    PLO_SH_CASE(1, PLO_PREC_FP32) PLO_SH_CASE(1, PLO_PREC_FP16) PLO_SH_CASE(1, PLO_PREC_BF16)
+#undef PLO_SH_CASE
+    r = g = b = 0.0f;
 }
 
 __device__ __forceinline__ float act_fn(float s, int act, float l_max) {
@@ -197,18 +228,18 @@ struct Ray {
     int slot;           // slot of the current cell in its parent (trace only)
     int state;
     int status;
+    int tree;           // index into the batch's tree table (batch kernel only)
 };
 
-__device__ __forceinline__ uint2 load_entry(const uint2* nodes, const uint2* s_nodes, int n_top, uint32_t node,
-                                            int slot) {
-    if (node < (uint32_t)n_top) return s_nodes[node * 8 + slot];
-    return __ldg(nodes + (size_t)node * 8 + slot);
+__device__ __forceinline__ uint2 load_entry(const TreeParams& tp, const uint2* s_nodes, uint32_t node, int slot) {
+    if (node < (uint32_t)tp.n_top) return s_nodes[tp.s_off + node * 8 + slot];
+    return __ldg(tp.nodes + (size_t)node * 8 + slot);
 }
 
 // Descends from R.node (cell coords R.c at R.level) through the shared-memory
 // levels and at most one global level.  Ends in ST_LEAF (leaf or empty
 // octant found) or stays in ST_DESCEND with the next node to load.
-__device__ __forceinline__ void descend_step(const KParams& kp, const uint2* s_nodes, Ray& R, uint32_t* stack) {
+__device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* s_nodes, Ray& R, uint32_t* stack) {
     for (int guard = 0; guard <= MAX_DEPTH; ++guard) {
         const float sc = pow2i(-(R.level + 1));
         int bx = above(R.p[0], (float)(2u * R.c[0] + 1u) * sc, R.d[0]);
@@ -218,10 +249,10 @@ __device__ __forceinline__ void descend_step(const KParams& kp, const uint2* s_n
         R.c[1] = 2u * R.c[1] + by;
         R.c[2] = 2u * R.c[2] + bz;
         R.slot = bx | (by << 1) | (bz << 2);
-        const bool global = R.node >= (uint32_t)kp.n_top;
-        uint2 e = load_entry(kp.nodes, s_nodes, kp.n_top, R.node, R.slot);
+        const bool global = R.node >= (uint32_t)tp.n_top;
+        uint2 e = load_entry(tp, s_nodes, R.node, R.slot);
         ++R.level;
-        if ((e.x & LEAF_BIT) || R.level >= kp.depth) {  // leaf, empty octant (or a malformed table)
+        if ((e.x & LEAF_BIT) || R.level >= tp.depth) {  // leaf, empty octant (or a malformed table)
             if (!(e.x & LEAF_BIT)) e = make_uint2(ENTRY_EMPTY, 0u);
             R.entry_x = e.x;
             R.entry_y = e.y;
@@ -232,7 +263,7 @@ __device__ __forceinline__ void descend_step(const KParams& kp, const uint2* s_n
         const uint32_t parent = R.node;
         R.node = e.x;
         (void)parent;
-        if (global || R.node >= (uint32_t)kp.n_top) return;  // next lookup needs a global load
+        if (global || R.node >= (uint32_t)tp.n_top) return;  // next lookup needs a global load
     }
 }
 
@@ -248,7 +279,7 @@ __device__ __forceinline__ void ray_store(const KParams& kp, int64_t i, const Ra
 // Proxy clip.  On a hit the lane enters ST_DESCEND at the root; on a miss or
 // an invalid ray the outputs are written and the lane stays ST_IDLE.
 template <bool TRACE>
-__device__ void ray_begin(const KParams& kp, int64_t i, Ray& R, uint32_t* stack) {
+__device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ray& R, uint32_t* stack) {
     const float* q = kp.rays + 6 * i;
     float o[3], dw[3];
 #pragma unroll
@@ -277,8 +308,8 @@ __device__ void ray_begin(const KParams& kp, int64_t i, Ray& R, uint32_t* stack)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         R.dirn[a] = dw[a] * inv_n;
-        ou[a] = df_mul(two_sum(o[a], -kp.bmin[a]), kp.inv_ext[a], kp.inv_ext_lo[a]);
-        DF du = df_mul(DF{dw[a], 0.0f}, kp.inv_ext[a], kp.inv_ext_lo[a]);
+        ou[a] = df_mul(two_sum(o[a], -tp.bmin[a]), tp.inv_ext[a], tp.inv_ext_lo[a]);
+        DF du = df_mul(DF{dw[a], 0.0f}, tp.inv_ext[a], tp.inv_ext_lo[a]);
         R.d[a] = du.hi;
         R.dl[a] = du.lo;
     }
@@ -331,7 +362,7 @@ __device__ void ray_begin(const KParams& kp, int64_t i, Ray& R, uint32_t* stack)
 // One cell: segment length, compositing, advance.  Leaves the lane in
 // ST_DESCEND (next cell) or ST_IDLE (ray finished, outputs written).
 template <int K, int PREC, bool TRACE>
-__device__ void leaf_step(const KParams& kp, int64_t i, Ray& R, uint32_t* stack) {
+__device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ray& R, uint32_t* stack) {
     // segment: exit parameter of the current cell along each axis
     const int L = R.level;
     const float size = pow2i(-L);
@@ -362,7 +393,7 @@ __device__ void leaf_step(const KParams& kp, int64_t i, Ray& R, uint32_t* stack)
         if (k < kp.trace_max) {
             size_t o = (size_t)i * kp.trace_max + k;
             kp.tr_leaf[o] = R.entry_x == ENTRY_EMPTY ? -1
-                                                     : __ldg(kp.leaf_ids + (size_t)stack[L - 1] * 8 + R.slot);
+                                                     : __ldg(tp.leaf_ids + (size_t)stack[L - 1] * 8 + R.slot);
             kp.tr_t[2 * o] = R.t.hi;
             kp.tr_t[2 * o + 1] = t1.hi;
         }
@@ -371,7 +402,7 @@ __device__ void leaf_step(const KParams& kp, int64_t i, Ray& R, uint32_t* stack)
 
     // composite the leaf (Eq. 3-5)
     if (R.entry_x != ENTRY_EMPTY) {
-        float sigma = decode_sigma<PREC>(R.entry_y);
+        float sigma = decode_sigma<PREC>(R.entry_y, tp.prec);
         if (sigma < kp.sigma_min) sigma = 0.0f;
         if (sigma > 0.0f) {
             float a = sigma * seg;
@@ -390,11 +421,7 @@ __device__ void leaf_step(const KParams& kp, int64_t i, Ray& R, uint32_t* stack)
             uint32_t rec = R.entry_x & ~LEAF_BIT;
             float cr = 0.0f, cg = 0.0f, cb = 0.0f;
             bool emits = rec != NO_SH_RECORD;
-            if (emits) {
-                float Y[K];
-                sh_basis<K>(R.dirn[0], R.dirn[1], R.dirn[2], Y);
-                sh_eval<K, PREC>(kp.sh + (size_t)rec * kp.sh_stride, R.entry_y, Y, cr, cg, cb);
-            }
+            if (emits) sh_emission<K, PREC>(tp, rec, R.entry_y, R.dirn, cr, cg, cb);
             if (emits || kp.activation != PLO_ACT_RELU) {
                 R.r = __fmaf_rn(w, act_fn(cr, kp.activation, kp.l_max), R.r);
                 R.g = __fmaf_rn(w, act_fn(cg, kp.activation, kp.l_max), R.g);
@@ -408,9 +435,9 @@ __device__ void leaf_step(const KParams& kp, int64_t i, Ray& R, uint32_t* stack)
             }
         }
     }
-    if (R.steps >= kp.max_steps) {
+    if (R.steps >= tp.max_steps) {
         R.status = PLO_RAY_STEP_LIMIT;
-        atomicOr(kp.flags, 1u);
+        atomicOr(tp.flags, 1u);
         ray_store(kp, i, R);
         R.state = ST_IDLE;
         return;
@@ -453,7 +480,8 @@ template <int K, int PREC, bool TRACE>
 __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams kp) {
     // nodes of the top levels, staged once per (persistent) block
     extern __shared__ uint2 s_nodes[];
-    for (int j = threadIdx.x; j < kp.n_top * 8; j += BLOCK) s_nodes[j] = kp.nodes[j];
+    const TreeParams& tp = kp.tree;
+    for (int j = threadIdx.x; j < tp.n_top * 8; j += BLOCK) s_nodes[j] = tp.nodes[j];
     __syncthreads();
 
     uint32_t stack[STACK];  // node id per level of the current cell's path
@@ -478,12 +506,86 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams
             next += __popc(idle);
             if (R.state == ST_IDLE && cand < end) {
                 my = cand;
-                ray_begin<TRACE>(kp, my, R, stack);
+                ray_begin<TRACE>(kp, tp, my, R, stack);
             }
         }
         if (__ballot_sync(0xffffffffu, R.state != ST_IDLE) == 0u) break;
-        if (R.state == ST_LEAF) leaf_step<K, PREC, TRACE>(kp, my, R, stack);
-        if (R.state == ST_DESCEND) descend_step(kp, s_nodes, R, stack);
+        if (R.state == ST_LEAF) leaf_step<K, PREC, TRACE>(kp, tp, my, R, stack);
+        if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
+    }
+}
+
+// ---------------------------------------------------------------- batched render
+// Several luminaires in one launch: rays of tree t occupy [off[t], off[t+1])
+// of one concatenated array.  Persistent warps claim `claim` rays at a time
+// from a global cursor (one queue for all trees, so uneven ray counts
+// balance themselves); lanes refill from the warp's claim as in k_render.
+// Leaf precision and SH degree are read from the tree table per ray.
+constexpr int MAX_BATCH = 16;
+constexpr int BATCH_TOP_NODES = 73;  // levels 0..2 of a full octree
+
+struct BatchParams {
+    KParams base;  // render parameters and outputs (base.tree unused)
+    TreeParams trees[MAX_BATCH];
+    int64_t off[MAX_BATCH + 1];
+    int32_t n_trees;
+    int32_t claim;
+    unsigned long long* cursor;  // zeroed before each launch
+};
+
+__global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(BatchParams bp) {
+    extern __shared__ uint2 s_nodes[];
+    __shared__ TreeParams s_tp[MAX_BATCH];
+    __shared__ long long s_off[MAX_BATCH + 1];
+    if (threadIdx.x < bp.n_trees) s_tp[threadIdx.x] = bp.trees[threadIdx.x];
+    if (threadIdx.x <= bp.n_trees) s_off[threadIdx.x] = bp.off[threadIdx.x];
+    for (int t = 0; t < bp.n_trees; ++t) {
+        const TreeParams& tp = bp.trees[t];
+        for (int j = threadIdx.x; j < tp.n_top * 8; j += BLOCK) s_nodes[tp.s_off + j] = tp.nodes[j];
+    }
+    __syncthreads();
+    const KParams& kp = bp.base;
+    const long long total = s_off[bp.n_trees];
+    uint32_t stack[STACK];
+    const int lane = threadIdx.x & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+
+    Ray R;
+    R.state = ST_IDLE;
+    R.tree = 0;
+    int64_t my = 0;
+    long long next = 0, end = 0;  // the warp's current claim (warp-uniform)
+    bool drained = false;
+    for (;;) {
+        for (;;) {
+            unsigned idle = __ballot_sync(0xffffffffu, R.state == ST_IDLE);
+            if (idle == 0u) break;
+            if (next >= end) {
+                if (drained) break;
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(bp.cursor, (unsigned long long)bp.claim);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if ((long long)base >= total) {
+                    drained = true;
+                    break;
+                }
+                next = (long long)base;
+                end = min((long long)base + bp.claim, total);
+            }
+            const long long cand = next + __popc(idle & lanes_below);
+            next += __popc(idle);
+            if (R.state == ST_IDLE && cand < end) {
+                my = cand;
+                int t = 0;
+                while (t + 1 < bp.n_trees && s_off[t + 1] <= cand) ++t;
+                R.tree = t;
+                ray_begin<false>(kp, s_tp[t], my, R, stack);
+            }
+        }
+        if (__ballot_sync(0xffffffffu, R.state != ST_IDLE) == 0u) break;
+        const TreeParams& tp = s_tp[R.tree];
+        if (R.state == ST_LEAF) leaf_step<0, -1, false>(kp, tp, my, R, stack);
+        if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
     }
 }
 
@@ -561,6 +663,25 @@ cudaError_t dispatch(const plo_tree* t, const KParams& kp, size_t smem, cudaStre
     return cudaErrorInvalidValue;
 }
 
+void fill_tree_params(const plo_tree* t, const plo_render_params* p, TreeParams* tp) {
+    tp->nodes = static_cast<const uint2*>(t->d_nodes);
+    tp->leaf_ids = t->d_leaf_ids;
+    tp->sh = static_cast<const uint8_t*>(t->d_sh);
+    tp->flags = t->d_flags;
+    tp->sh_stride = t->sh_stride;
+    tp->depth = t->depth;
+    tp->n_top = t->n_top;
+    tp->s_off = 0;
+    tp->K = t->K;
+    tp->prec = t->precision;
+    tp->max_steps = p->max_steps > 0 ? p->max_steps : 4 * (1 << t->depth) + 64;
+    for (int a = 0; a < 3; ++a) {
+        tp->bmin[a] = t->bbox_min[a];
+        tp->inv_ext[a] = t->inv_ext[a];
+        tp->inv_ext_lo[a] = t->inv_ext_lo[a];
+    }
+}
+
 plo_status check_params(const plo_render_params* p) {
     if (!p) return set_error(PLO_ERR_INVALID_ARG, "params is NULL");
     if (p->transmittance < PLO_TRANS_EXP || p->transmittance > PLO_TRANS_LINEAR_LITERAL)
@@ -589,29 +710,17 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     if (TRACE && (trace_max <= 0 || !tr_leaf || !tr_t || !tr_count))
         return set_error(PLO_ERR_INVALID_ARG, "trace buffers are NULL or max_cells <= 0");
     KParams kp{};
-    kp.nodes = static_cast<const uint2*>(t->d_nodes);
-    kp.leaf_ids = t->d_leaf_ids;
-    kp.sh = static_cast<const uint8_t*>(t->d_sh);
-    kp.sh_stride = t->sh_stride;
-    kp.depth = t->depth;
-    kp.n_top = t->n_top;
-    for (int a = 0; a < 3; ++a) {
-        kp.bmin[a] = t->bbox_min[a];
-        kp.inv_ext[a] = t->inv_ext[a];
-        kp.inv_ext_lo[a] = t->inv_ext_lo[a];
-    }
+    fill_tree_params(t, p, &kp.tree);
     kp.transmittance = p->transmittance;
     kp.activation = p->activation;
     kp.l_max = p->l_max;
     kp.t_stop = p->t_stop;
     kp.sigma_min = p->sigma_min;
-    kp.max_steps = p->max_steps > 0 ? p->max_steps : 4 * (1 << t->depth) + 64;
     kp.rays = d_rays;
     kp.n = n;
     kp.rgb = d_rgb;
     kp.T = d_T;
     kp.status = d_status;
-    kp.flags = t->d_flags;
     kp.trace_max = trace_max;
     kp.tr_leaf = tr_leaf;
     kp.tr_t = tr_t;
@@ -731,5 +840,231 @@ extern "C" plo_status plo_render_rays_host_noalloc(const plo_tree* tree, const f
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_T, d_T, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "plo_render_rays_host_noalloc");
+    return PLO_OK;
+}
+
+// ---------------------------------------------------------------- batch handle
+struct plo_batch {
+    BatchParams bp;
+    int32_t n_trees;
+    int64_t n_rays;
+    size_t smem;
+    int sm_count;
+    int device;
+    plo_batch_config cfg;
+    int32_t full_top[MAX_BATCH];  // stageable top nodes per tree (<= BATCH_TOP_NODES)
+    unsigned long long* d_cursor;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+void apply_config(plo_batch* b) {
+    int32_t off = 0;
+    for (int t = 0; t < b->n_trees; ++t) {
+        const int32_t n = b->cfg.top_nodes > 0 ? std::min(b->full_top[t], b->cfg.top_nodes) : 0;
+        b->bp.trees[t].n_top = n;
+        b->bp.trees[t].s_off = off;
+        off += n * 8;
+    }
+    b->smem = (size_t)off * sizeof(uint2);
+    b->bp.claim = b->cfg.claim_rays;
+}
+
+cudaError_t launch_batch(plo_batch* b, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_render_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_batch, BLOCK, b->smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int bps = b->cfg.blocks_per_sm > 0 && b->cfg.blocks_per_sm < per_sm ? b->cfg.blocks_per_sm : per_sm;
+    int64_t warps_needed = (b->n_rays + 31) / 32;
+    int64_t grid = std::min<int64_t>((warps_needed + WARPS - 1) / WARPS, (int64_t)b->sm_count * bps);
+    if (grid < 1) return cudaSuccess;
+    e = cudaMemsetAsync(b->d_cursor, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_render_batch<<<(unsigned)grid, BLOCK, b->smem, s>>>(b->bp);
+    return cudaGetLastError();
+}
+
+void set_buffers(plo_batch* b, const float* d_rays, float* d_rgb, float* d_T, int32_t* d_status) {
+    b->bp.base.rays = d_rays;
+    b->bp.base.rgb = d_rgb;
+    b->bp.base.T = d_T;
+    b->bp.base.status = d_status;
+}
+
+void drop_graph(plo_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" plo_status plo_batch_create(const plo_tree* const* trees, int32_t n_trees, const int64_t* ray_offsets,
+                                       const plo_render_params* params, plo_batch** out) {
+    if (!out) return set_error(PLO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!trees || !ray_offsets) return set_error(PLO_ERR_INVALID_ARG, "trees or ray_offsets is NULL");
+    if (n_trees < 1 || n_trees > MAX_BATCH)
+        return set_error(PLO_ERR_INVALID_ARG, "n_trees must be in [1, " + std::to_string(MAX_BATCH) + "]");
+    plo_status st = check_params(params);
+    if (st != PLO_OK) return st;
+    if (ray_offsets[0] != 0) return set_error(PLO_ERR_INVALID_ARG, "ray_offsets[0] must be 0");
+    for (int t = 0; t < n_trees; ++t) {
+        if (!trees[t]) return set_error(PLO_ERR_INVALID_ARG, "a tree is NULL");
+        if (ray_offsets[t + 1] < ray_offsets[t]) return set_error(PLO_ERR_INVALID_ARG, "ray_offsets must not decrease");
+        if (t > 0 && trees[t]->device != trees[0]->device)
+            return set_error(PLO_ERR_INVALID_ARG, "all trees must live on one device");
+    }
+    plo_batch* b = new (std::nothrow) plo_batch();
+    if (!b) return set_error(PLO_ERR_OOM, "host allocation failed");
+    b->n_trees = n_trees;
+    b->n_rays = ray_offsets[n_trees];
+    b->device = trees[0]->device;
+    b->sm_count = trees[0]->sm_count;
+    KParams& kp = b->bp.base;
+    kp.transmittance = params->transmittance;
+    kp.activation = params->activation;
+    kp.l_max = params->l_max;
+    kp.t_stop = params->t_stop;
+    kp.sigma_min = params->sigma_min;
+    kp.n = b->n_rays;
+    for (int t = 0; t < n_trees; ++t) {
+        fill_tree_params(trees[t], params, &b->bp.trees[t]);
+        b->full_top[t] = std::min<int32_t>(trees[t]->n_top, BATCH_TOP_NODES);
+    }
+    for (int t = 0; t <= n_trees; ++t) b->bp.off[t] = ray_offsets[t];
+    b->bp.n_trees = n_trees;
+    b->cfg = {256, 0, BATCH_TOP_NODES};
+    apply_config(b);
+    cudaError_t e = cudaMalloc((void**)&b->d_cursor, 256);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_error(e, "batch cursor allocation");
+    }
+    b->bp.cursor = b->d_cursor;
+    *out = b;
+    return PLO_OK;
+}
+
+extern "C" void plo_batch_free(plo_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    cudaFree(b->d_cursor);
+    delete b;
+}
+
+extern "C" plo_status plo_batch_set_config(plo_batch* b, const plo_batch_config* cfg) {
+    if (!b || !cfg) return set_error(PLO_ERR_INVALID_ARG, "batch or config is NULL");
+    if (cfg->claim_rays < 32 || cfg->claim_rays > (1 << 20) || cfg->claim_rays % 32)
+        return set_error(PLO_ERR_INVALID_ARG, "claim_rays must be a multiple of 32 in [32, 2^20]");
+    if (cfg->blocks_per_sm < 0 || cfg->top_nodes < 0 || cfg->top_nodes > BATCH_TOP_NODES)
+        return set_error(PLO_ERR_INVALID_ARG, "blocks_per_sm must be >= 0, top_nodes in [0, 73]");
+    b->cfg = *cfg;
+    apply_config(b);
+    drop_graph(b);
+    return PLO_OK;
+}
+
+extern "C" plo_status plo_batch_get_config(const plo_batch* b, plo_batch_config* cfg) {
+    if (!b || !cfg) return set_error(PLO_ERR_INVALID_ARG, "batch or config is NULL");
+    *cfg = b->cfg;
+    return PLO_OK;
+}
+
+extern "C" plo_status plo_batch_render(plo_batch* b, const float* d_rays, float* d_rgb, float* d_T,
+                                       int32_t* d_status, void* stream) {
+    if (!b) return set_error(PLO_ERR_INVALID_ARG, "batch is NULL");
+    if (b->n_rays == 0) return PLO_OK;
+    if (!d_rays || !d_rgb || !d_T) return set_error(PLO_ERR_INVALID_ARG, "rays, rgb or T is NULL");
+    set_buffers(b, d_rays, d_rgb, d_T, d_status);
+    cudaError_t e = launch_batch(b, (cudaStream_t)stream);
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "batch render launch");
+}
+
+extern "C" plo_status plo_batch_capture(plo_batch* b, const float* d_rays, float* d_rgb, float* d_T,
+                                        int32_t* d_status, void* stream) {
+    if (!b) return set_error(PLO_ERR_INVALID_ARG, "batch is NULL");
+    if (!d_rays || !d_rgb || !d_T) return set_error(PLO_ERR_INVALID_ARG, "rays, rgb or T is NULL");
+    drop_graph(b);
+    set_buffers(b, d_rays, d_rgb, d_T, d_status);
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_error(e, "capture stream");
+    // the occupancy query and attribute set happen outside the capture
+    e = cudaFuncSetAttribute(k_render_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = launch_batch(b, cs);
+        e = cudaStreamEndCapture(cs, &b->graph);
+        if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    cudaStreamDestroy(cs);
+    (void)stream;
+    if (e != cudaSuccess) {
+        drop_graph(b);
+        return cuda_error(e, "batch graph capture");
+    }
+    return PLO_OK;
+}
+
+extern "C" plo_status plo_batch_replay(plo_batch* b, void* stream) {
+    if (!b) return set_error(PLO_ERR_INVALID_ARG, "batch is NULL");
+    if (!b->exec) return set_error(PLO_ERR_INVALID_ARG, "no captured graph: call plo_batch_capture first");
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "batch graph launch");
+}
+
+extern "C" plo_status plo_batch_autotune(plo_batch* b, const float* d_rays, float* d_rgb, float* d_T, int32_t reps,
+                                         void* stream, plo_batch_config* best_out, float* best_ms) {
+    if (!b || !best_out) return set_error(PLO_ERR_INVALID_ARG, "batch or output is NULL");
+    if (!d_rays || !d_rgb || !d_T) return set_error(PLO_ERR_INVALID_ARG, "rays, rgb or T is NULL");
+    if (reps < 1) reps = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    set_buffers(b, d_rays, d_rgb, d_T, nullptr);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const plo_batch_config saved = b->cfg;
+    plo_batch_config best = saved;
+    float best_t = 1e30f;
+    const int claims[] = {32, 64, 128, 256, 1024};
+    const int bpss[] = {0, 1, 2};
+    const int tops[] = {0, BATCH_TOP_NODES};
+    cudaError_t err = cudaSuccess;
+    for (int ci = 0; ci < 5 && err == cudaSuccess; ++ci)
+        for (int bi = 0; bi < 3 && err == cudaSuccess; ++bi)
+            for (int ti = 0; ti < 2 && err == cudaSuccess; ++ti) {
+                b->cfg = {claims[ci], bpss[bi], tops[ti]};
+                apply_config(b);
+                err = launch_batch(b, s);  // warm-up
+                if (err != cudaSuccess) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && err == cudaSuccess; ++r) err = launch_batch(b, s);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= (float)reps;
+                if (ms < best_t) {
+                    best_t = ms;
+                    best = b->cfg;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cfg = err == cudaSuccess ? best : saved;
+    apply_config(b);
+    drop_graph(b);
+    if (err != cudaSuccess) return cuda_error(err, "batch autotune");
+    *best_out = best;
+    if (best_ms) *best_ms = best_t;
     return PLO_OK;
 }

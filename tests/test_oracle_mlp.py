@@ -161,3 +161,20 @@ def test_distill_constant_field():
     bs[-1][0] = 0.005  # below the 0.01 threshold: everything pruned
     ijk, *_ = mlp.distill_dense(Ws, bs, 3, None)
     assert len(ijk) == 0
+
+
+def test_splitmix64_published_vectors_and_morton():
+    # first two outputs of SplitMix64 seeded with 0 (reference implementation)
+    assert mlp._mix64(0) == 0xE220A8397B1DCDAF
+    assert mlp._mix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
+    # Morton code: brute force over a 4^3 grid against the per-level slots
+    ijk = np.array([[x, y, z] for z in range(4) for y in range(4) for x in range(4)])
+    codes = mlp.morton_code(ijk, 2)
+    for (x, y, z), c in zip(ijk, codes):
+        s0 = (x >> 1) | ((y >> 1) << 1) | ((z >> 1) << 2)
+        s1 = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2)
+        assert c == s0 * 8 + s1
+    assert sorted(codes) == list(range(64))
+    u = mlp.distill_jitter(3, [0, 17], 5)
+    assert u.shape == (2, 5, 3) and np.all((u >= 0) & (u < 1))
+    assert len(np.unique(u)) == u.size
