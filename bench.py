@@ -46,6 +46,11 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1 << 20, help="rays in the oracle's timed sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 8-luminaire batched-render section")
+    ap.add_argument("--learned", action="store_true",
+                    help="run the learned-part experiment (train, distill, error vs ground truth) instead")
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--distill-depth", type=int, default=10)
     return ap.parse_args()
 
 
@@ -157,6 +162,112 @@ def rel_errors(rgb, T, ref):
     return float(e_c.max()), float(e_T.max())
 
 
+def batch_workload(seed: int = 4242, total: int = 12_000_000):
+    """8 luminaires of depth 7-10 with SH degree 2 or 3 and ray counts drawn
+    log-uniform in [1e3, 4e6], rescaled to ~12M in all (clamped to the range)."""
+    import plogen
+    rng = np.random.default_rng(seed)
+    draws = np.exp(rng.uniform(np.log(1e3), np.log(4e6), 8))
+    # rescale to the total, clamping to the range; repeat so that the clamped
+    # entries' excess goes to the others (water-filling)
+    counts = draws.copy()
+    for _ in range(20):
+        free = (counts > 1e3) & (counts < 4e6)
+        fixed = counts[~free].sum()
+        if free.any():
+            counts[free] *= (total - fixed) / counts[free].sum()
+        counts = np.clip(counts, 1e3, 4e6)
+    counts = np.round(counts).astype(np.int64)
+    recs = [plogen.LUMINAIRE_D10.with_(depth=d, sh_degree=2 + (i % 2), seed=1000 + i)
+            for i, d in enumerate([7, 8, 9, 10, 7, 8, 9, 10])]
+    return recs, counts
+
+
+def run_batch(args, plo, torch, W, K):
+    """Batched render of the 8-luminaire workload: one graph-replayed
+    persistent launch (autotuned launch shape) vs 8 separate launches."""
+    import plogen
+    recs, counts = batch_workload()
+    trees, rays = [], []
+    for i, (rec, c) in enumerate(zip(recs, counts)):
+        trees.append(plo.Tree(plogen.luminaire_tree(rec), plo.PREC_FP32))
+        rays.append(plogen.rays_room(int(c), seed=300 + i))
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    n = int(offs[-1])
+    d_rays = torch.from_numpy(np.concatenate(rays)).cuda()
+    rgb = torch.empty((n, 3), device="cuda")
+    T = torch.empty(n, device="cuda")
+    batch = plo.Batch(trees, offs)
+    cfg, src = plo.autotune_cached(batch, f"batch8-{n}", d_rays, rgb, T)
+    batch.capture(d_rays, rgb, T)
+    stream = torch.cuda.current_stream()
+
+    def time_it(fn):
+        for _ in range(W):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(K):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / K
+
+    def separate():
+        for t, (lo, hi) in zip(trees, zip(offs[:-1], offs[1:])):
+            plo.render(t, d_rays[lo:hi], rgb=rgb[lo:hi], T=T[lo:hi])
+
+    ms_batch = time_it(batch.replay)
+    ref_rgb = rgb.clone()
+    ms_sep = time_it(separate)
+    same = bool(torch.equal(rgb, ref_rgb))
+    for t in trees:
+        t.check()
+    return {"workload": "8 luminaires, depth 7-10, SH degree 2/3, ray counts log-uniform 1e3-4e6 rescaled to ~12M",
+            "rays": n, "ray_counts": [int(c) for c in counts],
+            "leaves": [int(t.info()["n_leaves"]) for t in trees],
+            "persistent_graph": {"value": n / ms_batch / 1e3, "unit": UNIT, "ms_per_step": ms_batch,
+                                 "launches_per_step": 1},
+            "separate_launches": {"value": n / ms_sep / 1e3, "unit": UNIT, "ms_per_step": ms_sep,
+                                  "launches_per_step": len(trees)},
+            "speedup": ms_sep / ms_batch, "bitwise_equal": same, "config": cfg, "config_source": src}
+
+
+def run_learned(args):
+    """Train the NeRF-SH network on targets rendered from the depth-6
+    luminaire (4096 rays x 128 samples per step, the paper's loss), distil it
+    into an octree, and state the distilled octree's error against the ground
+    truth next to the untrained network's and an MSE-trained network's."""
+    import torch
+    import paper_2207_05009_gb300 as plo
+    import plogen
+    from paper_2207_05009_gb300 import learned
+    torch.cuda.set_device(0)
+    gt = plo.Tree(plogen.luminaire_tree(plogen.LUMINAIRE_D6))
+    train_b = learned.target_batches(gt, [plogen.rays_sphere(4096, seed=200 + k) for k in range(64)])
+    test_b = learned.target_batches(gt, [plogen.rays_sphere(65536, seed=900)])
+    l_max, c0 = learned.emission_scale(train_b)
+    out = {"metric": "learned luminaire: distilled octree error vs ground truth", "data": "synthetic",
+           "config": {"workload": "depth-6 luminaire targets, 4096 rays x 128 samples per step",
+                      "train_steps": args.train_steps, "distill_depth": args.distill_depth, "l_max": l_max}}
+    flops_step = 4096 * 128 * 2 * 3 * (63 * 256 + 7 * 256 * 256 + 256 * 49)
+    for name, loss, steps in (("paper_loss", plo.LOSS_PAPER, args.train_steps),
+                              ("mse_loss", plo.LOSS_MSE, args.train_steps), ("untrained", plo.LOSS_PAPER, 0)):
+        net, losses, dt = learned.train(train_b, steps, loss, l_max=l_max)
+        res = {"train_s": dt, "ms_per_step": dt / max(steps, 1) * 1e3,
+               "tflops": flops_step * steps / max(dt, 1e-9) / 1e12 if steps else None,
+               "final_loss": float(np.mean(losses[-32:])) if steps else None}
+        for depth in sorted({7, args.distill_depth}):
+            e = learned.distilled_error(net, l_max, test_b, depth=depth)
+            res[f"depth{depth}"] = e.__dict__
+        out[name] = res
+        del net
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_reference(args, world, rank):
     """FP64 oracle on the host cores, on bounded samples of the workload."""
     if rank != 0:
@@ -191,6 +302,8 @@ def run_reference(args, world, rank):
 def main():
     args = parse_args()
     world, rank, local = dist_env()
+    if args.learned:
+        return run_learned(args) if rank == 0 else 0
     if args.impl == "reference":
         return run_reference(args, world, rank)
 
@@ -268,6 +381,9 @@ def main():
             e2e_s = float(tt.item())
         e2e = {"value": world * n * K / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": n * 24,
                "d2h_bytes_per_step": n * 16, "ms_per_step": e2e_s / K * 1e3}
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(args, plo, torch, W, K)
     clocks = sampler.stop()
 
     # FP32 outputs of the last timed pass, for the parity spot check below
@@ -343,6 +459,7 @@ def main():
         "bf16": {k: v for k, v in lines["bf16"].items()},
         "fp16_speedup_vs_fp32": lines["fp16"]["value"] / lines["fp32"]["value"],
         "parity": parity,
+        "batch": batch,
     }
     line["fp16"]["roofline"]["frac"] = line["fp16"]["roofline"]["achieved"] / peak
     print(json.dumps(line), flush=True)

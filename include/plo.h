@@ -341,6 +341,18 @@ plo_status plo_gemm_bf16(const void* d_A, const void* d_B, int32_t M, int32_t N,
 plo_status plo_wgrad_bf16(const void* d_dZ, int32_t n_out, const void* d_H, int32_t n_in, int32_t M, float* d_dW,
                           unsigned int* d_err, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Test hooks for failure detection (nothing here faults or hangs a GPU).
+ * plo_debug_fail_alloc_after(n): the n-th following device allocation made
+ *   by the library fails as out-of-memory (n < 0 turns the hook off).
+ * plo_debug_gemm_stall: launches the tensor-core GEMM (N = 256, K = 64) with
+ *   a producer that issues no loads, so every pipeline wait gives up after
+ *   `wait_limit` polls; the kernel sets bit 1 of *d_err, frees its TMEM and
+ *   returns, leaving the context usable.  Async. */
+void plo_debug_fail_alloc_after(int32_t n);
+plo_status plo_debug_gemm_stall(const void* d_A, const void* d_B, int32_t M, void* d_out, unsigned int* d_err,
+                                uint32_t wait_limit, void* stream);
+
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* plo_last_error(void);
 

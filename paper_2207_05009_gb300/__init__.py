@@ -506,3 +506,22 @@ def autotune_cached(batch: "Batch", key: str, rays, rgb, T, reps: int = 2, path:
         json.dump(cache, f, indent=1)
     os.replace(tmp, path)
     return cfg, "tuned"
+
+
+# ---------------------------------------------------------------- test hooks
+def debug_fail_alloc_after(n: int) -> None:
+    """The n-th following device allocation of the library fails (n < 0: off)."""
+    lib = load()
+    lib.plo_debug_fail_alloc_after.restype = None
+    lib.plo_debug_fail_alloc_after.argtypes = [ctypes.c_int32]
+    lib.plo_debug_fail_alloc_after(n)
+
+
+def debug_gemm_stall(A, B, out, err, wait_limit: int, stream=None):
+    """plo_debug_gemm_stall: a GEMM whose pipeline waits run out."""
+    lib = load()
+    fn = lib.plo_debug_gemm_stall
+    fn.restype = ctypes.c_int32
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_uint32, ctypes.c_void_p]
+    _check(fn(_ptr(A), _ptr(B), A.shape[0], _ptr(out), _ptr(err), wait_limit, _stream(stream)))

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 
 #include "plo_internal.h"
@@ -17,6 +18,24 @@ plo_status set_error(plo_status s, const std::string& msg) {
     return s;
 }
 
+namespace {
+std::atomic<int> g_fail_after{-1};
+}
+
+int dev_malloc(void** p, size_t bytes) {
+    int n = g_fail_after.load();
+    while (n >= 0) {
+        if (g_fail_after.compare_exchange_weak(n, n - 1)) {
+            if (n == 0) {
+                *p = nullptr;
+                return (int)cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return (int)cudaMalloc(p, bytes);
+}
+
 plo_status cuda_error(int err, const char* what) {
     cudaError_t e = static_cast<cudaError_t>(err);
     return set_error(e == cudaErrorMemoryAllocation ? PLO_ERR_OOM : PLO_ERR_CUDA,
@@ -30,6 +49,8 @@ using namespace plo;
 extern "C" const char* plo_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" const char* plo_version(void) { return "plo 0.1.0 (sm_103a)"; }
+
+extern "C" void plo_debug_fail_alloc_after(int32_t n) { g_fail_after.store(n < 0 ? -1 : n); }
 
 // Host-buffer render: chunks of rays alternate between two internal streams,
 // so the host->device copy of one chunk overlaps the render and the

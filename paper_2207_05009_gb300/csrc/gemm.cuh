@@ -45,6 +45,8 @@ struct EpiArgs {
     const __nv_bfloat16* mask;    // [M][ldm] (EPI_MASK_BF16)
     int ldm;
     unsigned int* err;            // device error word (bit 1: GEMM wait timeout)
+    uint32_t wait_limit;          // polls per barrier wait (0: sm100::WAIT_LIMIT)
+    int debug_skip_loads;         // test hook: the producer issues no loads, so the waits run out
 };
 
 __host__ __device__ constexpr int tmem_cols_for(int n) {
@@ -57,12 +59,14 @@ __host__ __device__ constexpr size_t gemm_smem_bytes(int N, int K) {
 struct Ctl {
     uint64_t full[STAGES], empty[STAGES], bfull, tfull[2], tempty[2], drain;
     uint32_t tmem;
+    uint32_t limit;
     int abort;
 };
 
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t ph, Ctl* ctl, unsigned int* err) {
     const uint32_t a = sm100::smem_addr(bar);
-    for (uint32_t it = 0; it < sm100::WAIT_LIMIT; ++it) {
+    const uint32_t limit = ctl->limit;
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -147,6 +151,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         sm100::mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
+        ctl->limit = ep.wait_limit ? ep.wait_limit : sm100::WAIT_LIMIT;
         sm100::fence_mbar_init();
     }
     if (warp == 1) sm100::tmem_alloc(&ctl->tmem, TMEM_COLS);
@@ -156,7 +161,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t tmem = ctl->tmem;
     const int n_tiles = (M + BM - 1) / BM;
 
-    if (warp == 0 && lane == 0) {
+    if (warp == 0 && lane == 0 && !ep.debug_skip_loads) {
         // ---------------- TMA producer
         sm100::prefetch_tmap(&tmA);
         sm100::prefetch_tmap(&tmB);
@@ -301,6 +306,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         sm100::mbar_init(&ctl->tfull[0], 1);
         sm100::mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
+        ctl->limit = sm100::WAIT_LIMIT;
         sm100::fence_mbar_init();
     }
     if (warp == 1) sm100::tmem_alloc(&ctl->tmem, TMEM_COLS);

@@ -613,7 +613,7 @@ plo_status ensure_workspace(plo_mlp* m, int64_t samples, int rays) {
     free_workspace(m);
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) e = (cudaError_t)dev_malloc(p, bytes);
     };
     alloc((void**)&m->H[0], (size_t)samples * PE_PAD * 2);
     for (int l = 1; l < N_LAYERS; ++l) alloc((void**)&m->H[l], (size_t)samples * WIDTH * 2);
@@ -757,7 +757,7 @@ extern "C" plo_status plo_mlp_create(const plo_mlp_desc* desc, uint64_t seed, pl
     const size_t pbytes = (size_t)m->n_params_pad * 4;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) e = (cudaError_t)dev_malloc(p, bytes);
     };
     alloc((void**)&m->master, pbytes);
     alloc((void**)&m->adam_m, pbytes);
@@ -1017,6 +1017,29 @@ extern "C" plo_status plo_gemm_bf16(const void* d_A, const void* d_B, int32_t M,
     return e == cudaSuccess ? PLO_OK : cuda_error(e, "GEMM launch");
 }
 
+// Test hook for failure detection: a GEMM whose producer issues no loads, so
+// that every pipeline wait runs out after `wait_limit` polls; the kernel sets
+// bit 1 of *d_err, frees its TMEM and returns (no trap, the context stays
+// usable).  Same buffers as plo_gemm_bf16 with N = 256, K = 64.
+extern "C" plo_status plo_debug_gemm_stall(const void* d_A, const void* d_B, int32_t M, void* d_out,
+                                          unsigned int* d_err, uint32_t wait_limit, void* stream) {
+    if (!d_A || !d_B || !d_out || !d_err || M <= 0) return set_error(PLO_ERR_INVALID_ARG, "bad argument");
+    CUtensorMap mA, mB;
+    plo_status st = make_map(&mA, d_A, (uint64_t)M, 64, 128);
+    if (st == PLO_OK) st = make_map(&mB, d_B, 256, 64, 256);
+    if (st != PLO_OK) return st;
+    gemm::EpiArgs ep{};
+    ep.out_bf16 = static_cast<__nv_bfloat16*>(d_out);
+    ep.ldo = 256;
+    ep.err = d_err;
+    ep.wait_limit = wait_limit > 0 ? wait_limit : 1;
+    ep.debug_skip_loads = 1;
+    ep.mask = static_cast<const __nv_bfloat16*>(d_out);
+    ep.ldm = 256;
+    cudaError_t e = launch_gemm<256, 64>(mA, mB, ep, gemm::EPI_MASK_BF16, M, sm_count_of_current(), (cudaStream_t)stream);
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "GEMM launch");
+}
+
 extern "C" plo_status plo_wgrad_bf16(const void* d_dZ, int32_t n_out, const void* d_H, int32_t n_in, int32_t M,
                                      float* d_dW, unsigned int* d_err, void* stream) {
     if (!d_dZ || !d_H || !d_dW || !d_err) return set_error(PLO_ERR_INVALID_ARG, "dZ, H, dW or err is NULL");
@@ -1058,9 +1081,9 @@ extern "C" plo_status plo_distill(plo_mlp* m, int32_t depth, int32_t samples, fl
     unsigned long long* d_codes = nullptr;
     float* d_avg = nullptr;
     const int64_t vmax = C / samples > 0 ? C / samples : 1;
-    cudaError_t e = cudaMalloc((void**)&d_flags, (size_t)C);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_codes, (size_t)vmax * 8);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_avg, (size_t)vmax * n_out * 4);
+    cudaError_t e = (cudaError_t)dev_malloc((void**)&d_flags, (size_t)C);
+    if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_codes, (size_t)vmax * 8);
+    if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_avg, (size_t)vmax * n_out * 4);
     std::vector<uint8_t> flags(C);
     std::vector<unsigned long long> codes;
     std::vector<float> vals;

@@ -52,6 +52,10 @@ inline int sh_stride_bytes(int K, int precision) {
 plo_status set_error(plo_status s, const std::string& msg);
 plo_status cuda_error(int err, const char* what);
 
+// Every device allocation of the library goes through here, so that tests
+// can make the n-th one fail (plo_debug_fail_alloc_after).
+int dev_malloc(void** p, size_t bytes);
+
 }  // namespace plo
 
 struct plo_tree {

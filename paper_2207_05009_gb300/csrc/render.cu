@@ -303,11 +303,12 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
         ray_store(kp, i, R);
         return;
     }
-    float inv_n = rsqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
+    const float inv_n = rsqrtf(__fadd_rn(__fadd_rn(__fmul_rn(dw[0], dw[0]), __fmul_rn(dw[1], dw[1])),
+                                         __fmul_rn(dw[2], dw[2])));
     DF ou[3];  // origin in unit-cube coordinates, (o - bmin) / extent in double-float
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        R.dirn[a] = dw[a] * inv_n;
+        R.dirn[a] = __fmul_rn(dw[a], inv_n);
         ou[a] = df_mul(two_sum(o[a], -tp.bmin[a]), tp.inv_ext[a], tp.inv_ext_lo[a]);
         DF du = df_mul(DF{dw[a], 0.0f}, tp.inv_ext[a], tp.inv_ext_lo[a]);
         R.d[a] = du.hi;
@@ -942,7 +943,7 @@ extern "C" plo_status plo_batch_create(const plo_tree* const* trees, int32_t n_t
     b->bp.n_trees = n_trees;
     b->cfg = {256, 0, BATCH_TOP_NODES};
     apply_config(b);
-    cudaError_t e = cudaMalloc((void**)&b->d_cursor, 256);
+    cudaError_t e = (cudaError_t)dev_malloc((void**)&b->d_cursor, 256);
     if (e != cudaSuccess) {
         delete b;
         return cuda_error(e, "batch cursor allocation");

@@ -296,10 +296,11 @@ extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precisio
         return cuda_error(err, "cudaGetDevice");
     }
     size_t sh_alloc = (size_t)(n_sh > 0 ? n_sh : 1) * stride;
-    if ((err = cudaMalloc(&t->d_nodes, (size_t)t->node_bytes)) != cudaSuccess ||
-        (err = cudaMalloc((void**)&t->d_leaf_ids, (size_t)n_packed * 8 * sizeof(int32_t))) != cudaSuccess ||
-        (err = cudaMalloc(&t->d_sh, sh_alloc)) != cudaSuccess ||
-        (err = cudaMalloc((void**)&t->d_flags, 256)) != cudaSuccess) {
+    if ((err = (cudaError_t)dev_malloc(&t->d_nodes, (size_t)t->node_bytes)) != cudaSuccess ||
+        (err = (cudaError_t)dev_malloc((void**)&t->d_leaf_ids, (size_t)n_packed * 8 * sizeof(int32_t))) !=
+            cudaSuccess ||
+        (err = (cudaError_t)dev_malloc(&t->d_sh, sh_alloc)) != cudaSuccess ||
+        (err = (cudaError_t)dev_malloc((void**)&t->d_flags, 256)) != cudaSuccess) {
         plo_tree_free(t);
         cudaGetLastError();
         return err == cudaErrorMemoryAllocation ? set_error(PLO_ERR_OOM, "device allocation for the tree failed")
