@@ -258,9 +258,19 @@ def run_learned(args):
         res = {"train_s": dt, "ms_per_step": dt / max(steps, 1) * 1e3,
                "tflops": flops_step * steps / max(dt, 1e-9) / 1e12 if steps else None,
                "final_loss": float(np.mean(losses[-32:])) if steps else None}
-        for depth in sorted({7, args.distill_depth}):
-            e = learned.distilled_error(net, l_max, test_b, depth=depth)
-            res[f"depth{depth}"] = e.__dict__
+        e7 = learned.distilled_error(net, l_max, test_b, depth=7)
+        res["depth7"] = e7.__dict__
+        # the deepest distillation whose leaf count (predicted from depth 7,
+        # 8x per level) fits comfortably in memory: <= 80M leaves
+        frac = e7.leaves / 8 ** 7
+        depth = args.distill_depth
+        while depth > 7 and frac * 8 ** depth > 80e6:
+            depth -= 1
+        if depth > 7:
+            res[f"depth{depth}"] = learned.distilled_error(net, l_max, test_b, depth=depth).__dict__
+        if depth < args.distill_depth:
+            res["note"] = (f"depth {args.distill_depth} skipped: {frac:.1%} of depth-7 voxels are kept, "
+                           f"~{frac * 8 ** args.distill_depth / 1e6:.0f}M leaves")
         out[name] = res
         del net
         torch.cuda.empty_cache()

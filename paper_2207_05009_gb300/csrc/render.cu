@@ -182,8 +182,15 @@ __device__ __forceinline__ float decode_sigma(uint32_t y, int prec) {
 // the tree when K == 0 (the batch kernel mixes trees).
 template <int K, int PREC>
 __device__ __forceinline__ void sh_emission(const TreeParams& tp, uint32_t rec, uint32_t yword, const float* dirn,
-                                            float& r, float& g, float& b) {
+                                            float& r, float& g, float& b, const float* sY = nullptr) {
     const uint8_t* p = tp.sh + (size_t)rec * tp.sh_stride;
+    if (K > 0 && sY) {
+        float Y[K > 0 ? K : 1];
+#pragma unroll
+        for (int k = 0; k < (K > 0 ? K : 1); ++k) Y[k] = sY[k * BLOCK];
+        sh_eval<(K > 0 ? K : 1), PREC>(p, yword, Y, r, g, b);
+        return;
+    }
     if (K > 0) {
         float Y[K > 0 ? K : 1];
         sh_basis<(K > 0 ? K : 1)>(dirn[0], dirn[1], dirn[2], Y);
@@ -216,6 +223,7 @@ enum : int { ST_IDLE = 0, ST_DESCEND = 1, ST_LEAF = 2 };
 struct Ray {
     DF p[3];
     float d[3], dl[3];  // unit-cube direction as a double-float (dl = 0 for the unit box)
+    float rh[3], rl[3]; // 1/d as a double-float
     float dirn[3];      // normalised world direction for the SH basis
     float T, r, g, b;
     DF od;
@@ -257,6 +265,13 @@ __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* 
             R.entry_x = e.x;
             R.entry_y = e.y;
             R.state = ST_LEAF;
+            // the SH record is read in the next iteration: start pulling it into L2 now
+            const uint32_t rec = e.x & ~LEAF_BIT;
+            if (e.x != ENTRY_EMPTY && rec != NO_SH_RECORD) {
+                const char* a = reinterpret_cast<const char*>(tp.sh) + (size_t)rec * tp.sh_stride;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a + tp.sh_stride - 1));
+            }
             return;
         }
         stack[R.level] = e.x;
@@ -329,6 +344,8 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
         }
         float rh, rl;
         df_recip(R.d[a], R.dl[a], rh, rl);
+        R.rh[a] = rh;
+        R.rl[a] = rl;
         DF t0 = df_mul(df_from_plane(0.0f, ou[a]), rh, rl);
         DF t1 = df_mul(df_from_plane(1.0f, ou[a]), rh, rl);
         if (df_less(t1, t0)) {
@@ -363,7 +380,8 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
 // One cell: segment length, compositing, advance.  Leaves the lane in
 // ST_DESCEND (next cell) or ST_IDLE (ray finished, outputs written).
 template <int K, int PREC, bool TRACE>
-__device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ray& R, uint32_t* stack) {
+__device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ray& R, uint32_t* stack,
+                          const float* sY = nullptr) {
     // segment: exit parameter of the current cell along each axis
     const int L = R.level;
     const float size = pow2i(-L);
@@ -377,9 +395,7 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
         if (R.d[a] == 0.0f) continue;
         float P = (float)(R.c[a] + (R.d[a] > 0.0f ? 1u : 0u)) * size;
         planes[a] = P;
-        float rh, rl;
-        df_recip(R.d[a], R.dl[a], rh, rl);
-        DF v = df_mul(df_from_plane(P, R.p[a]), rh, rl);
+        DF v = df_mul(df_from_plane(P, R.p[a]), R.rh[a], R.rl[a]);
         if (v.hi < 0.0f) v = {0.0f, 0.0f};
         dts[a] = v;
         if (df_less(v, dt)) dt = v;
@@ -422,7 +438,7 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
             uint32_t rec = R.entry_x & ~LEAF_BIT;
             float cr = 0.0f, cg = 0.0f, cb = 0.0f;
             bool emits = rec != NO_SH_RECORD;
-            if (emits) sh_emission<K, PREC>(tp, rec, R.entry_y, R.dirn, cr, cg, cb);
+            if (emits) sh_emission<K, PREC>(tp, rec, R.entry_y, R.dirn, cr, cg, cb, sY);
             if (emits || kp.activation != PLO_ACT_RELU) {
                 R.r = __fmaf_rn(w, act_fn(cr, kp.activation, kp.l_max), R.r);
                 R.g = __fmaf_rn(w, act_fn(cg, kp.activation, kp.l_max), R.g);
@@ -486,6 +502,8 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams
     __syncthreads();
 
     uint32_t stack[STACK];  // node id per level of the current cell's path
+    __shared__ float s_Y[16 * BLOCK];
+    float* sY = s_Y + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
     const int64_t warp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
@@ -508,10 +526,16 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams
             if (R.state == ST_IDLE && cand < end) {
                 my = cand;
                 ray_begin<TRACE>(kp, tp, my, R, stack);
+                if (R.state != ST_IDLE) {
+                    float Y[K];
+                    sh_basis<K>(R.dirn[0], R.dirn[1], R.dirn[2], Y);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) sY[k * BLOCK] = Y[k];
+                }
             }
         }
         if (__ballot_sync(0xffffffffu, R.state != ST_IDLE) == 0u) break;
-        if (R.state == ST_LEAF) leaf_step<K, PREC, TRACE>(kp, tp, my, R, stack);
+        if (R.state == ST_LEAF) leaf_step<K, PREC, TRACE>(kp, tp, my, R, stack, sY);
         if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
     }
 }
@@ -943,7 +967,7 @@ extern "C" plo_status plo_batch_create(const plo_tree* const* trees, int32_t n_t
     b->bp.n_trees = n_trees;
     b->cfg = {256, 0, BATCH_TOP_NODES};
     apply_config(b);
-    cudaError_t e = (cudaError_t)dev_malloc((void**)&b->d_cursor, 256);
+    cudaError_t e = cudaMalloc((void**)&b->d_cursor, 256);
     if (e != cudaSuccess) {
         delete b;
         return cuda_error(e, "batch cursor allocation");
