@@ -49,7 +49,8 @@ class _Tree(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("transmittance", ctypes.c_int32), ("activation", ctypes.c_int32),
-                ("l_max", ctypes.c_double), ("t_stop", ctypes.c_double), ("sigma_min", ctypes.c_double)]
+                ("l_max", ctypes.c_double), ("t_stop", ctypes.c_double), ("sigma_min", ctypes.c_double),
+                ("saturate", ctypes.c_int32), ("proxy", ctypes.c_int32), ("sphere", ctypes.c_double * 4)]
 
 
 def _load():
@@ -86,10 +87,15 @@ class _Bound:
         self.struct = s
 
 
-def _params(transmittance=EXPONENTIAL, activation=RELU, l_max=1.0, t_stop=0.0, sigma_min=0.0):
+def _params(transmittance=EXPONENTIAL, activation=RELU, l_max=1.0, t_stop=0.0, sigma_min=0.0, saturate=False,
+            sphere=None):
+    """sphere = (cx, cy, cz, radius) in world units selects the sphere proxy."""
     p = _Params()
     p.transmittance, p.activation = transmittance, activation
     p.l_max, p.t_stop, p.sigma_min = l_max, t_stop, sigma_min
+    p.saturate = int(bool(saturate))
+    p.proxy = 0 if sphere is None else 1
+    p.sphere[:] = (0.0, 0.0, 0.0, 0.0) if sphere is None else tuple(float(v) for v in sphere)
     return p
 
 
@@ -121,7 +127,7 @@ def lookup(tree, pts, dirs=None):
 
 
 def render(tree, rays, transmittance=EXPONENTIAL, activation=RELU, l_max=1.0, t_stop=0.0, sigma_min=0.0,
-           n_threads: int = 0) -> dict:
+           saturate=False, sphere=None, n_threads: int = 0) -> dict:
     """Exact FP64 render of float32 rays [n,6].  Returns a dict of arrays:
     rgb [n,3], T [n], bound [n,3] (per-channel error scale), cond [n,3]
     (sensitivity to optical-depth errors), n_leaf, n_sh,
@@ -134,7 +140,7 @@ def render(tree, rays, transmittance=EXPONENTIAL, activation=RELU, l_max=1.0, t_
     out = {"rgb": np.zeros((n, 3)), "T": np.ones(n), "bound": np.zeros((n, 3)), "cond": np.zeros((n, 3)),
            "n_leaf": np.zeros(n, np.int32), "n_sh": np.zeros(n, np.int32), "n_cell": np.zeros(n, np.int32),
            "status": np.zeros(n, np.int32)}
-    p = _params(transmittance, activation, l_max, t_stop, sigma_min)
+    p = _params(transmittance, activation, l_max, t_stop, sigma_min, saturate, sphere)
     lib.oracle_render(ctypes.byref(b.struct), rays.ctypes.data, n, ctypes.byref(p),
                       *(out[k].ctypes.data for k in ("rgb", "T", "bound", "cond", "n_leaf", "n_sh", "n_cell",
                                                       "status")),

@@ -35,7 +35,13 @@
  *     the root box is closed;
  *   - after a segment, the exit coordinate(s) are snapped to the exact plane;
  *   - early stop: after a segment, stop if T < t_stop or T <= 0;
- *   - sigma < sigma_min is treated as zero density (Sec. 6.2 heuristic).
+ *   - sigma < sigma_min is treated as zero density, and with `saturate` a ray
+ *     whose final T is below t_stop counts as opaque (T = 0): the sigma_min /
+ *     alpha_max heuristics of Sec. 6 ("Performance vs Quality"), with
+ *     t_stop = 1 - alpha_max;
+ *   - proxy geometry (Sec. 5, "a sphere or a box"): the box is the tree's
+ *     bounding box; a sphere proxy restricts the integral to the part of the
+ *     ray inside both the box and the ball.
  */
 #include <math.h>
 #include <stdint.h>
@@ -61,6 +67,9 @@ typedef struct {
     double l_max;
     double t_stop;
     double sigma_min;
+    int32_t saturate;      /* 1: T = 0 when the final T < t_stop */
+    int32_t proxy;         /* 0 box, 1 sphere */
+    double sphere[4];      /* sphere proxy: centre xyz and radius, world units */
 } oracle_params;
 
 #define OR_PI 3.14159265358979323846
@@ -220,6 +229,24 @@ static void render_one(const oracle_tree* t, const oracle_params* prm, const flo
         if (t1 < tf) tf = t1;
     }
     if (!(tn < tf) || !(tf > 0.0)) return;
+    if (prm->proxy == 1) {
+        /* |o + t d - c|^2 = r^2 in unit-cube coordinates (the box is a cube,
+         * so the ball stays a ball) */
+        double c[3], b = 0.0, a2 = 0.0, q = 0.0;
+        const double r = prm->sphere[3] / ext[0];
+        for (int a = 0; a < 3; ++a) {
+            c[a] = (prm->sphere[a] - t->bbox_min[a]) / ext[a];
+            a2 += d[a] * d[a];
+            b += (o[a] - c[a]) * d[a];
+            q += (o[a] - c[a]) * (o[a] - c[a]);
+        }
+        double disc = b * b - a2 * (q - r * r);
+        if (!(disc > 0.0)) return;
+        double ts0 = (-b - sqrt(disc)) / a2, ts1 = (-b + sqrt(disc)) / a2;
+        if (ts0 > tn) tn = ts0;
+        if (ts1 < tf) tf = ts1;
+        if (!(tn < tf) || !(tf > 0.0)) return;
+    }
 
     double Y[16];
     oracle_sh_basis(t->sh_degree, dw[0], dw[1], dw[2], Y);
@@ -325,6 +352,7 @@ static void render_one(const oracle_tree* t, const oracle_params* prm, const flo
             }
         }
     }
+    if (prm->saturate && T < prm->t_stop) T = 0.0;
     res->T = T;
 }
 

@@ -10,7 +10,7 @@ import pytest
 import oracle
 import plogen
 from plogen import HostTree
-from tests.trees import cartesian_table, chord, midpoint_quadrature, random_tree, uniform_tree
+from tests.trees import ball_chord, cartesian_table, chord, midpoint_quadrature, random_tree, uniform_tree
 
 EXP, LIN, LIT = oracle.EXPONENTIAL, oracle.LINEAR, oracle.LINEAR_LITERAL
 
@@ -277,3 +277,97 @@ def test_corner_rays_match_midpoint_quadrature():
         rgb, T = midpoint_quadrature(tree, r, 2.5e-4)
         scale = max(np.abs(out["rgb"][i]).max(), 1e-3)
         assert np.abs(rgb - out["rgb"][i]).max() / scale < 3e-3
+
+
+# ---------------------------------------------------------------- proxy sphere and the paper's
+# render heuristics (Sec. 5 proxy geometry; Sec. 6 sigma_min / alpha_max)
+
+@pytest.mark.parametrize("model", [EXP, LIN])
+def test_sphere_proxy_uniform_closed_form(model):
+    rng = np.random.default_rng(21)
+    c = coeffs9(rng)
+    sigma = float(np.float32(2.3))
+    tree = uniform_tree(2, sigma, c)
+    centre, radius = (0.5, 0.47, 0.53), 0.41
+    rays = plogen.rays_sphere(256, seed=22)
+    inside = np.concatenate([rng.uniform(0.3, 0.7, (32, 3)), rng.normal(size=(32, 3))], 1)
+    inside[:, 3:] /= np.linalg.norm(inside[:, 3:], axis=1, keepdims=True)
+    rays = np.concatenate([rays, inside.astype(np.float32)])
+    out = oracle.render(tree, rays, transmittance=model, sphere=(*centre, radius))
+    assert np.all(out["status"] == 0)
+    hits = 0
+    for i, r in enumerate(rays):
+        ch = ball_chord(r[:3], r[3:], centre, radius)  # the ball lies inside the cube
+        L = 0.0 if ch is None else ch[1] - ch[0]
+        hits += L > 0
+        T = math.exp(-sigma * L) if model == EXP else max(0.0, 1.0 - sigma * L)
+        assert out["T"][i] == pytest.approx(T, rel=1e-10, abs=1e-13)
+        np.testing.assert_allclose(out["rgb"][i], emission(c, r[3:]) * (1 - T), rtol=1e-10, atol=1e-12)
+    assert hits > 100
+
+
+def test_sphere_enclosing_the_box_changes_nothing():
+    tree = plogen.luminaire_tree(plogen.LUMINAIRE_D6)
+    rays = plogen.rays_sphere(2048, seed=23)
+    a = oracle.render(tree, rays)
+    b = oracle.render(tree, rays, sphere=(0.5, 0.5, 0.5, 0.87))  # sqrt(3)/2 < 0.87
+    for k in ("rgb", "T", "n_cell"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_sphere_proxy_cut_matches_midpoint_quadrature():
+    # a ball that cuts through cells: brute force restricted to the ball
+    rng = np.random.default_rng(24)
+    tree = random_tree(3, rng, sigma_range=(0.1, 8.0))
+    ball = ((0.45, 0.55, 0.5), 0.33)
+    rays = plogen.rays_sphere(24, seed=25, radius=2.0)
+    out = oracle.render(tree, rays, sphere=(*ball[0], ball[1]))
+    errs = np.zeros((len(rays), 2))
+    for i, r in enumerate(rays):
+        for j, h in enumerate((1e-3, 2.5e-4)):
+            rgb, T = midpoint_quadrature(tree, r, h, ball=ball)
+            scale = max(1.0, np.abs(rgb).max())
+            errs[i, j] = max(np.abs(rgb - out["rgb"][i]).max() / scale, abs(T - out["T"][i]))
+    # midpoint errors are O(h) but not monotone ray by ray
+    assert errs[:, 1].max() < 2e-3, errs
+    assert errs[:, 1].mean() < 0.6 * errs[:, 0].mean(), errs.mean(0)
+
+
+def test_saturation_sets_T_to_zero_after_early_stop():
+    rng = np.random.default_rng(26)
+    c1, c2 = coeffs9(rng), coeffs9(rng)
+    s1, s2 = 6.0, float(np.float32(0.4))  # T after the first half: e^-3 < 0.1
+    tree = two_stack_tree(s1, c1, s2, c2)
+    e1 = math.exp(-s1 * 0.5)
+    up = np.array([[0.3, 0.7, -1.0, 0, 0, 1]], np.float32)
+    down = np.array([[0.3, 0.7, 2.0, 0, 0, -1]], np.float32)
+    plain = oracle.render(tree, up, t_stop=0.1)
+    sat = oracle.render(tree, up, t_stop=0.1, saturate=True)
+    np.testing.assert_allclose(sat["rgb"][0], emission(c1, (0, 0, 1)) * (1 - e1), rtol=1e-12)
+    np.testing.assert_array_equal(sat["rgb"], plain["rgb"])
+    assert plain["T"][0] == pytest.approx(e1, rel=1e-13)
+    assert sat["T"][0] == 0.0 and sat["n_leaf"][0] == 1
+    # a ray that never gets below t_stop keeps its T
+    e2 = math.exp(-s2 * 0.5)
+    sat = oracle.render(tree, down, t_stop=e2 * 0.5, saturate=True)
+    full = oracle.render(tree, down)
+    assert sat["T"][0] == pytest.approx(e2 * e1, rel=1e-13) or sat["T"][0] == 0.0
+    assert sat["T"][0] == 0.0  # e2 * e1 < e2 / 2: saturated after the second leaf
+    np.testing.assert_array_equal(sat["rgb"], full["rgb"])
+    sat = oracle.render(tree, down, t_stop=1e-3, saturate=True)
+    assert sat["T"][0] == pytest.approx(e2 * e1, rel=1e-13)
+
+
+def test_sphere_proxy_world_bbox():
+    c = coeffs9(np.random.default_rng(27))
+    tree = uniform_tree(2, 0.3, c)
+    tree.bbox_min, tree.bbox_max = (-1.0, -2.0, 0.0), (3.0, 2.0, 4.0)
+    centre, radius = (1.2, -0.3, 2.1), 1.6
+    rays = plogen.rays_sphere(128, seed=28, radius=9.0, center=(1.0, 0.0, 2.0))
+    out = oracle.render(tree, rays, sphere=(*centre, radius))
+    for i, r in enumerate(rays):
+        ch = ball_chord(r[:3], r[3:], centre, radius)
+        L = 0.0 if ch is None else ch[1] - ch[0]
+        T = math.exp(-float(np.float32(0.3)) * L)
+        assert out["T"][i] == pytest.approx(T, rel=1e-11)
+        np.testing.assert_allclose(out["rgb"][i], emission(c, r[3:]) * (1 - T), rtol=1e-10, atol=1e-13)

@@ -198,13 +198,37 @@ def brute_force_cells(boxes, P, d):
     return np.argmax(ok, axis=1)
 
 
-def midpoint_quadrature(tree, ray, h, model="exp", act="relu", l_max=1.0):
+def ball_chord(o, d, centre, radius):
+    """[t0, t1] of the ray o + t d (any |d|) inside the ball, from the impact
+    parameter: the closest approach t_m = (c - o).d / |d|^2 and the half chord
+    sqrt(r^2 - h^2) / |d|.  None for a miss."""
+    o, d, c = (np.asarray(v, np.float64) for v in (o, d, centre))
+    dd = float(d @ d)
+    tm = float((c - o) @ d) / dd
+    h2 = float(np.sum((o + tm * d - c) ** 2))
+    if h2 >= radius * radius:
+        return None
+    s = math.sqrt(radius * radius - h2) / math.sqrt(dd)
+    t0, t1 = tm - s, tm + s
+    if t1 <= max(t0, 0.0):
+        return None
+    return max(t0, 0.0), t1
+
+
+def midpoint_quadrature(tree, ray, h, model="exp", act="relu", l_max=1.0, ball=None):
     """Brute-force Riemann sum of Eq. 3 along one ray: midpoint samples of
     step ~h, the cell of each sample found by box membership, Phi from the
     Cartesian SH table, transmittance from the running sum of sigma h
-    (exponential, or the literal linear form of Eq. 4).  Returns (rgb, T)."""
+    (exponential, or the literal linear form of Eq. 4).  `ball` = (centre,
+    radius) restricts the integral to the part of the ray inside the ball.
+    Returns (rgb, T)."""
     o, d = np.asarray(ray[:3], np.float64), np.asarray(ray[3:], np.float64)
     ch = chord(o, d)
+    if ch is not None and ball is not None:
+        bc = ball_chord(o, d, *ball)
+        ch = None if bc is None else (max(ch[0], bc[0]), min(ch[1], bc[1]))
+        if ch is not None and ch[1] <= ch[0]:
+            ch = None
     if ch is None:
         return np.zeros(3), 1.0
     t0, t1 = ch
