@@ -15,7 +15,10 @@ matrix products are the only library primitive.  Follows:
   - Adam with the learning rate decaying exponentially from 5e-4 to 5e-6
     (Sec. 4.4);
   - distillation (Sec. 5, "Creating the plenoctree"): centre sample of each
-    voxel, prune sigma < threshold, average jittered samples in kept voxels.
+    voxel, prune sigma < threshold, average jittered samples in kept voxels;
+  - the paper's full setup (Sec. 4.2-4.4): the extra 128-wide SH output
+    layer, coarse and fine networks, fine samples placed by the coarse
+    weights, loss L_c + L_f + L_alpha.
 
 The SH basis is the oracle's own (``oracle.sh_basis``, Legendre recursion).
 """
@@ -215,6 +218,143 @@ def train_loss_and_grads(Ws, bs, rays, jitter, C_gt, alpha_gt, l_max_scale, l_ma
     draw = composite_backward(cache, dC / R, dA / R).reshape(R * N, -1)
     dWs, dbs = backward(Ws, H, draw)
     return loss, dWs, dbs, dict(C=C, alpha=alpha, raw=raw, draw=draw, X=X)
+
+
+# ---------------------------------------------------------------- the paper's full training setup
+# Sec. 4.2 "Network architecture": the 8 x 256 trunk with "an extra output
+# layer of 128 neurons" returning the 3 (l_max+1)^2 SH coefficients; sigma is
+# read linearly from the trunk.  Sec. 4.3 / 4.4: a coarse and a fine network,
+# N_c = 64 stratified samples for the coarse one and N_f = 128 more, placed
+# by the coarse weights, for the fine one; loss L_c + L_f + L_alpha.
+
+FEAT = 128
+
+
+def layer_shapes_paper(l_max: int = 3):
+    """[(out, in)]: 8 trunk layers, then sigma (1 x 256), the 128-wide
+    feature layer (128 x 256) and the SH layer (3K x 128)."""
+    K = (l_max + 1) ** 2
+    return [(WIDTH, PE_DIM)] + [(WIDTH, WIDTH)] * (DEPTH - 1) + [(1, WIDTH), (FEAT, WIDTH), (3 * K, FEAT)]
+
+
+def init_params_paper(rng: np.random.Generator, l_max: int = 3):
+    Ws, bs = [], []
+    for (o, i) in layer_shapes_paper(l_max):
+        lim = math.sqrt(6.0 / i)
+        Ws.append(rng.uniform(-lim, lim, (o, i)))
+        bs.append(np.zeros(o))
+    return Ws, bs
+
+
+def forward_paper(Ws, bs, X):
+    """Trunk, then raw sigma = W_s h8 + b_s and SH = W_c ReLU(W_f h8 + b_f) + b_c.
+    Returns (raw [M, 1 + 3K] with sigma first, activations [X, h1..h8, feat])."""
+    H = [X]
+    h = X
+    for l in range(DEPTH):
+        h = np.maximum(h @ Ws[l].T + bs[l], 0.0)
+        H.append(h)
+    sig = h @ Ws[DEPTH].T + bs[DEPTH]
+    feat = np.maximum(h @ Ws[DEPTH + 1].T + bs[DEPTH + 1], 0.0)
+    H.append(feat)
+    sh = feat @ Ws[DEPTH + 2].T + bs[DEPTH + 2]
+    return np.concatenate([sig, sh], axis=1), H
+
+
+def backward_paper(Ws, H, draw):
+    """Parameter gradients of forward_paper given d loss / d raw."""
+    n = DEPTH + 3
+    dWs, dbs = [None] * n, [None] * n
+    dsig, dsh = draw[:, :1], draw[:, 1:]
+    h8, feat = H[DEPTH], H[DEPTH + 1]
+    dWs[DEPTH + 2] = dsh.T @ feat
+    dbs[DEPTH + 2] = dsh.sum(0)
+    gf = (dsh @ Ws[DEPTH + 2]) * (feat > 0)
+    dWs[DEPTH + 1] = gf.T @ h8
+    dbs[DEPTH + 1] = gf.sum(0)
+    dWs[DEPTH] = dsig.T @ h8
+    dbs[DEPTH] = dsig.sum(0)
+    g = gf @ Ws[DEPTH + 1] + dsig @ Ws[DEPTH]
+    for l in range(DEPTH - 1, -1, -1):
+        g = g * (H[l + 1] > 0)
+        dWs[l] = g.T @ H[l]
+        dbs[l] = g.sum(0)
+        g = g @ Ws[l]
+    return dWs, dbs
+
+
+FINE_FLOOR = 1e-5
+
+
+def fine_samples(t, delta, w, xi):
+    """N_f samples per ray from the coarse pass.  Coarse sample i owns the
+    segment [t_i, t_i + delta_i); the density is constant on each segment
+    and its mass there is proportional to w_i + 1e-5 (the floor keeps
+    the density defined where the coarse weights vanish).  Stratified
+    u_j = (j + xi_j) / N_f is mapped through the inverse CDF:
+    t = t_i + (u - C_i) / (C_{i+1} - C_i) * delta_i for C_i <= u < C_{i+1}.
+    t, delta, w [R, N_c]; xi [R, N_f] in [0, 1).  Returns t_fine [R, N_f]
+    (ascending in j)."""
+    R, Nc = t.shape
+    Nf = xi.shape[1]
+    m = w + FINE_FLOOR
+    C = np.concatenate([np.zeros((R, 1)), np.cumsum(m, axis=1)], axis=1)
+    C = C / C[:, -1:]
+    u = (np.arange(Nf)[None, :] + xi) / Nf
+    out = np.empty((R, Nf))
+    for r in range(R):
+        i = np.searchsorted(C[r], u[r], side="right") - 1
+        i = np.clip(i, 0, Nc - 1)
+        frac = (u[r] - C[r, i]) / (C[r, i + 1] - C[r, i])
+        out[r] = t[r, i] + frac * delta[r, i]
+    return out
+
+
+def merge_samples(t_coarse, t_fine, t1):
+    """Union of the coarse and fine parameters per ray in ascending order,
+    with delta_j = t_{j+1} - t_j and the last segment ending at t1."""
+    t = np.sort(np.concatenate([t_coarse, t_fine], axis=1), axis=1, kind="stable")
+    nxt = np.concatenate([t[:, 1:], t1[:, None]], axis=1)
+    return t, nxt - t
+
+
+def train_loss_and_grads_hier(Wc, bc, Wf, bf, rays, jitter, xi, C_gt, alpha_gt, l_max_scale, l_max=3,
+                              transmittance="exp", arch="paper", denoms=(None, None), t_fine=None):
+    """One batch of the paper's training (Eq. finaloss): coarse colour loss
+    L_c on N_c stratified samples (jitter [R, N_c]), fine colour loss L_f
+    and alpha loss L_alpha on the coarse plus N_f fine samples (xi [R, N_f]).
+    No gradient flows through the sample placement.  `denoms` overrides the
+    held-constant loss denominators (coarse, fine); `t_fine` overrides the
+    fine samples (to hold them fixed).  Returns (mean loss, (dWc, dbc),
+    (dWf, dbf), extras)."""
+    fwd, bwd = (forward_paper, backward_paper) if arch == "paper" else (forward, backward)
+    R, Nc = jitter.shape
+    d = rays[:, 3:].astype(np.float64)
+    o = rays[:, :3].astype(np.float64)
+    Y = sh_matrix(d, l_max)
+    t, delta, x, hit = stratified_samples(rays, jitter)
+    raw_c, Hc = fwd(Wc, bc, positional_encoding(x.reshape(R * Nc, 3)))
+    raw_c = raw_c.reshape(R, Nc, -1)
+    C_c, a_c, cache_c = composite(raw_c, delta, Y, l_max_scale, transmittance)
+    per_c, dC_c, _ = loss_terms(C_c, a_c, C_gt, alpha_gt, l_max_scale, "reg", denom=denoms[0])
+    t0, t1, _ = clip_unit_cube(o, d)
+    t1 = np.where(hit, t1, 0.0)
+    tf = fine_samples(t, delta, cache_c["w"], xi) if t_fine is None else t_fine
+    ta, da = merge_samples(t, tf, t1)
+    da = np.where(hit[:, None], da, 0.0)
+    N = ta.shape[1]
+    xa = o[:, None, :] + ta[..., None] * d[:, None, :]
+    raw_f, Hf = fwd(Wf, bf, positional_encoding(xa.reshape(R * N, 3)))
+    raw_f = raw_f.reshape(R, N, -1)
+    C_f, a_f, cache_f = composite(raw_f, da, Y, l_max_scale, transmittance)
+    per_f, dC_f, dA_f = loss_terms(C_f, a_f, C_gt, alpha_gt, l_max_scale, "paper", denom=denoms[1])
+    loss = (per_c + per_f).mean()
+    draw_c = composite_backward(cache_c, dC_c / R, np.zeros(R)).reshape(R * Nc, -1)
+    draw_f = composite_backward(cache_f, dC_f / R, dA_f / R).reshape(R * N, -1)
+    gc = bwd(Wc, Hc, draw_c)
+    gf = bwd(Wf, Hf, draw_f)
+    return loss, gc, gf, dict(C_c=C_c, C_f=C_f, alpha_f=a_f, t_fine=tf, t_all=ta, delta_all=da,
+                              w_c=cache_c["w"], loss_c=per_c.mean(), loss_f=per_f.mean())
 
 
 def lr_at(step: int, total: int, lr0=5e-4, lr1=5e-6) -> float:

@@ -178,3 +178,178 @@ def test_splitmix64_published_vectors_and_morton():
     u = mlp.distill_jitter(3, [0, 17], 5)
     assert u.shape == (2, 5, 3) and np.all((u >= 0) & (u < 1))
     assert len(np.unique(u)) == u.size
+
+
+# ---------------------------------------------------------------- the paper's full training setup
+# (Sec. 4.2 extra 128-wide output layer; Sec. 4.3-4.4 coarse/fine networks)
+
+def _paper_nets(seed, l_max=3):
+    rng = np.random.default_rng(seed)
+    nets = []
+    for _ in range(2):
+        Ws, bs = mlp.init_params_paper(rng, l_max)
+        Ws = [w * 0.5 for w in Ws]
+        bs = [rng.normal(0, 0.05, b.shape) for b in bs]
+        bs[mlp.DEPTH][0] = 1.0  # sigma bias: a visible density
+        nets.append((Ws, bs))
+    return nets
+
+
+def test_paper_head_shapes_and_forward_by_hand():
+    (Ws, bs), _ = _paper_nets(0)
+    assert [w.shape for w in Ws][-3:] == [(1, 256), (128, 256), (48, 128)]
+    X = np.random.default_rng(1).normal(size=(5, 63))
+    raw, H = mlp.forward_paper(Ws, bs, X)
+    h = X
+    for l in range(8):
+        h = np.maximum(Ws[l] @ h.T + bs[l][:, None], 0).T
+    feat = np.maximum(h @ Ws[9].T + bs[9], 0)
+    np.testing.assert_allclose(raw[:, 0], h @ Ws[8][0] + bs[8][0], rtol=1e-12)
+    np.testing.assert_allclose(raw[:, 1:], feat @ Ws[10].T + bs[10], rtol=1e-12, atol=1e-12)
+
+
+def test_fine_samples_uniform_weights_closed_form():
+    R, Nc, Nf = 3, 64, 128
+    rays = plogen.rays_sphere(R, seed=5)
+    t, delta, _, hit = mlp.stratified_samples(rays, np.zeros((R, Nc)))  # evenly spaced
+    assert hit.all()
+    xi = np.random.default_rng(2).random((R, Nf))
+    tf = mlp.fine_samples(t, delta, np.full((R, Nc), 0.3), xi)
+    t0, t1 = t[:, :1], (t[:, -1] + delta[:, -1])[:, None]
+    u = (np.arange(Nf)[None] + xi) / Nf
+    np.testing.assert_allclose(tf, t0 + u * (t1 - t0), rtol=1e-12, atol=1e-12)
+
+
+def test_fine_samples_match_bisection_of_the_cdf():
+    rng = np.random.default_rng(3)
+    R, Nc, Nf = 4, 16, 40
+    t = np.sort(rng.uniform(1, 3, (R, Nc)), 1)
+    delta = np.concatenate([np.diff(t, axis=1), rng.uniform(0.01, 0.2, (R, 1))], 1)
+    w = rng.random((R, Nc)) ** 3
+    w[:, 5] = 0.0
+    xi = rng.random((R, Nf))
+    tf = mlp.fine_samples(t, delta, w, xi)
+    for r in range(R):
+        m = w[r] + 1e-5
+        m = m / m.sum()
+
+        def cdf(x):  # mass below x: piecewise-linear inside each segment
+            inside = np.clip((x - t[r]) / delta[r], 0.0, 1.0)
+            return float((m * inside).sum())
+        for j in range(Nf):
+            u = (j + xi[r, j]) / Nf
+            lo, hi = t[r, 0], t[r, -1] + delta[r, -1]
+            for _ in range(80):
+                mid = 0.5 * (lo + hi)
+                lo, hi = (mid, hi) if cdf(mid) < u else (lo, mid)
+            assert tf[r, j] == pytest.approx(0.5 * (lo + hi), abs=1e-10)
+    assert np.all(np.diff(tf, axis=1) >= 0)
+
+
+def test_fine_samples_counts_follow_the_weights():
+    # stratified draws (one per stratum of width 1/N_f) put N_f m_i +- 2 samples in segment i
+    rng = np.random.default_rng(4)
+    R, Nc, Nf = 6, 64, 128
+    t = np.cumsum(rng.uniform(0.01, 0.03, (R, Nc)), 1)
+    delta = np.concatenate([np.diff(t, axis=1), np.full((R, 1), 0.02)], 1)
+    w = rng.random((R, Nc)) ** 4
+    tf = mlp.fine_samples(t, delta, w, rng.random((R, Nf)))
+    for r in range(R):
+        m = (w[r] + 1e-5) / (w[r] + 1e-5).sum()
+        seg = np.searchsorted(t[r], tf[r], side="right") - 1
+        counts = np.bincount(seg, minlength=Nc)
+        assert np.all(np.abs(counts - Nf * m) < 2.0)
+
+
+def test_merge_is_sorted_and_tiles_the_chord():
+    rng = np.random.default_rng(5)
+    R = 4
+    rays = plogen.rays_sphere(R, seed=6)
+    t, delta, _, hit = mlp.stratified_samples(rays, rng.random((R, 64)))
+    tf = mlp.fine_samples(t, delta, rng.random((R, 64)), rng.random((R, 128)))
+    t1 = t[:, -1] + delta[:, -1]
+    ta, da = mlp.merge_samples(t, tf, t1)
+    assert ta.shape == (R, 192)
+    assert np.all(np.diff(ta, axis=1) >= 0) and np.all(da >= 0)
+    np.testing.assert_allclose(ta[:, 0] + da.sum(1), t1, rtol=1e-12)
+    for r in range(R):
+        np.testing.assert_array_equal(np.sort(np.concatenate([t[r], tf[r]])), ta[r])
+
+
+def test_hier_loss_constant_field_closed_form():
+    # zero weights: sigma and the SH sum are the biases everywhere, so both
+    # passes see a uniform medium: alpha = 1 - exp(-sigma L), C = Phi alpha
+    R, l_max = 5, 3
+    K = (l_max + 1) ** 2
+    Ws = [np.zeros(s) for s in mlp.layer_shapes_paper(l_max)]
+    bs = [np.zeros(s[0]) for s in mlp.layer_shapes_paper(l_max)]
+    rng = np.random.default_rng(6)
+    bs[8][0] = 2.5
+    bs[10][:] = rng.normal(0, 1, 3 * K)
+    rays = plogen.rays_sphere(R, seed=7)
+    Lm = 4.0
+    C_gt, a_gt = rng.uniform(0, 3, (R, 3)), rng.random(R)
+    jit = rng.random((R, 64))
+    loss, _, _, ex = mlp.train_loss_and_grads_hier(Ws, bs, Ws, bs, rays, jit, rng.random((R, 128)), C_gt, a_gt, Lm)
+    t, _, _, _ = mlp.stratified_samples(rays, jit)
+    d = rays[:, 3:].astype(np.float64)
+    ref = 0.0
+    for r in range(R):
+        # both passes integrate from the first coarse sample to the exit
+        # (the fine samples are drawn inside the coarse segments)
+        ch = chord(rays[r, :3], rays[r, 3:])
+        L = 0.0 if ch is None else ch[1] - t[r, 0]
+        alpha = 1 - math.exp(-2.5 * L)
+        Y = oracle.sh_basis(l_max, d[r] / np.linalg.norm(d[r]))
+        phi = Lm / (1 + np.exp(-(bs[10].reshape(3, K) @ Y)))
+        C = phi * alpha
+        np.testing.assert_allclose(ex["C_c"][r], C, rtol=1e-12)
+        np.testing.assert_allclose(ex["C_f"][r], C, rtol=1e-12)
+        assert ex["alpha_f"][r] == pytest.approx(alpha, rel=1e-12)
+        cn, gn = C / Lm, C_gt[r] / Lm
+        col = (((cn - gn) / (cn + 0.01)) ** 2).sum()
+        ref += 2 * col + (alpha - a_gt[r]) ** 2
+    assert loss == pytest.approx(ref / R, rel=1e-12)
+
+
+@pytest.mark.parametrize("seed,trans", [(1, "exp"), (2, "exp"), (3, "linear")])
+def test_hier_gradients_match_central_differences(seed, trans):
+    (Wc, bc), (Wf, bf) = _paper_nets(seed)
+    R = 4
+    rng = np.random.default_rng(seed + 100)
+    rays = plogen.rays_sphere(R, seed=seed + 60)
+    jit, xi = rng.random((R, 8)), rng.random((R, 16))
+    C_gt, a_gt = rng.uniform(0, 5, (R, 3)), rng.uniform(0, 1, R)
+    Lm = 6.0
+    loss0, (dWc, dbc), (dWf, dbf), ex = mlp.train_loss_and_grads_hier(Wc, bc, Wf, bf, rays, jit, xi, C_gt, a_gt, Lm,
+                                                                     transmittance=trans)
+    den = (ex["C_c"] / Lm + 0.01, ex["C_f"] / Lm + 0.01)
+    tf = ex["t_fine"]
+
+    def part(which, Wc2, bc2, Wf2, bf2):
+        ex2 = mlp.train_loss_and_grads_hier(Wc2, bc2, Wf2, bf2, rays, jit, xi, C_gt, a_gt, Lm, transmittance=trans,
+                                            denoms=den, t_fine=tf)[3]
+        return ex2["loss_c"] if which == "c" else ex2["loss_f"]
+
+    checks = 0
+    for which, Ws, bs, dWs, dbs in (("c", Wc, bc, dWc, dbc), ("f", Wf, bf, dWf, dbf)):
+        for l in [0, 7, 8, 9, 10]:
+            scale = float(np.sqrt((dWs[l] ** 2).mean())) + 1e-300
+            done = tries = 0
+            while done < 2 and tries < 40:
+                tries += 1
+                i, j = rng.integers(0, Ws[l].shape[0]), rng.integers(0, Ws[l].shape[1])
+
+                def f(h, i=i, j=j, l=l):
+                    W2 = [w.copy() for w in Ws]
+                    W2[l][i, j] += h
+                    args = (W2, bs, Wf, bf) if which == "c" else (Wc, bc, W2, bs)
+                    return part(which, *args)
+                f1 = (f(1e-5) - f(-1e-5)) / 2e-5
+                f2 = (f(5e-6) - f(-5e-6)) / 1e-5
+                if abs(f1 - f2) > 1e-4 * abs(f1) + 1e-6 * scale:
+                    continue
+                assert dWs[l][i, j] == pytest.approx(f1, rel=1e-4, abs=1e-5 * scale), (which, l, i, j)
+                done += 1
+                checks += 1
+    assert checks == 20
