@@ -47,10 +47,13 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 8-luminaire batched-render section")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the linear / sigma_min-alpha_max / sphere-proxy timings")
     ap.add_argument("--learned", action="store_true",
                     help="run the learned-part experiment (train, distill, error vs ground truth) instead")
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--distill-depth", type=int, default=10)
+    ap.add_argument("--no-hier", action="store_true", help="--learned: skip the coarse/fine arm")
     return ap.parse_args()
 
 
@@ -234,11 +237,47 @@ def run_batch(args, plo, torch, W, K):
             "speedup": ms_sep / ms_batch, "bitwise_equal": same, "config": cfg, "config_source": src}
 
 
+def run_variants(plo, torch, tree32, rays, rgb, T, timed, rays_total):
+    """Speed and error of the paper's render options on the same rays (FP32
+    leaves): the linear transmittance model (Sec. 6.2 "Transmittance model"),
+    the sigma_min = 0.1 / alpha_max = 0.9 heuristics (Sec. 6.2 "Performance vs
+    Quality") and a sphere proxy around the luminaire (Sec. 5).  Errors are
+    against the exact render with the box proxy and the same transmittance."""
+    def outputs(params):
+        plo.render(tree32, rays, params, rgb=rgb, T=T)
+        return rgb.clone(), T.clone()
+
+    def err(a, b):
+        (c, t), (c0, t0) = a, b
+        d = (c - c0).double()
+        return {"rel_l2_radiance": float(d.norm() / c0.double().norm().clamp_min(1e-300)),
+                "alpha_rmse": float((t - t0).double().pow(2).mean().sqrt()),
+                "max_abs_alpha": float((t - t0).abs().max())}
+
+    P = plo.RenderParams
+    cases = {"exp": P(), "linear": P(transmittance=plo.TRANS_LINEAR),
+             "exp_heuristics": P.paper_heuristics(),
+             "linear_heuristics": P.paper_heuristics(transmittance=plo.TRANS_LINEAR),
+             "exp_sphere_r0.5": P(sphere=(0.5, 0.5, 0.5, 0.5))}
+    exact = {"exp": outputs(cases["exp"]), "linear": outputs(cases["linear"])}
+    out = {}
+    for name, p in cases.items():
+        total, per_launch = timed(tree32, p)
+        base = "linear" if p.transmittance == plo.TRANS_LINEAR else "exp"
+        out[name] = {"value": rays_total / (total / 1e3) / 1e6, "unit": UNIT, "kernel_ms": per_launch,
+                     "error_vs_exact": err(outputs(p), exact[base])}
+    out["linear_speedup_vs_exp"] = out["linear"]["value"] / out["exp"]["value"]
+    out["heuristics_speedup_exp"] = out["exp_heuristics"]["value"] / out["exp"]["value"]
+    return out
+
+
 def run_learned(args):
     """Train the NeRF-SH network on targets rendered from the depth-6
     luminaire (4096 rays x 128 samples per step, the paper's loss), distil it
     into an octree, and state the distilled octree's error against the ground
-    truth next to the untrained network's and an MSE-trained network's."""
+    truth next to the untrained network's, an MSE-trained network's, and the
+    paper's full setup (coarse/fine networks with the 128-wide SH layer,
+    64 + 128 samples, distilled from the fine network)."""
     import torch
     import paper_2207_05009_gb300 as plo
     import plogen
@@ -251,12 +290,24 @@ def run_learned(args):
     out = {"metric": "learned luminaire: distilled octree error vs ground truth", "data": "synthetic",
            "config": {"workload": "depth-6 luminaire targets, 4096 rays x 128 samples per step",
                       "train_steps": args.train_steps, "distill_depth": args.distill_depth, "l_max": l_max}}
-    flops_step = 4096 * 128 * 2 * 3 * (63 * 256 + 7 * 256 * 256 + 256 * 49)
-    for name, loss, steps in (("paper_loss", plo.LOSS_PAPER, args.train_steps),
-                              ("mse_loss", plo.LOSS_MSE, args.train_steps), ("untrained", plo.LOSS_PAPER, 0)):
-        net, losses, dt = learned.train(train_b, steps, loss, l_max=l_max)
+    trunk = 63 * 256 + 7 * 256 * 256
+    flops_step = 4096 * 128 * 2 * 3 * (trunk + 256 * 49)
+    # coarse (64 samples) + fine (64 + 128 samples) with the 128-wide SH layer
+    flops_hier = 4096 * (64 + 192) * 2 * 3 * (trunk + 256 + 256 * 128 + 128 * 48)
+    arms = [("paper_loss", plo.LOSS_PAPER, args.train_steps), ("mse_loss", plo.LOSS_MSE, args.train_steps),
+            ("untrained", plo.LOSS_PAPER, 0)]
+    if not args.no_hier:
+        arms.insert(1, ("paper_setup_coarse_fine", "hier", args.train_steps))
+    for name, loss, steps in arms:
+        if loss == "hier":
+            coarse, net, losses, dt = learned.train_hier(train_b, steps, l_max=l_max)
+            del coarse
+            fl = flops_hier
+        else:
+            net, losses, dt = learned.train(train_b, steps, loss, l_max=l_max)
+            fl = flops_step
         res = {"train_s": dt, "ms_per_step": dt / max(steps, 1) * 1e3,
-               "tflops": flops_step * steps / max(dt, 1e-9) / 1e12 if steps else None,
+               "tflops": fl * steps / max(dt, 1e-9) / 1e12 if steps else None,
                "final_loss": float(np.mean(losses[-32:])) if steps else None}
         e7 = learned.distilled_error(net, l_max, test_b, depth=7)
         res["depth7"] = e7.__dict__
@@ -345,7 +396,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def timed(tr):
+    def timed(tr, params=params):
         for _ in range(W):
             plo.render(tr, rays, params, rgb=rgb, T=T)
         barrier()
@@ -372,6 +423,8 @@ def main():
     res = {}
     for name in ("fp32", "fp16", "bf16"):
         res[name] = timed(trees[name])
+    variants = None if args.no_variants else run_variants(plo, torch, trees["fp32"], rays, rgb, T, timed,
+                                                          world * n * K)
     e2e = None
     if not args.no_e2e:
         rays_h = torch.from_numpy(rays_np).pin_memory()
@@ -470,6 +523,7 @@ def main():
         "fp16_speedup_vs_fp32": lines["fp16"]["value"] / lines["fp32"]["value"],
         "parity": parity,
         "batch": batch,
+        "variants": variants,
     }
     line["fp16"]["roofline"]["frac"] = line["fp16"]["roofline"]["achieved"] / peak
     print(json.dumps(line), flush=True)

@@ -56,6 +56,11 @@ enum { PLO_TRANS_EXP = 0, PLO_TRANS_LINEAR = 1, PLO_TRANS_LINEAR_LITERAL = 2 };
 /* Emission activation S of Eq. 6: max(0, x), or l_max * sigmoid(x). */
 enum { PLO_ACT_RELU = 0, PLO_ACT_SIGMOID = 1 };
 
+/* Proxy geometry (Sec. 5: the luminaire is attached to a sphere or a box).
+ * BOX integrates over the part of the ray inside the tree's bounding box;
+ * SPHERE over the part inside both that box and the ball `sphere`. */
+enum { PLO_PROXY_BOX = 0, PLO_PROXY_SPHERE = 1 };
+
 /* Per-ray status codes written to the optional d_status arrays. */
 enum { PLO_RAY_OK = 0, PLO_RAY_STEP_LIMIT = 1, PLO_RAY_INVALID = 3 };
 
@@ -84,13 +89,21 @@ typedef struct {
     float bbox_max[3];
 } plo_tree_desc;
 
-/* Render parameters.
+/* Render parameters.  Zero-initialised fields give the exact integral over
+ * the proxy box with exponential transmittance and max(0, .) emission.
  *   transmittance  PLO_TRANS_*          activation  PLO_ACT_*
  *   l_max          scale of the sigmoid activation (Eq. 6); ignored for RELU
  *   t_stop         stop a ray once T < t_stop after a leaf (0 = never early;
  *                  alpha_max of Sec. 6.2 is t_stop = 1 - alpha_max)
  *   sigma_min      leaves with sigma < sigma_min count as empty (Sec. 6.2)
- *   max_steps      per-ray cap on cells visited; 0 = 4 * 2^depth + 64 */
+ *   max_steps      per-ray cap on cells visited; 0 = 4 * 2^depth + 64
+ *   saturate       1: a ray whose final T is below t_stop counts as opaque and
+ *                  returns T = 0 (the "saturated" ray of Sec. 6.2); 0: it
+ *                  returns the T it reached
+ *   proxy          PLO_PROXY_BOX or PLO_PROXY_SPHERE
+ *   sphere         sphere proxy centre xyz and radius (world space, radius
+ *                  > 0); ignored for PLO_PROXY_BOX.  Not supported by the
+ *                  batch entry points (their luminaires use their boxes). */
 typedef struct {
     int32_t transmittance;
     int32_t activation;
@@ -98,6 +111,9 @@ typedef struct {
     float t_stop;
     float sigma_min;
     int32_t max_steps;
+    int32_t saturate;
+    int32_t proxy;
+    float sphere[4];
 } plo_render_params;
 
 typedef struct {
@@ -130,7 +146,7 @@ void plo_tree_free(plo_tree* tree);
 
 plo_status plo_tree_get_info(const plo_tree* tree, plo_tree_info* out);
 
-/* Renders n rays (async).  Per ray, paper Eq. 3-5: clip to the proxy box,
+/* Renders n rays (async).  Per ray, paper Eq. 3-5: clip to the proxy,
  * walk the octree front to back over exact per-leaf segments, evaluate the
  * leaf's SH emission in the ray direction, composite emission/absorption.
  *   d_rays    float [n][6]: origin xyz, direction xyz (world space; the
@@ -245,14 +261,24 @@ plo_status plo_tree_check(const plo_tree* tree, void* stream);
  *
  * Network: positional encoding of the sample position x in the unit cube,
  * gamma(x) = [x, sin(2^j pi x), cos(2^j pi x)]_{j<10} (63 features), eight
- * fully connected layers of 256 with ReLU, and a linear head to sigma_raw
- * and 3 (l_max+1)^2 SH coefficients (channel-major).  sigma = ReLU(raw);
- * emission = l_max * sigmoid(sum_k c_k Y_k(d)) (Eq. 6).  BF16 weights and
- * activations, FP32 accumulation on the tensor cores, FP32 master weights.
- * Parameters are exchanged in the canonical FP32 order: for each layer
- * W [out][in] then b [out], layers 1..9 (in: 63, 256 x 7, 256; out: 256 x 8,
- * 1 + 3K).  Rays for training are given in the unit cube (the proxy box). */
+ * fully connected layers of 256 with ReLU (the trunk), then the output
+ * layers of the chosen architecture:
+ *   PLO_ARCH_LINEAR_HEAD  one linear layer 256 -> 1 + 3K (sigma_raw, SH);
+ *   PLO_ARCH_PAPER        "an extra output layer of 128 neurons" (Sec. 4.2):
+ *                         sigma_raw = w_s . h8 + b_s and
+ *                         SH = W_c ReLU(W_f h8 + b_f) + b_c (128 -> 3K).
+ * sigma = ReLU(sigma_raw); emission = l_max * sigmoid(sum_k c_k Y_k(d))
+ * (Eq. 6); SH coefficients channel-major.  BF16 weights and activations,
+ * FP32 accumulation on the tensor cores, FP32 master weights.  Parameters
+ * are exchanged in a canonical FP32 order of (W [out][in], b [out]) blocks:
+ * the trunk's 8 layers (in 63, then 256), then LINEAR_HEAD: the head
+ * (1 + 3K x 256); PAPER: sigma (1 x 256), the 128-wide layer (128 x 256),
+ * the SH layer (3K x 128).  Rays for training are given in the unit cube
+ * (the proxy box). */
 typedef struct plo_mlp plo_mlp;
+
+/* Output architecture (plo_mlp_desc.arch). */
+enum { PLO_ARCH_LINEAR_HEAD = 0, PLO_ARCH_PAPER = 1 };
 
 /* Loss of Sec. 4.3 on values divided by l_max: PAPER = sum over channels of
  * ((C^ - C) / (C^ + eps))^2 (denominator held constant) + (alpha^ - alpha)^2
@@ -268,19 +294,22 @@ typedef struct {
     float eps;              /* loss regulariser, 0.01 in the paper                 */
     float lr0, lr1;         /* exponential decay lr0 -> lr1 (5e-4 -> 5e-6)         */
     float init_radiance;    /* emission the network starts from (0: l_max / 2)     */
-    int32_t reserved;       /* must be 0                                           */
+    int32_t arch;           /* PLO_ARCH_LINEAR_HEAD or PLO_ARCH_PAPER               */
     uint64_t seed;          /* stream of the stratified-sampling and distillation
                                jitter                                              */
 } plo_mlp_desc;
 
-/* Number of parameters of the network for SH degree `sh_degree`. */
+/* Number of parameters of the network for SH degree `sh_degree`:
+ * plo_mlp_param_count for PLO_ARCH_LINEAR_HEAD; _arch for either (-1 for an
+ * unknown arch). */
 int64_t plo_mlp_param_count(int32_t sh_degree);
+int64_t plo_mlp_param_count_arch(int32_t sh_degree, int32_t arch);
 
 /* Creates the network on the current device.  Initial parameters (drawn
- * from `seed`): He-uniform hidden weights and zero hidden biases; the head's
- * weights He-uniform scaled by 0.1, sigma bias 0.5 (every sample starts with
- * positive density), and the DC SH bias of each channel set so that the
- * emission starts at init_radiance.  Starting at l_max / 2 against HDR
+ * from `seed`): He-uniform hidden weights and zero hidden biases; the
+ * weights that produce sigma and SH He-uniform scaled by 0.1, sigma bias 0.5
+ * (every sample starts with positive density), and the DC SH bias of each
+ * channel set so that the emission starts at init_radiance.  Starting at l_max / 2 against HDR
  * targets far below l_max, the first updates drive sigma below zero
  * everywhere and the ReLU keeps it there. */
 plo_status plo_mlp_create(const plo_mlp_desc* desc, uint64_t seed, plo_mlp** out);
@@ -309,6 +338,37 @@ plo_status plo_mlp_forward(plo_mlp* mlp, const float* d_points, int64_t n, float
 plo_status plo_mlp_train_step(plo_mlp* mlp, const float* d_rays, const float* d_rgb_gt, const float* d_alpha_gt,
                               int32_t n_rays, int32_t n_samples, const float* d_jitter, float* d_loss_out,
                               void* stream);
+
+/* One step of the paper's coarse/fine training (Sec. 4.3-4.4, Eq. 7) on two
+ * networks with the same l_max, transmittance and loss (async):
+ *   coarse: n_coarse stratified samples (jitter as in plo_mlp_train_step),
+ *           loss L_c = the colour term (PAPER trains the coarse network with
+ *           REG; MSE and REG train both networks with that loss);
+ *   fine:   the coarse samples plus n_fine samples drawn from the coarse
+ *           weights: coarse sample i owns [t_i, t_{i+1}) (the last one ends
+ *           at the exit), the density is constant there with mass
+ *           proportional to w_i + 1e-5, and u_j = (j + xi_j) / n_fine goes
+ *           through the inverse CDF; the network is trained on all
+ *           n_coarse + n_fine samples in ascending order with L_f + L_alpha.
+ * No gradient flows through the placement.  Each network takes one Adam
+ * step.  n_coarse, n_fine multiples of 32, n_coarse <= 128, n_coarse +
+ * n_fine in {64, 96, 128, 192, 256} (the paper: 64 + 128); n_rays *
+ * n_coarse a multiple of 128.  d_xi float [n_rays][n_fine] in [0,1), or NULL
+ * to draw it from the fine network's seed.  d_loss_out float [1]: mean over
+ * rays of L_c + L_f + L_alpha before the updates. */
+plo_status plo_mlp_train_step_hier(plo_mlp* coarse, plo_mlp* fine, const float* d_rays, const float* d_rgb_gt,
+                                   const float* d_alpha_gt, int32_t n_rays, int32_t n_coarse, int32_t n_fine,
+                                   const float* d_jitter, const float* d_xi, float* d_loss_out, void* stream);
+
+/* The fine-sample placement of plo_mlp_train_step_hier alone (async), for
+ * testing: given the coarse parameters d_t, lengths d_delta and weights d_w
+ * (float [n_rays][n_coarse]) and d_xi (float [n_rays][n_fine]), writes the
+ * merged parameters d_t_out and lengths d_delta_out (float [n_rays][n_coarse
+ * + n_fine], ascending; the last length ends where the ray leaves the unit
+ * cube, 0 for rays that miss it). */
+plo_status plo_hier_samples(const float* d_rays, int32_t n_rays, int32_t n_coarse, int32_t n_fine, const float* d_t,
+                            const float* d_delta, const float* d_w, const float* d_xi, float* d_t_out,
+                            float* d_delta_out, void* stream);
 
 /* Distils the network into a plenoctree (Sec. 5, "Creating the plenoctree";
  * synchronous).  Every voxel of the 2^depth grid (depth 1..10) is evaluated

@@ -203,12 +203,14 @@ def composite_backward(cache, dC, dA):
 
 
 def train_loss_and_grads(Ws, bs, rays, jitter, C_gt, alpha_gt, l_max_scale, l_max=3, kind="paper",
-                         transmittance="exp", denom=None):
-    """One training batch: returns (mean loss, dWs, dbs, extras)."""
+                         transmittance="exp", denom=None, arch="linear"):
+    """One training batch: returns (mean loss, dWs, dbs, extras).  arch:
+    'linear' (linear head) or 'paper' (the 128-wide SH layer)."""
+    fwd, bwd = (forward_paper, backward_paper) if arch == "paper" else (forward, backward)
     t, delta, x, hit = stratified_samples(rays, jitter)
     R, N = jitter.shape
     X = positional_encoding(x.reshape(R * N, 3))
-    raw, H = forward(Ws, bs, X)
+    raw, H = fwd(Ws, bs, X)
     raw = raw.reshape(R, N, -1)
     d = rays[:, 3:].astype(np.float64)
     Y = sh_matrix(d, l_max)
@@ -216,7 +218,7 @@ def train_loss_and_grads(Ws, bs, rays, jitter, C_gt, alpha_gt, l_max_scale, l_ma
     per_ray, dC, dA = loss_terms(C, alpha, C_gt, alpha_gt, l_max_scale, kind, denom=denom)
     loss = per_ray.mean()
     draw = composite_backward(cache, dC / R, dA / R).reshape(R * N, -1)
-    dWs, dbs = backward(Ws, H, draw)
+    dWs, dbs = bwd(Ws, H, draw)
     return loss, dWs, dbs, dict(C=C, alpha=alpha, raw=raw, draw=draw, X=X)
 
 

@@ -17,11 +17,12 @@ from . import _build
 
 __all__ = ["PloError", "Tree", "RenderParams", "load", "render", "render_host", "lookup", "trace",
            "PREC_FP32", "PREC_FP16", "PREC_BF16", "TRANS_EXP", "TRANS_LINEAR", "TRANS_LINEAR_LITERAL",
-           "ACT_RELU", "ACT_SIGMOID"]
+           "ACT_RELU", "ACT_SIGMOID", "PROXY_BOX", "PROXY_SPHERE"]
 
 PREC_FP32, PREC_FP16, PREC_BF16 = 0, 1, 2
 TRANS_EXP, TRANS_LINEAR, TRANS_LINEAR_LITERAL = 0, 1, 2
 ACT_RELU, ACT_SIGMOID = 0, 1
+PROXY_BOX, PROXY_SPHERE = 0, 1
 RAY_OK, RAY_STEP_LIMIT, RAY_INVALID = 0, 1, 3
 
 STATUS_NAMES = {0: "PLO_OK", -1: "PLO_ERR_INVALID_ARG", -2: "PLO_ERR_BAD_TREE", -3: "PLO_ERR_OOM",
@@ -45,7 +46,8 @@ class TreeDesc(ctypes.Structure):
 class _RenderParams(ctypes.Structure):
     _fields_ = [("transmittance", ctypes.c_int32), ("activation", ctypes.c_int32),
                 ("l_max", ctypes.c_float), ("t_stop", ctypes.c_float), ("sigma_min", ctypes.c_float),
-                ("max_steps", ctypes.c_int32)]
+                ("max_steps", ctypes.c_int32), ("saturate", ctypes.c_int32), ("proxy", ctypes.c_int32),
+                ("sphere", ctypes.c_float * 4)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -63,12 +65,27 @@ class RenderParams:
     t_stop: float = 0.0
     sigma_min: float = 0.0
     max_steps: int = 0
+    saturate: bool = False
+    sphere: tuple | None = None  # (cx, cy, cz, radius) selects the sphere proxy
 
     def _c(self) -> _RenderParams:
         p = _RenderParams()
         p.transmittance, p.activation = self.transmittance, self.activation
         p.l_max, p.t_stop, p.sigma_min, p.max_steps = self.l_max, self.t_stop, self.sigma_min, self.max_steps
+        p.saturate = int(bool(self.saturate))
+        p.proxy = PROXY_BOX if self.sphere is None else PROXY_SPHERE
+        if self.sphere is not None:
+            p.sphere[:] = tuple(float(v) for v in self.sphere)
         return p
+
+    @classmethod
+    def paper_heuristics(cls, **kw) -> "RenderParams":
+        """sigma_min = 0.1 and alpha_max = 0.9 (t_stop = 0.1, saturated rays
+        opaque), the values Sec. 6.2 sets empirically."""
+        kw.setdefault("sigma_min", 0.1)
+        kw.setdefault("t_stop", 0.1)
+        kw.setdefault("saturate", True)
+        return cls(**kw)
 
 
 _lib = None
@@ -261,19 +278,23 @@ def trace(tree: Tree, rays, max_cells: int, params: RenderParams | None = None, 
 
 # ---------------------------------------------------------------- learned part
 LOSS_PAPER, LOSS_REG, LOSS_MSE = 0, 1, 2
+ARCH_LINEAR_HEAD, ARCH_PAPER = 0, 1
 
 
 class MlpDesc(ctypes.Structure):
     _fields_ = [("sh_degree", ctypes.c_int32), ("transmittance", ctypes.c_int32), ("loss", ctypes.c_int32),
                 ("total_steps", ctypes.c_int32), ("l_max", ctypes.c_float), ("eps", ctypes.c_float),
                 ("lr0", ctypes.c_float), ("lr1", ctypes.c_float), ("init_radiance", ctypes.c_float),
-                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("arch", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 def _load_mlp_sigs(lib):
     P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     sigs = {
         "plo_mlp_param_count": (I64, [I32]),
+        "plo_mlp_param_count_arch": (I64, [I32, I32]),
+        "plo_mlp_train_step_hier": (I32, [P, P, P, P, P, I32, I32, I32, P, P, P, P]),
+        "plo_hier_samples": (I32, [P, I32, I32, I32, P, P, P, P, P, P, P]),
         "plo_mlp_create": (I32, [P, ctypes.c_uint64, P]),
         "plo_mlp_free": (None, [P]),
         "plo_mlp_set_params": (I32, [P, P, I64]),
@@ -305,16 +326,17 @@ class Mlp:
 
     def __init__(self, l_max: float, loss: int = LOSS_PAPER, transmittance: int = TRANS_EXP, total_steps: int = 1000,
                  lr0: float = 5e-4, lr1: float = 5e-6, eps: float = 0.01, seed: int = 1, jitter_seed: int = 2,
-                 init_radiance: float = 0.0):
+                 init_radiance: float = 0.0, arch: int = ARCH_LINEAR_HEAD):
         lib = mlp_lib()
         d = MlpDesc()
         d.sh_degree, d.transmittance, d.loss, d.total_steps = 3, transmittance, loss, total_steps
         d.l_max, d.eps, d.lr0, d.lr1, d.seed = l_max, eps, lr0, lr1, jitter_seed
-        d.init_radiance, d.reserved = init_radiance, 0
+        d.init_radiance, d.arch = init_radiance, arch
         h = ctypes.c_void_p()
         _check(lib.plo_mlp_create(ctypes.byref(d), seed, ctypes.byref(h)))
         self._h = h
-        self.n_params = int(lib.plo_mlp_param_count(3))
+        self.arch = arch
+        self.n_params = int(lib.plo_mlp_param_count_arch(3, arch))
 
     @property
     def handle(self):
@@ -350,6 +372,17 @@ class Mlp:
 
     def check(self, stream=None):
         _check(mlp_lib().plo_mlp_check(self._h, _stream(stream)))
+
+    @staticmethod
+    def train_step_hier(coarse: "Mlp", fine: "Mlp", rays, rgb_gt, alpha_gt, n_coarse: int = 64, n_fine: int = 128,
+                        jitter=None, xi=None, loss_out=None, stream=None):
+        """plo_mlp_train_step_hier: one coarse/fine step (Sec. 4.3-4.4)."""
+        import torch
+        loss_out = loss_out if loss_out is not None else torch.empty(1, device=rays.device, dtype=torch.float32)
+        _check(mlp_lib().plo_mlp_train_step_hier(coarse._h, fine._h, _ptr(rays), _ptr(rgb_gt), _ptr(alpha_gt),
+                                                 rays.shape[0], n_coarse, n_fine, _ptr(jitter), _ptr(xi),
+                                                 _ptr(loss_out), _stream(stream)))
+        return loss_out
 
     def distill(self, depth: int, samples: int = 8, sigma_thresh: float = 0.01, precision: int = PREC_FP32,
                 stream=None) -> "Tree":
@@ -389,6 +422,19 @@ def gemm_bf16(A, B, epilogue: int, bias=None, mask=None, out=None, err=None, str
     _check(mlp_lib().plo_gemm_bf16(_ptr(A), _ptr(B), M, N, K, epilogue, _ptr(bias), _ptr(mask), _ptr(out), _ptr(err),
                                    _stream(stream)))
     return out, err
+
+
+def hier_samples(rays, t, delta, w, xi, stream=None):
+    """plo_hier_samples: merged coarse + fine parameters and lengths
+    ([n_rays][n_coarse + n_fine]) for coarse t, delta, w and fine xi."""
+    import torch
+    n, nc = t.shape
+    nf = xi.shape[1]
+    t_out = torch.empty((n, nc + nf), device=t.device, dtype=torch.float32)
+    d_out = torch.empty_like(t_out)
+    _check(mlp_lib().plo_hier_samples(_ptr(rays), n, nc, nf, _ptr(t), _ptr(delta), _ptr(w), _ptr(xi), _ptr(t_out),
+                                      _ptr(d_out), _stream(stream)))
+    return t_out, d_out
 
 
 def wgrad_bf16(dZ, H, dW, err=None, stream=None):

@@ -3,7 +3,8 @@
 // 128-byte-swizzled shared memory.
 //
 // k_gemm:  C[M][N] = A[M][K] * B[N][K]^T  (both K-major), fused epilogue:
-//          bias + ReLU -> bf16, bias -> fp32, or (x mask>0) -> bf16.
+//          bias + ReLU -> bf16, bias -> fp32, (x mask>0) -> bf16, or a split
+//          (columns below `split`: bias + ReLU -> bf16; the rest: bias -> fp32).
 //          Persistent CTAs; B (the weights, N*K*2 <= 128 KB) stays resident
 //          in shared memory; A streams through a 4-stage ring of 128x64
 //          tiles; two TMEM accumulators let the epilogue of one 128-row tile
@@ -35,15 +36,19 @@ constexpr int BK = 64;  // one 128-byte swizzle row of bf16
 constexpr int STAGES = 4;
 constexpr int A_STAGE_BYTES = BM * BK * 2;  // 16 KB
 
-enum Epi : int { EPI_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK_BF16 = 2 };
+enum Epi : int { EPI_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK_BF16 = 2, EPI_SPLIT = 3 };
 
 struct EpiArgs {
-    const float* bias;            // [N] (EPI_RELU_BF16, EPI_BIAS_F32)
+    const float* bias;            // [N] (EPI_RELU_BF16, EPI_BIAS_F32, EPI_SPLIT)
     __nv_bfloat16* out_bf16;      // [M][ldo]
-    float* out_f32;               // [M][ldo]
+    float* out_f32;               // [M][ldo] (EPI_BIAS_F32); [M][ldo2] columns >= split (EPI_SPLIT)
     int ldo;
     const __nv_bfloat16* mask;    // [M][ldm] (EPI_MASK_BF16)
     int ldm;
+    int split;                    // EPI_SPLIT: first fp32 column (a multiple of 32)
+    int ldo2;                     // EPI_SPLIT: row stride of out_f32
+    const float* col0_add;        // EPI_BIAS_F32: added to column 0 of each row (nullable)
+    int ld_col0;                  // row stride of col0_add
     unsigned int* err;            // device error word (bit 1: GEMM wait timeout)
     uint32_t wait_limit;          // polls per barrier wait (0: sm100::WAIT_LIMIT)
     int debug_skip_loads;         // test hook: the producer issues no loads, so the waits run out
@@ -84,17 +89,21 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t ph, Ctl* c
 template <int N>
 __device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int row, int M, int col, const float* v) {
     if (row >= M) return;
-    if (epi == EPI_BIAS_F32) {
-        float4* dst = reinterpret_cast<float4*>(ep.out_f32 + (size_t)row * ep.ldo + col);
+    if (epi == EPI_BIAS_F32 || (epi == EPI_SPLIT && col >= ep.split)) {
+        const bool split = epi == EPI_SPLIT;
+        float4* dst = reinterpret_cast<float4*>(split ? ep.out_f32 + (size_t)row * ep.ldo2 + (col - ep.split)
+                                                      : ep.out_f32 + (size_t)row * ep.ldo + col);
+        const float c0 = (!split && col == 0 && ep.col0_add) ? __ldg(ep.col0_add + (size_t)row * ep.ld_col0) : 0.0f;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             float4 b = *reinterpret_cast<const float4*>(ep.bias + col + 4 * j);
-            dst[j] = make_float4(v[4 * j] + b.x, v[4 * j + 1] + b.y, v[4 * j + 2] + b.z, v[4 * j + 3] + b.w);
+            dst[j] = make_float4(v[4 * j] + b.x + (j == 0 ? c0 : 0.0f), v[4 * j + 1] + b.y, v[4 * j + 2] + b.z,
+                                 v[4 * j + 3] + b.w);
         }
         return;
     }
     uint32_t packed[16];
-    if (epi == EPI_RELU_BF16) {
+    if (epi == EPI_RELU_BF16 || epi == EPI_SPLIT) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             float a = fmaxf(v[2 * j] + __ldg(ep.bias + col + 2 * j), 0.0f);

@@ -12,6 +12,17 @@
 // FP32 masters plus bf16 copies W [out][in] (forward B operand) and W^T
 // [in][out] (data-gradient B operand), zero-padded to the GEMM tile shapes:
 // layer 1 input 63 -> 64 columns, head output 1 + 3K -> 64 rows.
+//
+// Two output architectures (Sec. 4.2):
+//   PLO_ARCH_LINEAR_HEAD  trunk -> linear 256 -> 1 + 3K (sigma, SH);
+//   PLO_ARCH_PAPER        trunk -> [ReLU(W_f h + b_f) (128) | sigma (1)] as
+//                         one 192-row layer with a split epilogue, then the
+//                         128 -> 3K SH layer whose output row 0 is a zero row
+//                         that carries sigma, so both architectures leave
+//                         raw[:, 0] = sigma_raw, raw[:, 1 + ch K + k] = SH.
+// The coarse/fine step (Sec. 4.3-4.4) runs a coarse network on stratified
+// samples, places fine samples by its weights (k_fine) and trains a fine
+// network on the union.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -38,7 +49,10 @@ constexpr int N_FREQ = 10;
 constexpr int PE_DIM = 3 + 6 * N_FREQ;  // 63
 constexpr int PE_PAD = 64;
 constexpr int OUT_PAD = 64;
-constexpr int N_LAYERS = DEPTH + 1;
+constexpr int N_LAYERS = DEPTH + 1;      // linear-head architecture
+constexpr int MAX_LAYERS = DEPTH + 2;    // paper architecture: + combined layer, + SH layer
+constexpr int FEAT = 128;                // width of the paper's extra output layer
+constexpr int COMB_PAD = 192;            // combined layer rows: 128 features, sigma, zero padding
 
 // ---------------------------------------------------------------- TMA maps
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -152,7 +166,7 @@ __device__ __forceinline__ void unit_cube_clip(const float* o, const float* d, f
 // lengths delta_j = t_{j+1} - t_j (the last ends at t1), and the positional
 // encoding of x_j = o + t_j d -> X[ray*N + j][0..63] (column 63 is zero).
 __global__ void k_pe(const float* rays, int n_rays, int N, const float* jitter, uint64_t seed, uint64_t step,
-                     __nv_bfloat16* X, float* delta) {
+                     __nv_bfloat16* X, float* delta, float* t_out) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n_rays * N) return;
     const int r = (int)(idx / N), j = (int)(idx % N);
@@ -174,6 +188,7 @@ __global__ void k_pe(const float* rays, int n_rays, int N, const float* jitter, 
         tn = t0 + ((float)(j + 1) + un) * span / (float)N;
     }
     delta[idx] = hit ? tn - t : 0.0f;
+    if (t_out) t_out[idx] = t;
     float x[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) x[a] = fminf(fmaxf(o[a] + t * d[a], 0.0f), 1.0f);
@@ -324,7 +339,8 @@ __global__ void k_average(const float* raw, int64_t nv, int S, int n_out, float*
 template <int K, int S>
 __global__ void k_quad(const float* raw, const float* delta, const float* rays, const float* rgb_gt,
                        const float* alpha_gt, int n_rays, float l_max, float eps, int transmittance, int loss_kind,
-                       float inv_rays, __nv_bfloat16* dO, float* ray_loss) {
+                       float inv_rays, __nv_bfloat16* dO, float* ray_loss, __nv_bfloat16* dsig_out, int dsig_ld,
+                       float* w_out) {
     const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= n_rays) return;
@@ -452,7 +468,10 @@ __global__ void k_quad(const float* raw, const float* delta, const float* rays, 
         float out[OUT_PAD];
 #pragma unroll
         for (int k = 0; k < OUT_PAD; ++k) out[k] = 0.0f;
-        out[0] = pos[s] ? da[s] * dl[s] : 0.0f;
+        const float dsig = pos[s] ? da[s] * dl[s] : 0.0f;
+        out[0] = dsig_out ? 0.0f : dsig;
+        if (dsig_out) dsig_out[row * dsig_ld] = __float2bfloat16_rn(dsig);
+        if (w_out) w_out[row] = w[s];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             const float ds = w[s] * dC[ch] * l_max * sig[s][ch] * (1.0f - sig[s][ch]);
@@ -475,14 +494,14 @@ __global__ void k_quad(const float* raw, const float* delta, const float* rays, 
 
 // db[n] += sum_m dZ[m][n], n < ncols (bf16 input, fp32 sums).
 __global__ void k_colsum(const __nv_bfloat16* dZ, int64_t M, int ncols, int rows_per_block, float* db) {
-    const int pairs = ncols / 2;
+    const int pairs = ncols / 2;  // ncols even, <= 2 * blockDim.x
     const int p = threadIdx.x % pairs;
     const int rg = threadIdx.x / pairs;
-    const int groups = blockDim.x / pairs;
+    const int groups = blockDim.x / pairs;  // threads beyond groups * pairs only hold zeros
     const int64_t m0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t m1 = min(m0 + rows_per_block, M);
     float sx = 0.0f, sy = 0.0f;
-    for (int64_t m = m0 + rg; m < m1; m += groups) {
+    for (int64_t m = m0 + rg; rg < groups && m < m1; m += groups) {
         __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(dZ + m * ncols + 2 * p);
         float2 f = __bfloat1622float2(v);
         sx += f.x;
@@ -502,16 +521,138 @@ __global__ void k_colsum(const __nv_bfloat16* dZ, int64_t M, int ncols, int rows
     }
 }
 
+// Fine samples of the coarse/fine scheme (Sec. 4.3-4.4) and the merged
+// sample set; one warp per ray.  Coarse sample i owns [t_i, t_i + delta_i);
+// the density is constant there with mass proportional to w_i + 1e-5, and
+// stratified u_j = (j + xi_j) / Nf goes through the inverse CDF.  The merged
+// set lists the coarse and fine parameters in ascending order (a coarse
+// sample first at equal t): fine sample j of segment b has rank j + b + 1,
+// coarse sample i has rank i + (fine samples in segments before i).  Then
+// delta_k = t_{k+1} - t_k (the last ends at the exit of the unit cube) and X
+// gets the encoding of o + t_k d in row ray * (Nc + Nf) + k.
+constexpr int HIER_WARPS = 4;
+constexpr int HIER_MAX_NC = 128;
+constexpr int HIER_MAX_N = 256;
+constexpr float FINE_FLOOR = 1e-5f;
+
+__device__ __forceinline__ float fine_u(uint64_t seed, uint64_t step, uint64_t ray, uint64_t j) {
+    return jitter_u(seed ^ 0xF17E5A3B1E000000ULL, step, ray, j);
+}
+
+__global__ void __launch_bounds__(32 * HIER_WARPS)
+    k_fine(const float* rays, int n_rays, int Nc, int Nf, const float* t_c, const float* delta_c, const float* w_c,
+           const float* xi, uint64_t seed, uint64_t step, __nv_bfloat16* X, float* delta_out, float* t_out) {
+    __shared__ float sC[HIER_WARPS][HIER_MAX_NC + 1];
+    __shared__ float sT[HIER_WARPS][HIER_MAX_NC];
+    __shared__ float sD[HIER_WARPS][HIER_MAX_NC];
+    __shared__ int sCnt[HIER_WARPS][HIER_MAX_NC];
+    __shared__ float sM[HIER_WARPS][HIER_MAX_N];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * HIER_WARPS + wid;
+    if (r >= n_rays) return;  // the whole warp leaves together
+    const int N = Nc + Nf, PB = Nc / 32, QF = Nf / 32;
+    float* C = sC[wid];
+    float* T = sT[wid];
+    float* D = sD[wid];
+    int* cnt = sCnt[wid];
+    float* Mg = sM[wid];
+    const int64_t base = (int64_t)r * Nc;
+    float local = 0.0f;
+    for (int q = 0; q < PB; ++q) {
+        const int i = lane * PB + q;
+        T[i] = __ldg(t_c + base + i);
+        D[i] = __ldg(delta_c + base + i);
+        local += __ldg(w_c + base + i) + FINE_FLOOR;
+        cnt[i] = 0;
+    }
+    float incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    float run = incl - local;
+    for (int q = 0; q < PB; ++q) {
+        const int i = lane * PB + q;
+        C[i] = run;
+        run += __ldg(w_c + base + i) + FINE_FLOOR;
+    }
+    if (lane == 31) C[Nc] = run;
+    __syncwarp();
+    const float total = C[Nc];
+    float tf[HIER_MAX_N / 32];
+    int bf[HIER_MAX_N / 32];
+    for (int q = 0; q < QF; ++q) {
+        const int j = lane * QF + q;
+        const float x = xi ? __ldg(xi + (int64_t)r * Nf + j) : fine_u(seed, step, (uint64_t)r, (uint64_t)j);
+        const float u = ((float)j + x) / (float)Nf * total;
+        int lo = 0, hi = Nc - 1;  // the last segment i with C[i] <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (C[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const float span = C[lo + 1] - C[lo];
+        const float frac = span > 0.0f ? fminf(fmaxf((u - C[lo]) / span, 0.0f), 1.0f) : 0.0f;
+        tf[q] = T[lo] + frac * D[lo];
+        bf[q] = lo;
+        atomicAdd(&cnt[lo], 1);
+    }
+    __syncwarp();
+    // exclusive prefix of the per-segment counts
+    int lc = 0;
+    for (int q = 0; q < PB; ++q) lc += cnt[lane * PB + q];
+    int ic = lc;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, ic, off);
+        if (lane >= off) ic += v;
+    }
+    int before = ic - lc;
+    for (int q = 0; q < PB; ++q) {
+        const int i = lane * PB + q;
+        const int c = cnt[i];
+        Mg[i + before] = T[i];
+        before += c;
+    }
+    for (int q = 0; q < QF; ++q) Mg[lane * QF + q + bf[q] + 1] = tf[q];
+    __syncwarp();
+    float o[3], d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = __ldg(rays + 6 * (int64_t)r + a);
+        d[a] = __ldg(rays + 6 * (int64_t)r + 3 + a);
+    }
+    float t0, t1;
+    bool hit;
+    unit_cube_clip(o, d, t0, t1, hit);
+    for (int k = lane; k < N; k += 32) {
+        const float t = Mg[k];
+        const float tn = k + 1 < N ? Mg[k + 1] : t1;
+        const int64_t row = (int64_t)r * N + k;
+        delta_out[row] = hit ? tn - t : 0.0f;
+        if (t_out) t_out[row] = t;
+        if (X) {
+            float x[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) x[a] = fminf(fmaxf(o[a] + t * d[a], 0.0f), 1.0f);
+            encode_point(x, X + row * PE_PAD);
+        }
+    }
+}
+
 struct LayerGeom {
-    int64_t off[N_LAYERS + 1];  // offset of layer l's W in the padded flat array; bias follows W
-    int out_real[N_LAYERS], in_real[N_LAYERS], out_pad[N_LAYERS], in_pad[N_LAYERS];
+    int n_layers;
+    int64_t off[MAX_LAYERS + 1];  // offset of layer l's W in the padded flat array; bias follows W
+    int out_real[MAX_LAYERS], in_real[MAX_LAYERS], out_pad[MAX_LAYERS], in_pad[MAX_LAYERS];
+    int out_first[MAX_LAYERS];    // first trained row (the paper SH layer's row 0 carries sigma)
 };
 
 __device__ __forceinline__ int find_layer(const LayerGeom& g, int64_t i) {
     int l = 0;
 #pragma unroll
-    for (int k = 1; k < N_LAYERS; ++k)
-        if (i >= g.off[k]) l = k;
+    for (int k = 1; k < MAX_LAYERS; ++k)
+        if (k < g.n_layers && i >= g.off[k]) l = k;
     return l;
 }
 
@@ -528,7 +669,7 @@ __global__ void k_adam(LayerGeom g, float* master, float* m, float* v, const flo
     const bool is_w = loc < wsz;
     const int o = is_w ? (int)(loc / g.in_pad[l]) : (int)(loc - wsz);
     const int in = is_w ? (int)(loc % g.in_pad[l]) : 0;
-    const bool real = o < g.out_real[l] && (!is_w || in < g.in_real[l]);
+    const bool real = o >= g.out_first[l] && o < g.out_real[l] && (!is_w || in < g.in_real[l]);
     float p = master[i];
     if (update && real) {
         const float gi = grad[i];
@@ -547,10 +688,10 @@ __global__ void k_adam(LayerGeom g, float* master, float* m, float* v, const flo
     }
 }
 
-__global__ void k_mean(const float* x, int n, float* out) {
+__global__ void k_mean(const float* x, int n, float* out, const float* y = nullptr) {
     __shared__ float red[256];
     float s = 0.0f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i] + (y ? y[i] : 0.0f);
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -567,42 +708,51 @@ __global__ void k_mean(const float* x, int n, float* out) {
 struct plo_mlp {
     plo_mlp_desc desc;
     int K, n_out;
+    int arch, n_layers;
     int device, sms;
     LayerGeom geom;
     int64_t n_params_pad;
     float *master = nullptr, *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
-    __nv_bfloat16* W[N_LAYERS] = {};
-    __nv_bfloat16* WT[N_LAYERS] = {};
+    __nv_bfloat16* W[MAX_LAYERS] = {};
+    __nv_bfloat16* WT[MAX_LAYERS] = {};
     __nv_bfloat16** d_W = nullptr;
     __nv_bfloat16** d_WT = nullptr;
-    CUtensorMap mapW[N_LAYERS], mapWT[N_LAYERS];
+    CUtensorMap mapW[MAX_LAYERS], mapWT[MAX_LAYERS];
     int64_t step = 0;
     unsigned int* d_err = nullptr;
     // workspace (samples capacity)
     int64_t cap = 0;
     int cap_rays = 0;
-    __nv_bfloat16* H[N_LAYERS] = {};  // H[0] = X [cap][64], H[1..8] [cap][256]
-    float* raw = nullptr;             // [cap][64]
-    __nv_bfloat16* dO = nullptr;      // [cap][64]
-    __nv_bfloat16* dZ[2] = {};        // [cap][256]
+    __nv_bfloat16* H[MAX_LAYERS] = {};  // H[0] = X [cap][64], H[1..8] [cap][256], H[9] [cap][128] (paper)
+    float* raw = nullptr;               // [cap][64]
+    float* sraw = nullptr;              // [cap][64] fp32 half of the paper combined layer (column 0: sigma)
+    __nv_bfloat16* dO = nullptr;        // [cap][64]
+    __nv_bfloat16* dZ[2] = {};          // [cap][256]
+    __nv_bfloat16* dZc = nullptr;       // [cap][192] gradient of the paper combined layer's output
     float* delta = nullptr;
+    float* tsamp = nullptr;             // [cap] sample parameters (coarse pass)
+    float* wts = nullptr;               // [cap] quadrature weights (coarse pass)
     float* ray_loss = nullptr;
-    CUtensorMap mapA_H[N_LAYERS], mapA_dO, mapA_dZ[2];   // A operand boxes (128 rows)
-    CUtensorMap mapW_H[N_LAYERS], mapW_dO, mapW_dZ[2];   // wgrad boxes (64 rows)
+    CUtensorMap mapA_H[MAX_LAYERS], mapA_dO, mapA_dZ[2], mapA_dZc;  // A operand boxes (128 rows)
+    CUtensorMap mapW_H[MAX_LAYERS], mapW_dO, mapW_dZ[2], mapW_dZc;  // wgrad boxes (64 rows)
 };
 
 namespace {
 
 void free_workspace(plo_mlp* m) {
-    for (int l = 0; l < N_LAYERS; ++l) cudaFree(m->H[l]), m->H[l] = nullptr;
+    for (int l = 0; l < MAX_LAYERS; ++l) cudaFree(m->H[l]), m->H[l] = nullptr;
     cudaFree(m->raw);
+    cudaFree(m->sraw);
     cudaFree(m->dO);
     cudaFree(m->dZ[0]);
     cudaFree(m->dZ[1]);
+    cudaFree(m->dZc);
     cudaFree(m->delta);
+    cudaFree(m->tsamp);
+    cudaFree(m->wts);
     cudaFree(m->ray_loss);
-    m->raw = m->delta = m->ray_loss = nullptr;
-    m->dO = m->dZ[0] = m->dZ[1] = nullptr;
+    m->raw = m->sraw = m->delta = m->tsamp = m->wts = m->ray_loss = nullptr;
+    m->dO = m->dZ[0] = m->dZ[1] = m->dZc = nullptr;
     m->cap = 0;
     m->cap_rays = 0;
 }
@@ -615,14 +765,22 @@ plo_status ensure_workspace(plo_mlp* m, int64_t samples, int rays) {
     auto alloc = [&](void** p, size_t bytes) {
         if (e == cudaSuccess) e = (cudaError_t)dev_malloc(p, bytes);
     };
+    const bool paper = m->arch == PLO_ARCH_PAPER;
     alloc((void**)&m->H[0], (size_t)samples * PE_PAD * 2);
-    for (int l = 1; l < N_LAYERS; ++l) alloc((void**)&m->H[l], (size_t)samples * WIDTH * 2);
+    for (int l = 1; l <= DEPTH; ++l) alloc((void**)&m->H[l], (size_t)samples * WIDTH * 2);
+    if (paper) alloc((void**)&m->H[DEPTH + 1], (size_t)samples * FEAT * 2);
     alloc((void**)&m->raw, (size_t)samples * OUT_PAD * 4);
+    if (paper) alloc((void**)&m->sraw, (size_t)samples * OUT_PAD * 4);
     alloc((void**)&m->dO, (size_t)samples * OUT_PAD * 2);
     alloc((void**)&m->dZ[0], (size_t)samples * WIDTH * 2);
     alloc((void**)&m->dZ[1], (size_t)samples * WIDTH * 2);
+    if (paper) alloc((void**)&m->dZc, (size_t)samples * COMB_PAD * 2);
     alloc((void**)&m->delta, (size_t)samples * 4);
+    alloc((void**)&m->tsamp, (size_t)samples * 4);
+    alloc((void**)&m->wts, (size_t)samples * 4);
     alloc((void**)&m->ray_loss, (size_t)(rays > 0 ? rays : 1) * 4);
+    // columns of dZc that no kernel writes (sigma's padding) stay zero
+    if (e == cudaSuccess && paper) e = cudaMemset(m->dZc, 0, (size_t)samples * COMB_PAD * 2);
     if (e != cudaSuccess) {
         free_workspace(m);
         cudaGetLastError();
@@ -631,11 +789,13 @@ plo_status ensure_workspace(plo_mlp* m, int64_t samples, int rays) {
     m->cap = samples;
     m->cap_rays = rays;
     plo_status st = PLO_OK;
-    for (int l = 0; l < N_LAYERS && st == PLO_OK; ++l) {
-        const int cols = l == 0 ? PE_PAD : WIDTH;
+    for (int l = 0; l < m->n_layers && st == PLO_OK; ++l) {
+        const int cols = m->geom.in_pad[l];
         st = make_map(&m->mapA_H[l], m->H[l], samples, cols, 128);
         if (st == PLO_OK) st = make_map(&m->mapW_H[l], m->H[l], samples, cols, 64);
     }
+    if (st == PLO_OK && paper) st = make_map(&m->mapA_dZc, m->dZc, samples, COMB_PAD, 128);
+    if (st == PLO_OK && paper) st = make_map(&m->mapW_dZc, m->dZc, samples, COMB_PAD, 64);
     if (st == PLO_OK) st = make_map(&m->mapA_dO, m->dO, samples, OUT_PAD, 128);
     if (st == PLO_OK) st = make_map(&m->mapW_dO, m->dO, samples, OUT_PAD, 64);
     for (int k = 0; k < 2 && st == PLO_OK; ++k) {
@@ -647,16 +807,51 @@ plo_status ensure_workspace(plo_mlp* m, int64_t samples, int rays) {
 
 void init_geom(plo_mlp* m) {
     int64_t off = 0;
-    for (int l = 0; l < N_LAYERS; ++l) {
-        m->geom.in_real[l] = l == 0 ? PE_DIM : WIDTH;
-        m->geom.in_pad[l] = l == 0 ? PE_PAD : WIDTH;
-        m->geom.out_real[l] = l == DEPTH ? m->n_out : WIDTH;
-        m->geom.out_pad[l] = l == DEPTH ? OUT_PAD : WIDTH;
-        m->geom.off[l] = off;
-        off += (int64_t)m->geom.out_pad[l] * m->geom.in_pad[l] + m->geom.out_pad[l];
+    LayerGeom& g = m->geom;
+    g = LayerGeom{};
+    g.n_layers = m->n_layers;
+    for (int l = 0; l < m->n_layers; ++l) {
+        g.in_real[l] = l == 0 ? PE_DIM : WIDTH;
+        g.in_pad[l] = l == 0 ? PE_PAD : WIDTH;
+        g.out_real[l] = WIDTH;
+        g.out_pad[l] = WIDTH;
+        g.out_first[l] = 0;
+        if (l == DEPTH && m->arch == PLO_ARCH_LINEAR_HEAD) {
+            g.out_real[l] = m->n_out;
+            g.out_pad[l] = OUT_PAD;
+        } else if (l == DEPTH) {  // paper: [features (128) | sigma | padding]
+            g.out_real[l] = FEAT + 1;
+            g.out_pad[l] = COMB_PAD;
+        } else if (l == DEPTH + 1) {  // paper: SH layer, row 0 carries sigma
+            g.in_real[l] = g.in_pad[l] = FEAT;
+            g.out_real[l] = m->n_out;
+            g.out_pad[l] = OUT_PAD;
+            g.out_first[l] = 1;
+        }
+        g.off[l] = off;
+        off += (int64_t)g.out_pad[l] * g.in_pad[l] + g.out_pad[l];
     }
-    m->geom.off[N_LAYERS] = off;
+    g.off[m->n_layers] = off;
     m->n_params_pad = off;
+}
+
+// The canonical flat parameter order (the oracle's): blocks of (W [rows][cols]
+// then b [rows]); each block lands at `row0` of padded layer `layer`.
+struct Block {
+    int layer, row0, rows, cols;
+    float init_scale;  // multiplier of the He-uniform bound
+};
+int canonical_blocks(int arch, int n_out, Block* b) {
+    int n = 0;
+    for (int l = 0; l < DEPTH; ++l) b[n++] = {l, 0, WIDTH, l == 0 ? PE_DIM : WIDTH, 1.0f};
+    if (arch == PLO_ARCH_LINEAR_HEAD) {
+        b[n++] = {DEPTH, 0, n_out, WIDTH, 0.1f};
+    } else {
+        b[n++] = {DEPTH, FEAT, 1, WIDTH, 0.1f};          // sigma
+        b[n++] = {DEPTH, 0, FEAT, WIDTH, 1.0f};          // the 128-wide layer
+        b[n++] = {DEPTH + 1, 1, n_out - 1, FEAT, 0.1f};  // SH coefficients
+    }
+    return n;
 }
 
 float* bias_ptr(plo_mlp* m, float* base, int l) {
@@ -671,29 +866,39 @@ plo_status refresh_bf16(plo_mlp* m, cudaStream_t s) {
     return e == cudaSuccess ? PLO_OK : cuda_error(e, "weight cast kernel");
 }
 
-// canonical flat order of the oracle: W_l [out][in] then b_l, l = 1..9
-int64_t canonical_count(int n_out) {
-    return (int64_t)WIDTH * PE_DIM + WIDTH + (int64_t)(DEPTH - 1) * (WIDTH * WIDTH + WIDTH) + (int64_t)n_out * WIDTH +
-           n_out;
+int64_t canonical_count(int arch, int n_out) {
+    Block bl[MAX_LAYERS + 2];
+    const int nb = canonical_blocks(arch, n_out, bl);
+    int64_t c = 0;
+    for (int k = 0; k < nb; ++k) c += (int64_t)bl[k].rows * bl[k].cols + bl[k].rows;
+    return c;
 }
 
 void canonical_to_padded(const plo_mlp* m, const float* c, std::vector<float>& p) {
     p.assign(m->n_params_pad, 0.0f);
+    Block bl[MAX_LAYERS + 2];
+    const int nb = canonical_blocks(m->arch, m->n_out, bl);
+    const LayerGeom& g = m->geom;
     int64_t ci = 0;
-    for (int l = 0; l < N_LAYERS; ++l) {
-        const LayerGeom& g = m->geom;
-        for (int o = 0; o < g.out_real[l]; ++o)
-            for (int i = 0; i < g.in_real[l]; ++i) p[g.off[l] + (int64_t)o * g.in_pad[l] + i] = c[ci++];
-        for (int o = 0; o < g.out_real[l]; ++o) p[g.off[l] + (int64_t)g.out_pad[l] * g.in_pad[l] + o] = c[ci++];
+    for (int k = 0; k < nb; ++k) {
+        const Block& B = bl[k];
+        const int64_t w0 = g.off[B.layer], b0 = w0 + (int64_t)g.out_pad[B.layer] * g.in_pad[B.layer];
+        for (int o = 0; o < B.rows; ++o)
+            for (int i = 0; i < B.cols; ++i) p[w0 + (int64_t)(B.row0 + o) * g.in_pad[B.layer] + i] = c[ci++];
+        for (int o = 0; o < B.rows; ++o) p[b0 + B.row0 + o] = c[ci++];
     }
 }
 void padded_to_canonical(const plo_mlp* m, const std::vector<float>& p, float* c) {
+    Block bl[MAX_LAYERS + 2];
+    const int nb = canonical_blocks(m->arch, m->n_out, bl);
+    const LayerGeom& g = m->geom;
     int64_t ci = 0;
-    for (int l = 0; l < N_LAYERS; ++l) {
-        const LayerGeom& g = m->geom;
-        for (int o = 0; o < g.out_real[l]; ++o)
-            for (int i = 0; i < g.in_real[l]; ++i) c[ci++] = p[g.off[l] + (int64_t)o * g.in_pad[l] + i];
-        for (int o = 0; o < g.out_real[l]; ++o) c[ci++] = p[g.off[l] + (int64_t)g.out_pad[l] * g.in_pad[l] + o];
+    for (int k = 0; k < nb; ++k) {
+        const Block& B = bl[k];
+        const int64_t w0 = g.off[B.layer], b0 = w0 + (int64_t)g.out_pad[B.layer] * g.in_pad[B.layer];
+        for (int o = 0; o < B.rows; ++o)
+            for (int i = 0; i < B.cols; ++i) c[ci++] = p[w0 + (int64_t)(B.row0 + o) * g.in_pad[B.layer] + i];
+        for (int o = 0; o < B.rows; ++o) c[ci++] = p[b0 + B.row0 + o];
     }
 }
 
@@ -712,14 +917,136 @@ plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s) {
         else
             e = launch_gemm<WIDTH, WIDTH>(m->mapA_H[l], m->mapW[l], ep, gemm::EPI_RELU_BF16, (int)samples, m->sms, s);
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && m->arch == PLO_ARCH_LINEAR_HEAD) {
         ep.bias = bias_ptr(m, m->master, DEPTH);
         ep.out_f32 = m->raw;
         ep.ldo = OUT_PAD;
         e = launch_gemm<OUT_PAD, WIDTH>(m->mapA_H[DEPTH], m->mapW[DEPTH], ep, gemm::EPI_BIAS_F32, (int)samples, m->sms,
                                         s);
+    } else if (e == cudaSuccess) {
+        // [ReLU features -> H[9] (bf16) | sigma block -> sraw (fp32)], then the
+        // SH layer, whose zero row 0 picks up sigma from sraw
+        ep.bias = bias_ptr(m, m->master, DEPTH);
+        ep.out_bf16 = m->H[DEPTH + 1];
+        ep.ldo = FEAT;
+        ep.split = FEAT;
+        ep.out_f32 = m->sraw;
+        ep.ldo2 = OUT_PAD;
+        e = launch_gemm<COMB_PAD, WIDTH>(m->mapA_H[DEPTH], m->mapW[DEPTH], ep, gemm::EPI_SPLIT, (int)samples, m->sms,
+                                         s);
+        gemm::EpiArgs eh{};
+        eh.err = m->d_err;
+        eh.bias = bias_ptr(m, m->master, DEPTH + 1);
+        eh.out_f32 = m->raw;
+        eh.ldo = OUT_PAD;
+        eh.col0_add = m->sraw;
+        eh.ld_col0 = OUT_PAD;
+        if (e == cudaSuccess)
+            e = launch_gemm<OUT_PAD, FEAT>(m->mapA_H[DEPTH + 1], m->mapW[DEPTH + 1], eh, gemm::EPI_BIAS_F32,
+                                           (int)samples, m->sms, s);
     }
     return e == cudaSuccess ? PLO_OK : cuda_error(e, "MLP forward GEMM launch");
+}
+
+// k_quad for N samples per ray (one warp per ray, N / 32 samples per lane).
+// The paper architecture takes d loss / d sigma_raw in column 128 of dZc.
+cudaError_t launch_quad(plo_mlp* m, int N, const float* d_rays, const float* d_rgb_gt, const float* d_alpha_gt,
+                        int n_rays, int loss_kind, float* w_out, cudaStream_t s) {
+    const plo_mlp_desc& D = m->desc;
+    const float inv_rays = 1.0f / (float)n_rays;
+    const unsigned qblocks = (unsigned)((n_rays + 3) / 4);
+    __nv_bfloat16* dsig = m->arch == PLO_ARCH_PAPER ? m->dZc + FEAT : nullptr;
+#define PLO_QUAD(SS)                                                                                               \
+    k_quad<16, SS><<<qblocks, 128, 0, s>>>(m->raw, m->delta, d_rays, d_rgb_gt, d_alpha_gt, n_rays, D.l_max, D.eps, \
+                                           D.transmittance, loss_kind, inv_rays, m->dO, m->ray_loss, dsig, COMB_PAD, \
+                                           w_out)
+    switch (N) {
+        case 32: PLO_QUAD(1); break;
+        case 64: PLO_QUAD(2); break;
+        case 96: PLO_QUAD(3); break;
+        case 128: PLO_QUAD(4); break;
+        case 192: PLO_QUAD(6); break;
+        case 256: PLO_QUAD(8); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef PLO_QUAD
+    return cudaGetLastError();
+}
+
+// Backward from dO (d loss / d raw, and for the paper architecture d loss /
+// d sigma_raw in dZc) through every layer, then one Adam step with the
+// exponentially decaying learning rate.
+plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
+    const plo_mlp_desc& D = m->desc;
+    gemm::EpiArgs ep{};
+    ep.err = m->d_err;
+    auto colsum = [&](const __nv_bfloat16* dz, int ncols, float* db) {
+        const int rows = 4096;
+        k_colsum<<<(unsigned)((M + rows - 1) / rows), 256, 0, s>>>(dz, M, ncols, rows, db);
+    };
+    cudaError_t e;
+    if (m->arch == PLO_ARCH_LINEAR_HEAD) {
+        e = launch_wgrad<WIDTH>(m->mapW_dO, m->mapW_H[DEPTH], m->grad + m->geom.off[DEPTH], OUT_PAD, (int)M, m->sms,
+                                m->d_err, s);
+        colsum(m->dO, OUT_PAD, bias_ptr(m, m->grad, DEPTH));
+        ep.out_bf16 = m->dZ[0];
+        ep.ldo = WIDTH;
+        ep.mask = m->H[DEPTH];
+        ep.ldm = WIDTH;
+        if (e == cudaSuccess)
+            e = launch_gemm<WIDTH, OUT_PAD>(m->mapA_dO, m->mapWT[DEPTH], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+    } else {
+        const int SH = DEPTH + 1;
+        // SH layer: dW = dO^T feat, db = column sums; d feat -> dZc[:, 0:128]
+        e = launch_wgrad<FEAT>(m->mapW_dO, m->mapW_H[SH], m->grad + m->geom.off[SH], OUT_PAD, (int)M, m->sms,
+                               m->d_err, s);
+        colsum(m->dO, OUT_PAD, bias_ptr(m, m->grad, SH));
+        ep.out_bf16 = m->dZc;
+        ep.ldo = COMB_PAD;
+        ep.mask = m->H[SH];
+        ep.ldm = FEAT;
+        if (e == cudaSuccess)
+            e = launch_gemm<FEAT, OUT_PAD>(m->mapA_dO, m->mapWT[SH], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+        // combined layer [features | sigma]: dW = dZc^T h8; d h8 -> dZ[0]
+        if (e == cudaSuccess)
+            e = launch_wgrad<WIDTH>(m->mapW_dZc, m->mapW_H[DEPTH], m->grad + m->geom.off[DEPTH], COMB_PAD, (int)M,
+                                    m->sms, m->d_err, s);
+        colsum(m->dZc, COMB_PAD, bias_ptr(m, m->grad, DEPTH));
+        ep.out_bf16 = m->dZ[0];
+        ep.ldo = WIDTH;
+        ep.mask = m->H[DEPTH];
+        ep.ldm = WIDTH;
+        if (e == cudaSuccess)
+            e = launch_gemm<WIDTH, COMB_PAD>(m->mapA_dZc, m->mapWT[DEPTH], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+    }
+    // hidden layers l = 8 .. 2 (index l-1 = 7 .. 1), then layer 1
+    int cur = 0;
+    for (int l = DEPTH - 1; l >= 0 && e == cudaSuccess; --l) {
+        // dZ[cur] is d loss / d pre-activation of layer l (0-based), input H[l]
+        if (l == 0)
+            e = launch_wgrad<PE_PAD>(m->mapW_dZ[cur], m->mapW_H[0], m->grad + m->geom.off[0], WIDTH, (int)M, m->sms,
+                                     m->d_err, s);
+        else
+            e = launch_wgrad<WIDTH>(m->mapW_dZ[cur], m->mapW_H[l], m->grad + m->geom.off[l], WIDTH, (int)M, m->sms,
+                                    m->d_err, s);
+        colsum(m->dZ[cur], WIDTH, bias_ptr(m, m->grad, l));
+        if (l == 0 || e != cudaSuccess) break;
+        ep.out_bf16 = m->dZ[cur ^ 1];
+        ep.mask = m->H[l];
+        e = launch_gemm<WIDTH, WIDTH>(m->mapA_dZ[cur], m->mapWT[l], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+        cur ^= 1;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "MLP backward launch");
+    // Adam with exponential decay lr0 -> lr1 over total_steps
+    const double frac = std::fmin((double)(m->step - 1), (double)D.total_steps) / (double)D.total_steps;
+    const float lr = (float)(D.lr0 * std::pow((double)D.lr1 / D.lr0, frac));
+    const float bc1 = (float)(1.0 - std::pow(0.9, (double)m->step));
+    const float bc2 = (float)(1.0 - std::pow(0.999, (double)m->step));
+    const int64_t n = m->n_params_pad;
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->geom, m->master, m->adam_m, m->adam_v, m->grad, n, lr, 0.9f,
+                                                       0.999f, 1e-8f, bc1, bc2, 1, m->d_W, m->d_WT);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "Adam launch");
 }
 
 plo_status check_mlp_desc(const plo_mlp_desc* d) {
@@ -730,15 +1057,21 @@ plo_status check_mlp_desc(const plo_mlp_desc* d) {
     if (d->loss < PLO_LOSS_PAPER || d->loss > PLO_LOSS_MSE) return set_error(PLO_ERR_INVALID_ARG, "unknown loss");
     if (!(d->l_max > 0.0f) || !(d->lr0 > 0.0f) || !(d->lr1 > 0.0f) || d->total_steps < 1 || !(d->eps > 0.0f))
         return set_error(PLO_ERR_INVALID_ARG, "l_max, lr0, lr1, eps must be > 0 and total_steps >= 1");
-    if (!(d->init_radiance >= 0.0f) || d->reserved != 0)
-        return set_error(PLO_ERR_INVALID_ARG, "init_radiance must be >= 0 and reserved 0");
+    if (!(d->init_radiance >= 0.0f)) return set_error(PLO_ERR_INVALID_ARG, "init_radiance must be >= 0");
+    if (d->arch != PLO_ARCH_LINEAR_HEAD && d->arch != PLO_ARCH_PAPER)
+        return set_error(PLO_ERR_INVALID_ARG, "arch must be PLO_ARCH_LINEAR_HEAD or PLO_ARCH_PAPER");
     return PLO_OK;
 }
 
 }  // namespace
 
 extern "C" int64_t plo_mlp_param_count(int32_t sh_degree) {
-    return canonical_count(1 + 3 * (sh_degree + 1) * (sh_degree + 1));
+    return canonical_count(PLO_ARCH_LINEAR_HEAD, 1 + 3 * (sh_degree + 1) * (sh_degree + 1));
+}
+
+extern "C" int64_t plo_mlp_param_count_arch(int32_t sh_degree, int32_t arch) {
+    if (arch != PLO_ARCH_LINEAR_HEAD && arch != PLO_ARCH_PAPER) return -1;
+    return canonical_count(arch, 1 + 3 * (sh_degree + 1) * (sh_degree + 1));
 }
 
 extern "C" plo_status plo_mlp_create(const plo_mlp_desc* desc, uint64_t seed, plo_mlp** out) {
@@ -751,6 +1084,8 @@ extern "C" plo_status plo_mlp_create(const plo_mlp_desc* desc, uint64_t seed, pl
     m->desc = *desc;
     m->K = (desc->sh_degree + 1) * (desc->sh_degree + 1);
     m->n_out = 1 + 3 * m->K;
+    m->arch = desc->arch;
+    m->n_layers = m->arch == PLO_ARCH_PAPER ? MAX_LAYERS : N_LAYERS;
     cudaGetDevice(&m->device);
     m->sms = sm_count_of_current();
     init_geom(m);
@@ -764,24 +1099,24 @@ extern "C" plo_status plo_mlp_create(const plo_mlp_desc* desc, uint64_t seed, pl
     alloc((void**)&m->adam_v, pbytes);
     alloc((void**)&m->grad, pbytes);
     alloc((void**)&m->d_err, 256);
-    for (int l = 0; l < N_LAYERS; ++l) {
+    for (int l = 0; l < m->n_layers; ++l) {
         alloc((void**)&m->W[l], (size_t)m->geom.out_pad[l] * m->geom.in_pad[l] * 2);
         if (l >= 1) alloc((void**)&m->WT[l], (size_t)m->geom.out_pad[l] * m->geom.in_pad[l] * 2);
     }
-    alloc((void**)&m->d_W, sizeof(void*) * N_LAYERS);
-    alloc((void**)&m->d_WT, sizeof(void*) * N_LAYERS);
+    alloc((void**)&m->d_W, sizeof(void*) * MAX_LAYERS);
+    alloc((void**)&m->d_WT, sizeof(void*) * MAX_LAYERS);
     if (e != cudaSuccess) {
         plo_mlp_free(m);
         cudaGetLastError();
         return set_error(PLO_ERR_OOM, "device allocation of the network failed");
     }
-    cudaMemcpy(m->d_W, m->W, sizeof(void*) * N_LAYERS, cudaMemcpyHostToDevice);
-    cudaMemcpy(m->d_WT, m->WT, sizeof(void*) * N_LAYERS, cudaMemcpyHostToDevice);
+    cudaMemcpy(m->d_W, m->W, sizeof(void*) * MAX_LAYERS, cudaMemcpyHostToDevice);
+    cudaMemcpy(m->d_WT, m->WT, sizeof(void*) * MAX_LAYERS, cudaMemcpyHostToDevice);
     cudaMemset(m->adam_m, 0, pbytes);
     cudaMemset(m->adam_v, 0, pbytes);
     cudaMemset(m->grad, 0, pbytes);
     cudaMemset(m->d_err, 0, 256);
-    for (int l = 0; l < N_LAYERS && st == PLO_OK; ++l) {
+    for (int l = 0; l < m->n_layers && st == PLO_OK; ++l) {
         st = make_map(&m->mapW[l], m->W[l], m->geom.out_pad[l], m->geom.in_pad[l], (uint32_t)m->geom.out_pad[l]);
         if (st == PLO_OK && l >= 1)
             st = make_map(&m->mapWT[l], m->WT[l], m->geom.in_pad[l], m->geom.out_pad[l], (uint32_t)m->geom.in_pad[l]);
@@ -791,7 +1126,7 @@ extern "C" plo_status plo_mlp_create(const plo_mlp_desc* desc, uint64_t seed, pl
         return st;
     }
     // He-uniform initial weights, zero biases; counter-based (SplitMix64).
-    std::vector<float> canon(canonical_count(m->n_out));
+    std::vector<float> canon(canonical_count(m->arch, m->n_out));
     int64_t ci = 0;
     uint64_t ctr = 0;
     auto unif = [&]() {
@@ -801,18 +1136,27 @@ extern "C" plo_status plo_mlp_create(const plo_mlp_desc* desc, uint64_t seed, pl
         z ^= z >> 31;
         return (double)(z >> 11) * (1.0 / 9007199254740992.0);
     };
-    for (int l = 0; l < N_LAYERS; ++l) {
-        const double lim = std::sqrt(6.0 / m->geom.in_real[l]) * (l == DEPTH ? 0.1 : 1.0);
-        for (int k = 0; k < m->geom.out_real[l] * m->geom.in_real[l]; ++k) canon[ci++] = (float)((2 * unif() - 1) * lim);
-        for (int k = 0; k < m->geom.out_real[l]; ++k) canon[ci++] = 0.0f;
+    Block bl[MAX_LAYERS + 2];
+    const int nb = canonical_blocks(m->arch, m->n_out, bl);
+    std::vector<int64_t> bias_at(nb);
+    for (int k = 0; k < nb; ++k) {
+        const double lim = std::sqrt(6.0 / bl[k].cols) * bl[k].init_scale;
+        for (int q = 0; q < bl[k].rows * bl[k].cols; ++q) canon[ci++] = (float)((2 * unif() - 1) * lim);
+        bias_at[k] = ci;
+        for (int q = 0; q < bl[k].rows; ++q) canon[ci++] = 0.0f;
     }
-    // head biases: sigma starts positive, the DC coefficient sets the emission
-    float* head_b = canon.data() + canon.size() - m->n_out;
-    head_b[0] = 0.5f;
+    // output biases: sigma starts positive, the DC coefficient sets the emission
     const double p0 = desc->init_radiance > 0.0f ? std::fmin(std::fmax(desc->init_radiance / desc->l_max, 1e-6), 0.5)
                                                  : 0.5;
     const double dc = std::log(p0 / (1.0 - p0)) / 0.28209479177387814;  // logit / Y_0^0
-    for (int ch = 0; ch < 3; ++ch) head_b[1 + ch * m->K] = (float)dc;
+    if (m->arch == PLO_ARCH_LINEAR_HEAD) {
+        float* head_b = canon.data() + bias_at[nb - 1];
+        head_b[0] = 0.5f;
+        for (int ch = 0; ch < 3; ++ch) head_b[1 + ch * m->K] = (float)dc;
+    } else {
+        canon[bias_at[nb - 3]] = 0.5f;  // sigma
+        for (int ch = 0; ch < 3; ++ch) canon[bias_at[nb - 1] + ch * m->K] = (float)dc;
+    }
     *out = m;
     st = plo_mlp_set_params(m, canon.data(), (int64_t)canon.size());
     if (st != PLO_OK) {
@@ -831,7 +1175,7 @@ extern "C" void plo_mlp_free(plo_mlp* m) {
     cudaFree(m->adam_v);
     cudaFree(m->grad);
     cudaFree(m->d_err);
-    for (int l = 0; l < N_LAYERS; ++l) {
+    for (int l = 0; l < MAX_LAYERS; ++l) {
         cudaFree(m->W[l]);
         cudaFree(m->WT[l]);
     }
@@ -842,7 +1186,7 @@ extern "C" void plo_mlp_free(plo_mlp* m) {
 
 extern "C" plo_status plo_mlp_set_params(plo_mlp* m, const float* h_params, int64_t n) {
     if (!m || !h_params) return set_error(PLO_ERR_INVALID_ARG, "mlp or params is NULL");
-    if (n != canonical_count(m->n_out)) return set_error(PLO_ERR_INVALID_ARG, "wrong parameter count");
+    if (n != canonical_count(m->arch, m->n_out)) return set_error(PLO_ERR_INVALID_ARG, "wrong parameter count");
     std::vector<float> pad;
     canonical_to_padded(m, h_params, pad);
     cudaError_t e = cudaMemcpy(m->master, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice);
@@ -855,7 +1199,7 @@ extern "C" plo_status plo_mlp_set_params(plo_mlp* m, const float* h_params, int6
 
 static plo_status download_canonical(const plo_mlp* m, const float* dev, float* h, int64_t n) {
     if (!m || !h) return set_error(PLO_ERR_INVALID_ARG, "mlp or output is NULL");
-    if (n != canonical_count(m->n_out)) return set_error(PLO_ERR_INVALID_ARG, "wrong parameter count");
+    if (n != canonical_count(m->arch, m->n_out)) return set_error(PLO_ERR_INVALID_ARG, "wrong parameter count");
     std::vector<float> pad(m->n_params_pad);
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(pad.data(), dev, pad.size() * 4, cudaMemcpyDeviceToHost);
@@ -908,64 +1252,94 @@ extern "C" plo_status plo_mlp_train_step(plo_mlp* m, const float* d_rays, const 
     cudaError_t e = cudaMemsetAsync(m->grad, 0, (size_t)m->n_params_pad * 4, s);
     if (e != cudaSuccess) return cuda_error(e, "gradient clear");
     k_pe<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(d_rays, n_rays, n_samples, d_jitter, D.seed, (uint64_t)m->step,
-                                                     m->H[0], m->delta);
+                                                     m->H[0], m->delta, nullptr);
     st = forward_layers(m, M, s);
     if (st != PLO_OK) return st;
-    const float inv_rays = 1.0f / (float)n_rays;
-    const unsigned qblocks = (unsigned)((n_rays + 3) / 4);
-#define PLO_QUAD(SS)                                                                                               \
-    k_quad<16, SS><<<qblocks, 128, 0, s>>>(m->raw, m->delta, d_rays, d_rgb_gt, d_alpha_gt, n_rays, D.l_max, D.eps, \
-                                           D.transmittance, D.loss, inv_rays, m->dO, m->ray_loss)
-    if (n_samples == 32) PLO_QUAD(1);
-    else if (n_samples == 64) PLO_QUAD(2);
-    else if (n_samples == 128) PLO_QUAD(4);
-    else PLO_QUAD(8);
-#undef PLO_QUAD
-    // backward: head
-    gemm::EpiArgs ep{};
-    ep.err = m->d_err;
-    auto colsum = [&](const __nv_bfloat16* dz, int ncols, float* db) {
-        const int rows = 4096;
-        k_colsum<<<(unsigned)((M + rows - 1) / rows), 256, 0, s>>>(dz, M, ncols, rows, db);
-    };
-    e = launch_wgrad<WIDTH>(m->mapW_dO, m->mapW_H[DEPTH], m->grad + m->geom.off[DEPTH], OUT_PAD, (int)M, m->sms,
-                            m->d_err, s);
-    colsum(m->dO, OUT_PAD, bias_ptr(m, m->grad, DEPTH));
-    ep.out_bf16 = m->dZ[0];
-    ep.ldo = WIDTH;
-    ep.mask = m->H[DEPTH];
-    ep.ldm = WIDTH;
-    if (e == cudaSuccess)
-        e = launch_gemm<WIDTH, OUT_PAD>(m->mapA_dO, m->mapWT[DEPTH], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
-    // hidden layers l = 8 .. 2 (index l-1 = 7 .. 1), then layer 1
-    int cur = 0;
-    for (int l = DEPTH - 1; l >= 0 && e == cudaSuccess; --l) {
-        // dZ[cur] is d loss / d pre-activation of layer l (0-based), input H[l]
-        if (l == 0)
-            e = launch_wgrad<PE_PAD>(m->mapW_dZ[cur], m->mapW_H[0], m->grad + m->geom.off[0], WIDTH, (int)M, m->sms,
-                                     m->d_err, s);
-        else
-            e = launch_wgrad<WIDTH>(m->mapW_dZ[cur], m->mapW_H[l], m->grad + m->geom.off[l], WIDTH, (int)M, m->sms,
-                                    m->d_err, s);
-        colsum(m->dZ[cur], WIDTH, bias_ptr(m, m->grad, l));
-        if (l == 0 || e != cudaSuccess) break;
-        ep.out_bf16 = m->dZ[cur ^ 1];
-        ep.mask = m->H[l];
-        e = launch_gemm<WIDTH, WIDTH>(m->mapA_dZ[cur], m->mapWT[l], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
-        cur ^= 1;
-    }
-    if (e != cudaSuccess) return cuda_error(e, "MLP backward launch");
-    // Adam with exponential decay lr0 -> lr1 over total_steps
-    const double frac = std::fmin((double)(m->step - 1), (double)D.total_steps) / (double)D.total_steps;
-    const float lr = (float)(D.lr0 * std::pow((double)D.lr1 / D.lr0, frac));
-    const float bc1 = (float)(1.0 - std::pow(0.9, (double)m->step));
-    const float bc2 = (float)(1.0 - std::pow(0.999, (double)m->step));
-    const int64_t n = m->n_params_pad;
-    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->geom, m->master, m->adam_m, m->adam_v, m->grad, n, lr, 0.9f,
-                                                       0.999f, 1e-8f, bc1, bc2, 1, m->d_W, m->d_WT);
+    e = launch_quad(m, n_samples, d_rays, d_rgb_gt, d_alpha_gt, n_rays, D.loss, nullptr, s);
+    if (e != cudaSuccess) return cuda_error(e, "quadrature kernel launch");
+    st = backward_update(m, M, s);
+    if (st != PLO_OK) return st;
     k_mean<<<1, 256, 0, s>>>(m->ray_loss, n_rays, d_loss_out);
     e = cudaGetLastError();
     return e == cudaSuccess ? PLO_OK : cuda_error(e, "MLP update launch");
+}
+
+namespace {
+bool hier_counts_ok(int Nc, int Nf) {
+    const int N = Nc + Nf;
+    return Nc % 32 == 0 && Nf % 32 == 0 && Nc >= 32 && Nf >= 32 && Nc <= HIER_MAX_NC &&
+           (N == 64 || N == 96 || N == 128 || N == 192 || N == 256);
+}
+}  // namespace
+
+extern "C" plo_status plo_mlp_train_step_hier(plo_mlp* coarse, plo_mlp* fine, const float* d_rays,
+                                              const float* d_rgb_gt, const float* d_alpha_gt, int32_t n_rays,
+                                              int32_t n_coarse, int32_t n_fine, const float* d_jitter,
+                                              const float* d_xi, float* d_loss_out, void* stream) {
+    if (!coarse || !fine || coarse == fine) return set_error(PLO_ERR_INVALID_ARG, "need two distinct networks");
+    if (!d_rays || !d_rgb_gt || !d_alpha_gt || !d_loss_out)
+        return set_error(PLO_ERR_INVALID_ARG, "rays, targets or loss output is NULL");
+    if (n_rays <= 0) return set_error(PLO_ERR_INVALID_ARG, "n_rays must be > 0");
+    if (!hier_counts_ok(n_coarse, n_fine))
+        return set_error(PLO_ERR_UNSUPPORTED, "n_coarse, n_fine: multiples of 32, n_coarse <= 128, and "
+                                              "n_coarse + n_fine in {64, 96, 128, 192, 256}");
+    if (coarse->desc.l_max != fine->desc.l_max || coarse->desc.transmittance != fine->desc.transmittance ||
+        coarse->desc.loss != fine->desc.loss)
+        return set_error(PLO_ERR_INVALID_ARG, "coarse and fine networks need the same l_max, transmittance and loss");
+    const int N = n_coarse + n_fine;
+    const int64_t Mc = (int64_t)n_rays * n_coarse, Mf = (int64_t)n_rays * N;
+    if (Mc % 128 != 0) return set_error(PLO_ERR_INVALID_ARG, "n_rays * n_coarse must be a multiple of 128");
+    if (Mf > ((int64_t)1 << 28)) return set_error(PLO_ERR_INVALID_ARG, "batch too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    plo_status st = ensure_workspace(coarse, Mc, n_rays);
+    if (st == PLO_OK) st = ensure_workspace(fine, Mf, n_rays);
+    if (st != PLO_OK) return st;
+    ++coarse->step;
+    ++fine->step;
+    const plo_mlp_desc& D = fine->desc;
+    // coarse pass: colour loss only (alpha is supervised on the fine pass)
+    cudaError_t e = cudaMemsetAsync(coarse->grad, 0, (size_t)coarse->n_params_pad * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(fine->grad, 0, (size_t)fine->n_params_pad * 4, s);
+    if (e != cudaSuccess) return cuda_error(e, "gradient clear");
+    k_pe<<<(unsigned)((Mc + 255) / 256), 256, 0, s>>>(d_rays, n_rays, n_coarse, d_jitter, coarse->desc.seed,
+                                                      (uint64_t)coarse->step, coarse->H[0], coarse->delta,
+                                                      coarse->tsamp);
+    st = forward_layers(coarse, Mc, s);
+    if (st != PLO_OK) return st;
+    const int coarse_loss = D.loss == PLO_LOSS_PAPER ? PLO_LOSS_REG : D.loss;
+    e = launch_quad(coarse, n_coarse, d_rays, d_rgb_gt, d_alpha_gt, n_rays, coarse_loss, coarse->wts, s);
+    if (e != cudaSuccess) return cuda_error(e, "quadrature kernel launch");
+    // fine samples placed by the coarse weights (no gradient through them)
+    k_fine<<<(unsigned)((n_rays + HIER_WARPS - 1) / HIER_WARPS), 32 * HIER_WARPS, 0, s>>>(
+        d_rays, n_rays, n_coarse, n_fine, coarse->tsamp, coarse->delta, coarse->wts, d_xi, D.seed,
+        (uint64_t)fine->step, fine->H[0], fine->delta, nullptr);
+    st = backward_update(coarse, Mc, s);
+    if (st != PLO_OK) return st;
+    st = forward_layers(fine, Mf, s);
+    if (st != PLO_OK) return st;
+    e = launch_quad(fine, N, d_rays, d_rgb_gt, d_alpha_gt, n_rays, D.loss, nullptr, s);
+    if (e != cudaSuccess) return cuda_error(e, "quadrature kernel launch");
+    st = backward_update(fine, Mf, s);
+    if (st != PLO_OK) return st;
+    k_mean<<<1, 256, 0, s>>>(coarse->ray_loss, n_rays, d_loss_out, fine->ray_loss);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "loss reduction launch");
+}
+
+extern "C" plo_status plo_hier_samples(const float* d_rays, int32_t n_rays, int32_t n_coarse, int32_t n_fine,
+                                       const float* d_t, const float* d_delta, const float* d_w, const float* d_xi,
+                                       float* d_t_out, float* d_delta_out, void* stream) {
+    if (!d_rays || !d_t || !d_delta || !d_w || !d_xi || !d_t_out || !d_delta_out)
+        return set_error(PLO_ERR_INVALID_ARG, "a buffer is NULL");
+    if (n_rays < 0) return set_error(PLO_ERR_INVALID_ARG, "n_rays must be >= 0");
+    if (!hier_counts_ok(n_coarse, n_fine))
+        return set_error(PLO_ERR_UNSUPPORTED, "n_coarse, n_fine: multiples of 32, n_coarse <= 128, and "
+                                              "n_coarse + n_fine in {64, 96, 128, 192, 256}");
+    if (n_rays == 0) return PLO_OK;
+    k_fine<<<(unsigned)((n_rays + HIER_WARPS - 1) / HIER_WARPS), 32 * HIER_WARPS, 0, (cudaStream_t)stream>>>(
+        d_rays, n_rays, n_coarse, n_fine, d_t, d_delta, d_w, d_xi, 0, 0, nullptr, d_delta_out, d_t_out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "fine-sample kernel launch");
 }
 
 extern "C" plo_status plo_mlp_check(const plo_mlp* m, void* stream) {

@@ -61,6 +61,8 @@ struct KParams {
     TreeParams tree;
     int32_t transmittance, activation;
     float l_max, t_stop, sigma_min;
+    int32_t saturate, proxy;
+    float sphere[4];  // sphere proxy: centre, radius (world space)
     const float* rays;
     int64_t n;
     int64_t chunk;  // rays per warp
@@ -112,6 +114,14 @@ __device__ __forceinline__ DF df_axpy(DF p, DF t, float dh, float dl) {
     DF s = two_sum(p.hi, m);
     float lo = __fadd_rn(__fadd_rn(s.lo, p.lo), me);
     return fast_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) {
+    DF s = two_sum(a.hi, -b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_from_double(double x) {
+    const float hi = __double2float_rn(x);
+    return {hi, __double2float_rn(x - (double)hi)};
 }
 // (P - p) for an exact float plane P
 __device__ __forceinline__ DF df_from_plane(float P, DF p) {
@@ -228,6 +238,7 @@ struct Ray {
     float T, r, g, b;
     DF od;
     DF t;               // ray parameter at the current cell entry (trace only)
+    DF rem;             // ray parameter left inside the sphere proxy (sphere only)
     uint32_t c[3];      // integer cell coordinates at `level`
     uint32_t node;      // node whose child is looked up next (ST_DESCEND)
     uint32_t entry_x, entry_y;
@@ -274,7 +285,7 @@ __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* 
             }
             return;
         }
-        stack[R.level] = e.x;
+        stack[R.level * BLOCK] = e.x;
         const uint32_t parent = R.node;
         R.node = e.x;
         (void)parent;
@@ -286,14 +297,14 @@ __device__ __forceinline__ void ray_store(const KParams& kp, int64_t i, const Ra
     kp.rgb[3 * i + 0] = R.r;
     kp.rgb[3 * i + 1] = R.g;
     kp.rgb[3 * i + 2] = R.b;
-    kp.T[i] = R.T;
+    kp.T[i] = kp.saturate && R.T < kp.t_stop ? 0.0f : R.T;  // a saturated ray is opaque (Sec. 6.2)
     if (kp.status) kp.status[i] = R.status;
     if (kp.tr_count) kp.tr_count[i] = R.steps;
 }
 
 // Proxy clip.  On a hit the lane enters ST_DESCEND at the root; on a miss or
 // an invalid ray the outputs are written and the lane stays ST_IDLE.
-template <bool TRACE>
+template <bool TRACE, bool SPHERE>
 __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ray& R, uint32_t* stack) {
     const float* q = kp.rays + 6 * i;
     float o[3], dw[3];
@@ -361,7 +372,34 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
         ray_store(kp, i, R);
         return;
     }
+    if (SPHERE) {
+        // sphere proxy (Sec. 5): keep the part of [tn, tf] inside the ball
+        // |o + t d - c| <= r, solved once per ray in FP64 in world space
+        double a2 = 0.0, b = 0.0, q = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double oc = (double)o[a] - (double)kp.sphere[a], dd = (double)dw[a];
+            a2 += dd * dd;
+            b += oc * dd;
+            q += oc * oc;
+        }
+        const double r = (double)kp.sphere[3];
+        const double disc = b * b - a2 * (q - r * r);
+        if (!(disc > 0.0)) {
+            ray_store(kp, i, R);
+            return;
+        }
+        const double sq = sqrt(disc);
+        const DF s0 = df_from_double((-b - sq) / a2), s1 = df_from_double((-b + sq) / a2);
+        if (df_less(tn, s0)) tn = s0;
+        if (df_less(s1, tf)) tf = s1;
+        if (!df_less(tn, tf) || !(tf.hi > 0.0f || (tf.hi == 0.0f && tf.lo > 0.0f))) {
+            ray_store(kp, i, R);
+            return;
+        }
+    }
     bool outside = tn.hi > 0.0f || (tn.hi == 0.0f && tn.lo > 0.0f);
+    if (SPHERE) R.rem = outside ? df_sub(tf, tn) : tf;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         R.p[a] = outside ? df_axpy(ou[a], tn, R.d[a], R.dl[a]) : ou[a];
@@ -379,7 +417,7 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
 
 // One cell: segment length, compositing, advance.  Leaves the lane in
 // ST_DESCEND (next cell) or ST_IDLE (ray finished, outputs written).
-template <int K, int PREC, bool TRACE>
+template <int K, int PREC, bool TRACE, bool SPHERE>
 __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ray& R, uint32_t* stack,
                           const float* sY = nullptr) {
     // segment: exit parameter of the current cell along each axis
@@ -400,6 +438,15 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
         dts[a] = v;
         if (df_less(v, dt)) dt = v;
     }
+    bool last = false;  // the sphere proxy ends inside this cell
+    if (SPHERE) {
+        if (df_less(dt, R.rem)) {
+            R.rem = df_sub(R.rem, dt);
+        } else {
+            dt = R.rem;
+            last = true;
+        }
+    }
     const float seg = dt.hi;
     ++R.steps;
 
@@ -410,7 +457,7 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
         if (k < kp.trace_max) {
             size_t o = (size_t)i * kp.trace_max + k;
             kp.tr_leaf[o] = R.entry_x == ENTRY_EMPTY ? -1
-                                                     : __ldg(tp.leaf_ids + (size_t)stack[L - 1] * 8 + R.slot);
+                                                     : __ldg(tp.leaf_ids + (size_t)stack[(L - 1) * BLOCK] * 8 + R.slot);
             kp.tr_t[2 * o] = R.t.hi;
             kp.tr_t[2 * o + 1] = t1.hi;
         }
@@ -452,6 +499,11 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
             }
         }
     }
+    if (last) {
+        ray_store(kp, i, R);
+        R.state = ST_IDLE;
+        return;
+    }
     if (R.steps >= tp.max_steps) {
         R.status = PLO_RAY_STEP_LIMIT;
         atomicOr(tp.flags, 1u);
@@ -489,11 +541,11 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
 #pragma unroll
     for (int a = 0; a < 3; ++a) R.c[a] = nc[a] >> (L - l_anc);
     R.level = l_anc;
-    R.node = stack[l_anc];
+    R.node = stack[l_anc * BLOCK];
     R.state = ST_DESCEND;
 }
 
-template <int K, int PREC, bool TRACE>
+template <int K, int PREC, bool TRACE, bool SPHERE>
 __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams kp) {
     // nodes of the top levels, staged once per (persistent) block
     extern __shared__ uint2 s_nodes[];
@@ -501,7 +553,9 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams
     for (int j = threadIdx.x; j < tp.n_top * 8; j += BLOCK) s_nodes[j] = tp.nodes[j];
     __syncthreads();
 
-    uint32_t stack[STACK];  // node id per level of the current cell's path
+    // node id per level of the current cell's path, one column per thread
+    __shared__ uint32_t s_stack[STACK * BLOCK];
+    uint32_t* stack = s_stack + threadIdx.x;
     __shared__ float s_Y[16 * BLOCK];
     float* sY = s_Y + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -520,12 +574,14 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams
         // finish at once, so repeat while lanes are idle and rays remain
         for (;;) {
             unsigned idle = __ballot_sync(0xffffffffu, R.state == ST_IDLE);
-            if (idle == 0u || next >= end) break;
+            // refill in groups: ray setup runs with at least 8 lanes (or when
+            // no ray is left in flight)
+            if (idle == 0u || next >= end || (__popc(idle) < 8 && idle != 0xffffffffu)) break;
             int64_t cand = next + __popc(idle & lanes_below);
             next += __popc(idle);
             if (R.state == ST_IDLE && cand < end) {
                 my = cand;
-                ray_begin<TRACE>(kp, tp, my, R, stack);
+                ray_begin<TRACE, SPHERE>(kp, tp, my, R, stack);
                 if (R.state != ST_IDLE) {
                     float Y[K];
                     sh_basis<K>(R.dirn[0], R.dirn[1], R.dirn[2], Y);
@@ -534,8 +590,13 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams
                 }
             }
         }
-        if (__ballot_sync(0xffffffffu, R.state != ST_IDLE) == 0u) break;
-        if (R.state == ST_LEAF) leaf_step<K, PREC, TRACE>(kp, tp, my, R, stack, sY);
+        const unsigned live = __ballot_sync(0xffffffffu, R.state != ST_IDLE);
+        if (live == 0u) break;
+        // composite in batches: while some lanes still descend, lanes that
+        // found their cell wait until enough of the live lanes have one
+        const unsigned at_leaf = __ballot_sync(0xffffffffu, R.state == ST_LEAF);
+        const bool composite = 2 * __popc(at_leaf) >= 1 * __popc(live);
+        if (composite && R.state == ST_LEAF) leaf_step<K, PREC, TRACE, SPHERE>(kp, tp, my, R, stack, sY);
         if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
     }
 }
@@ -571,7 +632,8 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(B
     __syncthreads();
     const KParams& kp = bp.base;
     const long long total = s_off[bp.n_trees];
-    uint32_t stack[STACK];
+    __shared__ uint32_t s_stack[STACK * BLOCK];
+    uint32_t* stack = s_stack + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
 
@@ -604,12 +666,12 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(B
                 int t = 0;
                 while (t + 1 < bp.n_trees && s_off[t + 1] <= cand) ++t;
                 R.tree = t;
-                ray_begin<false>(kp, s_tp[t], my, R, stack);
+                ray_begin<false, false>(kp, s_tp[t], my, R, stack);
             }
         }
         if (__ballot_sync(0xffffffffu, R.state != ST_IDLE) == 0u) break;
         const TreeParams& tp = s_tp[R.tree];
-        if (R.state == ST_LEAF) leaf_step<0, -1, false>(kp, tp, my, R, stack);
+        if (R.state == ST_LEAF) leaf_step<0, -1, false, false>(kp, tp, my, R, stack);
         if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
     }
 }
@@ -658,9 +720,9 @@ __global__ void k_lookup(const uint2* nodes, const int32_t* leaf_ids, int depth,
 
 // Persistent grid: as many blocks as fit on the device at once (occupancy
 // API), each warp owning a contiguous chunk of the rays.
-template <int K, int PREC, bool TRACE>
+template <int K, int PREC, bool TRACE, bool SPHERE>
 cudaError_t launch_k(KParams kp, int sm_count, size_t smem, cudaStream_t s) {
-    auto fn = k_render<K, PREC, TRACE>;
+    auto fn = k_render<K, PREC, TRACE, SPHERE>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -677,10 +739,10 @@ cudaError_t launch_k(KParams kp, int sm_count, size_t smem, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <bool TRACE>
+template <bool TRACE, bool SPHERE>
 cudaError_t dispatch(const plo_tree* t, const KParams& kp, size_t smem, cudaStream_t s) {
 #define PLO_CASE(KK, PP)                                                   \
-    if (t->K == KK && t->precision == PP) return launch_k<KK, PP, TRACE>(kp, t->sm_count, smem, s);
+    if (t->K == KK && t->precision == PP) return launch_k<KK, PP, TRACE, SPHERE>(kp, t->sm_count, smem, s);
     PLO_CASE(1, PLO_PREC_FP32) PLO_CASE(4, PLO_PREC_FP32) PLO_CASE(9, PLO_PREC_FP32) PLO_CASE(16, PLO_PREC_FP32)
     PLO_CASE(1, PLO_PREC_FP16) PLO_CASE(4, PLO_PREC_FP16) PLO_CASE(9, PLO_PREC_FP16) PLO_CASE(16, PLO_PREC_FP16)
     PLO_CASE(1, PLO_PREC_BF16) PLO_CASE(4, PLO_PREC_BF16) PLO_CASE(9, PLO_PREC_BF16) PLO_CASE(16, PLO_PREC_BF16)
@@ -719,6 +781,14 @@ plo_status check_params(const plo_render_params* p) {
     if (p->activation == PLO_ACT_SIGMOID && !std::isfinite(p->l_max))
         return set_error(PLO_ERR_INVALID_ARG, "l_max must be finite");
     if (p->max_steps < 0) return set_error(PLO_ERR_INVALID_ARG, "max_steps must be >= 0");
+    if (p->saturate != 0 && p->saturate != 1) return set_error(PLO_ERR_INVALID_ARG, "saturate must be 0 or 1");
+    if (p->proxy != PLO_PROXY_BOX && p->proxy != PLO_PROXY_SPHERE)
+        return set_error(PLO_ERR_INVALID_ARG, "unknown proxy");
+    if (p->proxy == PLO_PROXY_SPHERE) {
+        for (int a = 0; a < 4; ++a)
+            if (!std::isfinite(p->sphere[a])) return set_error(PLO_ERR_INVALID_ARG, "sphere must be finite");
+        if (!(p->sphere[3] > 0.0f)) return set_error(PLO_ERR_INVALID_ARG, "sphere radius must be > 0");
+    }
     return PLO_OK;
 }
 
@@ -734,6 +804,8 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     if (!d_rays || !d_rgb || !d_T) return set_error(PLO_ERR_INVALID_ARG, "rays, rgb or T is NULL");
     if (TRACE && (trace_max <= 0 || !tr_leaf || !tr_t || !tr_count))
         return set_error(PLO_ERR_INVALID_ARG, "trace buffers are NULL or max_cells <= 0");
+    if (TRACE && p->proxy != PLO_PROXY_BOX)
+        return set_error(PLO_ERR_UNSUPPORTED, "plo_trace_rays follows the box proxy only");
     KParams kp{};
     fill_tree_params(t, p, &kp.tree);
     kp.transmittance = p->transmittance;
@@ -741,6 +813,9 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     kp.l_max = p->l_max;
     kp.t_stop = p->t_stop;
     kp.sigma_min = p->sigma_min;
+    kp.saturate = p->saturate;
+    kp.proxy = p->proxy;
+    for (int a = 0; a < 4; ++a) kp.sphere[a] = p->sphere[a];
     kp.rays = d_rays;
     kp.n = n;
     kp.rgb = d_rgb;
@@ -751,7 +826,13 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     kp.tr_t = tr_t;
     kp.tr_count = tr_count;
     size_t smem = (size_t)t->n_top * 8 * sizeof(uint2);
-    cudaError_t e = dispatch<TRACE>(t, kp, smem, (cudaStream_t)stream);
+    cudaError_t e;
+    if (TRACE)
+        e = dispatch<TRACE, false>(t, kp, smem, (cudaStream_t)stream);
+    else if (kp.proxy == PLO_PROXY_SPHERE)
+        e = dispatch<false, true>(t, kp, smem, (cudaStream_t)stream);
+    else
+        e = dispatch<false, false>(t, kp, smem, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_error(e, "render kernel launch");
     return PLO_OK;
 }
@@ -939,6 +1020,8 @@ extern "C" plo_status plo_batch_create(const plo_tree* const* trees, int32_t n_t
         return set_error(PLO_ERR_INVALID_ARG, "n_trees must be in [1, " + std::to_string(MAX_BATCH) + "]");
     plo_status st = check_params(params);
     if (st != PLO_OK) return st;
+    if (params->proxy != PLO_PROXY_BOX)
+        return set_error(PLO_ERR_UNSUPPORTED, "the batch render clips to each tree's box (PLO_PROXY_BOX only)");
     if (ray_offsets[0] != 0) return set_error(PLO_ERR_INVALID_ARG, "ray_offsets[0] must be 0");
     for (int t = 0; t < n_trees; ++t) {
         if (!trees[t]) return set_error(PLO_ERR_INVALID_ARG, "a tree is NULL");
@@ -958,6 +1041,8 @@ extern "C" plo_status plo_batch_create(const plo_tree* const* trees, int32_t n_t
     kp.l_max = params->l_max;
     kp.t_stop = params->t_stop;
     kp.sigma_min = params->sigma_min;
+    kp.saturate = params->saturate;
+    kp.proxy = PLO_PROXY_BOX;
     kp.n = b->n_rays;
     for (int t = 0; t < n_trees; ++t) {
         fill_tree_params(trees[t], params, &b->bp.trees[t]);
@@ -967,8 +1052,8 @@ extern "C" plo_status plo_batch_create(const plo_tree* const* trees, int32_t n_t
     b->bp.n_trees = n_trees;
     b->cfg = {256, 0, BATCH_TOP_NODES};
     apply_config(b);
-    cudaError_t e = cudaMalloc((void**)&b->d_cursor, 256);
-    if (e != cudaSuccess) {
+    int e = dev_malloc((void**)&b->d_cursor, 256);
+    if (e != 0) {
         delete b;
         return cuda_error(e, "batch cursor allocation");
     }

@@ -10,7 +10,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (ACT_SIGMOID, LOSS_PAPER, PREC_FP32, Mlp, RenderParams, Tree, render)
+from . import (ACT_SIGMOID, ARCH_PAPER, LOSS_PAPER, PREC_FP32, Mlp, RenderParams, Tree, render)
 
 
 def target_batches(gt_tree: Tree, ray_sets):
@@ -54,6 +54,32 @@ def train(batches, steps: int, loss: int = LOSS_PAPER, n_samples: int = 128, l_m
     dt = time.perf_counter() - t0
     net.check()
     return net, losses[:steps].cpu().numpy(), dt
+
+
+def train_hier(batches, steps: int, n_coarse: int = 64, n_fine: int = 128, l_max=None, init_radiance=None,
+               seed: int = 1, lr0: float = 5e-4, lr1: float = 5e-6, arch: int = ARCH_PAPER):
+    """The paper's full setup (Sec. 4.2-4.4): coarse and fine networks with
+    the 128-wide SH output layer, N_c + N_f samples, loss L_c + L_f + L_alpha.
+    Returns (coarse, fine, per-step losses, seconds)."""
+    import torch
+    lm, c0 = emission_scale(batches)
+    l_max = l_max or lm
+    kw = dict(l_max=l_max, loss=LOSS_PAPER, total_steps=max(steps, 1), lr0=lr0, lr1=lr1, arch=arch,
+              init_radiance=c0 if init_radiance is None else init_radiance)
+    coarse = Mlp(seed=seed, jitter_seed=2 * seed, **kw)
+    fine = Mlp(seed=seed + 1, jitter_seed=2 * seed + 1, **kw)
+    losses = torch.empty(max(steps, 1), device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        rays, rgb, alpha = batches[k % len(batches)]
+        Mlp.train_step_hier(coarse, fine, rays, rgb, alpha, n_coarse=n_coarse, n_fine=n_fine,
+                            loss_out=losses[k:k + 1])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    coarse.check()
+    fine.check()
+    return coarse, fine, losses[:steps].cpu().numpy(), dt
 
 
 @dataclass

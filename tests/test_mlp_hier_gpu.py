@@ -1,0 +1,211 @@
+"""GPU parity of the paper's full training setup (Sec. 4.2-4.4): the network
+with the extra 128-wide SH layer, the fine-sample placement, and one
+coarse/fine training step, against the FP64 oracle (oracle/mlp.py) on the
+same bf16-rounded weights and the same random inputs."""
+import numpy as np
+import pytest
+
+import paper_2207_05009_gb300 as plo
+import plogen
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(cuda_available):
+    import torch
+    return torch
+
+
+def bf16(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def unflatten(flat):
+    Ws, bs, i = [], [], 0
+    for (o, n) in omlp.layer_shapes_paper(3):
+        Ws.append(flat[i:i + o * n].reshape(o, n).astype(np.float64))
+        i += o * n
+        bs.append(flat[i:i + o].astype(np.float64))
+        i += o
+    assert i == flat.size
+    return Ws, bs
+
+
+def flatten(Ws, bs):
+    return np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(Ws, bs)])
+
+
+def paper_params(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    Ws, bs = omlp.init_params_paper(rng)
+    Ws = [w * scale for w in Ws]
+    bs = [rng.normal(0, 0.05, b.shape) for b in bs]
+    bs[omlp.DEPTH][0] = 1.0
+    return flatten(Ws, bs).astype(np.float32)
+
+
+def cosine(a, b):
+    return float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_paper_arch_param_layout_and_forward(torch_cuda):
+    torch = torch_cuda
+    flat = paper_params(1)
+    net = plo.Mlp(l_max=8.0, arch=plo.ARCH_PAPER)
+    assert net.n_params == flat.size
+    net.set_params(flat)
+    np.testing.assert_array_equal(net.get_params(), flat)
+    pts = np.random.default_rng(2).random((10_000, 3)).astype(np.float32)
+    raw = net.forward(dev(torch, pts))
+    torch.cuda.synchronize()
+    net.check()
+    raw = raw.cpu().numpy().astype(np.float64)
+    Ws, bs = unflatten(flat)
+    ref, _ = omlp.forward_paper([bf16(w) for w in Ws], bs, omlp.positional_encoding(pts.astype(np.float64)))
+    for cols in (slice(0, 1), slice(1, 49)):  # sigma, then the SH coefficients
+        a, b = raw[:, cols].ravel(), ref[:, cols].ravel()
+        assert cosine(a, b) > 0.999
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 3e-2
+
+
+@pytest.mark.parametrize("loss,trans", [(plo.LOSS_PAPER, plo.TRANS_EXP), (plo.LOSS_PAPER, plo.TRANS_LINEAR)])
+def test_paper_arch_gradients_match_oracle(torch_cuda, loss, trans):
+    torch = torch_cuda
+    R, N = 64, 32
+    flat = paper_params(3, scale=0.5)
+    net = plo.Mlp(l_max=6.0, loss=loss, transmittance=trans, arch=plo.ARCH_PAPER)
+    net.set_params(flat)
+    rays = plogen.rays_sphere(R, seed=4)
+    rng = np.random.default_rng(5)
+    jit = rng.random((R, N)).astype(np.float32)
+    C_gt = rng.uniform(0, 5, (R, 3)).astype(np.float32)
+    a_gt = rng.uniform(0, 1, R).astype(np.float32)
+    loss_gpu = net.train_step(dev(torch, rays), dev(torch, C_gt), dev(torch, a_gt), n_samples=N,
+                              jitter=dev(torch, jit))
+    torch.cuda.synchronize()
+    net.check()
+    g = net.get_grads().astype(np.float64)
+    Ws, bs = unflatten(flat)
+    tname = "exp" if trans == plo.TRANS_EXP else "linear"
+    L, dWs, dbs, _ = omlp.train_loss_and_grads([bf16(w) for w in Ws], bs, rays, jit.astype(np.float64),
+                                               C_gt.astype(np.float64), a_gt.astype(np.float64), 6.0,
+                                               transmittance=tname, arch="paper")
+    ref = flatten(dWs, dbs)
+    assert float(loss_gpu.item()) == pytest.approx(L, rel=2e-2)
+    assert cosine(g, ref) > 0.999
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 3e-2
+    i = 0
+    for w, b in zip(dWs, dbs):  # every block, including sigma, the 128 layer and the SH layer
+        n = w.size + b.size
+        assert cosine(g[i:i + n], ref[i:i + n]) > 0.99
+        i += n
+
+
+@pytest.mark.parametrize("nc,nf", [(64, 128), (32, 32), (64, 64), (128, 128)])
+def test_fine_sample_placement_matches_oracle(torch_cuda, nc, nf):
+    torch = torch_cuda
+    R = 257  # ragged: not a multiple of the 4 rays per block
+    rays = plogen.rays_sphere(R, seed=7)
+    rays[::17, 3:] *= -1.0  # some rays point away and miss the cube
+    rng = np.random.default_rng(8)
+    t, delta, _, hit = omlp.stratified_samples(rays, rng.random((R, nc)))
+    w = rng.random((R, nc)) ** 3 * (rng.random((R, nc)) < 0.7)
+    w = np.where(hit[:, None], w / np.maximum(w.sum(1, keepdims=True), 1e-12) * 0.9, 0.0)
+    xi = rng.random((R, nf))
+    f32 = lambda a: np.ascontiguousarray(a, np.float32)
+    # both sides see the same FP32 inputs
+    t, delta, w, xi = (f32(a).astype(np.float64) for a in (t, delta, w, xi))
+    t_g, d_g = plo.hier_samples(dev(torch, f32(rays)), dev(torch, f32(t)), dev(torch, f32(delta)),
+                                dev(torch, f32(w)), dev(torch, f32(xi)))
+    torch.cuda.synchronize()
+    t_g, d_g = t_g.cpu().numpy(), d_g.cpu().numpy()
+    tf = omlp.fine_samples(t, delta, w, xi)
+    o, d = rays[:, :3].astype(np.float64), rays[:, 3:].astype(np.float64)
+    _, t1, _ = omlp.clip_unit_cube(o, d)
+    ta, da = omlp.merge_samples(t, tf, np.where(hit, t1, 0.0))
+    da = np.where(hit[:, None], da, 0.0)
+    assert np.all(np.diff(t_g, axis=1) >= 0)
+    assert np.all(d_g[~hit] == 0) and np.all(t_g[~hit] == 0)
+    # FP32 placement: where the density is low a CDF rounding moves t a lot,
+    # where it is high a t rounding moves the CDF a lot; each merged sample
+    # must be within rounding of the exact one in t (8 ulp) or in the CDF
+    # of the coarse density (1e-5)
+    for r in np.nonzero(hit)[0]:
+        m = (w[r] + 1e-5) / (w[r] + 1e-5).sum()
+
+        def cdf(x):
+            inside = np.clip((x[:, None] - t[r][None]) / np.where(delta[r] > 0, delta[r], 1.0)[None], 0.0, 1.0)
+            return inside @ m
+        ulp = np.spacing(np.abs(ta[r]).astype(np.float32)).astype(np.float64)
+        score = np.minimum(np.abs(t_g[r] - ta[r]) / (8 * ulp), np.abs(cdf(t_g[r].astype(np.float64)) - cdf(ta[r])) / 1e-5)
+        assert score.max() <= 1.0, (r, score.max())
+        # the coarse parameters are carried over exactly
+        assert np.isin(f32(t[r]), t_g[r]).all()
+        # lengths are the gaps of the merged list, the last one ends at the exit
+        np.testing.assert_array_equal(d_g[r, :-1], np.diff(t_g[r]).astype(np.float32))
+        assert d_g[r, -1] == pytest.approx(t1[r] - ta[r, -1], abs=1e-5)
+
+
+@pytest.mark.parametrize("trans", [plo.TRANS_EXP, plo.TRANS_LINEAR])
+def test_coarse_fine_step_matches_oracle(torch_cuda, trans):
+    torch = torch_cuda
+    R, NC, NF = 64, 32, 64
+    fc, ff = paper_params(11, scale=0.5), paper_params(12, scale=0.5)
+    kw = dict(l_max=6.0, loss=plo.LOSS_PAPER, transmittance=trans, arch=plo.ARCH_PAPER)
+    coarse, fine = plo.Mlp(**kw), plo.Mlp(**kw)
+    coarse.set_params(fc)
+    fine.set_params(ff)
+    rays = plogen.rays_sphere(R, seed=13)
+    rng = np.random.default_rng(14)
+    jit = rng.random((R, NC)).astype(np.float32)
+    xi = rng.random((R, NF)).astype(np.float32)
+    C_gt = rng.uniform(0, 5, (R, 3)).astype(np.float32)
+    a_gt = rng.uniform(0, 1, R).astype(np.float32)
+    loss_gpu = plo.Mlp.train_step_hier(coarse, fine, dev(torch, rays), dev(torch, C_gt), dev(torch, a_gt),
+                                       n_coarse=NC, n_fine=NF, jitter=dev(torch, jit), xi=dev(torch, xi))
+    torch.cuda.synchronize()
+    coarse.check()
+    fine.check()
+    gc, gf = coarse.get_grads().astype(np.float64), fine.get_grads().astype(np.float64)
+    Wc, bc = unflatten(fc)
+    Wf, bf = unflatten(ff)
+    tname = "exp" if trans == plo.TRANS_EXP else "linear"
+    L, (dWc, dbc), (dWf, dbf), ex = omlp.train_loss_and_grads_hier(
+        [bf16(w) for w in Wc], bc, [bf16(w) for w in Wf], bf, rays, jit.astype(np.float64), xi.astype(np.float64),
+        C_gt.astype(np.float64), a_gt.astype(np.float64), 6.0, transmittance=tname)
+    assert float(loss_gpu.item()) == pytest.approx(L, rel=3e-2)
+    rc, rf = flatten(dWc, dbc), flatten(dWf, dbf)
+    assert cosine(gc, rc) > 0.999
+    # the fine samples follow the coarse weights of the bf16 network, so the
+    # fine network sees slightly moved samples
+    assert cosine(gf, rf) > 0.99
+    assert coarse.step == 1 and fine.step == 1
+
+
+def test_coarse_fine_training_reduces_loss(torch_cuda):
+    torch = torch_cuda
+    t = plo.Tree(plogen.luminaire_tree(plogen.LUMINAIRE_D6))
+    batches = []
+    for k in range(8):
+        rays = torch.from_numpy(plogen.rays_sphere(1024, seed=300 + k)).cuda()
+        rgb, T, _ = plo.render(t, rays)
+        batches.append((rays, rgb, 1.0 - T))
+    l_max = float(max(b[1].max().item() for b in batches))
+    c0 = float(sum(b[1].mean().item() for b in batches) / max(sum(b[2].mean().item() for b in batches), 1e-3))
+    kw = dict(l_max=l_max, total_steps=400, init_radiance=c0, arch=plo.ARCH_PAPER)
+    coarse, fine = plo.Mlp(seed=1, **kw), plo.Mlp(seed=2, jitter_seed=5, **kw)
+    losses = []
+    for step in range(200):
+        rays, rgb, alpha = batches[step % 8]
+        losses.append(float(plo.Mlp.train_step_hier(coarse, fine, rays, rgb, alpha).item()))
+    coarse.check()
+    fine.check()
+    assert np.all(np.isfinite(losses))
+    assert np.mean(losses[-20:]) < 0.7 * np.mean(losses[:20])

@@ -247,3 +247,70 @@ def test_deterministic_and_host_path(torch_cuda, d6):
     h_rgb, h_T = plo.render_host(t, rays)
     np.testing.assert_array_equal(h_rgb, a[0].cpu().numpy())
     np.testing.assert_array_equal(h_T, a[1].cpu().numpy())
+
+
+# ---------------------------------------------------------------- sphere proxy (Sec. 5) and the
+# sigma_min / alpha_max heuristics (Sec. 6.2)
+
+def cube_rays(n, seed):
+    """Origins uniform inside the unit cube, isotropic unit directions."""
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return np.concatenate([rng.uniform(0, 1, (n, 3)), d], 1).astype(np.float32)
+
+
+@pytest.mark.parametrize("model", ["exp", "lin"])
+@pytest.mark.parametrize("sphere", [(0.5, 0.5, 0.5, 0.4), (0.62, 0.45, 0.5, 0.55), (0.5, 0.5, 0.5, 0.9)])
+def test_sphere_proxy_parity(torch_cuda, d6, model, sphere):
+    rays = np.concatenate([plogen.rays_sphere(32768, seed=31), cube_rays(4096, 33)])
+    g_rgb, g_T, st = gpu_render(torch_cuda, d6, rays, transmittance=TRANS[model][0], sphere=sphere)
+    # the API takes the sphere in FP32: give the oracle the same values
+    sphere = tuple(float(np.float32(v)) for v in sphere)
+    ref = oracle.render(d6, rays, transmittance=TRANS[model][1], sphere=sphere)
+    assert np.all(st == 0)
+    eta = 0.0 if model == "exp" else COND_ETA_LINEAR
+    assert_radiance_close(g_rgb, g_T, ref, RTOL_FP32, what=f"sphere {sphere} {model}", cond_eta=eta)
+    box = oracle.render(d6, rays, transmittance=TRANS[model][1])
+    clipped = np.abs(box["T"] - ref["T"]) > 1e-6
+    if sphere[3] < 0.87:
+        assert clipped.sum() > 100  # the ball cuts the luminaire: the clip is exercised
+    else:
+        assert not clipped.any()
+
+
+def test_paper_heuristics_parity(torch_cuda, d6):
+    rays = plogen.rays_sphere(65536, seed=32)
+    hp = dict(sigma_min=0.1, saturate=True)
+    g_rgb, g_T, _ = gpu_render(torch_cuda, d6, rays, t_stop=0.1, **hp)
+    ref = oracle.render(d6, rays, t_stop=0.1, **hp)
+    # rays whose running T passes within FP32 rounding of t_stop may stop one
+    # leaf apart: find them by moving the threshold by 1e-5 either way
+    lo = oracle.render(d6, rays, t_stop=0.1 * (1 - 1e-5), **hp)
+    hi = oracle.render(d6, rays, t_stop=0.1 * (1 + 1e-5), **hp)
+    near = (lo["n_leaf"] != hi["n_leaf"]) | ((lo["T"] == 0) != (hi["T"] == 0))
+    assert near.mean() < 1e-3
+    assert_radiance_close(g_rgb, g_T, ref, RTOL_FP32, mask=~near, what="sigma_min 0.1, alpha_max 0.9")
+    saturated = ref["T"] == 0
+    assert saturated.sum() > 1000
+    assert np.all(g_T[saturated & ~near] == 0)
+    # the preset in the binding is the same parameter set
+    p = plo.RenderParams.paper_heuristics()
+    assert (p.sigma_min, p.t_stop, p.saturate) == (0.1, 0.1, True)
+
+
+def test_sphere_proxy_rejected_where_unsupported(torch_cuda, d6):
+    import torch
+    t = plo.Tree(d6)
+    rays = torch.from_numpy(plogen.rays_sphere(64, seed=34)).cuda()
+    sp = plo.RenderParams(sphere=(0.5, 0.5, 0.5, 0.4))
+    with pytest.raises(plo.PloError) as ei:
+        plo.trace(t, rays, 16, sp)
+    assert ei.value.status == -7
+    with pytest.raises(plo.PloError) as ei:
+        plo.Batch([t], [0, 64], sp)
+    assert ei.value.status == -7
+    for bad in ((0.5, 0.5, 0.5, 0.0), (0.5, float("nan"), 0.5, 0.3)):
+        with pytest.raises(plo.PloError) as ei:
+            plo.render(t, rays, plo.RenderParams(sphere=bad))
+        assert ei.value.status == -1
