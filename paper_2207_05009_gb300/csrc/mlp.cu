@@ -594,7 +594,10 @@ __global__ void __launch_bounds__(32 * HIER_WARPS)
         }
         const float span = C[lo + 1] - C[lo];
         const float frac = span > 0.0f ? fminf(fmaxf((u - C[lo]) / span, 0.0f), 1.0f) : 0.0f;
-        tf[q] = T[lo] + frac * D[lo];
+        // inside the segment, also after rounding, so the ranks below give an
+        // ascending list
+        const float hi_t = lo + 1 < Nc ? T[lo + 1] : T[lo] + D[lo];
+        tf[q] = fminf(fmaxf(T[lo] + frac * D[lo], T[lo]), hi_t);
         bf[q] = lo;
         atomicAdd(&cnt[lo], 1);
     }

@@ -135,6 +135,19 @@ __device__ __forceinline__ int above(DF p, float m, float d) {
     return p.hi > m || (p.hi == m && (p.lo > 0.0f || (p.lo == 0.0f && d >= 0.0f)));
 }
 __device__ __forceinline__ float pow2i(int e) { return __int_as_float((127 + e) << 23); }  // e in [-126, 127]
+// Finest-grid coordinate of p (depth D, scale = 2^D): floor(p 2^D), except
+// that a point exactly on a grid plane belongs to the cell below it when the
+// direction is negative (the tie rule), clamped to [0, 2^D - 1] (the root box
+// is closed).  Bit D-1-l of the result is the child bit at level l: the same
+// decision as comparing p with every mid-plane on the way down.
+__device__ __forceinline__ uint32_t quantize(DF p, float scale, uint32_t qmax, float d) {
+    const float h = p.hi * scale;  // exact: scale is a power of two
+    const float f = floorf(h);
+    int q = (int)f;
+    if (h == f && (p.lo < 0.0f || (p.lo == 0.0f && d < 0.0f))) --q;
+    q = max(q, 0);
+    return min((uint32_t)q, qmax);
+}
 
 // Loads one SH record and returns sum_k c_{ch,k} Y_k for the three channels.
 template <int K, int PREC>
@@ -239,7 +252,7 @@ struct Ray {
     DF od;
     DF t;               // ray parameter at the current cell entry (trace only)
     DF rem;             // ray parameter left inside the sphere proxy (sphere only)
-    uint32_t c[3];      // integer cell coordinates at `level`
+    uint32_t q[3];      // integer coordinates of the current point on the finest (depth-D) grid
     uint32_t node;      // node whose child is looked up next (ST_DESCEND)
     uint32_t entry_x, entry_y;
     int level;
@@ -255,19 +268,14 @@ __device__ __forceinline__ uint2 load_entry(const TreeParams& tp, const uint2* s
     return __ldg(tp.nodes + (size_t)node * 8 + slot);
 }
 
-// Descends from R.node (cell coords R.c at R.level) through the shared-memory
-// levels and at most one global level.  Ends in ST_LEAF (leaf or empty
-// octant found) or stays in ST_DESCEND with the next node to load.
+// Descends from R.node (level R.level) through the shared-memory levels and
+// at most one global level, taking the child bits from the finest-grid
+// coordinates R.q.  Ends in ST_LEAF (leaf or empty octant found) or stays in
+// ST_DESCEND with the next node to load.
 __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* s_nodes, Ray& R, uint32_t* stack) {
     for (int guard = 0; guard <= MAX_DEPTH; ++guard) {
-        const float sc = pow2i(-(R.level + 1));
-        int bx = above(R.p[0], (float)(2u * R.c[0] + 1u) * sc, R.d[0]);
-        int by = above(R.p[1], (float)(2u * R.c[1] + 1u) * sc, R.d[1]);
-        int bz = above(R.p[2], (float)(2u * R.c[2] + 1u) * sc, R.d[2]);
-        R.c[0] = 2u * R.c[0] + bx;
-        R.c[1] = 2u * R.c[1] + by;
-        R.c[2] = 2u * R.c[2] + bz;
-        R.slot = bx | (by << 1) | (bz << 2);
+        const int sh = tp.depth - 1 - R.level;
+        R.slot = (int)(((R.q[0] >> sh) & 1u) | (((R.q[1] >> sh) & 1u) << 1) | (((R.q[2] >> sh) & 1u) << 2));
         const bool global = R.node >= (uint32_t)tp.n_top;
         uint2 e = load_entry(tp, s_nodes, R.node, R.slot);
         ++R.level;
@@ -408,10 +416,13 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
         if (R.p[a].hi > 1.0f || (R.p[a].hi == 1.0f && R.p[a].lo > 0.0f)) R.p[a] = {1.0f, 0.0f};
     }
     if (TRACE) R.t = outside ? tn : DF{0.0f, 0.0f};
+    const float scale = pow2i(tp.depth);
+    const uint32_t qmax = (1u << tp.depth) - 1u;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) R.q[a] = quantize(R.p[a], scale, qmax, R.d[a]);
     stack[0] = 0;
     R.node = 0;
     R.level = 0;
-    R.c[0] = R.c[1] = R.c[2] = 0;
     R.state = ST_DESCEND;
 }
 
@@ -420,20 +431,34 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
 template <int K, int PREC, bool TRACE, bool SPHERE>
 __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ray& R, uint32_t* stack,
                           const float* sY = nullptr) {
-    // segment: exit parameter of the current cell along each axis
+    // segment: exit parameter of the current cell along each axis.  An FP32
+    // estimate (error below 6e-8 |1/d| + 2e-7 v) picks the candidate exit
+    // axes; only those get the double-float value.
     const int L = R.level;
+    const int down = tp.depth - L;
     const float size = pow2i(-L);
+    uint32_t c[3];
+    float planes[3], va[3];
+    float vmin = INFINITY, rmin = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        c[a] = R.q[a] >> down;
+        planes[a] = (float)(c[a] + (R.d[a] > 0.0f ? 1u : 0u)) * size;
+        va[a] = INFINITY;
+        if (R.d[a] == 0.0f) continue;
+        va[a] = fmaxf(__fmul_rn(__fsub_rn(planes[a], R.p[a].hi), R.rh[a]), 0.0f);
+        if (va[a] < vmin) {
+            vmin = va[a];
+            rmin = fabsf(R.rh[a]);
+        }
+    }
     DF dt = {INFINITY, 0.0f};
     DF dts[3];
-    float planes[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         dts[a] = {INFINITY, 0.0f};
-        planes[a] = 0.0f;
-        if (R.d[a] == 0.0f) continue;
-        float P = (float)(R.c[a] + (R.d[a] > 0.0f ? 1u : 0u)) * size;
-        planes[a] = P;
-        DF v = df_mul(df_from_plane(P, R.p[a]), R.rh[a], R.rl[a]);
+        if (!(va[a] <= vmin + 2.5e-7f * (fabsf(R.rh[a]) + rmin) + 1e-6f * vmin)) continue;
+        DF v = df_mul(df_from_plane(planes[a], R.p[a]), R.rh[a], R.rl[a]);
         if (v.hi < 0.0f) v = {0.0f, 0.0f};
         dts[a] = v;
         if (df_less(v, dt)) dt = v;
@@ -517,20 +542,23 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
     // too, so a ray through a shared edge or corner crosses it in one step
     // instead of leaving a sliver segment behind.
     int l_anc = L;
-    uint32_t nc[3] = {R.c[0], R.c[1], R.c[2]};
     const float tie = __fmaf_rn(dt.hi, 1.4551915228366852e-11f, dt.hi);
+    const float scale = pow2i(tp.depth);
+    const uint32_t qmax = (1u << tp.depth) - 1u;
     bool left = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (R.d[a] != 0.0f && (df_eq(dts[a], dt) || dts[a].hi <= tie)) {
             R.p[a] = {planes[a], 0.0f};
-            uint32_t cn = R.d[a] > 0.0f ? R.c[a] + 1u : R.c[a] - 1u;
+            const uint32_t cn = R.d[a] > 0.0f ? c[a] + 1u : c[a] - 1u;
             left |= (cn >> L) != 0u;  // left the root cube (also catches 0 - 1)
-            nc[a] = cn;
-            int diff = 32 - __clz(cn ^ R.c[a]);
+            // first (d > 0) or last (d < 0) finest cell of the neighbour
+            R.q[a] = R.d[a] > 0.0f ? cn << down : (c[a] << down) - 1u;
+            const int diff = 32 - __clz(cn ^ c[a]);
             if (L - diff < l_anc) l_anc = L - diff;
         } else {
             R.p[a] = df_axpy(R.p[a], dt, R.d[a], R.dl[a]);
+            R.q[a] = quantize(R.p[a], scale, qmax, R.d[a]);
         }
     }
     if (left) {
@@ -538,8 +566,6 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
         R.state = ST_IDLE;
         return;
     }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) R.c[a] = nc[a] >> (L - l_anc);
     R.level = l_anc;
     R.node = stack[l_anc * BLOCK];
     R.state = ST_DESCEND;
@@ -825,7 +851,10 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     kp.tr_leaf = tr_leaf;
     kp.tr_t = tr_t;
     kp.tr_count = tr_count;
-    size_t smem = (size_t)t->n_top * 8 * sizeof(uint2);
+    // stage only the nodes of levels 0..2 (measured: the shared memory left
+    // over goes to L1, which serves the deeper node loads better)
+    if (kp.tree.n_top > BATCH_TOP_NODES) kp.tree.n_top = BATCH_TOP_NODES;
+    size_t smem = (size_t)kp.tree.n_top * 8 * sizeof(uint2);
     cudaError_t e;
     if (TRACE)
         e = dispatch<TRACE, false>(t, kp, smem, (cudaStream_t)stream);
