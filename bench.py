@@ -47,6 +47,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 8-luminaire batched-render section")
+    ap.add_argument("--no-pt", action="store_true", help="skip the path-tracer emitter timing")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the linear / sigma_min-alpha_max / sphere-proxy timings")
     ap.add_argument("--learned", action="store_true",
@@ -271,6 +272,39 @@ def run_variants(plo, torch, tree32, rays, rgb, T, timed, rays_total):
     return out
 
 
+def run_pt(plo, torch, tree32, W, K):
+    """The luminaire as an emitter in a path tracer (Sec. 3 Eq. 2, Sec. 5):
+    paths per second with the octree luminaire, and with an opaque box of
+    constant radiance in its place (the explicitly handled emitter); the
+    overhead per sample is their time ratio minus one (Sec. 6.2 quotes 20%
+    for its Mitsuba integration against the luminaires' real geometry)."""
+    sc = dict(room_min=(-1.0, -1.0, -1.0), room_max=(2.0, 2.0, 2.0), albedo=[(0.6, 0.6, 0.6)] * 6,
+              cam_pos=(0.5, 0.4, -0.9), cam_target=(0.5, 0.5, 0.5), cam_up=(0.0, 1.0, 0.0), fov_y=1.2, width=512,
+              height=512, max_bounces=3, emitter=plo.PT_OCTREE, box_radiance=(1.0, 1.0, 1.0))
+    spp = 4
+    stream = torch.cuda.current_stream()
+    out = {"scene": "room [-1,2]^3, diffuse walls (albedo 0.6), the depth-10 luminaire in [0,1]^3; "
+                    f"{sc['width']}x{sc['height']} pixels, {spp} samples, {sc['max_bounces']} bounces, "
+                    "2 luminaire queries per bounce"}
+    for name, emitter in (("octree", plo.PT_OCTREE), ("constant_box", plo.PT_CONSTANT_BOX)):
+        sc["emitter"] = emitter
+        for _ in range(W):
+            plo.pt_render(tree32, sc, spp, seed=1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in range(K):
+            plo.pt_render(tree32, sc, spp, seed=2 + k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / K
+        paths = sc["width"] * sc["height"] * spp
+        out[name] = {"ms_per_frame": ms, "paths_per_s": paths / (ms / 1e3),
+                     "luminaire_queries_per_s": 2 * sc["max_bounces"] * paths / (ms / 1e3)}
+    out["overhead_per_sample"] = out["octree"]["ms_per_frame"] / out["constant_box"]["ms_per_frame"] - 1.0
+    return out
+
+
 def run_learned(args):
     """Train the NeRF-SH network on targets rendered from the depth-6
     luminaire (4096 rays x 128 samples per step, the paper's loss), distil it
@@ -425,6 +459,7 @@ def main():
         res[name] = timed(trees[name])
     variants = None if args.no_variants else run_variants(plo, torch, trees["fp32"], rays, rgb, T, timed,
                                                           world * n * K)
+    pt = None if args.no_pt else run_pt(plo, torch, trees["fp32"], W, K)
     e2e = None
     if not args.no_e2e:
         rays_h = torch.from_numpy(rays_np).pin_memory()
@@ -524,6 +559,7 @@ def main():
         "parity": parity,
         "batch": batch,
         "variants": variants,
+        "path_tracer": pt,
     }
     line["fp16"]["roofline"]["frac"] = line["fp16"]["roofline"]["achieved"] / peak
     print(json.dumps(line), flush=True)

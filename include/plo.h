@@ -402,6 +402,57 @@ plo_status plo_wgrad_bf16(const void* d_dZ, int32_t n_out, const void* d_H, int3
                           unsigned int* d_err, void* stream);
 
 /* ------------------------------------------------------------------------
+ * The luminaire as an emitter in a path tracer (Sec. 3 Eq. 2: what leaves
+ * the proxy is L_o = L_e + T L_i; Sec. 5 "Sampling": the proxy surface is
+ * sampled uniformly).
+ *
+ * Scene: a closed room (axis-aligned box, diffuse walls seen from inside)
+ * holding the luminaire; the proxy is the tree's bounding box, which must
+ * lie inside the room.  Per path (pixel p % (width * height) of sample
+ * p / (width * height)), with uniforms u[0 .. 2 + 5 * max_bounces):
+ *   camera ray through pixel (px + u0, py + u1) of a pinhole camera
+ *   (cam_pos looking at cam_target, cam_up, vertical field of view fov_y);
+ *   per bounce b (u[2+5b] picks a proxy face by area, u[3+5b], u[4+5b] a
+ *   point y on it, u[5+5b], u[6+5b] the bounce):
+ *     the luminaire along the ray: camera rays add its L_e; the throughput
+ *       is multiplied by its T (light from behind passes through);
+ *     wall point x, inward normal n, albedo rho of that wall (walls
+ *       x-, x+, y-, y+, z-, z+);
+ *     next event: if y's face faces x, add
+ *       thr * rho / pi * L_e(x -> y) * cos_x * cos_y / |y - x|^2 * A
+ *       (A: proxy surface area; L_e(x -> y) the luminaire's emission along
+ *       the ray from x through y);
+ *     cosine-weighted bounce about n (u5 -> cos^2 of the polar angle
+ *       1 - u5, u6 -> azimuth), thr *= rho.
+ * emitter PLO_PT_OCTREE queries the tree (plo_render_rays with `params`);
+ * PLO_PT_CONSTANT_BOX replaces it by an opaque box of radiance
+ * box_radiance, the "explicitly handled" emitter the overhead is measured
+ * against. */
+enum { PLO_PT_OCTREE = 0, PLO_PT_CONSTANT_BOX = 1 };
+
+typedef struct {
+    float room_min[3], room_max[3];
+    float albedo[6][3];
+    float cam_pos[3], cam_target[3], cam_up[3];
+    float fov_y;               /* radians, in (0, 3.1)                  */
+    int32_t width, height;
+    int32_t max_bounces;       /* 1 .. 16                               */
+    int32_t emitter;           /* PLO_PT_*                              */
+    float box_radiance[3];     /* PLO_PT_CONSTANT_BOX only              */
+} plo_pt_scene;
+
+/* Renders spp samples per pixel (async on `stream`).
+ *   params      luminaire queries (PLO_PROXY_BOX only)
+ *   d_uniforms  float [spp * width * height][2 + 5 * max_bounces] in [0, 1),
+ *               or NULL to draw them from `seed` (SplitMix64)
+ *   d_image     float [height][width][3]: mean radiance over the samples
+ *   d_samples   float [spp][height][width][3] per-sample radiance, or NULL
+ * Allocates its wavefront buffers with cudaMallocAsync on `stream`. */
+plo_status plo_pt_render(const plo_tree* lum, const plo_render_params* params, const plo_pt_scene* scene,
+                         int32_t spp, uint64_t seed, const float* d_uniforms, float* d_image, float* d_samples,
+                         void* stream);
+
+/* ------------------------------------------------------------------------
  * Test hooks for failure detection (nothing here faults or hangs a GPU).
  * plo_debug_fail_alloc_after(n): the n-th following device allocation made
  *   by the library fails as out-of-memory (n < 0 turns the hook off).

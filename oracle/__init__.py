@@ -7,7 +7,9 @@ imports this package and shares no code with it.
 ``render.c`` (plain C, FP64) holds the render oracle: SH basis from the
 associated-Legendre recursion, point -> leaf descent, and the exact per-leaf
 segment integral of Eq. 3 with exponential or linear (Eq. 4) transmittance
-and alpha = 1 - T (Eq. 5). ``mlp.py`` holds the learned-part oracle.
+and alpha = 1 - T (Eq. 5); and a path tracer that uses the luminaire as an
+emitter (Eq. 2, Sec. 5 "Sampling") with its random numbers passed in.
+``mlp.py`` holds the learned-part oracle.
 """
 from __future__ import annotations
 
@@ -160,3 +162,45 @@ def trace(tree, ray, max_cells: int = 100000, **kw):
     m = lib.oracle_trace(ctypes.byref(b.struct), ctypes.byref(p), ray.ctypes.data, max_cells,
                          leaf.ctypes.data, t.ctypes.data)
     return leaf[:m].copy(), t[:m].copy()
+
+
+class _PtScene(ctypes.Structure):
+    _fields_ = [("room_min", ctypes.c_double * 3), ("room_max", ctypes.c_double * 3),
+                ("albedo", (ctypes.c_double * 3) * 6), ("cam_pos", ctypes.c_double * 3),
+                ("cam_target", ctypes.c_double * 3), ("cam_up", ctypes.c_double * 3), ("fov_y", ctypes.c_double),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("max_bounces", ctypes.c_int32),
+                ("emitter", ctypes.c_int32), ("box_radiance", ctypes.c_double * 3)]
+
+
+def _pt_scene(sc: dict) -> _PtScene:
+    s = _PtScene()
+    for k in ("room_min", "room_max", "cam_pos", "cam_target", "cam_up", "box_radiance"):
+        getattr(s, k)[:] = tuple(float(v) for v in sc[k])
+    for w in range(6):
+        s.albedo[w][:] = tuple(float(v) for v in sc["albedo"][w])
+    s.fov_y = float(sc["fov_y"])
+    s.width, s.height = int(sc["width"]), int(sc["height"])
+    s.max_bounces, s.emitter = int(sc["max_bounces"]), int(sc["emitter"])
+    return s
+
+
+def pt_render(tree, scene: dict, uniforms, n_threads: int = 0, **params) -> np.ndarray:
+    """Radiance of each path [n, 3] (FP64) of the path tracer with the
+    luminaire as emitter.  uniforms [n, 2 + 5 * max_bounces] in [0, 1); path
+    p is pixel p % (width * height).  scene: dict with the fields of
+    plo_pt_scene; params: the render parameters of the luminaire queries."""
+    lib = _load()
+    if not getattr(lib, "_pt_sigs", False):
+        lib.oracle_pt_render.restype = None
+        lib.oracle_pt_render.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+        lib._pt_sigs = True
+    b = _Bound(tree)
+    u = np.ascontiguousarray(uniforms, np.float64)
+    n = u.shape[0]
+    assert u.shape[1] == 2 + 5 * int(scene["max_bounces"])
+    out = np.zeros((n, 3))
+    p = _params(**params)
+    s = _pt_scene(scene)
+    lib.oracle_pt_render(ctypes.byref(b.struct), ctypes.byref(p), ctypes.byref(s), u.ctypes.data, n, int(n_threads),
+                         out.ctypes.data)
+    return out

@@ -400,3 +400,164 @@ int oracle_max_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* The luminaire as an emitter in a path tracer (Sec. 3 Eq. 2, Sec. 5   */
+/* "Sampling").  One path per call, FP64, random numbers passed in.     */
+/*   camera: pinhole, pixel (px + u0, py + u1);                          */
+/*   per bounce b (uniforms u[2+5b .. 6+5b]):                            */
+/*     luminaire along the ray: camera rays add L_e, the throughput is   */
+/*       multiplied by T (light from behind passes through);             */
+/*     wall hit x (room seen from inside), inward normal n, albedo rho;  */
+/*     next event: y uniform on the proxy box surface (face by area, then */
+/*       uniform on it); if y's face faces x, add                         */
+/*       thr rho/pi L_e(x -> y) cos_x cos_y / |y-x|^2 A;                   */
+/*     cosine-weighted bounce about n, thr *= rho.                        */
+/* emitter 0 queries the tree; emitter 1 is an opaque box of constant     */
+/* radiance (the comparison emitter).                                     */
+
+typedef struct {
+    double room_min[3], room_max[3];
+    double albedo[6][3];
+    double cam_pos[3], cam_target[3], cam_up[3];
+    double fov_y;
+    int32_t width, height, max_bounces, emitter;
+    double box_radiance[3];
+} oracle_pt_scene;
+
+static void pt_luminaire(const oracle_tree* t, const oracle_params* prm, const oracle_pt_scene* sc,
+                         const double o[3], const double d[3], double Le[3], double* T) {
+    if (sc->emitter == 1) {
+        double tn = -INFINITY, tf = INFINITY;
+        int miss = 0;
+        for (int a = 0; a < 3; ++a) {
+            if (d[a] == 0.0) {
+                if (o[a] < t->bbox_min[a] || o[a] > t->bbox_max[a]) miss = 1;
+                continue;
+            }
+            double t0 = (t->bbox_min[a] - o[a]) / d[a], t1 = (t->bbox_max[a] - o[a]) / d[a];
+            if (t0 > t1) { double s = t0; t0 = t1; t1 = s; }
+            if (t0 > tn) tn = t0;
+            if (t1 < tf) tf = t1;
+        }
+        int hit = !miss && tn < tf && tf > 0.0;
+        for (int c = 0; c < 3; ++c) Le[c] = hit ? sc->box_radiance[c] : 0.0;
+        *T = hit ? 0.0 : 1.0;
+        return;
+    }
+    float ray[6];
+    for (int a = 0; a < 3; ++a) {
+        ray[a] = (float)o[a];
+        ray[3 + a] = (float)d[a];
+    }
+    ray_result r;
+    render_one(t, prm, ray, &r, NULL, NULL, 0, NULL);
+    for (int c = 0; c < 3; ++c) Le[c] = r.rgb[c];
+    *T = r.T;
+}
+
+static void pt_norm(double* v) {
+    double s = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= s; v[1] /= s; v[2] /= s;
+}
+
+void oracle_pt_sample(const oracle_tree* t, const oracle_params* prm, const oracle_pt_scene* sc, const double* u,
+                      int32_t px, int32_t py, double out[3]) {
+    double fwd[3], right[3], up[3], o[3], d[3], thr[3] = {1.0, 1.0, 1.0}, L[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 3; ++k) fwd[k] = sc->cam_target[k] - sc->cam_pos[k];
+    pt_norm(fwd);
+    right[0] = fwd[1] * sc->cam_up[2] - fwd[2] * sc->cam_up[1];
+    right[1] = fwd[2] * sc->cam_up[0] - fwd[0] * sc->cam_up[2];
+    right[2] = fwd[0] * sc->cam_up[1] - fwd[1] * sc->cam_up[0];
+    pt_norm(right);
+    up[0] = right[1] * fwd[2] - right[2] * fwd[1];
+    up[1] = right[2] * fwd[0] - right[0] * fwd[2];
+    up[2] = right[0] * fwd[1] - right[1] * fwd[0];
+    double th = tan(0.5 * sc->fov_y);
+    double sx = (2.0 * (px + u[0]) / sc->width - 1.0) * th * sc->width / sc->height;
+    double sy = (1.0 - 2.0 * (py + u[1]) / sc->height) * th;
+    for (int k = 0; k < 3; ++k) {
+        o[k] = sc->cam_pos[k];
+        d[k] = fwd[k] + sx * right[k] + sy * up[k];
+    }
+    pt_norm(d);
+    double ext[3], area = 0.0, fa[6];
+    for (int k = 0; k < 3; ++k) ext[k] = t->bbox_max[k] - t->bbox_min[k];
+    for (int f = 0; f < 6; ++f) {
+        fa[f] = ext[((f >> 1) + 1) % 3] * ext[((f >> 1) + 2) % 3];
+        area += fa[f];
+    }
+    for (int b = 0; b < sc->max_bounces; ++b) {
+        const double* ub = u + 2 + 5 * b;
+        double Le[3], T;
+        pt_luminaire(t, prm, sc, o, d, Le, &T);
+        for (int c = 0; c < 3; ++c) {
+            if (b == 0) L[c] += thr[c] * Le[c];
+            thr[c] *= T;
+        }
+        double tw = INFINITY;
+        int ax = 0;
+        for (int k = 0; k < 3; ++k) {
+            if (d[k] == 0.0) continue;
+            double tt = ((d[k] > 0.0 ? sc->room_max[k] : sc->room_min[k]) - o[k]) / d[k];
+            if (tt < tw) { tw = tt; ax = k; }
+        }
+        int wall = 2 * ax + (d[ax] > 0.0 ? 1 : 0);
+        double x[3], n[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 3; ++k) x[k] = o[k] + tw * d[k];
+        x[ax] = d[ax] > 0.0 ? sc->room_max[ax] : sc->room_min[ax];
+        n[ax] = d[ax] > 0.0 ? -1.0 : 1.0;
+        /* next event toward a uniform point of the proxy surface */
+        double acc = 0.0;
+        int f = 0;
+        for (f = 0; f < 5; ++f) {
+            acc += fa[f] / area;
+            if (ub[0] < acc) break;
+        }
+        int fa_ = f >> 1, fb = (fa_ + 1) % 3, fc = (fa_ + 2) % 3;
+        double y[3];
+        y[fa_] = (f & 1) ? t->bbox_max[fa_] : t->bbox_min[fa_];
+        y[fb] = t->bbox_min[fb] + ub[1] * ext[fb];
+        y[fc] = t->bbox_min[fc] + ub[2] * ext[fc];
+        double w[3];
+        for (int k = 0; k < 3; ++k) w[k] = y[k] - x[k];
+        double dist2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        pt_norm(w);
+        int faces = (f & 1) ? x[fa_] > y[fa_] : x[fa_] < y[fa_];
+        double cos_x = n[0] * w[0] + n[1] * w[1] + n[2] * w[2];
+        double cos_y = fabs(w[fa_]);
+        if (faces && cos_x > 0.0) {
+            double Le2[3], T2;
+            pt_luminaire(t, prm, sc, x, w, Le2, &T2);
+            double g = cos_x * cos_y / dist2 * area / OR_PI;
+            for (int c = 0; c < 3; ++c) L[c] += thr[c] * sc->albedo[wall][c] * g * Le2[c];
+        }
+        /* cosine-weighted bounce */
+        double r = sqrt(ub[3]), phi = 2.0 * OR_PI * ub[4];
+        double nd[3];
+        nd[ax] = n[ax] * sqrt(fmax(0.0, 1.0 - ub[3]));
+        nd[(ax + 1) % 3] = r * cos(phi);
+        nd[(ax + 2) % 3] = r * sin(phi);
+        for (int k = 0; k < 3; ++k) {
+            o[k] = x[k];
+            d[k] = nd[k];
+            thr[k] *= sc->albedo[wall][k];
+        }
+    }
+    for (int c = 0; c < 3; ++c) out[c] = L[c];
+}
+
+/* n paths: path p uses uniforms u[p*dims ..], pixel p % (width*height). */
+void oracle_pt_render(const oracle_tree* t, const oracle_params* prm, const oracle_pt_scene* sc, const double* u,
+                      int64_t n_paths, int n_threads, double* out) {
+    const int dims = 2 + 5 * sc->max_bounces;
+    const int64_t pixels = (int64_t)sc->width * sc->height;
+#ifdef _OPENMP
+    if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(n_threads)
+#endif
+    for (int64_t p = 0; p < n_paths; ++p) {
+        int64_t pix = p % pixels;
+        oracle_pt_sample(t, prm, sc, u + p * dims, (int32_t)(pix % sc->width), (int32_t)(pix / sc->width), out + 3 * p);
+    }
+}

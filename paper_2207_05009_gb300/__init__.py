@@ -446,6 +446,49 @@ def wgrad_bf16(dZ, H, dW, err=None, stream=None):
     return dW, err
 
 
+# ---------------------------------------------------------------- path tracer with the luminaire as emitter
+PT_OCTREE, PT_CONSTANT_BOX = 0, 1
+
+
+class PtScene(ctypes.Structure):
+    _fields_ = [("room_min", ctypes.c_float * 3), ("room_max", ctypes.c_float * 3),
+                ("albedo", (ctypes.c_float * 3) * 6), ("cam_pos", ctypes.c_float * 3),
+                ("cam_target", ctypes.c_float * 3), ("cam_up", ctypes.c_float * 3), ("fov_y", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("max_bounces", ctypes.c_int32),
+                ("emitter", ctypes.c_int32), ("box_radiance", ctypes.c_float * 3)]
+
+    @classmethod
+    def from_dict(cls, sc: dict) -> "PtScene":
+        s = cls()
+        for k in ("room_min", "room_max", "cam_pos", "cam_target", "cam_up", "box_radiance"):
+            getattr(s, k)[:] = tuple(float(v) for v in sc[k])
+        for w in range(6):
+            s.albedo[w][:] = tuple(float(v) for v in sc["albedo"][w])
+        s.fov_y = float(sc["fov_y"])
+        s.width, s.height = int(sc["width"]), int(sc["height"])
+        s.max_bounces, s.emitter = int(sc["max_bounces"]), int(sc["emitter"])
+        return s
+
+
+def pt_render(tree: Tree, scene: dict, spp: int, params: RenderParams | None = None, seed: int = 1, uniforms=None,
+              samples: bool = False, stream=None):
+    """plo_pt_render: (image [H, W, 3], per-sample radiance [spp, H, W, 3] or None)."""
+    import torch
+    lib = load()
+    if not getattr(lib, "_pt_sigs", False):
+        P = ctypes.c_void_p
+        lib.plo_pt_render.restype = ctypes.c_int32
+        lib.plo_pt_render.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_uint64, P, P, P, P]
+        lib._pt_sigs = True
+    s = PtScene.from_dict(scene)
+    p = (params or RenderParams())._c()
+    img = torch.empty((s.height, s.width, 3), device="cuda", dtype=torch.float32)
+    smp = torch.empty((spp, s.height, s.width, 3), device="cuda", dtype=torch.float32) if samples else None
+    _check(lib.plo_pt_render(tree.handle, ctypes.byref(p), ctypes.byref(s), spp, seed, _ptr(uniforms), _ptr(img),
+                             _ptr(smp), _stream(stream)))
+    return img, smp
+
+
 # ---------------------------------------------------------------- batched render
 class BatchConfig(ctypes.Structure):
     _fields_ = [("claim_rays", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("top_nodes", ctypes.c_int32)]

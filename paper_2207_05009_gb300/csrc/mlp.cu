@@ -501,11 +501,14 @@ __global__ void k_colsum(const __nv_bfloat16* dZ, int64_t M, int ncols, int rows
     const int64_t m0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t m1 = min(m0 + rows_per_block, M);
     float sx = 0.0f, sy = 0.0f;
-    for (int64_t m = m0 + rg; rg < groups && m < m1; m += groups) {
-        __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(dZ + m * ncols + 2 * p);
-        float2 f = __bfloat1622float2(v);
-        sx += f.x;
-        sy += f.y;
+    if (rg < groups) {
+#pragma unroll 8
+        for (int64_t m = m0 + rg; m < m1; m += groups) {
+            __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(dZ + m * ncols + 2 * p);
+            float2 f = __bfloat1622float2(v);
+            sx += f.x;
+            sy += f.y;
+        }
     }
     __shared__ float red[2][256];
     red[0][threadIdx.x] = sx;
@@ -984,7 +987,7 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
     gemm::EpiArgs ep{};
     ep.err = m->d_err;
     auto colsum = [&](const __nv_bfloat16* dz, int ncols, float* db) {
-        const int rows = 4096;
+        const int rows = 512;
         k_colsum<<<(unsigned)((M + rows - 1) / rows), 256, 0, s>>>(dz, M, ncols, rows, db);
     };
     cudaError_t e;

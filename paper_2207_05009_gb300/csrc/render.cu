@@ -130,10 +130,6 @@ __device__ __forceinline__ DF df_from_plane(float P, DF p) {
 }
 __device__ __forceinline__ bool df_less(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ bool df_eq(DF a, DF b) { return a.hi == b.hi && a.lo == b.lo; }
-// tie rule: p above the plane m, or on it with a non-negative direction
-__device__ __forceinline__ int above(DF p, float m, float d) {
-    return p.hi > m || (p.hi == m && (p.lo > 0.0f || (p.lo == 0.0f && d >= 0.0f)));
-}
 __device__ __forceinline__ float pow2i(int e) { return __int_as_float((127 + e) << 23); }  // e in [-126, 127]
 // Finest-grid coordinate of p (depth D, scale = 2^D): floor(p 2^D), except
 // that a point exactly on a grid plane belongs to the cell below it when the
@@ -695,9 +691,13 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(B
                 ray_begin<false, false>(kp, s_tp[t], my, R, stack);
             }
         }
-        if (__ballot_sync(0xffffffffu, R.state != ST_IDLE) == 0u) break;
+        const unsigned live = __ballot_sync(0xffffffffu, R.state != ST_IDLE);
+        if (live == 0u) break;
         const TreeParams& tp = s_tp[R.tree];
-        if (R.state == ST_LEAF) leaf_step<0, -1, false, false>(kp, tp, my, R, stack);
+        // composite in batches, as in k_render
+        const unsigned at_leaf = __ballot_sync(0xffffffffu, R.state == ST_LEAF);
+        const bool composite = 2 * __popc(at_leaf) >= __popc(live);
+        if (composite && R.state == ST_LEAF) leaf_step<0, -1, false, false>(kp, tp, my, R, stack);
         if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
     }
 }
