@@ -157,7 +157,9 @@ plo_status plo_tree_get_info(const plo_tree* tree, plo_tree_info* out);
  * A ray with a NaN/Inf component or a zero direction gets NaN outputs and
  * PLO_RAY_INVALID.  A ray that exceeds max_steps keeps its partial result,
  * gets PLO_RAY_STEP_LIMIT and raises the tree's device error flag (read by
- * plo_tree_check).  n == 0 is a no-op. */
+ * plo_tree_check).  n == 0 is a no-op.  Calls with n >= 2^20 take an 8-byte
+ * work counter from the stream-ordered allocator (cudaMallocAsync on
+ * `stream`), so that warps claim rays dynamically. */
 plo_status plo_render_rays(const plo_tree* tree, const float* d_rays, int64_t n, const plo_render_params* params,
                            float* d_rgb, float* d_T, int32_t* d_status, void* stream);
 

@@ -87,7 +87,9 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t ph, Ctl* c
 }
 
 template <int N>
-__device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int row, int M, int col, const float* v) {
+// mk: the chunk's 32 mask values (EPI_MASK_BF16), loaded ahead by the caller
+__device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int row, int M, int col, const float* v,
+                                               const uint4* mk) {
     if (row >= M) return;
     if (epi == EPI_BIAS_F32 || (epi == EPI_SPLIT && col >= ep.split)) {
         const bool split = epi == EPI_SPLIT;
@@ -112,10 +114,9 @@ __device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int r
             packed[j] = *reinterpret_cast<uint32_t*>(&h);
         }
     } else {  // EPI_MASK_BF16
-        const uint4* m4 = reinterpret_cast<const uint4*>(ep.mask + (size_t)row * ep.ldm + col);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            uint4 mw = __ldg(m4 + q);
+            const uint4 mw = mk[q];
             uint32_t w[4] = {mw.x, mw.y, mw.z, mw.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -252,14 +253,27 @@ __global__ void __launch_bounds__(THREADS, 1)
         int acc = 0;
         uint32_t aph = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            const int row = tile * BM + q * 32 + lane;
+            // the mask is read one chunk ahead, so its latency overlaps the
+            // accumulator wait and the previous chunk's work
+            const bool masked = epi == EPI_MASK_BF16 && row < M;
+            const uint4* mrow = masked ? reinterpret_cast<const uint4*>(ep.mask + (size_t)row * ep.ldm) : nullptr;
+            uint4 mk[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mk[j] = masked ? __ldg(mrow + j) : make_uint4(0u, 0u, 0u, 0u);
             if (!wait_or_abort(&ctl->tfull[acc], aph, ctl, ep.err)) break;
             sm100::tc_fence_after();
-            const int row = tile * BM + q * 32 + lane;
 #pragma unroll 1
             for (int c = 0; c < N / 32; ++c) {
                 float v[32];
                 sm100::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * N + c * 32), v);
-                epilogue_chunk<N>(ep, epi, row, M, c * 32, v);
+                uint4 nx[4];
+                const bool more = masked && c + 1 < N / 32;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) nx[j] = more ? __ldg(mrow + 4 * (c + 1) + j) : make_uint4(0u, 0u, 0u, 0u);
+                epilogue_chunk<N>(ep, epi, row, M, c * 32, v, mk);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mk[j] = nx[j];
             }
             sm100::tc_fence_before();
             sm100::mbar_arrive(&ctl->tempty[acc]);

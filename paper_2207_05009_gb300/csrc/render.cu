@@ -41,6 +41,7 @@ constexpr int BLOCK = 256;
 #endif
 constexpr int WARPS = BLOCK / 32;
 constexpr int STACK = MAX_DEPTH + 1;
+constexpr int64_t RENDER_CLAIM = 64;  // rays a warp claims at a time from the shared cursor
 
 // One packed tree as the kernels see it.
 struct TreeParams {
@@ -64,6 +65,7 @@ struct KParams {
     int32_t saturate, proxy;
     float sphere[4];  // sphere proxy: centre, radius (world space)
     const float* rays;
+    unsigned long long* cursor;  // shared claim counter (NULL: static chunks per warp)
     int64_t n;
     int64_t chunk;  // rays per warp
     float* rgb;
@@ -583,22 +585,37 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams
     const int lane = threadIdx.x & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
     const int64_t warp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
-    const int64_t beg = warp * kp.chunk;
-    if (beg >= kp.n) return;  // whole warp exits together
-    const int64_t end = min(beg + kp.chunk, kp.n);
+    int64_t next = 0, end = 0;  // warp-uniform range of rays being handed out
+    if (!kp.cursor) {
+        next = warp * kp.chunk;
+        if (next >= kp.n) return;  // whole warp exits together
+        end = min(next + kp.chunk, kp.n);
+    }
+    bool drained = false;
 
     Ray R;
     R.state = ST_IDLE;
     int64_t my = 0;
-    int64_t next = beg;  // warp-uniform cursor into the chunk
     for (;;) {
-        // idle lanes take the next rays of the chunk; rays that miss the proxy
-        // finish at once, so repeat while lanes are idle and rays remain
+        // idle lanes take the next rays; rays that miss the proxy finish at
+        // once, so repeat while lanes are idle and rays remain
         for (;;) {
             unsigned idle = __ballot_sync(0xffffffffu, R.state == ST_IDLE);
             // refill in groups: ray setup runs with at least 8 lanes (or when
             // no ray is left in flight)
-            if (idle == 0u || next >= end || (__popc(idle) < 8 && idle != 0xffffffffu)) break;
+            if (idle == 0u || (__popc(idle) < 8 && idle != 0xffffffffu)) break;
+            if (next >= end) {
+                if (!kp.cursor || drained) break;
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(kp.cursor, (unsigned long long)RENDER_CLAIM);
+                b = __shfl_sync(0xffffffffu, b, 0);
+                if ((int64_t)b >= kp.n) {
+                    drained = true;
+                    break;
+                }
+                next = (int64_t)b;
+                end = min(next + RENDER_CLAIM, kp.n);
+            }
             int64_t cand = next + __popc(idle & lanes_below);
             next += __popc(idle);
             if (R.state == ST_IDLE && cand < end) {
@@ -617,7 +634,7 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams
         // composite in batches: while some lanes still descend, lanes that
         // found their cell wait until enough of the live lanes have one
         const unsigned at_leaf = __ballot_sync(0xffffffffu, R.state == ST_LEAF);
-        const bool composite = 2 * __popc(at_leaf) >= 1 * __popc(live);
+        const bool composite = 4 * __popc(at_leaf) >= 3 * __popc(live);
         if (composite && R.state == ST_LEAF) leaf_step<K, PREC, TRACE, SPHERE>(kp, tp, my, R, stack, sY);
         if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
     }
@@ -818,6 +835,14 @@ plo_status check_params(const plo_render_params* p) {
     return PLO_OK;
 }
 
+
+// ---------------------------------------------------------------- work distribution
+// Large wavefronts are handed out dynamically: warps claim RENDER_CLAIM rays
+// at a time from a counter allocated for the call, so a warp whose rays are
+// long does not hold up the end of the launch (static per-warp chunks are
+// kept below DYNAMIC_MIN_RAYS, where a call must not allocate).
+constexpr int64_t DYNAMIC_MIN_RAYS = (int64_t)1 << 20;
+
 template <bool TRACE>
 plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, const plo_render_params* p,
                          float* d_rgb, float* d_T, int32_t* d_status, int32_t trace_max, int64_t* tr_leaf,
@@ -855,13 +880,25 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     // over goes to L1, which serves the deeper node loads better)
     if (kp.tree.n_top > BATCH_TOP_NODES) kp.tree.n_top = BATCH_TOP_NODES;
     size_t smem = (size_t)kp.tree.n_top * 8 * sizeof(uint2);
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
+    cudaStream_t cs = (cudaStream_t)stream;
+    unsigned long long* cursor = nullptr;
+    if (!TRACE && n >= DYNAMIC_MIN_RAYS) {
+        e = cudaMallocAsync((void**)&cursor, sizeof(unsigned long long), cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), cs);
+        if (e != cudaSuccess) {
+            if (cursor) cudaFreeAsync(cursor, cs);
+            return cuda_error(e, "render work counter");
+        }
+        kp.cursor = cursor;
+    }
     if (TRACE)
         e = dispatch<TRACE, false>(t, kp, smem, (cudaStream_t)stream);
     else if (kp.proxy == PLO_PROXY_SPHERE)
         e = dispatch<false, true>(t, kp, smem, (cudaStream_t)stream);
     else
         e = dispatch<false, false>(t, kp, smem, (cudaStream_t)stream);
+    if (cursor) cudaFreeAsync(cursor, cs);
     if (e != cudaSuccess) return cuda_error(e, "render kernel launch");
     return PLO_OK;
 }
