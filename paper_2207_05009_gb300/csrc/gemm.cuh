@@ -49,6 +49,7 @@ struct EpiArgs {
     int ldo2;                     // EPI_SPLIT: row stride of out_f32
     const float* col0_add;        // EPI_BIAS_F32: added to column 0 of each row (nullable)
     int ld_col0;                  // row stride of col0_add
+    int tma_out;                  // bf16 outputs leave through the output tensor map (boxes of 32 x 32)
     unsigned int* err;            // device error word (bit 1: GEMM wait timeout)
     uint32_t wait_limit;          // polls per barrier wait (0: sm100::WAIT_LIMIT)
     int debug_skip_loads;         // test hook: the producer issues no loads, so the waits run out
@@ -57,8 +58,10 @@ struct EpiArgs {
 __host__ __device__ constexpr int tmem_cols_for(int n) {
     return n * 2 <= 32 ? 32 : (n * 2 <= 64 ? 64 : (n * 2 <= 128 ? 128 : (n * 2 <= 256 ? 256 : 512)));
 }
+constexpr int OUT_STAGE_BYTES = 32 * 32 * 2;  // one 32 x 32 bf16 box, per epilogue warp and buffer
 __host__ __device__ constexpr size_t gemm_smem_bytes(int N, int K) {
-    return 1024 /*align*/ + (size_t)N * K * 2 + (size_t)STAGES * A_STAGE_BYTES + 256 /*barriers*/;
+    return 1024 /*align*/ + (size_t)N * K * 2 + (size_t)STAGES * A_STAGE_BYTES + 8 * OUT_STAGE_BYTES +
+           256 /*barriers*/;
 }
 
 struct Ctl {
@@ -87,9 +90,10 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t ph, Ctl* c
 }
 
 template <int N>
-// mk: the chunk's 32 mask values (EPI_MASK_BF16), loaded ahead by the caller
+// mk: the chunk's 32 mask values (EPI_MASK_BF16), loaded ahead by the caller;
+// stage: where the 32 bf16 results go instead of global memory (nullable)
 __device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int row, int M, int col, const float* v,
-                                               const uint4* mk) {
+                                               const uint4* mk, uint4* stage) {
     if (row >= M) return;
     if (epi == EPI_BIAS_F32 || (epi == EPI_SPLIT && col >= ep.split)) {
         const bool split = epi == EPI_SPLIT;
@@ -129,7 +133,7 @@ __device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int r
             }
         }
     }
-    uint4* dst = reinterpret_cast<uint4*>(ep.out_bf16 + (size_t)row * ep.ldo + col);
+    uint4* dst = stage ? stage : reinterpret_cast<uint4*>(ep.out_bf16 + (size_t)row * ep.ldo + col);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
@@ -137,7 +141,8 @@ __device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int r
 
 template <int N, int K>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiArgs ep, int epi, int M) {
+    k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+           const __grid_constant__ CUtensorMap tmO, EpiArgs ep, int epi, int M) {
     static_assert(K % BK == 0 && N % 32 == 0 && N <= 256, "tile shape");
     constexpr int KB = K / BK;
     constexpr int TMEM_COLS = tmem_cols_for(N);
@@ -146,7 +151,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* sB = smem;                    // KB blocks of [N rows][128 B]
     uint8_t* sA = sB + (size_t)N * K * 2;  // STAGES x [128 rows][128 B]
-    Ctl* ctl = reinterpret_cast<Ctl*>(sA + STAGES * A_STAGE_BYTES);
+    uint8_t* sO = sA + STAGES * A_STAGE_BYTES;  // 4 epilogue warps x 2 output boxes
+    Ctl* ctl = reinterpret_cast<Ctl*>(sO + 8 * OUT_STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -250,7 +256,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp >= 2) {
         // ---------------- epilogue
         const int q = warp & 3;
-        int acc = 0;
+        int acc = 0, sbuf = 0;
         uint32_t aph = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
             const int row = tile * BM + q * 32 + lane;
@@ -271,7 +277,25 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const bool more = masked && c + 1 < N / 32;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) nx[j] = more ? __ldg(mrow + 4 * (c + 1) + j) : make_uint4(0u, 0u, 0u, 0u);
-                epilogue_chunk<N>(ep, epi, row, M, c * 32, v, mk);
+                const bool tma = ep.tma_out && epi != EPI_BIAS_F32 && !(epi == EPI_SPLIT && c * 32 >= ep.split);
+                if (tma) {
+                    // stage the warp's 32 x 32 box, then one thread stores it;
+                    // a buffer is refilled once the store issued from it two
+                    // chunks ago has read it (rows past M are clipped)
+                    uint8_t* st = sO + (size_t)(q * 2 + sbuf) * OUT_STAGE_BYTES;
+                    if (lane == 0) sm100::bulk_wait_read_1();
+                    __syncwarp();
+                    epilogue_chunk<N>(ep, epi, row, M, c * 32, v, mk, reinterpret_cast<uint4*>(st + lane * 64));
+                    sm100::fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        sm100::tma_store_2d(&tmO, c * 32, tile * BM + q * 32, st);
+                        sm100::bulk_commit();
+                    }
+                    sbuf ^= 1;
+                } else {
+                    epilogue_chunk<N>(ep, epi, row, M, c * 32, v, mk, nullptr);
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) mk[j] = nx[j];
             }
@@ -282,6 +306,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 aph ^= 1u;
             }
         }
+        if (lane == 0) sm100::bulk_wait_all();  // the output stores are complete before the CTA exits
     }
     sm100::tc_fence_before();
     __syncthreads();

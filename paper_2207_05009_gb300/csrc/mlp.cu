@@ -89,6 +89,22 @@ plo_status make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t co
     return PLO_OK;
 }
 
+// bf16 matrix [rows][cols] written by TMA stores in boxes of 32 columns x 32
+// rows, unswizzled (the epilogue stages each box row-major in shared memory).
+plo_status make_store_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols) {
+    EncodeFn fn = encoder();
+    if (!fn) return set_error(PLO_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 2};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(PLO_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+    return PLO_OK;
+}
+
 int sm_count_of_current() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -97,16 +113,19 @@ int sm_count_of_current() {
 }
 
 // ---------------------------------------------------------------- GEMM launchers
+// O: tensor map of the bf16 output (boxes of 32 x 32) for TMA stores, or
+// NULL for direct stores from the epilogue threads.
 template <int N, int K>
-cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, const gemm::EpiArgs& ep, int epi, int M,
-                        int sms, cudaStream_t s) {
+cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, const CUtensorMap* O, gemm::EpiArgs ep, int epi,
+                        int M, int sms, cudaStream_t s) {
+    ep.tma_out = O ? 1 : 0;
     const size_t smem = gemm::gemm_smem_bytes(N, K);
     cudaError_t e = cudaFuncSetAttribute(gemm::k_gemm<N, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int tiles = (M + gemm::BM - 1) / gemm::BM;
     int grid = tiles < sms ? tiles : sms;
     if (grid < 1) return cudaSuccess;
-    gemm::k_gemm<N, K><<<grid, gemm::THREADS, smem, s>>>(A, B, ep, epi, M);
+    gemm::k_gemm<N, K><<<grid, gemm::THREADS, smem, s>>>(A, B, O ? *O : A, ep, epi, M);
     return cudaGetLastError();
 }
 
@@ -741,6 +760,7 @@ struct plo_mlp {
     float* ray_loss = nullptr;
     CUtensorMap mapA_H[MAX_LAYERS], mapA_dO, mapA_dZ[2], mapA_dZc;  // A operand boxes (128 rows)
     CUtensorMap mapW_H[MAX_LAYERS], mapW_dO, mapW_dZ[2], mapW_dZc;  // wgrad boxes (64 rows)
+    CUtensorMap mapO_H[MAX_LAYERS], mapO_dZ[2], mapO_dZc;           // TMA-store boxes (32 x 32)
 };
 
 namespace {
@@ -802,6 +822,10 @@ plo_status ensure_workspace(plo_mlp* m, int64_t samples, int rays) {
     }
     if (st == PLO_OK && paper) st = make_map(&m->mapA_dZc, m->dZc, samples, COMB_PAD, 128);
     if (st == PLO_OK && paper) st = make_map(&m->mapW_dZc, m->dZc, samples, COMB_PAD, 64);
+    if (st == PLO_OK && paper) st = make_store_map(&m->mapO_dZc, m->dZc, samples, COMB_PAD);
+    for (int l = 1; l < m->n_layers && st == PLO_OK; ++l)
+        st = make_store_map(&m->mapO_H[l], m->H[l], samples, m->geom.in_pad[l]);
+    for (int k = 0; k < 2 && st == PLO_OK; ++k) st = make_store_map(&m->mapO_dZ[k], m->dZ[k], samples, WIDTH);
     if (st == PLO_OK) st = make_map(&m->mapA_dO, m->dO, samples, OUT_PAD, 128);
     if (st == PLO_OK) st = make_map(&m->mapW_dO, m->dO, samples, OUT_PAD, 64);
     for (int k = 0; k < 2 && st == PLO_OK; ++k) {
@@ -919,15 +943,15 @@ plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s) {
         ep.out_bf16 = m->H[l + 1];
         ep.ldo = WIDTH;
         if (l == 0)
-            e = launch_gemm<WIDTH, PE_PAD>(m->mapA_H[0], m->mapW[0], ep, gemm::EPI_RELU_BF16, (int)samples, m->sms, s);
+            e = launch_gemm<WIDTH, PE_PAD>(m->mapA_H[0], m->mapW[0], &m->mapO_H[1], ep, gemm::EPI_RELU_BF16, (int)samples, m->sms, s);
         else
-            e = launch_gemm<WIDTH, WIDTH>(m->mapA_H[l], m->mapW[l], ep, gemm::EPI_RELU_BF16, (int)samples, m->sms, s);
+            e = launch_gemm<WIDTH, WIDTH>(m->mapA_H[l], m->mapW[l], &m->mapO_H[l + 1], ep, gemm::EPI_RELU_BF16, (int)samples, m->sms, s);
     }
     if (e == cudaSuccess && m->arch == PLO_ARCH_LINEAR_HEAD) {
         ep.bias = bias_ptr(m, m->master, DEPTH);
         ep.out_f32 = m->raw;
         ep.ldo = OUT_PAD;
-        e = launch_gemm<OUT_PAD, WIDTH>(m->mapA_H[DEPTH], m->mapW[DEPTH], ep, gemm::EPI_BIAS_F32, (int)samples, m->sms,
+        e = launch_gemm<OUT_PAD, WIDTH>(m->mapA_H[DEPTH], m->mapW[DEPTH], nullptr, ep, gemm::EPI_BIAS_F32, (int)samples, m->sms,
                                         s);
     } else if (e == cudaSuccess) {
         // [ReLU features -> H[9] (bf16) | sigma block -> sraw (fp32)], then the
@@ -938,7 +962,7 @@ plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s) {
         ep.split = FEAT;
         ep.out_f32 = m->sraw;
         ep.ldo2 = OUT_PAD;
-        e = launch_gemm<COMB_PAD, WIDTH>(m->mapA_H[DEPTH], m->mapW[DEPTH], ep, gemm::EPI_SPLIT, (int)samples, m->sms,
+        e = launch_gemm<COMB_PAD, WIDTH>(m->mapA_H[DEPTH], m->mapW[DEPTH], &m->mapO_H[DEPTH + 1], ep, gemm::EPI_SPLIT, (int)samples, m->sms,
                                          s);
         gemm::EpiArgs eh{};
         eh.err = m->d_err;
@@ -948,7 +972,7 @@ plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s) {
         eh.col0_add = m->sraw;
         eh.ld_col0 = OUT_PAD;
         if (e == cudaSuccess)
-            e = launch_gemm<OUT_PAD, FEAT>(m->mapA_H[DEPTH + 1], m->mapW[DEPTH + 1], eh, gemm::EPI_BIAS_F32,
+            e = launch_gemm<OUT_PAD, FEAT>(m->mapA_H[DEPTH + 1], m->mapW[DEPTH + 1], nullptr, eh, gemm::EPI_BIAS_F32,
                                            (int)samples, m->sms, s);
     }
     return e == cudaSuccess ? PLO_OK : cuda_error(e, "MLP forward GEMM launch");
@@ -1000,7 +1024,7 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
         ep.mask = m->H[DEPTH];
         ep.ldm = WIDTH;
         if (e == cudaSuccess)
-            e = launch_gemm<WIDTH, OUT_PAD>(m->mapA_dO, m->mapWT[DEPTH], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+            e = launch_gemm<WIDTH, OUT_PAD>(m->mapA_dO, m->mapWT[DEPTH], &m->mapO_dZ[0], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
     } else {
         const int SH = DEPTH + 1;
         // SH layer: dW = dO^T feat, db = column sums; d feat -> dZc[:, 0:128]
@@ -1012,7 +1036,7 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
         ep.mask = m->H[SH];
         ep.ldm = FEAT;
         if (e == cudaSuccess)
-            e = launch_gemm<FEAT, OUT_PAD>(m->mapA_dO, m->mapWT[SH], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+            e = launch_gemm<FEAT, OUT_PAD>(m->mapA_dO, m->mapWT[SH], &m->mapO_dZc, ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
         // combined layer [features | sigma]: dW = dZc^T h8; d h8 -> dZ[0]
         if (e == cudaSuccess)
             e = launch_wgrad<WIDTH>(m->mapW_dZc, m->mapW_H[DEPTH], m->grad + m->geom.off[DEPTH], COMB_PAD, (int)M,
@@ -1023,7 +1047,7 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
         ep.mask = m->H[DEPTH];
         ep.ldm = WIDTH;
         if (e == cudaSuccess)
-            e = launch_gemm<WIDTH, COMB_PAD>(m->mapA_dZc, m->mapWT[DEPTH], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+            e = launch_gemm<WIDTH, COMB_PAD>(m->mapA_dZc, m->mapWT[DEPTH], &m->mapO_dZ[0], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
     }
     // hidden layers l = 8 .. 2 (index l-1 = 7 .. 1), then layer 1
     int cur = 0;
@@ -1039,7 +1063,7 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
         if (l == 0 || e != cudaSuccess) break;
         ep.out_bf16 = m->dZ[cur ^ 1];
         ep.mask = m->H[l];
-        e = launch_gemm<WIDTH, WIDTH>(m->mapA_dZ[cur], m->mapWT[l], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+        e = launch_gemm<WIDTH, WIDTH>(m->mapA_dZ[cur], m->mapWT[l], &m->mapO_dZ[cur ^ 1], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
         cur ^= 1;
     }
     if (e != cudaSuccess) return cuda_error(e, "MLP backward launch");
@@ -1376,9 +1400,10 @@ extern "C" plo_status plo_gemm_bf16(const void* d_A, const void* d_B, int32_t M,
     if (epilogue < 0 || epilogue > 2) return set_error(PLO_ERR_INVALID_ARG, "unknown epilogue");
     if ((epilogue != gemm::EPI_MASK_BF16 && !d_bias) || (epilogue == gemm::EPI_MASK_BF16 && !d_mask))
         return set_error(PLO_ERR_INVALID_ARG, "bias (epilogues 0, 1) or mask (epilogue 2) is NULL");
-    CUtensorMap mA, mB;
+    CUtensorMap mA, mB, mO;
     plo_status st = make_map(&mA, d_A, (uint64_t)M, (uint64_t)K, 128);
     if (st == PLO_OK) st = make_map(&mB, d_B, (uint64_t)N, (uint64_t)K, (uint32_t)N);
+    if (st == PLO_OK && epilogue != gemm::EPI_BIAS_F32) st = make_store_map(&mO, d_out, (uint64_t)M, (uint64_t)N);
     if (st != PLO_OK) return st;
     gemm::EpiArgs ep{};
     ep.bias = d_bias;
@@ -1391,9 +1416,10 @@ extern "C" plo_status plo_gemm_bf16(const void* d_A, const void* d_B, int32_t M,
     const int sms = sm_count_of_current();
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
-    if (N == 256 && K == 64) e = launch_gemm<256, 64>(mA, mB, ep, epilogue, M, sms, s);
-    else if (N == 256) e = launch_gemm<256, 256>(mA, mB, ep, epilogue, M, sms, s);
-    else e = launch_gemm<64, 256>(mA, mB, ep, epilogue, M, sms, s);
+    const CUtensorMap* O = epilogue == gemm::EPI_BIAS_F32 ? nullptr : &mO;
+    if (N == 256 && K == 64) e = launch_gemm<256, 64>(mA, mB, O, ep, epilogue, M, sms, s);
+    else if (N == 256) e = launch_gemm<256, 256>(mA, mB, O, ep, epilogue, M, sms, s);
+    else e = launch_gemm<64, 256>(mA, mB, O, ep, epilogue, M, sms, s);
     return e == cudaSuccess ? PLO_OK : cuda_error(e, "GEMM launch");
 }
 
@@ -1416,7 +1442,8 @@ extern "C" plo_status plo_debug_gemm_stall(const void* d_A, const void* d_B, int
     ep.debug_skip_loads = 1;
     ep.mask = static_cast<const __nv_bfloat16*>(d_out);
     ep.ldm = 256;
-    cudaError_t e = launch_gemm<256, 64>(mA, mB, ep, gemm::EPI_MASK_BF16, M, sm_count_of_current(), (cudaStream_t)stream);
+    cudaError_t e =
+        launch_gemm<256, 64>(mA, mB, nullptr, ep, gemm::EPI_MASK_BF16, M, sm_count_of_current(), (cudaStream_t)stream);
     return e == cudaSuccess ? PLO_OK : cuda_error(e, "GEMM launch");
 }
 

@@ -37,7 +37,7 @@ namespace {
 
 constexpr int BLOCK = 256;
 #ifndef PLO_RENDER_MIN_BLOCKS
-#define PLO_RENDER_MIN_BLOCKS 3  // resident blocks per SM the register budget is sized for (measured best)
+#define PLO_RENDER_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for (measured best)
 #endif
 constexpr int WARPS = BLOCK / 32;
 constexpr int STACK = MAX_DEPTH + 1;
@@ -205,16 +205,10 @@ template <int K, int PREC>
 __device__ __forceinline__ void sh_emission(const TreeParams& tp, uint32_t rec, uint32_t yword, const float* dirn,
                                             float& r, float& g, float& b, const float* sY = nullptr) {
     const uint8_t* p = tp.sh + (size_t)rec * tp.sh_stride;
-    if (K > 0 && sY) {
+    if (K > 0) {  // the per-lane basis in shared memory (sY, set at the ray's start)
         float Y[K > 0 ? K : 1];
 #pragma unroll
         for (int k = 0; k < (K > 0 ? K : 1); ++k) Y[k] = sY[k * BLOCK];
-        sh_eval<(K > 0 ? K : 1), PREC>(p, yword, Y, r, g, b);
-        return;
-    }
-    if (K > 0) {
-        float Y[K > 0 ? K : 1];
-        sh_basis<(K > 0 ? K : 1)>(dirn[0], dirn[1], dirn[2], Y);
         sh_eval<(K > 0 ? K : 1), PREC>(p, yword, Y, r, g, b);
         return;
     }
@@ -243,8 +237,7 @@ enum : int { ST_IDLE = 0, ST_DESCEND = 1, ST_LEAF = 2 };
 
 struct Ray {
     DF p[3];
-    float d[3], dl[3];  // unit-cube direction as a double-float (dl = 0 for the unit box)
-    float rh[3], rl[3]; // 1/d as a double-float
+    float d[3];         // unit-cube direction (high part; the low part is in low_parts())
     float dirn[3];      // normalised world direction for the SH basis
     float T, r, g, b;
     DF od;
@@ -260,6 +253,16 @@ struct Ray {
     int status;
     int tree;           // index into the batch's tree table (batch kernel only)
 };
+
+// Per-ray constants read once per cell, kept in shared memory to leave
+// registers to the hot state: the low-order part of the double-float
+// direction (dl, zero for the unit box) at [a * BLOCK], the reciprocal 1/d
+// as a double-float, low part rl at [(3 + a) * BLOCK] and high part rh at
+// [(6 + a) * BLOCK].  Column per thread.
+__device__ __forceinline__ float* low_parts() {
+    __shared__ float s_low[9 * BLOCK];
+    return s_low + threadIdx.x;
+}
 
 __device__ __forceinline__ uint2 load_entry(const TreeParams& tp, const uint2* s_nodes, uint32_t node, int slot) {
     if (node < (uint32_t)tp.n_top) return s_nodes[tp.s_off + node * 8 + slot];
@@ -344,7 +347,7 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
         ou[a] = df_mul(two_sum(o[a], -tp.bmin[a]), tp.inv_ext[a], tp.inv_ext_lo[a]);
         DF du = df_mul(DF{dw[a], 0.0f}, tp.inv_ext[a], tp.inv_ext_lo[a]);
         R.d[a] = du.hi;
-        R.dl[a] = du.lo;
+        low_parts()[a * BLOCK] = du.lo;
     }
     // slab test in double-float
     DF tn = {-INFINITY, 0.0f}, tf = {INFINITY, 0.0f};
@@ -360,9 +363,9 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
             continue;
         }
         float rh, rl;
-        df_recip(R.d[a], R.dl[a], rh, rl);
-        R.rh[a] = rh;
-        R.rl[a] = rl;
+        df_recip(R.d[a], low_parts()[a * BLOCK], rh, rl);
+        low_parts()[(6 + a) * BLOCK] = rh;
+        low_parts()[(3 + a) * BLOCK] = rl;
         DF t0 = df_mul(df_from_plane(0.0f, ou[a]), rh, rl);
         DF t1 = df_mul(df_from_plane(1.0f, ou[a]), rh, rl);
         if (df_less(t1, t0)) {
@@ -408,7 +411,7 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
     if (SPHERE) R.rem = outside ? df_sub(tf, tn) : tf;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        R.p[a] = outside ? df_axpy(ou[a], tn, R.d[a], R.dl[a]) : ou[a];
+        R.p[a] = outside ? df_axpy(ou[a], tn, R.d[a], low_parts()[a * BLOCK]) : ou[a];
         if (outside && R.d[a] != 0.0f && df_eq(near_a[a], tn)) R.p[a] = {R.d[a] > 0.0f ? 0.0f : 1.0f, 0.0f};
         if (R.p[a].hi < 0.0f) R.p[a] = {0.0f, 0.0f};  // rounding guard
         if (R.p[a].hi > 1.0f || (R.p[a].hi == 1.0f && R.p[a].lo > 0.0f)) R.p[a] = {1.0f, 0.0f};
@@ -436,18 +439,19 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
     const int down = tp.depth - L;
     const float size = pow2i(-L);
     uint32_t c[3];
-    float planes[3], va[3];
+    float planes[3], va[3], rh[3];
     float vmin = INFINITY, rmin = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+        rh[a] = low_parts()[(6 + a) * BLOCK];
         c[a] = R.q[a] >> down;
         planes[a] = (float)(c[a] + (R.d[a] > 0.0f ? 1u : 0u)) * size;
         va[a] = INFINITY;
         if (R.d[a] == 0.0f) continue;
-        va[a] = fmaxf(__fmul_rn(__fsub_rn(planes[a], R.p[a].hi), R.rh[a]), 0.0f);
+        va[a] = fmaxf(__fmul_rn(__fsub_rn(planes[a], R.p[a].hi), rh[a]), 0.0f);
         if (va[a] < vmin) {
             vmin = va[a];
-            rmin = fabsf(R.rh[a]);
+            rmin = fabsf(rh[a]);
         }
     }
     DF dt = {INFINITY, 0.0f};
@@ -455,8 +459,8 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         dts[a] = {INFINITY, 0.0f};
-        if (!(va[a] <= vmin + 2.5e-7f * (fabsf(R.rh[a]) + rmin) + 1e-6f * vmin)) continue;
-        DF v = df_mul(df_from_plane(planes[a], R.p[a]), R.rh[a], R.rl[a]);
+        if (!(va[a] <= vmin + 2.5e-7f * (fabsf(rh[a]) + rmin) + 1e-6f * vmin)) continue;
+        DF v = df_mul(df_from_plane(planes[a], R.p[a]), rh[a], low_parts()[(3 + a) * BLOCK]);
         if (v.hi < 0.0f) v = {0.0f, 0.0f};
         dts[a] = v;
         if (df_less(v, dt)) dt = v;
@@ -555,7 +559,7 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
             const int diff = 32 - __clz(cn ^ c[a]);
             if (L - diff < l_anc) l_anc = L - diff;
         } else {
-            R.p[a] = df_axpy(R.p[a], dt, R.d[a], R.dl[a]);
+            R.p[a] = df_axpy(R.p[a], dt, R.d[a], low_parts()[a * BLOCK]);
             R.q[a] = quantize(R.p[a], scale, qmax, R.d[a]);
         }
     }
