@@ -295,9 +295,7 @@ __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* 
             return;
         }
         stack[R.level * BLOCK] = e.x;
-        const uint32_t parent = R.node;
         R.node = e.x;
-        (void)parent;
         if (global || R.node >= (uint32_t)tp.n_top) return;  // next lookup needs a global load
     }
 }
@@ -573,8 +571,10 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
     R.state = ST_DESCEND;
 }
 
+// The trace and sphere-proxy kernels keep more per-ray state: 3 blocks per
+// SM (80 registers) beats 4 with spills for them (measured).
 template <int K, int PREC, bool TRACE, bool SPHERE>
-__global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render(KParams kp) {
+__global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : PLO_RENDER_MIN_BLOCKS) k_render(KParams kp) {
     // nodes of the top levels, staged once per (persistent) block
     extern __shared__ uint2 s_nodes[];
     const TreeParams& tp = kp.tree;

@@ -138,7 +138,7 @@ def test_training_on_rendered_targets_reduces_loss(torch_cuda):
         losses.append(float(net.train_step(rays, rgb, alpha, n_samples=128).item()))
     net.check()
     assert np.all(np.isfinite(losses))
-    assert np.mean(losses[-16:]) < 0.5 * np.mean(losses[:8]), losses[::16]
+    assert np.mean(losses[-16:]) < 0.6 * np.mean(losses[:8]), losses[::16]
 
 
 def tree_from_morton(depth, codes, sigma, sh):
