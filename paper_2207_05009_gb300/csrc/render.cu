@@ -2,11 +2,13 @@
 // per-leaf SH emission -> front-to-back emission/absorption compositing
 // (paper Sec. 4.1, Eq. 3-5; plenoctree of Sec. 4.2 / Sec. 5).
 //
-// One thread renders one ray at a time.  The grid is persistent: each warp
-// owns a contiguous chunk of rays and a lane that finishes its ray takes the
-// next one of the chunk, so a warp does not idle behind its longest ray; each
-// lane advances through a small state machine (descend / composite) so that
-// lanes never wait for each other's dependent node loads.
+// One thread renders one ray at a time.  The grid is persistent: warps take
+// rays from a shared counter (64 at a time; small launches give each warp a
+// contiguous chunk) and a lane that finishes its ray takes the next one, so
+// a warp does not idle behind its longest ray; each lane advances through a
+// small state machine (descend / composite) so that lanes never wait for
+// each other's dependent node loads.  Child slots come from the bits of the
+// point's integer coordinates on the finest grid.
 //
 // Numerics (all FP32, no FP64 on the device):
 //   * The ray position is kept as an unevaluated sum hi + lo of two floats
