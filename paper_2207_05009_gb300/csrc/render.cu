@@ -434,13 +434,16 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
                           const float* sY = nullptr) {
     // segment: exit parameter of the current cell along each axis.  An FP32
     // estimate (error below 6e-8 |1/d| + 2e-7 v) picks the candidate exit
-    // axes; only those get the double-float value.
+    // axes; only those get the double-float value.  Nearly always there is
+    // one candidate: its operands are picked by selects so that the
+    // double-float work is issued once per warp instead of once per axis.
     const int L = R.level;
     const int down = tp.depth - L;
     const float size = pow2i(-L);
     uint32_t c[3];
     float planes[3], va[3], rh[3];
     float vmin = INFINITY, rmin = 0.0f;
+    int ax = 0;  // axis of the smallest estimate
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         rh[a] = low_parts()[(6 + a) * BLOCK];
@@ -452,18 +455,40 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
         if (va[a] < vmin) {
             vmin = va[a];
             rmin = fabsf(rh[a]);
+            ax = a;
         }
     }
     DF dt = {INFINITY, 0.0f};
     DF dts[3];
+    bool cand[3];
+    int n_cand = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         dts[a] = {INFINITY, 0.0f};
-        if (!(va[a] <= vmin + 2.5e-7f * (fabsf(rh[a]) + rmin) + 1e-6f * vmin)) continue;
-        DF v = df_mul(df_from_plane(planes[a], R.p[a]), rh[a], low_parts()[(3 + a) * BLOCK]);
+        cand[a] = va[a] <= vmin + 2.5e-7f * (fabsf(rh[a]) + rmin) + 1e-6f * vmin;
+        n_cand += cand[a] ? 1 : 0;
+    }
+    if (n_cand == 1) {
+        // the usual case: one candidate axis, gathered by selects so that the
+        // double-float work runs once for every lane whatever its axis
+        const float P = ax == 0 ? planes[0] : (ax == 1 ? planes[1] : planes[2]);
+        const DF pa = ax == 0 ? R.p[0] : (ax == 1 ? R.p[1] : R.p[2]);
+        const float rha = ax == 0 ? rh[0] : (ax == 1 ? rh[1] : rh[2]);
+        DF v = df_mul(df_from_plane(P, pa), rha, low_parts()[(3 + ax) * BLOCK]);
         if (v.hi < 0.0f) v = {0.0f, 0.0f};
-        dts[a] = v;
-        if (df_less(v, dt)) dt = v;
+        dt = v;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (a == ax) dts[a] = v;
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!cand[a]) continue;
+            DF v = df_mul(df_from_plane(planes[a], R.p[a]), rh[a], low_parts()[(3 + a) * BLOCK]);
+            if (v.hi < 0.0f) v = {0.0f, 0.0f};
+            dts[a] = v;
+            if (df_less(v, dt)) dt = v;
+        }
     }
     bool last = false;  // the sphere proxy ends inside this cell
     if (SPHERE) {
