@@ -716,7 +716,8 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(B
     for (;;) {
         for (;;) {
             unsigned idle = __ballot_sync(0xffffffffu, R.state == ST_IDLE);
-            if (idle == 0u) break;
+            // refill in groups of at least 8 lanes, as in k_render
+            if (idle == 0u || (__popc(idle) < 8 && idle != 0xffffffffu)) break;
             if (next >= end) {
                 if (drained) break;
                 unsigned long long base = 0;
@@ -744,7 +745,7 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(B
         const TreeParams& tp = s_tp[R.tree];
         // composite in batches, as in k_render
         const unsigned at_leaf = __ballot_sync(0xffffffffu, R.state == ST_LEAF);
-        const bool composite = 2 * __popc(at_leaf) >= __popc(live);
+        const bool composite = 4 * __popc(at_leaf) >= 3 * __popc(live);
         if (composite && R.state == ST_LEAF) leaf_step<0, -1, false, false>(kp, tp, my, R, stack);
         if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
     }
