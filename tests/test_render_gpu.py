@@ -247,6 +247,12 @@ def test_deterministic_and_host_path(torch_cuda, d6):
     h_rgb, h_T = plo.render_host(t, rays)
     np.testing.assert_array_equal(h_rgb, a[0].cpu().numpy())
     np.testing.assert_array_equal(h_T, a[1].cpu().numpy())
+    # four chunks of a quarter of the rays each, the last one ragged
+    rays = plogen.rays_sphere(4 * (1 << 20) + 12345, seed=16)
+    a = plo.render(t, torch.from_numpy(rays).cuda())
+    h_rgb, h_T = plo.render_host(t, rays)
+    np.testing.assert_array_equal(h_rgb, a[0].cpu().numpy())
+    np.testing.assert_array_equal(h_T, a[1].cpu().numpy())
 
 
 # ---------------------------------------------------------------- sphere proxy (Sec. 5) and the
