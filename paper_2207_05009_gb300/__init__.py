@@ -305,7 +305,7 @@ def _load_mlp_sigs(lib):
         "plo_mlp_check": (I32, [P, P]),
         "plo_mlp_step": (I64, [P]),
         "plo_gemm_bf16": (I32, [P, P, I32, I32, I32, I32, P, P, P, P, P]),
-        "plo_wgrad_bf16": (I32, [P, I32, P, I32, I32, P, P, P]),
+        "plo_wgrad_bf16": (I32, [P, I32, P, I32, I32, P, P, P, P]),
         "plo_distill": (I32, [P, I32, I32, ctypes.c_float, I32, P, P]),
     }
     for name, (res, args) in sigs.items():
@@ -437,12 +437,13 @@ def hier_samples(rays, t, delta, w, xi, stream=None):
     return t_out, d_out
 
 
-def wgrad_bf16(dZ, H, dW, err=None, stream=None):
-    """plo_wgrad_bf16: dW [n_out][n_in] (fp32) += dZ^T H."""
+def wgrad_bf16(dZ, H, dW, db=None, err=None, stream=None):
+    """plo_wgrad_bf16: dW [n_out][n_in] (fp32) += dZ^T H; db [n_out] (fp32,
+    optional) += the column sums of dZ."""
     import torch
     err = err if err is not None else torch.zeros(1, device=dZ.device, dtype=torch.int32)
-    _check(mlp_lib().plo_wgrad_bf16(_ptr(dZ), dZ.shape[1], _ptr(H), H.shape[1], dZ.shape[0], _ptr(dW), _ptr(err),
-                                    _stream(stream)))
+    _check(mlp_lib().plo_wgrad_bf16(_ptr(dZ), dZ.shape[1], _ptr(H), H.shape[1], dZ.shape[0], _ptr(dW), _ptr(db),
+                                    _ptr(err), _stream(stream)))
     return dW, err
 
 

@@ -321,25 +321,35 @@ __global__ void __launch_bounds__(THREADS, 1)
 // A' = dZ^T tile: two TMA boxes of 64 (o) x 64 (m) -> MN-major, LBO = 8 KB
 // between the 64-wide o blocks, SBO = 1 KB between 8-row m groups.  B' = H^T
 // tile: NIN/64 boxes of 64 (i) x 64 (m), same strides.
+// With db: db[o] += sum_m dZ[m][o] (the bias gradient) as one more MMA per
+// k-step, A' against a 16 x 64 tile of ones kept in shared memory, into 16
+// spare accumulator columns: the column sums cost no extra pass over dZ.
 template <int NIN>
 __host__ __device__ constexpr size_t wgrad_stage_bytes() {
     return (size_t)(2 + NIN / 64) * 64 * 128;
 }
+constexpr int WGRAD_ONES_BYTES = 16 * 128;  // 16 rows (n) x 64 (k) bf16 ones, K-major
 template <int NIN>
 __host__ __device__ constexpr size_t wgrad_smem_bytes() {
-    return 1024 + STAGES * wgrad_stage_bytes<NIN>() + 256;
+    return 1024 + STAGES * wgrad_stage_bytes<NIN>() + 1024 /*barriers, padded*/ + WGRAD_ONES_BYTES;
+}
+template <int NIN>
+__host__ __device__ constexpr int wgrad_tmem_cols() {  // NIN accumulator columns + 16 for the bias sums
+    return NIN + 16 <= 32 ? 32 : (NIN + 16 <= 64 ? 64 : (NIN + 16 <= 128 ? 128 : (NIN + 16 <= 256 ? 256 : 512)));
 }
 
 template <int NIN>
 __global__ void __launch_bounds__(THREADS, 1)
     k_wgrad(const __grid_constant__ CUtensorMap tmDZ, const __grid_constant__ CUtensorMap tmH, float* dW, int n_out,
-            int M, int chunk, unsigned int* err) {
-    constexpr int TMEM_COLS = NIN < 32 ? 32 : NIN;
+            int M, int chunk, unsigned int* err, float* db) {
+    constexpr int TMEM_COLS = wgrad_tmem_cols<NIN>();
     constexpr uint32_t IDESC = sm100::idesc_bf16(BM, NIN, 1, 1);
+    constexpr uint32_t IDESC_ONES = sm100::idesc_bf16(BM, 16, 1, 0);
     constexpr uint32_t STAGE = (uint32_t)wgrad_stage_bytes<NIN>();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     Ctl* ctl = reinterpret_cast<Ctl*>(smem + STAGES * STAGE);
+    uint8_t* ones = smem + STAGES * STAGE + 1024;  // 1 KB aligned
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int out_base = blockIdx.y * BM;
     const int m_beg = blockIdx.x * chunk;
@@ -356,6 +366,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         ctl->abort = 0;
         ctl->limit = sm100::WAIT_LIMIT;
         sm100::fence_mbar_init();
+    }
+    if (db) {  // bf16 1.0 everywhere, so the swizzle of the tile does not matter
+        for (int j = threadIdx.x; j < WGRAD_ONES_BYTES / 4; j += THREADS)
+            reinterpret_cast<uint32_t*>(ones)[j] = 0x3F803F80u;
+        sm100::fence_proxy_async();  // visible to the tensor core
     }
     if (warp == 1) sm100::tmem_alloc(&ctl->tmem, TMEM_COLS);
     sm100::tc_fence_before();
@@ -409,6 +424,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 uint64_t adesc = sm100::smem_desc_sw128(a0 + 2048 * k, 8192, 1024);
                 uint64_t bdesc = sm100::smem_desc_sw128(b0 + 2048 * k, 8192, 1024);
                 sm100::mma_bf16(tmem, adesc, bdesc, IDESC, (kb | k) != 0);
+                if (db) {
+                    uint64_t odesc = sm100::smem_desc_sw128(sm100::smem_addr(ones) + 32 * k, 16, 1024);
+                    sm100::mma_bf16(tmem + NIN, adesc, odesc, IDESC_ONES, (kb | k) != 0);
+                }
             }
             issued = true;
             sm100::mma_commit(&ctl->empty[stage]);
@@ -437,6 +456,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int j = 0; j < 8; ++j)
                         atomicAdd(dst + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
                 }
+            }
+            if (db) {  // the 16 ones-columns all hold the row sum; the first one is used
+                float v[32];
+                sm100::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)NIN, v);
+                if (o < n_out) atomicAdd(db + o, v[0]);
             }
         }
     }

@@ -4,7 +4,7 @@
 //   sampling + positional encoding  k_pe        (Sec. 4.1 ray marching, Sec. 4.2 PE)
 //   8 x 256 ReLU layers + SH head   k_gemm      (tcgen05, gemm.cuh)
 //   quadrature, loss, d loss/d raw  k_quad      (Eq. 3-6, Eq. 7-9)
-//   weight / bias gradients         k_wgrad, k_colsum
+//   weight and bias gradients       k_wgrad (bias: an extra MMA against ones)
 //   data gradients through ReLU     k_gemm (mask epilogue)
 //   Adam + exponential lr decay     k_adam      (Sec. 4.4)
 //
@@ -131,7 +131,7 @@ cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, const CUtens
 
 template <int NIN>
 cudaError_t launch_wgrad(const CUtensorMap& dZ, const CUtensorMap& H, float* dW, int n_out, int M, int sms,
-                         unsigned int* err, cudaStream_t s) {
+                         unsigned int* err, cudaStream_t s, float* db = nullptr) {
     const size_t smem = gemm::wgrad_smem_bytes<NIN>();
     cudaError_t e = cudaFuncSetAttribute(gemm::k_wgrad<NIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -143,7 +143,7 @@ cudaError_t launch_wgrad(const CUtensorMap& dZ, const CUtensorMap& H, float* dW,
     const int chunk = ((blocks64 + n_chunks - 1) / n_chunks) * 64;
     n_chunks = (M + chunk - 1) / chunk;
     dim3 grid(n_chunks, out_tiles);
-    gemm::k_wgrad<NIN><<<grid, gemm::THREADS, smem, s>>>(dZ, H, dW, n_out, M, chunk, err);
+    gemm::k_wgrad<NIN><<<grid, gemm::THREADS, smem, s>>>(dZ, H, dW, n_out, M, chunk, err, db);
     return cudaGetLastError();
 }
 
@@ -508,38 +508,6 @@ __global__ void k_quad(const float* raw, const float* delta, const float* rays, 
             }
             dst[q] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
-    }
-}
-
-// db[n] += sum_m dZ[m][n], n < ncols (bf16 input, fp32 sums).
-__global__ void k_colsum(const __nv_bfloat16* dZ, int64_t M, int ncols, int rows_per_block, float* db) {
-    const int pairs = ncols / 2;  // ncols even, <= 2 * blockDim.x
-    const int p = threadIdx.x % pairs;
-    const int rg = threadIdx.x / pairs;
-    const int groups = blockDim.x / pairs;  // threads beyond groups * pairs only hold zeros
-    const int64_t m0 = (int64_t)blockIdx.x * rows_per_block;
-    const int64_t m1 = min(m0 + rows_per_block, M);
-    float sx = 0.0f, sy = 0.0f;
-    if (rg < groups) {
-#pragma unroll 8
-        for (int64_t m = m0 + rg; m < m1; m += groups) {
-            __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(dZ + m * ncols + 2 * p);
-            float2 f = __bfloat1622float2(v);
-            sx += f.x;
-            sy += f.y;
-        }
-    }
-    __shared__ float red[2][256];
-    red[0][threadIdx.x] = sx;
-    red[1][threadIdx.x] = sy;
-    __syncthreads();
-    if (rg == 0) {
-        for (int g = 1; g < groups; ++g) {
-            sx += red[0][g * pairs + p];
-            sy += red[1][g * pairs + p];
-        }
-        atomicAdd(db + 2 * p, sx);
-        atomicAdd(db + 2 * p + 1, sy);
     }
 }
 
@@ -1010,15 +978,10 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
     const plo_mlp_desc& D = m->desc;
     gemm::EpiArgs ep{};
     ep.err = m->d_err;
-    auto colsum = [&](const __nv_bfloat16* dz, int ncols, float* db) {
-        const int rows = 512;
-        k_colsum<<<(unsigned)((M + rows - 1) / rows), 256, 0, s>>>(dz, M, ncols, rows, db);
-    };
     cudaError_t e;
     if (m->arch == PLO_ARCH_LINEAR_HEAD) {
         e = launch_wgrad<WIDTH>(m->mapW_dO, m->mapW_H[DEPTH], m->grad + m->geom.off[DEPTH], OUT_PAD, (int)M, m->sms,
-                                m->d_err, s);
-        colsum(m->dO, OUT_PAD, bias_ptr(m, m->grad, DEPTH));
+                                m->d_err, s, bias_ptr(m, m->grad, DEPTH));
         ep.out_bf16 = m->dZ[0];
         ep.ldo = WIDTH;
         ep.mask = m->H[DEPTH];
@@ -1029,8 +992,7 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
         const int SH = DEPTH + 1;
         // SH layer: dW = dO^T feat, db = column sums; d feat -> dZc[:, 0:128]
         e = launch_wgrad<FEAT>(m->mapW_dO, m->mapW_H[SH], m->grad + m->geom.off[SH], OUT_PAD, (int)M, m->sms,
-                               m->d_err, s);
-        colsum(m->dO, OUT_PAD, bias_ptr(m, m->grad, SH));
+                               m->d_err, s, bias_ptr(m, m->grad, SH));
         ep.out_bf16 = m->dZc;
         ep.ldo = COMB_PAD;
         ep.mask = m->H[SH];
@@ -1040,8 +1002,7 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
         // combined layer [features | sigma]: dW = dZc^T h8; d h8 -> dZ[0]
         if (e == cudaSuccess)
             e = launch_wgrad<WIDTH>(m->mapW_dZc, m->mapW_H[DEPTH], m->grad + m->geom.off[DEPTH], COMB_PAD, (int)M,
-                                    m->sms, m->d_err, s);
-        colsum(m->dZc, COMB_PAD, bias_ptr(m, m->grad, DEPTH));
+                                    m->sms, m->d_err, s, bias_ptr(m, m->grad, DEPTH));
         ep.out_bf16 = m->dZ[0];
         ep.ldo = WIDTH;
         ep.mask = m->H[DEPTH];
@@ -1049,17 +1010,17 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
         if (e == cudaSuccess)
             e = launch_gemm<WIDTH, COMB_PAD>(m->mapA_dZc, m->mapWT[DEPTH], &m->mapO_dZ[0], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
     }
-    // hidden layers l = 8 .. 2 (index l-1 = 7 .. 1), then layer 1
+    // hidden layers l = 8 .. 2 (index l-1 = 7 .. 1), then layer 1; each
+    // weight-gradient launch also sums the layer's bias gradient
     int cur = 0;
     for (int l = DEPTH - 1; l >= 0 && e == cudaSuccess; --l) {
         // dZ[cur] is d loss / d pre-activation of layer l (0-based), input H[l]
         if (l == 0)
             e = launch_wgrad<PE_PAD>(m->mapW_dZ[cur], m->mapW_H[0], m->grad + m->geom.off[0], WIDTH, (int)M, m->sms,
-                                     m->d_err, s);
+                                     m->d_err, s, bias_ptr(m, m->grad, l));
         else
             e = launch_wgrad<WIDTH>(m->mapW_dZ[cur], m->mapW_H[l], m->grad + m->geom.off[l], WIDTH, (int)M, m->sms,
-                                    m->d_err, s);
-        colsum(m->dZ[cur], WIDTH, bias_ptr(m, m->grad, l));
+                                    m->d_err, s, bias_ptr(m, m->grad, l));
         if (l == 0 || e != cudaSuccess) break;
         ep.out_bf16 = m->dZ[cur ^ 1];
         ep.mask = m->H[l];
@@ -1448,7 +1409,7 @@ extern "C" plo_status plo_debug_gemm_stall(const void* d_A, const void* d_B, int
 }
 
 extern "C" plo_status plo_wgrad_bf16(const void* d_dZ, int32_t n_out, const void* d_H, int32_t n_in, int32_t M,
-                                     float* d_dW, unsigned int* d_err, void* stream) {
+                                     float* d_dW, float* d_db, unsigned int* d_err, void* stream) {
     if (!d_dZ || !d_H || !d_dW || !d_err) return set_error(PLO_ERR_INVALID_ARG, "dZ, H, dW or err is NULL");
     if (M <= 0 || M % 64) return set_error(PLO_ERR_INVALID_ARG, "M must be a positive multiple of 64");
     if (!((n_out == 64 || n_out == 256) && (n_in == 64 || n_in == 256)))
@@ -1459,8 +1420,8 @@ extern "C" plo_status plo_wgrad_bf16(const void* d_dZ, int32_t n_out, const void
     if (st != PLO_OK) return st;
     const int sms = sm_count_of_current();
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = n_in == 256 ? launch_wgrad<256>(mZ, mH, d_dW, n_out, M, sms, d_err, s)
-                                : launch_wgrad<64>(mZ, mH, d_dW, n_out, M, sms, d_err, s);
+    cudaError_t e = n_in == 256 ? launch_wgrad<256>(mZ, mH, d_dW, n_out, M, sms, d_err, s, d_db)
+                                : launch_wgrad<64>(mZ, mH, d_dW, n_out, M, sms, d_err, s, d_db);
     return e == cudaSuccess ? PLO_OK : cuda_error(e, "weight-gradient GEMM launch");
 }
 

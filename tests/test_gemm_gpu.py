@@ -50,8 +50,17 @@ def test_weight_gradient(torch_cuda, n_out, n_in, M):
     dZ = (torch.randn(M, n_out, device="cuda", generator=g) * 0.1).to(torch.bfloat16)
     H = torch.relu(torch.randn(M, n_in, device="cuda", generator=g)).to(torch.bfloat16)
     dW = torch.full((n_out, n_in), 0.5, device="cuda")
-    dW, err = plo.wgrad_bf16(dZ, H, dW)
+    db = torch.full((n_out,), -0.25, device="cuda")
+    dW, err = plo.wgrad_bf16(dZ, H, dW, db=db)
     ref = dZ.float().t() @ H.float() + 0.5
+    ref_db = dZ.double().sum(0).float() - 0.25
     torch.cuda.synchronize()
     assert int(err.item()) == 0
     assert rel_err(dW, ref) < 1e-4
+    # the bias gradient (column sums of dZ) from the same pass
+    assert rel_err(db, ref_db) < 1e-4
+    # without db the weight gradient alone
+    dW2 = torch.zeros((n_out, n_in), device="cuda")
+    plo.wgrad_bf16(dZ, H, dW2)
+    torch.cuda.synchronize()
+    assert rel_err(dW2, ref - 0.5) < 1e-4
