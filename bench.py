@@ -65,6 +65,28 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of every rank's value (the job's time is its slowest
+    rank's); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, rays_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job Mrays/s: every rank renders its own rays_per_rank per step
+    (weak scaling), over the slowest rank's time."""
+    return world * rays_per_rank * steps / seconds / 1e6
+
+
+def shard_seed(rank: int) -> int:
+    """Seed of rank's rays: each rank renders a shard of its own."""
+    return 11 + rank
+
+
 def workload(depth: int, n_rays: int, seed: int):
     import plogen
     rec = plogen.LUMINAIRE_D10.with_(depth=depth)
@@ -368,7 +390,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return 0
     import oracle
-    rec, tree, rays, gen_s = workload(args.depth, args.rays, seed=11)
+    rec, tree, rays, gen_s = workload(args.depth, args.rays, seed=shard_seed(0))
     cores = len(os.sched_getaffinity(0))
     per_step = min(args.cpu_sample // 4 if args.cpu_sample >= 4 else 1, len(rays))
     for w in range(args.warmup):
@@ -413,7 +435,7 @@ def main():
     K, W = args.steps, args.warmup
     assert W >= 3, "at least 3 warm-up steps"
 
-    rec, tree, rays_np, gen_s = workload(args.depth, args.rays, seed=11 + rank)
+    rec, tree, rays_np, gen_s = workload(args.depth, args.rays, seed=shard_seed(rank))
     n = len(rays_np)
     stream = torch.cuda.current_stream()
     t0 = time.time()
@@ -446,10 +468,7 @@ def main():
         total = start.elapsed_time(end)
         per_launch = [a.elapsed_time(b) for a, b in evs]
         tr.check()
-        if dist is not None:
-            tt = torch.tensor([total], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            total = float(tt.item())
+        total = max_over_ranks(total, dist, "cuda")
         return total, sum(per_launch) / len(per_launch)
 
     sampler = ClockSampler(torch.cuda.current_device())
@@ -472,12 +491,8 @@ def main():
         for _ in range(K):
             plo.render_host(trees["fp32"], rays_h, params, rgb=rgb_h, T=T_h)
         barrier()
-        e2e_s = time.perf_counter() - t1
-        if dist is not None:
-            tt = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
-        e2e = {"value": world * n * K / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": n * 24,
+        e2e_s = max_over_ranks(time.perf_counter() - t1, dist, "cuda")
+        e2e = {"value": job_rate(world, n, K, e2e_s), "unit": UNIT, "h2d_bytes_per_step": n * 24,
                "d2h_bytes_per_step": n * 16, "ms_per_step": e2e_s / K * 1e3}
     batch = None
     if not args.no_batch:
@@ -525,7 +540,7 @@ def main():
     bytes_ray["bf16"] = bytes_ray["fp16"]
     lines = {}
     for name, (total, per_launch) in res.items():
-        mrays = world * n * K / (total / 1e3) / 1e6
+        mrays = job_rate(world, n, K, total / 1e3)
         ach = bytes_ray[name] * n / (per_launch / 1e3) / 1e9
         traffic = ncu_traffic(name)
         lines[name] = {"value": mrays, "ms_per_step": total / K, "kernel_ms": per_launch,
