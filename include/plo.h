@@ -393,15 +393,19 @@ int64_t plo_mlp_step(const plo_mlp* mlp);
 /* The tensor-core building blocks (async), exposed for testing.
  * plo_gemm_bf16: C[M][N] = A[M][K] B[N][K]^T, A and B bf16 row-major,
  *   (N, K) in {(256, 64), (256, 256), (64, 256)}; epilogue 0: bf16
- *   ReLU(C + bias), 1: fp32 C + bias, 2: bf16 C * (mask > 0) with mask bf16
- *   [M][N]; d_out row-major [M][N].
+ *   ReLU(C + bias), and if d_bits is not NULL which outputs are > 0 as bits
+ *   (uint32 [M][N / 32], bit j of word c for column 32 c + j); 1: fp32
+ *   C + bias; 2: bf16 C * (mask > 0) with mask bf16 [M][N]; 3: bf16 C with
+ *   the columns whose bit in d_bits is clear set to 0; d_out row-major
+ *   [M][N].
  * plo_wgrad_bf16: dW[n_out][n_in] += dZ^T H over M rows (dZ bf16 [M][n_out],
  *   H bf16 [M][n_in], n_out, n_in in {64, 256}, M a multiple of 64); if
  *   d_db (fp32 [n_out]) is not NULL, also d_db[o] += sum_m dZ[m][o], the
  *   bias gradient, from the same pass over dZ.
  * d_err: device word, bit 1 set if a pipeline wait gave up. */
 plo_status plo_gemm_bf16(const void* d_A, const void* d_B, int32_t M, int32_t N, int32_t K, int32_t epilogue,
-                         const float* d_bias, const void* d_mask, void* d_out, unsigned int* d_err, void* stream);
+                         const float* d_bias, const void* d_mask, uint32_t* d_bits, void* d_out, unsigned int* d_err,
+                         void* stream);
 plo_status plo_wgrad_bf16(const void* d_dZ, int32_t n_out, const void* d_H, int32_t n_in, int32_t M, float* d_dW,
                           float* d_db, unsigned int* d_err, void* stream);
 

@@ -304,7 +304,7 @@ def _load_mlp_sigs(lib):
         "plo_mlp_train_step": (I32, [P, P, P, P, I32, I32, P, P, P]),
         "plo_mlp_check": (I32, [P, P]),
         "plo_mlp_step": (I64, [P]),
-        "plo_gemm_bf16": (I32, [P, P, I32, I32, I32, I32, P, P, P, P, P]),
+        "plo_gemm_bf16": (I32, [P, P, I32, I32, I32, I32, P, P, P, P, P, P]),
         "plo_wgrad_bf16": (I32, [P, I32, P, I32, I32, P, P, P, P]),
         "plo_distill": (I32, [P, I32, I32, ctypes.c_float, I32, P, P]),
     }
@@ -411,16 +411,17 @@ class Mlp:
             pass
 
 
-def gemm_bf16(A, B, epilogue: int, bias=None, mask=None, out=None, err=None, stream=None):
-    """plo_gemm_bf16 on CUDA tensors (A [M][K], B [N][K] bf16)."""
+def gemm_bf16(A, B, epilogue: int, bias=None, mask=None, out=None, err=None, bits=None, stream=None):
+    """plo_gemm_bf16 on CUDA tensors (A [M][K], B [N][K] bf16); bits: int32
+    [M][N / 32], written by epilogue 0 and read by epilogue 3."""
     import torch
     M, K = A.shape
     N = B.shape[0]
     if out is None:
         out = torch.empty((M, N), device=A.device, dtype=torch.float32 if epilogue == 1 else torch.bfloat16)
     err = err if err is not None else torch.zeros(1, device=A.device, dtype=torch.int32)
-    _check(mlp_lib().plo_gemm_bf16(_ptr(A), _ptr(B), M, N, K, epilogue, _ptr(bias), _ptr(mask), _ptr(out), _ptr(err),
-                                   _stream(stream)))
+    _check(mlp_lib().plo_gemm_bf16(_ptr(A), _ptr(B), M, N, K, epilogue, _ptr(bias), _ptr(mask), _ptr(bits), _ptr(out),
+                                   _ptr(err), _stream(stream)))
     return out, err
 
 

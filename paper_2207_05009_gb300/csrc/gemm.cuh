@@ -36,7 +36,7 @@ constexpr int BK = 64;  // one 128-byte swizzle row of bf16
 constexpr int STAGES = 4;
 constexpr int A_STAGE_BYTES = BM * BK * 2;  // 16 KB
 
-enum Epi : int { EPI_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK_BF16 = 2, EPI_SPLIT = 3 };
+enum Epi : int { EPI_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK_BF16 = 2, EPI_SPLIT = 3, EPI_MASKBITS_BF16 = 4 };
 
 struct EpiArgs {
     const float* bias;            // [N] (EPI_RELU_BF16, EPI_BIAS_F32, EPI_SPLIT)
@@ -50,6 +50,10 @@ struct EpiArgs {
     const float* col0_add;        // EPI_BIAS_F32: added to column 0 of each row (nullable)
     int ld_col0;                  // row stride of col0_add
     int tma_out;                  // bf16 outputs leave through the output tensor map (boxes of 32 x 32)
+    uint32_t* bits_out;           // EPI_RELU_BF16 / EPI_SPLIT: [M][ldb] words, bit j of word c set iff
+                                  // bf16 output column 32c + j is > 0 (nullable)
+    const uint32_t* bits;         // EPI_MASKBITS_BF16: the mask as such words, [M][ldb]
+    int ldb;                      // words per row of bits_out / bits
     unsigned int* err;            // device error word (bit 1: GEMM wait timeout)
     uint32_t wait_limit;          // polls per barrier wait (0: sm100::WAIT_LIMIT)
     int debug_skip_loads;         // test hook: the producer issues no loads, so the waits run out
@@ -90,7 +94,8 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t ph, Ctl* c
 }
 
 template <int N>
-// mk: the chunk's 32 mask values (EPI_MASK_BF16), loaded ahead by the caller;
+// mk: the chunk's 32 mask values (EPI_MASK_BF16), or its mask word in mk[0].x
+// (EPI_MASKBITS_BF16), loaded ahead by the caller;
 // stage: where the 32 bf16 results go instead of global memory (nullable)
 __device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int row, int M, int col, const float* v,
                                                const uint4* mk, uint4* stage) {
@@ -110,10 +115,24 @@ __device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int r
     }
     uint32_t packed[16];
     if (epi == EPI_RELU_BF16 || epi == EPI_SPLIT) {
+        uint32_t pos = 0u;  // bit j: bf16 output j is > 0 (nonzero, sign clear)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             float a = fmaxf(v[2 * j] + __ldg(ep.bias + col + 2 * j), 0.0f);
             float b = fmaxf(v[2 * j + 1] + __ldg(ep.bias + col + 2 * j + 1), 0.0f);
+            __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            packed[j] = *reinterpret_cast<uint32_t*>(&h);
+            const uint32_t lo = packed[j] & 0xFFFFu, hi = packed[j] >> 16;
+            pos |= (uint32_t)(lo != 0u && !(lo & 0x8000u)) << (2 * j);
+            pos |= (uint32_t)(hi != 0u && !(hi & 0x8000u)) << (2 * j + 1);
+        }
+        if (ep.bits_out) ep.bits_out[(size_t)row * ep.ldb + col / 32] = pos;
+    } else if (epi == EPI_MASKBITS_BF16) {
+        const uint32_t mw = mk[0].x;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float a = ((mw >> (2 * j)) & 1u) ? v[2 * j] : 0.0f;
+            float b = ((mw >> (2 * j + 1)) & 1u) ? v[2 * j + 1] : 0.0f;
             __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
             packed[j] = *reinterpret_cast<uint32_t*>(&h);
         }
@@ -263,10 +282,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             // the mask is read one chunk ahead, so its latency overlaps the
             // accumulator wait and the previous chunk's work
             const bool masked = epi == EPI_MASK_BF16 && row < M;
+            const bool bitmask = epi == EPI_MASKBITS_BF16 && row < M;
             const uint4* mrow = masked ? reinterpret_cast<const uint4*>(ep.mask + (size_t)row * ep.ldm) : nullptr;
+            const uint32_t* brow = bitmask ? ep.bits + (size_t)row * ep.ldb : nullptr;
             uint4 mk[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) mk[j] = masked ? __ldg(mrow + j) : make_uint4(0u, 0u, 0u, 0u);
+            if (bitmask) mk[0].x = __ldg(brow);
             if (!wait_or_abort(&ctl->tfull[acc], aph, ctl, ep.err)) break;
             sm100::tc_fence_after();
 #pragma unroll 1
@@ -277,6 +299,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const bool more = masked && c + 1 < N / 32;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) nx[j] = more ? __ldg(mrow + 4 * (c + 1) + j) : make_uint4(0u, 0u, 0u, 0u);
+                if (bitmask && c + 1 < N / 32) nx[0].x = __ldg(brow + c + 1);
                 const bool tma = ep.tma_out && epi != EPI_BIAS_F32 && !(epi == EPI_SPLIT && c * 32 >= ep.split);
                 if (tma) {
                     // stage the warp's 32 x 32 box, then one thread stores it;

@@ -5,7 +5,7 @@
 //   8 x 256 ReLU layers + SH head   k_gemm      (tcgen05, gemm.cuh)
 //   quadrature, loss, d loss/d raw  k_quad      (Eq. 3-6, Eq. 7-9)
 //   weight and bias gradients       k_wgrad (bias: an extra MMA against ones)
-//   data gradients through ReLU     k_gemm (mask epilogue)
+//   data gradients through ReLU     k_gemm (mask epilogue; the forward keeps the masks as bits)
 //   Adam + exponential lr decay     k_adam      (Sec. 4.4)
 //
 // Activations are bf16 [samples][features] row-major; weights are kept as
@@ -717,6 +717,7 @@ struct plo_mlp {
     int64_t cap = 0;
     int cap_rays = 0;
     __nv_bfloat16* H[MAX_LAYERS] = {};  // H[0] = X [cap][64], H[1..8] [cap][256], H[9] [cap][128] (paper)
+    uint32_t* HB[MAX_LAYERS] = {};      // H[l] > 0 as bits, [cap][in_pad[l] / 32] words (l >= 1; training)
     float* raw = nullptr;               // [cap][64]
     float* sraw = nullptr;              // [cap][64] fp32 half of the paper combined layer (column 0: sigma)
     __nv_bfloat16* dO = nullptr;        // [cap][64]
@@ -735,6 +736,7 @@ namespace {
 
 void free_workspace(plo_mlp* m) {
     for (int l = 0; l < MAX_LAYERS; ++l) cudaFree(m->H[l]), m->H[l] = nullptr;
+    for (int l = 0; l < MAX_LAYERS; ++l) cudaFree(m->HB[l]), m->HB[l] = nullptr;
     cudaFree(m->raw);
     cudaFree(m->sraw);
     cudaFree(m->dO);
@@ -763,6 +765,8 @@ plo_status ensure_workspace(plo_mlp* m, int64_t samples, int rays) {
     alloc((void**)&m->H[0], (size_t)samples * PE_PAD * 2);
     for (int l = 1; l <= DEPTH; ++l) alloc((void**)&m->H[l], (size_t)samples * WIDTH * 2);
     if (paper) alloc((void**)&m->H[DEPTH + 1], (size_t)samples * FEAT * 2);
+    for (int l = 1; l <= DEPTH; ++l) alloc((void**)&m->HB[l], (size_t)samples * (WIDTH / 32) * 4);
+    if (paper) alloc((void**)&m->HB[DEPTH + 1], (size_t)samples * (FEAT / 32) * 4);
     alloc((void**)&m->raw, (size_t)samples * OUT_PAD * 4);
     if (paper) alloc((void**)&m->sraw, (size_t)samples * OUT_PAD * 4);
     alloc((void**)&m->dO, (size_t)samples * OUT_PAD * 2);
@@ -901,8 +905,10 @@ void padded_to_canonical(const plo_mlp* m, const std::vector<float>& p, float* c
 }
 
 // Forward of the MLP over H[0] (already encoded) for `samples` rows; the head
-// writes fp32 raw outputs.
-plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s) {
+// writes fp32 raw outputs.  For training (`masks`), each ReLU layer also
+// writes which of its outputs are positive as bits (HB), the backward pass's
+// ReLU masks at 1/16 of the bytes of the activations.
+plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s, bool masks = false) {
     gemm::EpiArgs ep{};
     ep.err = m->d_err;
     cudaError_t e = cudaSuccess;
@@ -910,6 +916,8 @@ plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s) {
         ep.bias = bias_ptr(m, m->master, l);
         ep.out_bf16 = m->H[l + 1];
         ep.ldo = WIDTH;
+        ep.bits_out = masks ? m->HB[l + 1] : nullptr;
+        ep.ldb = WIDTH / 32;
         if (l == 0)
             e = launch_gemm<WIDTH, PE_PAD>(m->mapA_H[0], m->mapW[0], &m->mapO_H[1], ep, gemm::EPI_RELU_BF16, (int)samples, m->sms, s);
         else
@@ -927,6 +935,8 @@ plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s) {
         ep.bias = bias_ptr(m, m->master, DEPTH);
         ep.out_bf16 = m->H[DEPTH + 1];
         ep.ldo = FEAT;
+        ep.bits_out = masks ? m->HB[DEPTH + 1] : nullptr;
+        ep.ldb = FEAT / 32;
         ep.split = FEAT;
         ep.out_f32 = m->sraw;
         ep.ldo2 = OUT_PAD;
@@ -984,10 +994,10 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
                                 m->d_err, s, bias_ptr(m, m->grad, DEPTH));
         ep.out_bf16 = m->dZ[0];
         ep.ldo = WIDTH;
-        ep.mask = m->H[DEPTH];
-        ep.ldm = WIDTH;
+        ep.bits = m->HB[DEPTH];
+        ep.ldb = WIDTH / 32;
         if (e == cudaSuccess)
-            e = launch_gemm<WIDTH, OUT_PAD>(m->mapA_dO, m->mapWT[DEPTH], &m->mapO_dZ[0], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+            e = launch_gemm<WIDTH, OUT_PAD>(m->mapA_dO, m->mapWT[DEPTH], &m->mapO_dZ[0], ep, gemm::EPI_MASKBITS_BF16, (int)M, m->sms, s);
     } else {
         const int SH = DEPTH + 1;
         // SH layer: dW = dO^T feat, db = column sums; d feat -> dZc[:, 0:128]
@@ -995,20 +1005,20 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
                                m->d_err, s, bias_ptr(m, m->grad, SH));
         ep.out_bf16 = m->dZc;
         ep.ldo = COMB_PAD;
-        ep.mask = m->H[SH];
-        ep.ldm = FEAT;
+        ep.bits = m->HB[SH];
+        ep.ldb = FEAT / 32;
         if (e == cudaSuccess)
-            e = launch_gemm<FEAT, OUT_PAD>(m->mapA_dO, m->mapWT[SH], &m->mapO_dZc, ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+            e = launch_gemm<FEAT, OUT_PAD>(m->mapA_dO, m->mapWT[SH], &m->mapO_dZc, ep, gemm::EPI_MASKBITS_BF16, (int)M, m->sms, s);
         // combined layer [features | sigma]: dW = dZc^T h8; d h8 -> dZ[0]
         if (e == cudaSuccess)
             e = launch_wgrad<WIDTH>(m->mapW_dZc, m->mapW_H[DEPTH], m->grad + m->geom.off[DEPTH], COMB_PAD, (int)M,
                                     m->sms, m->d_err, s, bias_ptr(m, m->grad, DEPTH));
         ep.out_bf16 = m->dZ[0];
         ep.ldo = WIDTH;
-        ep.mask = m->H[DEPTH];
-        ep.ldm = WIDTH;
+        ep.bits = m->HB[DEPTH];
+        ep.ldb = WIDTH / 32;
         if (e == cudaSuccess)
-            e = launch_gemm<WIDTH, COMB_PAD>(m->mapA_dZc, m->mapWT[DEPTH], &m->mapO_dZ[0], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+            e = launch_gemm<WIDTH, COMB_PAD>(m->mapA_dZc, m->mapWT[DEPTH], &m->mapO_dZ[0], ep, gemm::EPI_MASKBITS_BF16, (int)M, m->sms, s);
     }
     // hidden layers l = 8 .. 2 (index l-1 = 7 .. 1), then layer 1; each
     // weight-gradient launch also sums the layer's bias gradient
@@ -1023,8 +1033,8 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
                                     m->d_err, s, bias_ptr(m, m->grad, l));
         if (l == 0 || e != cudaSuccess) break;
         ep.out_bf16 = m->dZ[cur ^ 1];
-        ep.mask = m->H[l];
-        e = launch_gemm<WIDTH, WIDTH>(m->mapA_dZ[cur], m->mapWT[l], &m->mapO_dZ[cur ^ 1], ep, gemm::EPI_MASK_BF16, (int)M, m->sms, s);
+        ep.bits = m->HB[l];
+        e = launch_gemm<WIDTH, WIDTH>(m->mapA_dZ[cur], m->mapWT[l], &m->mapO_dZ[cur ^ 1], ep, gemm::EPI_MASKBITS_BF16, (int)M, m->sms, s);
         cur ^= 1;
     }
     if (e != cudaSuccess) return cuda_error(e, "MLP backward launch");
@@ -1244,7 +1254,7 @@ extern "C" plo_status plo_mlp_train_step(plo_mlp* m, const float* d_rays, const 
     if (e != cudaSuccess) return cuda_error(e, "gradient clear");
     k_pe<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(d_rays, n_rays, n_samples, d_jitter, D.seed, (uint64_t)m->step,
                                                      m->H[0], m->delta, nullptr);
-    st = forward_layers(m, M, s);
+    st = forward_layers(m, M, s, true);
     if (st != PLO_OK) return st;
     e = launch_quad(m, n_samples, d_rays, d_rgb_gt, d_alpha_gt, n_rays, D.loss, nullptr, s);
     if (e != cudaSuccess) return cuda_error(e, "quadrature kernel launch");
@@ -1295,7 +1305,7 @@ extern "C" plo_status plo_mlp_train_step_hier(plo_mlp* coarse, plo_mlp* fine, co
     k_pe<<<(unsigned)((Mc + 255) / 256), 256, 0, s>>>(d_rays, n_rays, n_coarse, d_jitter, coarse->desc.seed,
                                                       (uint64_t)coarse->step, coarse->H[0], coarse->delta,
                                                       coarse->tsamp);
-    st = forward_layers(coarse, Mc, s);
+    st = forward_layers(coarse, Mc, s, true);
     if (st != PLO_OK) return st;
     const int coarse_loss = D.loss == PLO_LOSS_PAPER ? PLO_LOSS_REG : D.loss;
     e = launch_quad(coarse, n_coarse, d_rays, d_rgb_gt, d_alpha_gt, n_rays, coarse_loss, coarse->wts, s);
@@ -1306,7 +1316,7 @@ extern "C" plo_status plo_mlp_train_step_hier(plo_mlp* coarse, plo_mlp* fine, co
         (uint64_t)fine->step, fine->H[0], fine->delta, nullptr);
     st = backward_update(coarse, Mc, s);
     if (st != PLO_OK) return st;
-    st = forward_layers(fine, Mf, s);
+    st = forward_layers(fine, Mf, s, true);
     if (st != PLO_OK) return st;
     e = launch_quad(fine, N, d_rays, d_rgb_gt, d_alpha_gt, n_rays, D.loss, nullptr, s);
     if (e != cudaSuccess) return cuda_error(e, "quadrature kernel launch");
@@ -1352,15 +1362,16 @@ extern "C" int64_t plo_mlp_step(const plo_mlp* m) { return m ? m->step : -1; }
 
 // ---------------------------------------------------------------- raw GEMM entry points
 extern "C" plo_status plo_gemm_bf16(const void* d_A, const void* d_B, int32_t M, int32_t N, int32_t K,
-                                    int32_t epilogue, const float* d_bias, const void* d_mask, void* d_out,
-                                    unsigned int* d_err, void* stream) {
+                                    int32_t epilogue, const float* d_bias, const void* d_mask, uint32_t* d_bits,
+                                    void* d_out, unsigned int* d_err, void* stream) {
     if (!d_A || !d_B || !d_out || !d_err) return set_error(PLO_ERR_INVALID_ARG, "A, B, out or err is NULL");
     if (M <= 0) return set_error(PLO_ERR_INVALID_ARG, "M must be > 0");
     const bool shape_ok = (N == 256 && (K == 64 || K == 256)) || (N == 64 && K == 256);
     if (!shape_ok) return set_error(PLO_ERR_UNSUPPORTED, "(N, K) must be (256, 64), (256, 256) or (64, 256)");
-    if (epilogue < 0 || epilogue > 2) return set_error(PLO_ERR_INVALID_ARG, "unknown epilogue");
-    if ((epilogue != gemm::EPI_MASK_BF16 && !d_bias) || (epilogue == gemm::EPI_MASK_BF16 && !d_mask))
-        return set_error(PLO_ERR_INVALID_ARG, "bias (epilogues 0, 1) or mask (epilogue 2) is NULL");
+    if (epilogue < 0 || epilogue > 3) return set_error(PLO_ERR_INVALID_ARG, "unknown epilogue");
+    if ((epilogue <= 1 && !d_bias) || (epilogue == 2 && !d_mask) || (epilogue == 3 && !d_bits))
+        return set_error(PLO_ERR_INVALID_ARG, "bias (epilogues 0, 1), mask (2) or bits (3) is NULL");
+    const int epi = epilogue == 3 ? (int)gemm::EPI_MASKBITS_BF16 : epilogue;
     CUtensorMap mA, mB, mO;
     plo_status st = make_map(&mA, d_A, (uint64_t)M, (uint64_t)K, 128);
     if (st == PLO_OK) st = make_map(&mB, d_B, (uint64_t)N, (uint64_t)K, (uint32_t)N);
@@ -1373,14 +1384,17 @@ extern "C" plo_status plo_gemm_bf16(const void* d_A, const void* d_B, int32_t M,
     ep.ldo = N;
     ep.mask = static_cast<const __nv_bfloat16*>(d_mask);
     ep.ldm = N;
+    ep.bits_out = epilogue == 0 ? d_bits : nullptr;
+    ep.bits = d_bits;
+    ep.ldb = N / 32;
     ep.err = d_err;
     const int sms = sm_count_of_current();
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     const CUtensorMap* O = epilogue == gemm::EPI_BIAS_F32 ? nullptr : &mO;
-    if (N == 256 && K == 64) e = launch_gemm<256, 64>(mA, mB, O, ep, epilogue, M, sms, s);
-    else if (N == 256) e = launch_gemm<256, 256>(mA, mB, O, ep, epilogue, M, sms, s);
-    else e = launch_gemm<64, 256>(mA, mB, O, ep, epilogue, M, sms, s);
+    if (N == 256 && K == 64) e = launch_gemm<256, 64>(mA, mB, O, ep, epi, M, sms, s);
+    else if (N == 256) e = launch_gemm<256, 256>(mA, mB, O, ep, epi, M, sms, s);
+    else e = launch_gemm<64, 256>(mA, mB, O, ep, epi, M, sms, s);
     return e == cudaSuccess ? PLO_OK : cuda_error(e, "GEMM launch");
 }
 

@@ -41,6 +41,21 @@ def test_gemm_epilogues(torch_cuda, N, K, M):
     torch.cuda.synchronize()
     assert int(err.item()) == 0
     assert (out.float() - r.float()).abs().max() <= 2 ** -7 * r.float().abs().max() + 1e-6
+    # ReLU with its positive outputs as bits, then the same mask applied from
+    # those bits: bit-identical to the bf16-mask epilogue with the ReLU output
+    bits = torch.full((M, N // 32), -1, device="cuda", dtype=torch.int32)
+    h, err = plo.gemm_bf16(A, B, 0, bias=bias, bits=bits)
+    h2, _ = plo.gemm_bf16(A, B, 0, bias=bias)
+    torch.cuda.synchronize()
+    assert torch.equal(h, h2)
+    want = (h.float() > 0).reshape(M, N // 32, 32).to(torch.int64)
+    want = (want << torch.arange(32, device="cuda", dtype=torch.int64)).sum(-1)
+    assert torch.equal(bits.to(torch.int64) & 0xFFFFFFFF, want)
+    out_b, err = plo.gemm_bf16(A, B, 3, bits=bits)
+    out_m, _ = plo.gemm_bf16(A, B, 2, mask=h)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    assert torch.equal(out_b, out_m)
 
 
 @pytest.mark.parametrize("n_out,n_in,M", [(256, 256, 64), (256, 256, 524288), (64, 256, 4096), (256, 64, 8192)])
