@@ -374,8 +374,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     Ctl* ctl = reinterpret_cast<Ctl*>(smem + STAGES * STAGE);
     uint8_t* ones = smem + STAGES * STAGE + 1024;  // 1 KB aligned
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int out_base = blockIdx.y * BM;
-    const int m_beg = blockIdx.x * chunk;
+    // blockIdx.x: output tile, so that the CTAs of one sample chunk run side
+    // by side and the second read of their shared H tiles hits L2
+    const int out_base = blockIdx.x * BM;
+    const int m_beg = blockIdx.y * chunk;
     const int m_end = min(m_beg + chunk, M);
     const int n_kb = m_end > m_beg ? (m_end - m_beg + 63) / 64 : 0;
 

@@ -142,7 +142,7 @@ cudaError_t launch_wgrad(const CUtensorMap& dZ, const CUtensorMap& H, float* dW,
     if (n_chunks < 1) n_chunks = 1;
     const int chunk = ((blocks64 + n_chunks - 1) / n_chunks) * 64;
     n_chunks = (M + chunk - 1) / chunk;
-    dim3 grid(n_chunks, out_tiles);
+    dim3 grid(out_tiles, n_chunks);
     gemm::k_wgrad<NIN><<<grid, gemm::THREADS, smem, s>>>(dZ, H, dW, n_out, M, chunk, err, db);
     return cudaGetLastError();
 }
@@ -923,6 +923,7 @@ plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s, bool mask
         else
             e = launch_gemm<WIDTH, WIDTH>(m->mapA_H[l], m->mapW[l], &m->mapO_H[l + 1], ep, gemm::EPI_RELU_BF16, (int)samples, m->sms, s);
     }
+    ep.bits_out = nullptr;  // no ReLU after the head
     if (e == cudaSuccess && m->arch == PLO_ARCH_LINEAR_HEAD) {
         ep.bias = bias_ptr(m, m->master, DEPTH);
         ep.out_f32 = m->raw;
