@@ -74,7 +74,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if force or jobs or _stale(LIB, objs):
         fd, tmp = tempfile.mkstemp(suffix=".so", dir=HERE)
         os.close(fd)
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             os.unlink(tmp)

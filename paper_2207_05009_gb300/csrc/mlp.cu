@@ -338,7 +338,9 @@ __global__ void k_keep(const float* raw, int64_t n, float thresh, uint8_t* flags
 }
 
 // out[i] = mean over the S samples of voxel i: ReLU(sigma_raw), raw SH.
-__global__ void k_average(const float* raw, int64_t nv, int S, int n_out, float* out) {
+// Mean over a voxel's S jittered samples of ReLU(sigma_raw) -> sigma[i] and
+// of each raw SH output -> sh[i][k] (n_out = 1 + 3K outputs per sample).
+__global__ void k_average(const float* raw, int64_t nv, int S, int n_out, float* sigma, float* sh) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nv * n_out) return;
     const int64_t i = idx / n_out;
@@ -348,7 +350,10 @@ __global__ void k_average(const float* raw, int64_t nv, int S, int n_out, float*
         const float v = __ldg(raw + (i * S + s) * OUT_PAD + k);
         acc += k == 0 ? fmaxf(v, 0.0f) : v;
     }
-    out[idx] = acc / (float)S;
+    if (k == 0)
+        sigma[i] = acc / (float)S;
+    else
+        sh[i * (n_out - 1) + (k - 1)] = acc / (float)S;
 }
 
 // Quadrature render of Eq. 3 from the head outputs, the loss of Eq. 7-9 and
@@ -1460,17 +1465,13 @@ extern "C" plo_status plo_distill(plo_mlp* m, int32_t depth, int32_t samples, fl
     plo_status st = ensure_workspace(m, C < 128 ? 128 : C, m->cap_rays);
     if (st != PLO_OK) return st;
     const int n_out = m->n_out;
+    const int K = m->K;
+    // pass 1: sigma at every voxel centre, in chunks of C voxels (Morton
+    // order); the kept voxels' codes are collected in that order
     uint8_t* d_flags = nullptr;
-    unsigned long long* d_codes = nullptr;
-    float* d_avg = nullptr;
-    const int64_t vmax = C / samples > 0 ? C / samples : 1;
     cudaError_t e = (cudaError_t)dev_malloc((void**)&d_flags, (size_t)C);
-    if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_codes, (size_t)vmax * 8);
-    if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_avg, (size_t)vmax * n_out * 4);
     std::vector<uint8_t> flags(C);
     std::vector<unsigned long long> codes;
-    std::vector<float> vals;
-    std::vector<unsigned long long> sub;
     for (int64_t base = 0; e == cudaSuccess && st == PLO_OK && base < total; base += C) {
         const int64_t n = total - base < C ? total - base : C;
         k_pe_centres<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((uint64_t)base, n, depth, m->H[0]);
@@ -1480,54 +1481,70 @@ extern "C" plo_status plo_distill(plo_mlp* m, int32_t depth, int32_t samples, fl
         e = cudaMemcpyAsync(flags.data(), d_flags, (size_t)n, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) break;
-        sub.clear();
         for (int64_t i = 0; i < n; ++i)
-            if (flags[i]) sub.push_back((unsigned long long)(base + i));
-        for (size_t off = 0; off < sub.size() && e == cudaSuccess && st == PLO_OK; off += (size_t)vmax) {
-            const int64_t nv = (int64_t)std::min(sub.size() - off, (size_t)vmax);
-            e = cudaMemcpyAsync(d_codes, sub.data() + off, (size_t)nv * 8, cudaMemcpyHostToDevice, s);
-            if (e != cudaSuccess) break;
-            k_pe_jitter<<<(unsigned)((nv * samples + 255) / 256), 256, 0, s>>>(
-                reinterpret_cast<const uint64_t*>(d_codes), nv, samples, depth, m->desc.seed, m->H[0]);
-            st = forward_layers(m, nv * samples, s);
-            if (st != PLO_OK) break;
-            k_average<<<(unsigned)((nv * n_out + 255) / 256), 256, 0, s>>>(m->raw, nv, samples, n_out, d_avg);
-            const size_t old = vals.size();
-            vals.resize(old + (size_t)nv * n_out);
-            e = cudaMemcpyAsync(vals.data() + old, d_avg, (size_t)nv * n_out * 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        }
-        codes.insert(codes.end(), sub.begin(), sub.end());
+            if (flags[i]) codes.push_back((unsigned long long)(base + i));
     }
     cudaFree(d_flags);
-    cudaFree(d_codes);
-    cudaFree(d_avg);
     if (st != PLO_OK) return st;
     if (e != cudaSuccess) return cuda_error(e, "plo_distill");
+    // pass 2: the mean of `samples` jittered evaluations per kept voxel, all
+    // on the device (sub-chunks of C samples), copied back once
+    const int64_t nl = (int64_t)codes.size();
+    std::vector<float> sigma(nl), sh((size_t)nl * 3 * K);
+    if (nl > 0) {
+        const int64_t vmax = C / samples > 0 ? C / samples : 1;
+        unsigned long long* d_codes = nullptr;
+        float *d_sigma = nullptr, *d_sh = nullptr;
+        e = (cudaError_t)dev_malloc((void**)&d_codes, (size_t)nl * 8);
+        if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_sigma, (size_t)nl * 4);
+        if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_sh, (size_t)nl * 3 * K * 4);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_codes, codes.data(), (size_t)nl * 8, cudaMemcpyHostToDevice, s);
+        for (int64_t off = 0; off < nl && e == cudaSuccess && st == PLO_OK; off += vmax) {
+            const int64_t nv = nl - off < vmax ? nl - off : vmax;
+            k_pe_jitter<<<(unsigned)((nv * samples + 255) / 256), 256, 0, s>>>(
+                reinterpret_cast<const uint64_t*>(d_codes + off), nv, samples, depth, m->desc.seed, m->H[0]);
+            st = forward_layers(m, nv * samples, s);
+            if (st != PLO_OK) break;
+            k_average<<<(unsigned)((nv * n_out + 255) / 256), 256, 0, s>>>(m->raw, nv, samples, n_out, d_sigma + off,
+                                                                           d_sh + off * 3 * K);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && st == PLO_OK)
+            e = cudaMemcpyAsync(sigma.data(), d_sigma, (size_t)nl * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && st == PLO_OK)
+            e = cudaMemcpyAsync(sh.data(), d_sh, (size_t)nl * 3 * K * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(d_codes);
+        cudaFree(d_sigma);
+        cudaFree(d_sh);
+        if (st != PLO_OK) return st;
+        if (e != cudaSuccess) return cuda_error(e, "plo_distill");
+    }
     st = plo_mlp_check(m, stream);
     if (st != PLO_OK) return st;
-    // octree over the kept voxels (Morton-sorted leaves at level `depth`)
-    const int64_t nl = (int64_t)codes.size();
-    const int K = m->K;
-    std::vector<int32_t> child;
-    child.assign(8, -1);
+    // octree over the kept voxels, leaves at level `depth`.  The codes are
+    // sorted, so one pass with the path of the previous leaf creates the
+    // nodes in pre-order: a leaf shares its previous neighbour's nodes down
+    // to the deepest level where their codes agree, and new nodes below.
+    std::vector<int32_t> child(8, -1);
     int32_t n_nodes = 1;
-    std::vector<float> sigma(nl), sh((size_t)nl * 3 * K);
+    int32_t path[MAX_DEPTH + 1] = {0};  // node id per level of the previous leaf's path
     for (int64_t i = 0; i < nl; ++i) {
         const unsigned long long c = codes[i];
-        int32_t node = 0;
-        for (int l = 0; l < depth - 1; ++l) {
-            const int slot = (int)((c >> (3 * (depth - 1 - l))) & 7ull);
-            int32_t& e2 = child[(size_t)node * 8 + slot];
-            if (e2 == -1) {
-                e2 = n_nodes++;
-                child.resize((size_t)n_nodes * 8, -1);
-            }
-            node = child[(size_t)node * 8 + slot];
+        int first_new = 1;  // levels 1 .. depth-1 hold nodes; the root is shared
+        if (i > 0) {
+            const unsigned long long x = c ^ codes[i - 1];
+            const int msb = 63 - __builtin_clzll(x);  // codes are distinct, so x != 0
+            first_new = depth - msb / 3;
         }
-        child[(size_t)node * 8 + (int)(c & 7ull)] = (int32_t)(-i - 2);
-        sigma[i] = vals[(size_t)i * n_out];
-        for (int k = 0; k < 3 * K; ++k) sh[(size_t)i * 3 * K + k] = vals[(size_t)i * n_out + 1 + k];
+        for (int l = first_new; l < depth; ++l) {
+            const int slot = (int)((c >> (3 * (depth - l))) & 7ull);
+            const int32_t node = n_nodes++;
+            child.resize((size_t)n_nodes * 8, -1);
+            child[(size_t)path[l - 1] * 8 + slot] = node;
+            path[l] = node;
+        }
+        child[(size_t)path[depth - 1] * 8 + (int)(c & 7ull)] = (int32_t)(-i - 2);
     }
     plo_tree_desc d{};
     d.depth = depth;

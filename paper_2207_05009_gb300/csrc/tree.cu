@@ -5,9 +5,13 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "plo_internal.h"
@@ -15,6 +19,27 @@
 using namespace plo;
 
 namespace {
+
+// f(begin, end) over [0, n) in contiguous ranges on the host's cores; the
+// per-leaf passes below (checks, emission flags, record packing) touch each
+// leaf's own data only, so the result does not depend on the split.
+template <class F>
+void parallel_ranges(int64_t n, F f) {
+    const int64_t min_per_thread = 1 << 16;
+    int threads = (int)std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), 32);
+    threads = (int)std::min<int64_t>(threads, (n + min_per_thread - 1) / min_per_thread);
+    if (threads <= 1) {
+        f((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    const int64_t per = (n + threads - 1) / threads;
+    for (int t = 0; t < threads; ++t) {
+        const int64_t b = t * per, e = std::min(n, b + per);
+        if (b < e) pool.emplace_back(f, b, e);
+    }
+    for (auto& th : pool) th.join();
+}
 
 plo_status validate(const plo_tree_desc* t) {
     if (!t) return set_error(PLO_ERR_INVALID_ARG, "tree descriptor is NULL");
@@ -71,16 +96,34 @@ plo_status validate(const plo_tree_desc* t) {
         }
     }
     const int K = sh_K(t->sh_degree);
-    for (int64_t i = 0; i < t->n_leaves; ++i) {
-        float s = t->sigma[i];
-        if (!std::isfinite(s) || s < 0.0f)
-            return set_error(PLO_ERR_BAD_TREE, "sigma of leaf " + std::to_string(i) + " is negative or not finite");
-    }
-    for (int64_t i = 0; i < t->n_leaves * 3 * K; ++i) {
-        if (!std::isfinite(t->sh[i]))
-            return set_error(PLO_ERR_BAD_TREE, "SH coefficient of leaf " + std::to_string(i / (3 * K)) +
-                                                   " is not finite");
-    }
+    // the first offending leaf of each kind is reported, whatever the split
+    std::atomic<int64_t> bad_sigma{INT64_MAX}, bad_sh{INT64_MAX};
+    parallel_ranges(t->n_leaves, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; ++i) {
+            const float s = t->sigma[i];
+            if (!std::isfinite(s) || s < 0.0f) {
+                int64_t cur = bad_sigma.load();
+                while (i < cur && !bad_sigma.compare_exchange_weak(cur, i)) {
+                }
+                break;
+            }
+        }
+        for (int64_t i = b * 3 * K; i < e * 3 * K; ++i) {
+            if (!std::isfinite(t->sh[i])) {
+                const int64_t leaf = i / (3 * K);
+                int64_t cur = bad_sh.load();
+                while (leaf < cur && !bad_sh.compare_exchange_weak(cur, leaf)) {
+                }
+                break;
+            }
+        }
+    });
+    if (bad_sigma.load() != INT64_MAX)
+        return set_error(PLO_ERR_BAD_TREE,
+                         "sigma of leaf " + std::to_string(bad_sigma.load()) + " is negative or not finite");
+    if (bad_sh.load() != INT64_MAX)
+        return set_error(PLO_ERR_BAD_TREE, "SH coefficient of leaf " + std::to_string(bad_sh.load()) +
+                                               " is not finite");
     return PLO_OK;
 }
 
@@ -179,6 +222,15 @@ extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precisio
 
     // SH records in depth-first (Morton) order of the leaves.
     std::vector<uint32_t> rec_of_leaf(desc->n_leaves > 0 ? desc->n_leaves : 1, NO_SH_RECORD);
+    std::vector<uint8_t> emits_of_leaf(desc->n_leaves > 0 ? desc->n_leaves : 1, 0);
+    parallel_ranges(desc->n_leaves, [&](int64_t b, int64_t e) {
+        for (int64_t leaf = b; leaf < e; ++leaf) {
+            const float* c = desc->sh + leaf * 3 * K;
+            bool emits = false;
+            for (int k = 0; k < 3 * K; ++k) emits |= c[k] != 0.0f;
+            emits_of_leaf[leaf] = emits ? 1 : 0;
+        }
+    });
     int64_t n_sh = 0;
     {
         std::vector<int32_t> st{0};
@@ -194,10 +246,7 @@ extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precisio
                 if (e <= -2) {
                     int64_t leaf = -(int64_t)e - 2;
                     if (rec_of_leaf[leaf] != NO_SH_RECORD) continue;  // root leaf repeated in 8 slots
-                    const float* c = desc->sh + leaf * 3 * K;
-                    bool emits = false;
-                    for (int k = 0; k < 3 * K; ++k) emits |= c[k] != 0.0f;
-                    if (emits) rec_of_leaf[leaf] = (uint32_t)n_sh++;
+                    if (emits_of_leaf[leaf]) rec_of_leaf[leaf] = (uint32_t)n_sh++;
                 }
             }
         }
@@ -208,43 +257,49 @@ extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precisio
     const int stride = sh_stride_bytes(K, precision);
     std::vector<uint32_t> nodes;
     std::vector<int32_t> leaf_ids;
-    std::vector<uint8_t> sh;
+    // every record is written whole (coefficients and zero padding) below,
+    // so the buffer is not cleared first
+    std::unique_ptr<uint8_t[]> sh;
     try {
         nodes.assign(n_packed * 16, 0);
         leaf_ids.assign(n_packed * 8, -1);
-        sh.assign((size_t)(n_sh > 0 ? n_sh : 1) * stride, 0);
+        sh.reset(new uint8_t[(size_t)(n_sh > 0 ? n_sh : 1) * stride]);
+        if (n_sh == 0) std::memset(sh.get(), 0, (size_t)stride);
     } catch (const std::bad_alloc&) {
         return set_error(PLO_ERR_OOM, "host allocation for the packed tree failed");
     }
     std::vector<int8_t> scale_exp(desc->n_leaves > 0 ? desc->n_leaves : 1, 0);
-    for (int64_t leaf = 0; leaf < desc->n_leaves; ++leaf) {
-        uint32_t r = rec_of_leaf[leaf];
-        if (r == NO_SH_RECORD) continue;
-        const float* c = desc->sh + leaf * 3 * K;
-        uint8_t* dst = sh.data() + (size_t)r * stride;
-        if (precision == PLO_PREC_FP32) {
-            std::memcpy(dst, c, sizeof(float) * 3 * K);
-            continue;
+    parallel_ranges(desc->n_leaves, [&](int64_t lb, int64_t le) {
+        for (int64_t leaf = lb; leaf < le; ++leaf) {
+            uint32_t r = rec_of_leaf[leaf];
+            if (r == NO_SH_RECORD) continue;
+            const float* c = desc->sh + leaf * 3 * K;
+            uint8_t* dst = sh.get() + (size_t)r * stride;
+            if (precision == PLO_PREC_FP32) {
+                std::memcpy(dst, c, sizeof(float) * 3 * K);
+                std::memset(dst + sizeof(float) * 3 * K, 0, (size_t)stride - sizeof(float) * 3 * K);
+                continue;
+            }
+            float m = 0.0f;
+            for (int k = 0; k < 3 * K; ++k) m = std::fmax(m, std::fabs(c[k]));
+            int e;
+            std::frexp(m, &e);  // m = f * 2^e, f in [0.5, 1)
+            // FP16: map the largest coefficient into [2^14, 2^15) so that the
+            // leaf's smaller coefficients keep binary16's normal range (down to
+            // 2^-29 of the largest); BF16 has FP32's range and uses [0.5, 1).
+            if (precision == PLO_PREC_FP16) e -= 15;
+            if (e < -126) e = -126;
+            if (e > 127) e = 127;
+            float inv = std::ldexp(1.0f, -e);
+            uint16_t* h = reinterpret_cast<uint16_t*>(dst);
+            for (int k = 0; k < 3 * K; ++k) {
+                float v = c[k] * inv;
+                h[k] = precision == PLO_PREC_FP16 ? half_bits(v) : bf16_bits(v);
+            }
+            std::memset(dst + 2 * 3 * K, 0, (size_t)stride - 2 * 3 * K);
+            scale_exp[leaf] = (int8_t)e;
         }
-        float m = 0.0f;
-        for (int k = 0; k < 3 * K; ++k) m = std::fmax(m, std::fabs(c[k]));
-        int e;
-        std::frexp(m, &e);  // m = f * 2^e, f in [0.5, 1)
-        // FP16: map the largest coefficient into [2^14, 2^15) so that the
-        // leaf's smaller coefficients keep binary16's normal range (down to
-        // 2^-29 of the largest); BF16 has FP32's range and uses [0.5, 1).
-        if (precision == PLO_PREC_FP16) e -= 15;
-        if (e < -126) e = -126;
-        if (e > 127) e = 127;
-        scale_exp[leaf] = (int8_t)0;  // placeholder, stored below
-        float inv = std::ldexp(1.0f, -e);
-        uint16_t* h = reinterpret_cast<uint16_t*>(dst);
-        for (int k = 0; k < 3 * K; ++k) {
-            float v = c[k] * inv;
-            h[k] = precision == PLO_PREC_FP16 ? half_bits(v) : bf16_bits(v);
-        }
-        scale_exp[leaf] = (int8_t)e;
-    }
+    });
     for (int64_t i = 0; i < n_packed; ++i) {
         int32_t v = order[i];
         for (int s = 0; s < 8; ++s) {
@@ -309,7 +364,7 @@ extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precisio
     if ((err = cudaMemcpy(t->d_nodes, nodes.data(), (size_t)t->node_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (err = cudaMemcpy(t->d_leaf_ids, leaf_ids.data(), (size_t)n_packed * 8 * sizeof(int32_t),
                           cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (err = cudaMemcpy(t->d_sh, sh.data(), sh_alloc, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (err = cudaMemcpy(t->d_sh, sh.get(), sh_alloc, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (err = cudaMemset(t->d_flags, 0, 256)) != cudaSuccess) {
         plo_tree_free(t);
         return cuda_error(err, "upload of the packed tree");
