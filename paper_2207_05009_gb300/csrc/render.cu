@@ -5,10 +5,10 @@
 // One thread renders one ray at a time.  The grid is persistent: warps take
 // rays from a shared counter (64 at a time; small launches give each warp a
 // contiguous chunk) and a lane that finishes its ray takes the next one, so
-// a warp does not idle behind its longest ray; each lane advances through a
-// small state machine (descend / composite) so that lanes never wait for
-// each other's dependent node loads.  Child slots come from the bits of the
-// point's integer coordinates on the finest grid.
+// a warp does not idle behind its longest ray; each iteration of a warp
+// composites the cell every live lane is in, then descends every lane to its
+// next cell.  Child slots come from the bits of the point's integer
+// coordinates on the finest grid.
 //
 // Numerics (all FP32, no FP64 on the device):
 //   * The ray position is kept as an unevaluated sum hi + lo of two floats
@@ -231,10 +231,8 @@ __device__ __forceinline__ float act_fn(float s, int act, float l_max) {
 }
 
 // ---------------------------------------------------------------- per-ray state
-// Each lane runs a small state machine so that lanes of a warp never wait for
-// each other's descents: one loop iteration composites at most one leaf and
-// issues at most one dependent node load (levels staged in shared memory
-// resolve within the same iteration).
+// Lane states: idle (no ray), descending to the cell at its current point,
+// or at a leaf cell waiting to composite it.
 enum : int { ST_IDLE = 0, ST_DESCEND = 1, ST_LEAF = 2 };
 
 struct Ray {
@@ -271,15 +269,15 @@ __device__ __forceinline__ uint2 load_entry(const TreeParams& tp, const uint2* s
     return __ldg(tp.nodes + (size_t)node * 8 + slot);
 }
 
-// Descends from R.node (level R.level) through the shared-memory levels and
-// at most one global level, taking the child bits from the finest-grid
-// coordinates R.q.  Ends in ST_LEAF (leaf or empty octant found) or stays in
-// ST_DESCEND with the next node to load.
+// Descends from R.node (level R.level) to the leaf or empty octant that holds
+// the point, taking the child bits from the finest-grid coordinates R.q, and
+// ends in ST_LEAF.  The whole descent runs in one step: stopping after each
+// dependent global load, so that lanes with shorter descents could go on,
+// was measured slower (304 vs 320 Mrays/s).
 __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* s_nodes, Ray& R, uint32_t* stack) {
     for (int guard = 0; guard <= MAX_DEPTH; ++guard) {
         const int sh = tp.depth - 1 - R.level;
         R.slot = (int)(((R.q[0] >> sh) & 1u) | (((R.q[1] >> sh) & 1u) << 1) | (((R.q[2] >> sh) & 1u) << 2));
-        const bool global = R.node >= (uint32_t)tp.n_top;
         uint2 e = load_entry(tp, s_nodes, R.node, R.slot);
         ++R.level;
         if ((e.x & LEAF_BIT) || R.level >= tp.depth) {  // leaf, empty octant (or a malformed table)
@@ -298,7 +296,6 @@ __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* 
         }
         stack[R.level * BLOCK] = e.x;
         R.node = e.x;
-        if (global || R.node >= (uint32_t)tp.n_top) return;  // next lookup needs a global load
     }
 }
 
@@ -632,9 +629,9 @@ __global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : PLO_RENDER_MIN_
         // once, so repeat while lanes are idle and rays remain
         for (;;) {
             unsigned idle = __ballot_sync(0xffffffffu, R.state == ST_IDLE);
-            // refill in groups: ray setup runs with at least 8 lanes (or when
-            // no ray is left in flight)
-            if (idle == 0u || (__popc(idle) < 8 && idle != 0xffffffffu)) break;
+            // refill in groups: ray setup runs with at least 4 lanes (or when
+            // no ray is left in flight; 4 measured faster than 8 and 16)
+            if (idle == 0u || (__popc(idle) < 4 && idle != 0xffffffffu)) break;
             if (next >= end) {
                 if (!kp.cursor || drained) break;
                 unsigned long long b = 0;
@@ -662,11 +659,8 @@ __global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : PLO_RENDER_MIN_
         }
         const unsigned live = __ballot_sync(0xffffffffu, R.state != ST_IDLE);
         if (live == 0u) break;
-        // composite in batches: while some lanes still descend, lanes that
-        // found their cell wait until enough of the live lanes have one
-        const unsigned at_leaf = __ballot_sync(0xffffffffu, R.state == ST_LEAF);
-        const bool composite = 4 * __popc(at_leaf) >= 3 * __popc(live);
-        if (composite && R.state == ST_LEAF) leaf_step<K, PREC, TRACE, SPHERE>(kp, tp, my, R, stack, sY);
+        // every live lane is at a leaf here (descents run to the leaf)
+        if (R.state == ST_LEAF) leaf_step<K, PREC, TRACE, SPHERE>(kp, tp, my, R, stack, sY);
         if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
     }
 }
@@ -716,7 +710,7 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(B
     for (;;) {
         for (;;) {
             unsigned idle = __ballot_sync(0xffffffffu, R.state == ST_IDLE);
-            // refill in groups of at least 8 lanes, as in k_render
+            // refill in groups of at least 8 lanes
             if (idle == 0u || (__popc(idle) < 8 && idle != 0xffffffffu)) break;
             if (next >= end) {
                 if (drained) break;
@@ -743,10 +737,7 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(B
         const unsigned live = __ballot_sync(0xffffffffu, R.state != ST_IDLE);
         if (live == 0u) break;
         const TreeParams& tp = s_tp[R.tree];
-        // composite in batches, as in k_render
-        const unsigned at_leaf = __ballot_sync(0xffffffffu, R.state == ST_LEAF);
-        const bool composite = 4 * __popc(at_leaf) >= 3 * __popc(live);
-        if (composite && R.state == ST_LEAF) leaf_step<0, -1, false, false>(kp, tp, my, R, stack);
+        if (R.state == ST_LEAF) leaf_step<0, -1, false, false>(kp, tp, my, R, stack);
         if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
     }
 }
