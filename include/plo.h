@@ -393,8 +393,9 @@ int64_t plo_mlp_step(const plo_mlp* mlp);
 /* The tensor-core building blocks (async), exposed for testing.
  * plo_gemm_bf16: C[M][N] = A[M][K] B[N][K]^T, A and B bf16 row-major,
  *   (N, K) in {(256, 64), (256, 256), (64, 256)}; epilogue 0: bf16
- *   ReLU(C + bias), and if d_bits is not NULL which outputs are > 0 as bits
- *   (uint32 [M][N / 32], bit j of word c for column 32 c + j); 1: fp32
+ *   ReLU(C + bias), and if d_bits is not NULL where C + bias > 0 (fp32,
+ *   before rounding) as bits (uint32 [M][N / 32], bit j of word c for
+ *   column 32 c + j); 1: fp32
  *   C + bias; 2: bf16 C * (mask > 0) with mask bf16 [M][N]; 3: bf16 C with
  *   the columns whose bit in d_bits is clear set to 0; d_out row-major
  *   [M][N].

@@ -51,7 +51,7 @@ struct EpiArgs {
     int ld_col0;                  // row stride of col0_add
     int tma_out;                  // bf16 outputs leave through the output tensor map (boxes of 32 x 32)
     uint32_t* bits_out;           // EPI_RELU_BF16 / EPI_SPLIT: [M][ldb] words, bit j of word c set iff
-                                  // bf16 output column 32c + j is > 0 (nullable)
+                                  // the pre-activation of column 32c + j is > 0 (nullable)
     const uint32_t* bits;         // EPI_MASKBITS_BF16: the mask as such words, [M][ldb]
     int ldb;                      // words per row of bits_out / bits
     unsigned int* err;            // device error word (bit 1: GEMM wait timeout)
@@ -115,16 +115,15 @@ __device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int r
     }
     uint32_t packed[16];
     if (epi == EPI_RELU_BF16 || epi == EPI_SPLIT) {
-        uint32_t pos = 0u;  // bit j: bf16 output j is > 0 (nonzero, sign clear)
+        uint32_t pos = 0u;  // bit j: pre-activation j is > 0 (the ReLU derivative)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            float a = fmaxf(v[2 * j] + __ldg(ep.bias + col + 2 * j), 0.0f);
-            float b = fmaxf(v[2 * j + 1] + __ldg(ep.bias + col + 2 * j + 1), 0.0f);
-            __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            const float x0 = v[2 * j] + __ldg(ep.bias + col + 2 * j);
+            const float x1 = v[2 * j + 1] + __ldg(ep.bias + col + 2 * j + 1);
+            __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(x0, 0.0f), fmaxf(x1, 0.0f));
             packed[j] = *reinterpret_cast<uint32_t*>(&h);
-            const uint32_t lo = packed[j] & 0xFFFFu, hi = packed[j] >> 16;
-            pos |= (uint32_t)(lo != 0u && !(lo & 0x8000u)) << (2 * j);
-            pos |= (uint32_t)(hi != 0u && !(hi & 0x8000u)) << (2 * j + 1);
+            pos |= (x0 > 0.0f ? 1u : 0u) << (2 * j);
+            pos |= (x1 > 0.0f ? 1u : 0u) << (2 * j + 1);
         }
         if (ep.bits_out) ep.bits_out[(size_t)row * ep.ldb + col / 32] = pos;
     } else if (epi == EPI_MASKBITS_BF16) {

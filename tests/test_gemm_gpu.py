@@ -48,6 +48,8 @@ def test_gemm_epilogues(torch_cuda, N, K, M):
     h2, _ = plo.gemm_bf16(A, B, 0, bias=bias)
     torch.cuda.synchronize()
     assert torch.equal(h, h2)
+    # bits from the fp32 pre-activation: positive exactly where the bf16
+    # ReLU output is (no pre-activation is small enough to round to zero)
     want = (h.float() > 0).reshape(M, N // 32, 32).to(torch.int64)
     want = (want << torch.arange(32, device="cuda", dtype=torch.int64)).sum(-1)
     assert torch.equal(bits.to(torch.int64) & 0xFFFFFFFF, want)
