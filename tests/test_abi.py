@@ -104,3 +104,23 @@ def test_build_rejects_bad_precision_before_any_device_work():
         bad[0, 3] = 99
         plo.Tree(HostTree(1, 2, bad, t.sigma, t.sh), plo.PREC_FP16)
     assert ei.value.status == -2
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the CUDA library the binding raises; there is no fallback."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import paper_2207_05009_gb300 as plo\n"
+            "from paper_2207_05009_gb300 import _build\n"
+            "_build.LIB = %r\n"
+            "plo._lib = None\n"
+            "try:\n"
+            "    plo.load(build=False)\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "    sys.exit(0)\n"
+            "sys.exit(1)\n") % (ROOT, str(tmp_path / "absent" / "libplo.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "libplo.so not found" in r.stdout
