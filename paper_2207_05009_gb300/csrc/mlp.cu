@@ -31,6 +31,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -1452,8 +1453,9 @@ extern "C" plo_status plo_wgrad_bf16(const void* d_dZ, int32_t n_out, const void
 // raw SH coefficients over `samples` jittered positions inside it.  Voxels
 // are visited in Morton order, so the kept list is sorted and the octree is
 // assembled on the host in one pass, then packed by plo_build_tree.
-extern "C" plo_status plo_distill(plo_mlp* m, int32_t depth, int32_t samples, float sigma_thresh,
-                                  int32_t precision, plo_tree** out, void* stream) {
+namespace {
+plo_status distill(plo_mlp* m, int32_t depth, int32_t samples, float sigma_thresh, int32_t precision, plo_tree** out,
+                   void* stream) {
     if (!m || !out) return set_error(PLO_ERR_INVALID_ARG, "mlp or out is NULL");
     *out = nullptr;
     if (depth < 1 || depth > 10) return set_error(PLO_ERR_INVALID_ARG, "depth must be in [1, 10]");
@@ -1559,4 +1561,18 @@ extern "C" plo_status plo_distill(plo_mlp* m, int32_t depth, int32_t samples, fl
         d.bbox_max[a] = 1.0f;
     }
     return plo_build_tree(&d, precision, out);
+}
+}  // namespace
+
+// The kept voxels' codes and averages live in host vectors (1 + 3K floats
+// per kept voxel: tens of GB at depth 10); an allocation failure is returned
+// as PLO_ERR_OOM, never thrown through the C ABI.
+extern "C" plo_status plo_distill(plo_mlp* m, int32_t depth, int32_t samples, float sigma_thresh,
+                                  int32_t precision, plo_tree** out, void* stream) {
+    try {
+        return distill(m, depth, samples, sigma_thresh, precision, out, stream);
+    } catch (const std::bad_alloc&) {
+        if (out) *out = nullptr;
+        return set_error(PLO_ERR_OOM, "host allocation during distillation failed");
+    }
 }

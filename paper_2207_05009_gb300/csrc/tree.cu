@@ -154,7 +154,8 @@ uint32_t sigma24_bits(float v) {
 
 extern "C" plo_status plo_validate_tree(const plo_tree_desc* desc) { return validate(desc); }
 
-extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out) {
+namespace {
+plo_status build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out) {
     if (!out) return set_error(PLO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (precision < PLO_PREC_FP32 || precision > PLO_PREC_BF16)
@@ -371,6 +372,19 @@ extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precisio
     }
     *out = t;
     return PLO_OK;
+}
+
+}  // namespace
+
+// Host allocations are large (the packed records alone are n_sh x stride
+// bytes); none of them may escape the C ABI as an exception.
+extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out) {
+    try {
+        return build_tree(desc, precision, out);
+    } catch (const std::bad_alloc&) {
+        if (out) *out = nullptr;
+        return set_error(PLO_ERR_OOM, "host allocation while packing the tree failed");
+    }
 }
 
 extern "C" void plo_tree_free(plo_tree* t) {
