@@ -1196,7 +1196,11 @@ extern "C" plo_status plo_mlp_set_params(plo_mlp* m, const float* h_params, int6
     if (!m || !h_params) return set_error(PLO_ERR_INVALID_ARG, "mlp or params is NULL");
     if (n != canonical_count(m->arch, m->n_out)) return set_error(PLO_ERR_INVALID_ARG, "wrong parameter count");
     std::vector<float> pad;
-    canonical_to_padded(m, h_params, pad);
+    try {
+        canonical_to_padded(m, h_params, pad);
+    } catch (const std::bad_alloc&) {
+        return set_error(PLO_ERR_OOM, "host allocation for the parameters failed");
+    }
     cudaError_t e = cudaMemcpy(m->master, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_error(e, "parameter upload");
     plo_status st = refresh_bf16(m, nullptr);
@@ -1208,7 +1212,12 @@ extern "C" plo_status plo_mlp_set_params(plo_mlp* m, const float* h_params, int6
 static plo_status download_canonical(const plo_mlp* m, const float* dev, float* h, int64_t n) {
     if (!m || !h) return set_error(PLO_ERR_INVALID_ARG, "mlp or output is NULL");
     if (n != canonical_count(m->arch, m->n_out)) return set_error(PLO_ERR_INVALID_ARG, "wrong parameter count");
-    std::vector<float> pad(m->n_params_pad);
+    std::vector<float> pad;
+    try {
+        pad.resize(m->n_params_pad);
+    } catch (const std::bad_alloc&) {
+        return set_error(PLO_ERR_OOM, "host allocation for the parameters failed");
+    }
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(pad.data(), dev, pad.size() * 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "parameter download");

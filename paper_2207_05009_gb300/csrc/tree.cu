@@ -152,7 +152,15 @@ uint32_t sigma24_bits(float v) {
 
 }  // namespace
 
-extern "C" plo_status plo_validate_tree(const plo_tree_desc* desc) { return validate(desc); }
+// Validation allocates per-node and per-leaf flags sized by the descriptor's
+// counts; a descriptor with huge counts gets PLO_ERR_OOM, not an exception.
+extern "C" plo_status plo_validate_tree(const plo_tree_desc* desc) {
+    try {
+        return validate(desc);
+    } catch (const std::bad_alloc&) {
+        return set_error(PLO_ERR_OOM, "host allocation while validating the tree failed");
+    }
+}
 
 namespace {
 plo_status build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out) {
