@@ -130,7 +130,8 @@ typedef struct {
 /* Checks a canonical tree on the host without touching a GPU: index ranges,
  * each node and leaf referenced at most once (no cycles or sharing), node
  * levels below `depth`, finite non-negative sigma, finite SH, box extents.
- * Returns PLO_OK, PLO_ERR_INVALID_ARG or PLO_ERR_BAD_TREE. */
+ * Returns PLO_OK, PLO_ERR_INVALID_ARG, PLO_ERR_BAD_TREE, or PLO_ERR_OOM when
+ * the host cannot hold the per-node and per-leaf flags for the given counts. */
 plo_status plo_validate_tree(const plo_tree_desc* desc);
 
 /* Validates `desc`, packs it into the device layout at `precision`
@@ -138,7 +139,10 @@ plo_status plo_validate_tree(const plo_tree_desc* desc);
  * FP16 / BF16 store each leaf's SH coefficients as binary16 / bfloat16 times a
  * per-leaf power-of-two FP32 scale, and sigma as a 24-bit float (8-bit
  * exponent, 16-bit mantissa, round-to-nearest-even).  On success *out owns the device copy; free it with
- * plo_tree_free.  The host arrays may be released after the call. */
+ * plo_tree_free.  The host arrays may be released after the call.  Packing
+ * runs on all host cores.  Errors: those of plo_validate_tree;
+ * PLO_ERR_INVALID_ARG for a bad precision; PLO_ERR_OOM when a host or device
+ * allocation fails (nothing of the tree is left allocated); PLO_ERR_CUDA. */
 plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out);
 
 /* Frees a tree (NULL is a no-op).  Synchronises the device first. */
@@ -379,7 +383,11 @@ plo_status plo_hier_samples(const float* d_rays, int32_t n_rays, int32_t n_coars
  * coefficients over `samples` (1..256) jittered positions inside it (offsets
  * from SplitMix64 keyed by the desc's seed and the voxel's Morton code).  The
  * tree is packed at `precision` and owned by *out; render it with
- * PLO_ACT_SIGMOID and the network's l_max. */
+ * PLO_ACT_SIGMOID and the network's l_max.  Host memory: 8 bytes per kept
+ * voxel for its code and 4 (1 + 3K) for its values, plus plo_build_tree's;
+ * device memory: the same values and codes, plus the network's workspace.
+ * Errors: PLO_ERR_INVALID_ARG; PLO_ERR_OOM when a host or device allocation
+ * fails; PLO_ERR_CUDA; PLO_ERR_TIMEOUT from the network's kernels. */
 plo_status plo_distill(plo_mlp* mlp, int32_t depth, int32_t samples, float sigma_thresh, int32_t precision,
                        plo_tree** out, void* stream);
 
