@@ -159,6 +159,26 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _require(t, name: str, shape, dtype, cuda: bool = True):
+    """Checks a caller-supplied tensor before its pointer reaches the library,
+    which trusts the sizes it is given: dtype, exact shape, contiguity, and
+    device memory (cuda) or host memory."""
+    shape = tuple(int(x) for x in shape)
+    if t.dtype != dtype or tuple(t.shape) != shape or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {shape}, "
+                         f"got {t.dtype} {tuple(t.shape)}{'' if t.is_contiguous() else ' (not contiguous)'}")
+    if bool(t.is_cuda) != cuda:
+        raise ValueError(f"{name} must be in {'CUDA device' if cuda else 'host'} memory")
+
+
+def _require_np(a, name: str, shape, dtype):
+    """The same for a numpy array in host memory."""
+    shape = tuple(int(x) for x in shape)
+    if a.dtype != dtype or a.shape != shape or not a.flags.c_contiguous:
+        raise ValueError(f"{name} must be a C-contiguous {np.dtype(dtype)} array of shape {shape}, "
+                         f"got {a.dtype} {a.shape}")
+
+
 class Tree:
     """A packed plenoctree on the current CUDA device (plo_build_tree)."""
 
@@ -203,6 +223,10 @@ def render(tree: Tree, rays, params: RenderParams | None = None, rgb=None, T=Non
     n = rays.shape[0]
     rgb = rgb if rgb is not None else torch.empty((n, 3), device=rays.device, dtype=torch.float32)
     T = T if T is not None else torch.empty(n, device=rays.device, dtype=torch.float32)
+    _require(rgb, "rgb", (n, 3), torch.float32)
+    _require(T, "T", (n,), torch.float32)
+    if status is not None:
+        _require(status, "status", (n,), torch.int32)
     p = params._c()
     _check(load().plo_render_rays(tree.handle, _ptr(rays), n, ctypes.byref(p), _ptr(rgb), _ptr(T), _ptr(status),
                                   _stream(stream)))
@@ -215,16 +239,23 @@ def render_host(tree: Tree, rays: np.ndarray, params: RenderParams | None = None
     import torch
     if isinstance(rays, torch.Tensor):
         n = rays.shape[0]
+        _require(rays, "rays", (n, 6), torch.float32, cuda=False)
         rp = rays.data_ptr()
         rgb = rgb if rgb is not None else torch.empty((n, 3), dtype=torch.float32, pin_memory=rays.is_pinned())
         T = T if T is not None else torch.empty(n, dtype=torch.float32, pin_memory=rays.is_pinned())
+        _require(rgb, "rgb", (n, 3), torch.float32, cuda=False)
+        _require(T, "T", (n,), torch.float32, cuda=False)
         op, tp = rgb.data_ptr(), T.data_ptr()
     else:
         rays = np.ascontiguousarray(rays, np.float32)
+        if rays.ndim != 2 or rays.shape[1] != 6:
+            raise ValueError(f"rays must have shape [n, 6], got {rays.shape}")
         n = rays.shape[0]
         rp = rays.ctypes.data
         rgb = rgb if rgb is not None else np.empty((n, 3), np.float32)
         T = T if T is not None else np.empty(n, np.float32)
+        _require_np(rgb, "rgb", (n, 3), np.float32)
+        _require_np(T, "T", (n,), np.float32)
         op, tp = rgb.ctypes.data, T.ctypes.data
     p = params._c()
     _check(load().plo_render_rays_host(tree.handle, ctypes.c_void_p(rp), n, ctypes.byref(p), ctypes.c_void_p(op),
@@ -241,6 +272,8 @@ def render_host_noalloc(tree: Tree, rays: np.ndarray, params: RenderParams | Non
     memory.  Returns (rgb [n,3], T [n]) as numpy arrays."""
     params = params or RenderParams()
     rays = np.ascontiguousarray(rays, np.float32)
+    if rays.ndim != 2 or rays.shape[1] != 6:
+        raise ValueError(f"rays must have shape [n, 6], got {rays.shape}")
     n = rays.shape[0]
     rgb = np.empty((n, 3), np.float32)
     T = np.empty(n, np.float32)
@@ -255,6 +288,9 @@ def lookup(tree: Tree, points, dirs=None, stream=None):
     """plo_lookup_points: points float32 [n,3] CUDA -> (leaf int64 [n], level int32 [n])."""
     import torch
     n = points.shape[0]
+    _require(points, "points", (n, 3), torch.float32)
+    if dirs is not None:
+        _require(dirs, "dirs", (n, 3), torch.float32)
     leaf = torch.empty(n, device=points.device, dtype=torch.int64)
     level = torch.empty(n, device=points.device, dtype=torch.int32)
     _check(load().plo_lookup_points(tree.handle, _ptr(points), _ptr(dirs), n, _ptr(leaf), _ptr(level),
@@ -267,6 +303,7 @@ def trace(tree: Tree, rays, max_cells: int, params: RenderParams | None = None, 
     import torch
     params = params or RenderParams()
     n = rays.shape[0]
+    _require(rays, "rays", (n, 6), torch.float32)
     leaf = torch.full((n, max_cells), -3, device=rays.device, dtype=torch.int64)
     t = torch.zeros((n, max_cells, 2), device=rays.device, dtype=torch.float32)
     cnt = torch.zeros(n, device=rays.device, dtype=torch.int32)
@@ -483,6 +520,8 @@ def pt_render(tree: Tree, scene: dict, spp: int, params: RenderParams | None = N
         lib.plo_pt_render.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_uint64, P, P, P, P]
         lib._pt_sigs = True
     s = PtScene.from_dict(scene)
+    if uniforms is not None:
+        _require(uniforms, "uniforms", (spp * s.width * s.height, 2 + 5 * s.max_bounces), torch.float32)
     p = (params or RenderParams())._c()
     img = torch.empty((s.height, s.width, 3), device="cuda", dtype=torch.float32)
     smp = torch.empty((spp, s.height, s.width, 3), device="cuda", dtype=torch.float32) if samples else None
