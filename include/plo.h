@@ -183,9 +183,15 @@ plo_status plo_render_rays_host(const plo_tree* tree, const float* h_rays, int64
  *   - Rays and results are staged in a fixed device array inside the library
  *     (10 MiB, held by every GPU that loads the library until exit), so at
  *     most 262,144 rays per call; larger n returns PLO_ERR_INVALID_ARG.
- *   - The call makes no device allocation and no allocating library call.
- *   - The first call on a device looks up the array's device address (once
- *     per device); make that first call before capturing any stream.
+ *   - After the set-up call below, a call makes no device allocation and no
+ *     allocating library call.
+ *   - The first call in a CUDA context (once per device, and again after
+ *     that device's context is reset) looks up the array's device address.
+ *     With lazy module loading (CUDA_MODULE_LOADING=LAZY, the runtime's
+ *     default) that lookup may also load the library's device code and with
+ *     it the 10 MiB array: the first call per context is the set-up step, so
+ *     make it at start-up and before capturing any stream.  Later calls make
+ *     no device allocation.
  *   - All calls share the array: calls whose work overlaps on the GPU (other
  *     streams, other host threads) race and corrupt each other's results.
  *   - Copies and the render run on `stream`; the call returns after h_rgb and
@@ -270,8 +276,8 @@ plo_status plo_tree_check(const plo_tree* tree, void* stream);
  * fully connected layers of 256 with ReLU (the trunk), then the output
  * layers of the chosen architecture:
  *   PLO_ARCH_LINEAR_HEAD  one linear layer 256 -> 1 + 3K (sigma_raw, SH);
- *   PLO_ARCH_PAPER        "an extra output layer of 128 neurons" (Sec. 4.2):
- *                         sigma_raw = w_s . h8 + b_s and
+ *   PLO_ARCH_PAPER        a 128-wide hidden layer before the SH outputs
+ *                         (Sec. 4.2): sigma_raw = w_s . h8 + b_s and
  *                         SH = W_c ReLU(W_f h8 + b_f) + b_c (128 -> 3K).
  * sigma = ReLU(sigma_raw); emission = l_max * sigmoid(sum_k c_k Y_k(d))
  * (Eq. 6); SH coefficients channel-major.  BF16 weights and activations,
@@ -390,6 +396,49 @@ plo_status plo_hier_samples(const float* d_rays, int32_t n_rays, int32_t n_coars
  * fails; PLO_ERR_CUDA; PLO_ERR_TIMEOUT from the network's kernels. */
 plo_status plo_distill(plo_mlp* mlp, int32_t depth, int32_t samples, float sigma_thresh, int32_t precision,
                        plo_tree** out, void* stream);
+
+/* Checkpoint of a network and its training state (Sec. 4.4 training runs for
+ * days; an interrupted run resumes where it stopped).  plo_mlp_save writes,
+ * synchronously, to a file at `path`:
+ *   "PLOMLP01", a uint64 header length H, an H-byte flat JSON header (format
+ *   "plo-mlp", version 1, the plo_mlp_desc fields, seed as a decimal string,
+ *   the step count, n_params, and the byte offset of each blob), then the
+ *   blobs at 64-byte-aligned offsets, little-endian: "master", "adam_m",
+ *   "adam_v" (float32 [n_params] each in the canonical parameter order of
+ *   plo_mlp_get_params: FP32 weights and Adam's first and second moments)
+ *   and "weights_bf16" (bfloat16 copies of every weight matrix, canonical
+ *   order, no biases).
+ * The sample jitter is keyed by (seed, step), so seed and step restore the
+ * training's random stream.  plo_mlp_load creates a network on the current
+ * device from such a file (the caller frees it with plo_mlp_free); it checks
+ * the header, the sizes and that the bf16 copies are the rounding of the FP32
+ * weights.  plo_mlp_checkpoint_info reads and checks only the header, on the
+ * host (no GPU), returning its description and step (either may be NULL).
+ * Errors: PLO_ERR_INVALID_ARG for an unreadable, truncated or inconsistent
+ * file; PLO_ERR_UNSUPPORTED for another format version; PLO_ERR_OOM. */
+plo_status plo_mlp_save(const plo_mlp* mlp, const char* path);
+plo_status plo_mlp_load(const char* path, plo_mlp** out);
+plo_status plo_mlp_checkpoint_info(const char* path, plo_mlp_desc* desc, int64_t* step);
+
+/* Test hooks of the training step (async), so that each stage can be compared
+ * with a reference element by element.
+ * plo_mlp_get_activation: copies rows [0, n_rows) of the bf16 input of
+ *   network layer `layer` as the last forward or training step left it:
+ *   layer 0 is the positional encoding (64 columns, column 63 zero),
+ *   1..8 the outputs of the eight trunk layers (256 columns), and for
+ *   PLO_ARCH_PAPER 9 the 128-wide layer's output.  d_out bf16 [n_rows][cols].
+ * plo_mlp_quad: the quadrature render and loss stage of plo_mlp_train_step
+ *   alone (Eq. 3-9, the network's l_max, eps, transmittance and loss) on
+ *   given raw outputs d_raw float [n_rays * n_samples][1 + 3K] (row
+ *   ray * n_samples + j) and segment lengths d_delta float [n_rays *
+ *   n_samples].  Writes d_ray_out float [n_rays][5] (C^ rgb, alpha^, the
+ *   ray's loss) and, if d_draw is not NULL, d (mean loss) / d raw float
+ *   [n_rays * n_samples][1 + 3K] as the backward pass receives it (rounded
+ *   to bf16).  n_samples in {32, 64, 96, 128, 192, 256}. */
+plo_status plo_mlp_get_activation(const plo_mlp* mlp, int32_t layer, void* d_out, int64_t n_rows, void* stream);
+plo_status plo_mlp_quad(plo_mlp* mlp, const float* d_rays, const float* d_raw, const float* d_delta,
+                        const float* d_rgb_gt, const float* d_alpha_gt, int32_t n_rays, int32_t n_samples,
+                        float* d_ray_out, float* d_draw, void* stream);
 
 /* Synchronises `stream`; PLO_ERR_TIMEOUT if a tensor-core kernel gave up on
  * a bounded pipeline wait since the last check (the flag is cleared). */

@@ -21,6 +21,14 @@ matrix products are the only library primitive.  Follows:
     weights, loss L_c + L_f + L_alpha.
 
 The SH basis is the oracle's own (``oracle.sh_basis``, Legendre recursion).
+
+Storage precision.  The workload fixes the network's arithmetic as BF16
+weights and activations with FP32 accumulation.  With ``storage="bf16"`` the
+forward and backward passes round what the network stores between layers to
+bfloat16 (round to nearest even, through FP32), at these points: the encoded
+input, every hidden ReLU output, d loss / d raw, and every hidden layer's
+d loss / d pre-activation after its ReLU mask.  Sums stay in FP64.  The
+default ``storage="fp64"`` rounds nothing.
 """
 from __future__ import annotations
 
@@ -67,26 +75,48 @@ def positional_encoding(x: np.ndarray) -> np.ndarray:
     return np.concatenate(feats, axis=1)
 
 
-def forward(Ws, bs, X):
-    """MLP forward.  Returns (raw outputs [M, n_out], hidden activations)."""
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """x rounded to bfloat16 (8 significant bits, FP32's exponent range):
+    first to FP32, then the low 16 bits of the FP32 pattern rounded away,
+    to nearest with ties to even.  Returned as FP64."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _store(x, storage):
+    return round_bf16(x) if storage == "bf16" else x
+
+
+def forward(Ws, bs, X, storage="fp64", masks=None):
+    """MLP forward.  Returns (raw outputs [M, n_out], hidden activations,
+    the stored ones under bf16 storage).  If `masks` is a list, the hidden
+    layers' pre-activation signs (taken before rounding) are appended."""
+    X = _store(X, storage)
     H = [X]
     h = X
+    masks = [] if masks is None else masks
     for l in range(DEPTH):
-        h = np.maximum(h @ Ws[l].T + bs[l], 0.0)
+        z = h @ Ws[l].T + bs[l]
+        masks.append(z > 0)
+        h = _store(np.maximum(z, 0.0), storage)
         H.append(h)
     raw = h @ Ws[DEPTH].T + bs[DEPTH]
     return raw, H
 
 
-def backward(Ws, H, draw):
-    """Gradients of the MLP parameters given d loss / d raw."""
+def backward(Ws, H, draw, storage="fp64", masks=None):
+    """Gradients of the MLP parameters given d loss / d raw.  `masks` are
+    the hidden layers' pre-activation signs (default: the stored outputs
+    > 0)."""
     dWs = [None] * (DEPTH + 1)
     dbs = [None] * (DEPTH + 1)
+    draw = _store(draw, storage)
     dWs[DEPTH] = draw.T @ H[DEPTH]
     dbs[DEPTH] = draw.sum(0)
     g = draw @ Ws[DEPTH]
     for l in range(DEPTH - 1, -1, -1):
-        g = g * (H[l + 1] > 0)
+        g = _store(g * (masks[l] if masks is not None else (H[l + 1] > 0)), storage)
         dWs[l] = g.T @ H[l]
         dbs[l] = g.sum(0)
         g = g @ Ws[l]
@@ -203,14 +233,19 @@ def composite_backward(cache, dC, dA):
 
 
 def train_loss_and_grads(Ws, bs, rays, jitter, C_gt, alpha_gt, l_max_scale, l_max=3, kind="paper",
-                         transmittance="exp", denom=None, arch="linear"):
+                         transmittance="exp", denom=None, arch="linear", storage="fp64", X=None):
     """One training batch: returns (mean loss, dWs, dbs, extras).  arch:
-    'linear' (linear head) or 'paper' (the 128-wide SH layer)."""
+    'linear' (linear head) or 'paper' (the 128-wide SH layer); storage:
+    'fp64' or 'bf16' (see the module's header); X overrides the encoded
+    samples [R * N, 63] (for example with another implementation's own
+    rounding of them)."""
     fwd, bwd = (forward_paper, backward_paper) if arch == "paper" else (forward, backward)
     t, delta, x, hit = stratified_samples(rays, jitter)
     R, N = jitter.shape
-    X = positional_encoding(x.reshape(R * N, 3))
-    raw, H = fwd(Ws, bs, X)
+    if X is None:
+        X = positional_encoding(x.reshape(R * N, 3))
+    masks = []
+    raw, H = fwd(Ws, bs, X, storage=storage, masks=masks)
     raw = raw.reshape(R, N, -1)
     d = rays[:, 3:].astype(np.float64)
     Y = sh_matrix(d, l_max)
@@ -218,8 +253,8 @@ def train_loss_and_grads(Ws, bs, rays, jitter, C_gt, alpha_gt, l_max_scale, l_ma
     per_ray, dC, dA = loss_terms(C, alpha, C_gt, alpha_gt, l_max_scale, kind, denom=denom)
     loss = per_ray.mean()
     draw = composite_backward(cache, dC / R, dA / R).reshape(R * N, -1)
-    dWs, dbs = bwd(Ws, H, draw)
-    return loss, dWs, dbs, dict(C=C, alpha=alpha, raw=raw, draw=draw, X=X)
+    dWs, dbs = bwd(Ws, H, draw, storage=storage, masks=masks)
+    return loss, dWs, dbs, dict(C=C, alpha=alpha, raw=raw, draw=draw, X=X, delta=delta)
 
 
 # ---------------------------------------------------------------- the paper's full training setup
@@ -248,37 +283,49 @@ def init_params_paper(rng: np.random.Generator, l_max: int = 3):
     return Ws, bs
 
 
-def forward_paper(Ws, bs, X):
+def forward_paper(Ws, bs, X, storage="fp64", masks=None):
     """Trunk, then raw sigma = W_s h8 + b_s and SH = W_c ReLU(W_f h8 + b_f) + b_c.
-    Returns (raw [M, 1 + 3K] with sigma first, activations [X, h1..h8, feat])."""
+    Returns (raw [M, 1 + 3K] with sigma first, activations [X, h1..h8, feat]);
+    `masks` as in forward, the 128-wide layer's last."""
+    X = _store(X, storage)
     H = [X]
     h = X
+    masks = [] if masks is None else masks
     for l in range(DEPTH):
-        h = np.maximum(h @ Ws[l].T + bs[l], 0.0)
+        z = h @ Ws[l].T + bs[l]
+        masks.append(z > 0)
+        h = _store(np.maximum(z, 0.0), storage)
         H.append(h)
     sig = h @ Ws[DEPTH].T + bs[DEPTH]
-    feat = np.maximum(h @ Ws[DEPTH + 1].T + bs[DEPTH + 1], 0.0)
+    zf = h @ Ws[DEPTH + 1].T + bs[DEPTH + 1]
+    masks.append(zf > 0)
+    feat = _store(np.maximum(zf, 0.0), storage)
     H.append(feat)
     sh = feat @ Ws[DEPTH + 2].T + bs[DEPTH + 2]
     return np.concatenate([sig, sh], axis=1), H
 
 
-def backward_paper(Ws, H, draw):
-    """Parameter gradients of forward_paper given d loss / d raw."""
+def backward_paper(Ws, H, draw, storage="fp64", masks=None):
+    """Parameter gradients of forward_paper given d loss / d raw.  `masks`:
+    the pre-activation signs of the trunk layers and the 128-wide layer
+    (default: the stored outputs > 0).  Under bf16 storage the gradient of
+    the 128-wide layer and sigma's is stored as one bf16 block."""
     n = DEPTH + 3
     dWs, dbs = [None] * n, [None] * n
+    draw = _store(draw, storage)
+    mk = (lambda l: masks[l]) if masks is not None else (lambda l: H[l + 1] > 0)
     dsig, dsh = draw[:, :1], draw[:, 1:]
     h8, feat = H[DEPTH], H[DEPTH + 1]
     dWs[DEPTH + 2] = dsh.T @ feat
     dbs[DEPTH + 2] = dsh.sum(0)
-    gf = (dsh @ Ws[DEPTH + 2]) * (feat > 0)
+    gf = _store((dsh @ Ws[DEPTH + 2]) * mk(DEPTH), storage)
     dWs[DEPTH + 1] = gf.T @ h8
     dbs[DEPTH + 1] = gf.sum(0)
     dWs[DEPTH] = dsig.T @ h8
     dbs[DEPTH] = dsig.sum(0)
     g = gf @ Ws[DEPTH + 1] + dsig @ Ws[DEPTH]
     for l in range(DEPTH - 1, -1, -1):
-        g = g * (H[l + 1] > 0)
+        g = _store(g * mk(l), storage)
         dWs[l] = g.T @ H[l]
         dbs[l] = g.sum(0)
         g = g @ Ws[l]
@@ -321,21 +368,25 @@ def merge_samples(t_coarse, t_fine, t1):
 
 
 def train_loss_and_grads_hier(Wc, bc, Wf, bf, rays, jitter, xi, C_gt, alpha_gt, l_max_scale, l_max=3,
-                              transmittance="exp", arch="paper", denoms=(None, None), t_fine=None):
+                              transmittance="exp", arch="paper", denoms=(None, None), t_fine=None,
+                              storage="fp64", X_coarse=None, X_fine=None):
     """One batch of the paper's training (Eq. finaloss): coarse colour loss
     L_c on N_c stratified samples (jitter [R, N_c]), fine colour loss L_f
     and alpha loss L_alpha on the coarse plus N_f fine samples (xi [R, N_f]).
     No gradient flows through the sample placement.  `denoms` overrides the
     held-constant loss denominators (coarse, fine); `t_fine` overrides the
-    fine samples (to hold them fixed).  Returns (mean loss, (dWc, dbc),
-    (dWf, dbf), extras)."""
+    fine samples (to hold them fixed); storage and X_coarse / X_fine (the
+    encoded samples of either pass) as in train_loss_and_grads.  Returns
+    (mean loss, (dWc, dbc), (dWf, dbf), extras)."""
     fwd, bwd = (forward_paper, backward_paper) if arch == "paper" else (forward, backward)
     R, Nc = jitter.shape
     d = rays[:, 3:].astype(np.float64)
     o = rays[:, :3].astype(np.float64)
     Y = sh_matrix(d, l_max)
     t, delta, x, hit = stratified_samples(rays, jitter)
-    raw_c, Hc = fwd(Wc, bc, positional_encoding(x.reshape(R * Nc, 3)))
+    mc, mf = [], []
+    Xc = positional_encoding(x.reshape(R * Nc, 3)) if X_coarse is None else X_coarse
+    raw_c, Hc = fwd(Wc, bc, Xc, storage=storage, masks=mc)
     raw_c = raw_c.reshape(R, Nc, -1)
     C_c, a_c, cache_c = composite(raw_c, delta, Y, l_max_scale, transmittance)
     per_c, dC_c, _ = loss_terms(C_c, a_c, C_gt, alpha_gt, l_max_scale, "reg", denom=denoms[0])
@@ -346,15 +397,16 @@ def train_loss_and_grads_hier(Wc, bc, Wf, bf, rays, jitter, xi, C_gt, alpha_gt, 
     da = np.where(hit[:, None], da, 0.0)
     N = ta.shape[1]
     xa = o[:, None, :] + ta[..., None] * d[:, None, :]
-    raw_f, Hf = fwd(Wf, bf, positional_encoding(xa.reshape(R * N, 3)))
+    Xf = positional_encoding(xa.reshape(R * N, 3)) if X_fine is None else X_fine
+    raw_f, Hf = fwd(Wf, bf, Xf, storage=storage, masks=mf)
     raw_f = raw_f.reshape(R, N, -1)
     C_f, a_f, cache_f = composite(raw_f, da, Y, l_max_scale, transmittance)
     per_f, dC_f, dA_f = loss_terms(C_f, a_f, C_gt, alpha_gt, l_max_scale, "paper", denom=denoms[1])
     loss = (per_c + per_f).mean()
     draw_c = composite_backward(cache_c, dC_c / R, np.zeros(R)).reshape(R * Nc, -1)
     draw_f = composite_backward(cache_f, dC_f / R, dA_f / R).reshape(R * N, -1)
-    gc = bwd(Wc, Hc, draw_c)
-    gf = bwd(Wf, Hf, draw_f)
+    gc = bwd(Wc, Hc, draw_c, storage=storage, masks=mc)
+    gf = bwd(Wf, Hf, draw_f, storage=storage, masks=mf)
     return loss, gc, gf, dict(C_c=C_c, C_f=C_f, alpha_f=a_f, t_fine=tf, t_all=ta, delta_all=da,
                               w_c=cache_c["w"], loss_c=per_c.mean(), loss_f=per_f.mean())
 

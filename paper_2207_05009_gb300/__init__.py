@@ -171,6 +171,27 @@ def _require(t, name: str, shape, dtype, cuda: bool = True):
         raise ValueError(f"{name} must be in {'CUDA device' if cuda else 'host'} memory")
 
 
+def _require_rays_targets(rays, rgb_gt, alpha_gt):
+    """Training rays [R, 6] with targets rgb [R, 3] and alpha [R] on the device."""
+    import torch
+    if rays.ndim != 2:
+        raise ValueError("rays must have shape [n_rays, 6]")
+    R = rays.shape[0]
+    _require_all((rays, "rays", (R, 6), torch.float32), (rgb_gt, "rgb_gt", (R, 3), torch.float32),
+                 (alpha_gt, "alpha_gt", (R,), torch.float32))
+
+
+def _require_all(*specs, cuda: bool = True):
+    """_require over several (tensor, name, shape, dtype) specs (None tensors
+    skipped): every shape, dtype and layout first, then every device, so a
+    caller learns of the first malformed buffer whatever memory it is in."""
+    specs = [sp for sp in specs if sp[0] is not None]
+    for t, name, shape, dtype in specs:
+        _require(t, name, shape, dtype, cuda=bool(t.is_cuda))
+    for t, name, shape, dtype in specs:
+        _require(t, name, shape, dtype, cuda=cuda)
+
+
 def _require_np(a, name: str, shape, dtype):
     """The same for a numpy array in host memory."""
     shape = tuple(int(x) for x in shape)
@@ -218,7 +239,8 @@ def render(tree: Tree, rays, params: RenderParams | None = None, rgb=None, T=Non
     """plo_render_rays on CUDA tensors: rays float32 [n, 6] -> (rgb [n,3], T [n], status [n] or None)."""
     import torch
     params = params or RenderParams()
-    if not (rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous() and rays.shape[-1] == 6):
+    if not (rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous() and rays.ndim == 2
+            and rays.shape[1] == 6):
         raise ValueError("rays must be a contiguous float32 CUDA tensor of shape [n, 6]")
     n = rays.shape[0]
     rgb = rgb if rgb is not None else torch.empty((n, 3), device=rays.device, dtype=torch.float32)
@@ -344,6 +366,11 @@ def _load_mlp_sigs(lib):
         "plo_gemm_bf16": (I32, [P, P, I32, I32, I32, I32, P, P, P, P, P, P]),
         "plo_wgrad_bf16": (I32, [P, I32, P, I32, I32, P, P, P, P]),
         "plo_distill": (I32, [P, I32, I32, ctypes.c_float, I32, P, P]),
+        "plo_mlp_save": (I32, [P, ctypes.c_char_p]),
+        "plo_mlp_load": (I32, [ctypes.c_char_p, P]),
+        "plo_mlp_checkpoint_info": (I32, [ctypes.c_char_p, P, P]),
+        "plo_mlp_get_activation": (I32, [P, I32, P, I64, P]),
+        "plo_mlp_quad": (I32, [P, P, P, P, P, P, I32, I32, P, P, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -396,12 +423,17 @@ class Mlp:
     def forward(self, points, stream=None):
         import torch
         n = points.shape[0]
+        _require(points, "points", (n, 3), torch.float32)
         raw = torch.empty((n, 49), device=points.device, dtype=torch.float32)
         _check(mlp_lib().plo_mlp_forward(self._h, _ptr(points), n, _ptr(raw), _stream(stream)))
         return raw
 
     def train_step(self, rays, rgb_gt, alpha_gt, n_samples: int = 128, jitter=None, loss_out=None, stream=None):
         import torch
+        R = rays.shape[0] if rays.ndim == 2 else -1
+        _require_all((jitter, "jitter", (R, n_samples), torch.float32),
+                     (loss_out, "loss_out", (1,), torch.float32))
+        _require_rays_targets(rays, rgb_gt, alpha_gt)
         loss_out = loss_out if loss_out is not None else torch.empty(1, device=rays.device, dtype=torch.float32)
         _check(mlp_lib().plo_mlp_train_step(self._h, _ptr(rays), _ptr(rgb_gt), _ptr(alpha_gt), rays.shape[0],
                                             n_samples, _ptr(jitter), _ptr(loss_out), _stream(stream)))
@@ -415,6 +447,10 @@ class Mlp:
                         jitter=None, xi=None, loss_out=None, stream=None):
         """plo_mlp_train_step_hier: one coarse/fine step (Sec. 4.3-4.4)."""
         import torch
+        R = rays.shape[0] if rays.ndim == 2 else -1
+        _require_all((jitter, "jitter", (R, n_coarse), torch.float32), (xi, "xi", (R, n_fine), torch.float32),
+                     (loss_out, "loss_out", (1,), torch.float32))
+        _require_rays_targets(rays, rgb_gt, alpha_gt)
         loss_out = loss_out if loss_out is not None else torch.empty(1, device=rays.device, dtype=torch.float32)
         _check(mlp_lib().plo_mlp_train_step_hier(coarse._h, fine._h, _ptr(rays), _ptr(rgb_gt), _ptr(alpha_gt),
                                                  rays.shape[0], n_coarse, n_fine, _ptr(jitter), _ptr(xi),
@@ -436,6 +472,57 @@ class Mlp:
     def step(self) -> int:
         return int(mlp_lib().plo_mlp_step(self._h))
 
+    def save(self, path: str) -> None:
+        """plo_mlp_save: the network and its Adam state to a checkpoint file."""
+        _check(mlp_lib().plo_mlp_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str) -> "Mlp":
+        """plo_mlp_load: a network on the current device from a checkpoint."""
+        lib = mlp_lib()
+        h = ctypes.c_void_p()
+        _check(lib.plo_mlp_load(os.fsencode(path), ctypes.byref(h)))
+        desc = MlpDesc()
+        _check(lib.plo_mlp_checkpoint_info(os.fsencode(path), ctypes.byref(desc), None))
+        net = cls.__new__(cls)
+        net._h = h
+        net.arch = desc.arch
+        net.n_params = int(lib.plo_mlp_param_count_arch(desc.sh_degree, desc.arch))
+        return net
+
+    def activation(self, layer: int, n_rows: int, stream=None):
+        """plo_mlp_get_activation: bf16 input of `layer` for the first n_rows
+        samples of the last forward or training step."""
+        import torch
+        cols = 64 if layer == 0 else (128 if layer == 9 else 256)
+        out = torch.empty((n_rows, cols), device="cuda", dtype=torch.bfloat16)
+        _check(mlp_lib().plo_mlp_get_activation(self._h, layer, _ptr(out), n_rows, _stream(stream)))
+        return out
+
+    def quad(self, rays, raw, delta, rgb_gt, alpha_gt, n_samples: int, stream=None):
+        """plo_mlp_quad: (ray_out [R, 5] = C^ rgb, alpha^, loss; d loss / d raw
+        [R * n_samples, 49]) for given raw outputs and segment lengths."""
+        import torch
+        R = rays.shape[0] if rays.ndim == 2 else -1
+        M = R * n_samples
+        _require_all((raw, "raw", (M, 49), torch.float32), (delta, "delta", (M,), torch.float32))
+        _require_rays_targets(rays, rgb_gt, alpha_gt)
+        ray_out = torch.empty((R, 5), device=rays.device, dtype=torch.float32)
+        draw = torch.empty((M, 49), device=rays.device, dtype=torch.float32)
+        _check(mlp_lib().plo_mlp_quad(self._h, _ptr(rays), _ptr(raw), _ptr(delta), _ptr(rgb_gt), _ptr(alpha_gt),
+                                      R, n_samples, _ptr(ray_out), _ptr(draw), _stream(stream)))
+        return ray_out, draw
+
+
+def checkpoint_info(path: str) -> tuple[dict, int]:
+    """plo_mlp_checkpoint_info: (network description, step) of a checkpoint
+    file, read on the host without a GPU."""
+    lib = mlp_lib()
+    desc = MlpDesc()
+    step = ctypes.c_int64()
+    _check(lib.plo_mlp_checkpoint_info(os.fsencode(path), ctypes.byref(desc), ctypes.byref(step)))
+    return {k: getattr(desc, k) for k, _ in MlpDesc._fields_}, int(step.value)
+
     def free(self):
         if getattr(self, "_h", None) and self._h.value:
             mlp_lib().plo_mlp_free(self._h)
@@ -452,10 +539,17 @@ def gemm_bf16(A, B, epilogue: int, bias=None, mask=None, out=None, err=None, bit
     """plo_gemm_bf16 on CUDA tensors (A [M][K], B [N][K] bf16); bits: int32
     [M][N / 32], written by epilogue 0 and read by epilogue 3."""
     import torch
+    if A.ndim != 2 or B.ndim != 2:
+        raise ValueError("A and B must be 2-D")
     M, K = A.shape
     N = B.shape[0]
+    odt = torch.float32 if epilogue == 1 else torch.bfloat16
+    _require_all((A, "A", (M, K), torch.bfloat16), (B, "B", (N, K), torch.bfloat16),
+                 (bias, "bias", (N,), torch.float32), (mask, "mask", (M, N), torch.bfloat16),
+                 (bits, "bits", (M, N // 32), torch.int32), (out, "out", (M, N), odt),
+                 (err, "err", (1,), torch.int32))
     if out is None:
-        out = torch.empty((M, N), device=A.device, dtype=torch.float32 if epilogue == 1 else torch.bfloat16)
+        out = torch.empty((M, N), device=A.device, dtype=odt)
     err = err if err is not None else torch.zeros(1, device=A.device, dtype=torch.int32)
     _check(mlp_lib().plo_gemm_bf16(_ptr(A), _ptr(B), M, N, K, epilogue, _ptr(bias), _ptr(mask), _ptr(bits), _ptr(out),
                                    _ptr(err), _stream(stream)))
@@ -466,8 +560,13 @@ def hier_samples(rays, t, delta, w, xi, stream=None):
     """plo_hier_samples: merged coarse + fine parameters and lengths
     ([n_rays][n_coarse + n_fine]) for coarse t, delta, w and fine xi."""
     import torch
+    if t.ndim != 2 or xi.ndim != 2:
+        raise ValueError("t and xi must be 2-D")
     n, nc = t.shape
     nf = xi.shape[1]
+    f32 = torch.float32
+    _require_all((rays, "rays", (n, 6), f32), (t, "t", (n, nc), f32), (delta, "delta", (n, nc), f32),
+                 (w, "w", (n, nc), f32), (xi, "xi", (n, nf), f32))
     t_out = torch.empty((n, nc + nf), device=t.device, dtype=torch.float32)
     d_out = torch.empty_like(t_out)
     _check(mlp_lib().plo_hier_samples(_ptr(rays), n, nc, nf, _ptr(t), _ptr(delta), _ptr(w), _ptr(xi), _ptr(t_out),
@@ -479,6 +578,13 @@ def wgrad_bf16(dZ, H, dW, db=None, err=None, stream=None):
     """plo_wgrad_bf16: dW [n_out][n_in] (fp32) += dZ^T H; db [n_out] (fp32,
     optional) += the column sums of dZ."""
     import torch
+    if dZ.ndim != 2 or H.ndim != 2:
+        raise ValueError("dZ and H must be 2-D")
+    M, n_out = dZ.shape
+    n_in = H.shape[1]
+    _require_all((dZ, "dZ", (M, n_out), torch.bfloat16), (H, "H", (M, n_in), torch.bfloat16),
+                 (dW, "dW", (n_out, n_in), torch.float32), (db, "db", (n_out,), torch.float32),
+                 (err, "err", (1,), torch.int32))
     err = err if err is not None else torch.zeros(1, device=dZ.device, dtype=torch.int32)
     _check(mlp_lib().plo_wgrad_bf16(_ptr(dZ), dZ.shape[1], _ptr(H), H.shape[1], dZ.shape[0], _ptr(dW), _ptr(db),
                                     _ptr(err), _stream(stream)))
@@ -581,10 +687,18 @@ class Batch:
         c = BatchConfig(claim_rays, blocks_per_sm, top_nodes)
         _check(_batch_lib().plo_batch_set_config(self._h, ctypes.byref(c)))
 
+    def _require_buffers(self, rays, rgb, T, status=None):
+        import torch
+        n = self.n_rays
+        _require_all((rays, "rays", (n, 6), torch.float32), (rgb, "rgb", (n, 3), torch.float32),
+                     (T, "T", (n,), torch.float32), (status, "status", (n,), torch.int32))
+
     def render(self, rays, rgb, T, status=None, stream=None):
+        self._require_buffers(rays, rgb, T, status)
         _check(_batch_lib().plo_batch_render(self._h, _ptr(rays), _ptr(rgb), _ptr(T), _ptr(status), _stream(stream)))
 
     def capture(self, rays, rgb, T, status=None, stream=None):
+        self._require_buffers(rays, rgb, T, status)
         _check(_batch_lib().plo_batch_capture(self._h, _ptr(rays), _ptr(rgb), _ptr(T), _ptr(status),
                                               _stream(stream)))
 
@@ -592,6 +706,7 @@ class Batch:
         _check(_batch_lib().plo_batch_replay(self._h, _stream(stream)))
 
     def autotune(self, rays, rgb, T, reps: int = 2, stream=None):
+        self._require_buffers(rays, rgb, T)
         c = BatchConfig()
         ms = ctypes.c_float()
         _check(_batch_lib().plo_batch_autotune(self._h, _ptr(rays), _ptr(rgb), _ptr(T), reps, _stream(stream),
@@ -649,6 +764,10 @@ def debug_fail_alloc_after(n: int) -> None:
 
 def debug_gemm_stall(A, B, out, err, wait_limit: int, stream=None):
     """plo_debug_gemm_stall: a GEMM whose pipeline waits run out."""
+    import torch
+    M = A.shape[0]
+    _require_all((A, "A", (M, 64), torch.bfloat16), (B, "B", (256, 64), torch.bfloat16),
+                 (out, "out", (M, 256), torch.bfloat16), (err, "err", (1,), torch.int32))
     lib = load()
     fn = lib.plo_debug_gemm_stall
     fn.restype = ctypes.c_int32

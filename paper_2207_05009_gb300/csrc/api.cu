@@ -22,18 +22,31 @@ namespace {
 std::atomic<int> g_fail_after{-1};
 }
 
-int dev_malloc(void** p, size_t bytes) {
+namespace {
+// true when the failure hook makes this allocation fail
+bool hook_fails() {
     int n = g_fail_after.load();
     while (n >= 0) {
-        if (g_fail_after.compare_exchange_weak(n, n - 1)) {
-            if (n == 0) {
-                *p = nullptr;
-                return (int)cudaErrorMemoryAllocation;
-            }
-            break;
-        }
+        if (g_fail_after.compare_exchange_weak(n, n - 1)) return n == 0;
+    }
+    return false;
+}
+}  // namespace
+
+int dev_malloc(void** p, size_t bytes) {
+    if (hook_fails()) {
+        *p = nullptr;
+        return (int)cudaErrorMemoryAllocation;
     }
     return (int)cudaMalloc(p, bytes);
+}
+
+int dev_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+    if (hook_fails()) {
+        *p = nullptr;
+        return (int)cudaErrorMemoryAllocation;
+    }
+    return (int)cudaMallocAsync(p, bytes, s);
 }
 
 plo_status cuda_error(int err, const char* what) {
@@ -78,7 +91,7 @@ extern "C" plo_status plo_render_rays_host(const plo_tree* tree, const float* h_
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(ready, user);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(s[k], ready, 0);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMallocAsync((void**)&buf[k], per, s[k]);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = (cudaError_t)dev_malloc_async((void**)&buf[k], per, s[k]);
     if (e != cudaSuccess) st = cuda_error(e, "plo_render_rays_host setup");
     for (int64_t off = 0, c = 0; st == PLO_OK && off < n; off += chunk, ++c) {
         const int64_t m = std::min(chunk, n - off);

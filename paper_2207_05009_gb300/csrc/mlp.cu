@@ -365,7 +365,7 @@ template <int K, int S>
 __global__ void k_quad(const float* raw, const float* delta, const float* rays, const float* rgb_gt,
                        const float* alpha_gt, int n_rays, float l_max, float eps, int transmittance, int loss_kind,
                        float inv_rays, __nv_bfloat16* dO, float* ray_loss, __nv_bfloat16* dsig_out, int dsig_ld,
-                       float* w_out) {
+                       float* w_out, float* ray_out) {
     const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= n_rays) return;
@@ -446,6 +446,14 @@ __global__ void k_quad(const float* raw, const float* delta, const float* rays, 
         dA = 2.0f * da * inv_rays;
     }
     if (lane == 0) ray_loss[r] = loss;
+    if (ray_out && lane == 0) {  // per-ray C^, alpha^ and loss (test hook)
+        float* o = ray_out + 5 * (int64_t)r;
+        o[0] = C[0];
+        o[1] = C[1];
+        o[2] = C[2];
+        o[3] = alpha;
+        o[4] = loss;
+    }
     // d loss / d w_j, then d loss / d a_j
     float g[S], wg_local = 0.0f, actg_local = 0.0f, actnext_local = 0.0f;
 #pragma unroll
@@ -966,7 +974,7 @@ plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s, bool mask
 // k_quad for N samples per ray (one warp per ray, N / 32 samples per lane).
 // The paper architecture takes d loss / d sigma_raw in column 128 of dZc.
 cudaError_t launch_quad(plo_mlp* m, int N, const float* d_rays, const float* d_rgb_gt, const float* d_alpha_gt,
-                        int n_rays, int loss_kind, float* w_out, cudaStream_t s) {
+                        int n_rays, int loss_kind, float* w_out, cudaStream_t s, float* ray_out = nullptr) {
     const plo_mlp_desc& D = m->desc;
     const float inv_rays = 1.0f / (float)n_rays;
     const unsigned qblocks = (unsigned)((n_rays + 3) / 4);
@@ -974,7 +982,7 @@ cudaError_t launch_quad(plo_mlp* m, int N, const float* d_rays, const float* d_r
 #define PLO_QUAD(SS)                                                                                               \
     k_quad<16, SS><<<qblocks, 128, 0, s>>>(m->raw, m->delta, d_rays, d_rgb_gt, d_alpha_gt, n_rays, D.l_max, D.eps, \
                                            D.transmittance, loss_kind, inv_rays, m->dO, m->ray_loss, dsig, COMB_PAD, \
-                                           w_out)
+                                           w_out, ray_out)
     switch (N) {
         case 32: PLO_QUAD(1); break;
         case 64: PLO_QUAD(2); break;
@@ -1376,6 +1384,64 @@ extern "C" plo_status plo_mlp_check(const plo_mlp* m, void* stream) {
 
 extern "C" int64_t plo_mlp_step(const plo_mlp* m) { return m ? m->step : -1; }
 
+// ---------------------------------------------------------------- test hooks of the training step
+namespace plo {
+namespace {
+// d loss / d raw as fp32 [M][n_out] from the kernel's bf16 [M][64] (column 0
+// from the paper architecture's sigma column when dsig is given)
+__global__ void k_widen_grad(const __nv_bfloat16* dO, const __nv_bfloat16* dsig, int dsig_ld, int64_t M, int n_out,
+                             float* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * n_out) return;
+    const int64_t row = i / n_out;
+    const int c = (int)(i - row * n_out);
+    out[i] = __bfloat162float(c == 0 && dsig ? dsig[row * dsig_ld] : dO[row * OUT_PAD + c]);
+}
+}  // namespace
+}  // namespace plo
+
+extern "C" plo_status plo_mlp_get_activation(const plo_mlp* m, int32_t layer, void* d_out, int64_t n_rows,
+                                             void* stream) {
+    if (!m || !d_out) return set_error(PLO_ERR_INVALID_ARG, "mlp or output is NULL");
+    if (layer < 0 || layer >= m->n_layers) return set_error(PLO_ERR_INVALID_ARG, "layer out of range");
+    if (n_rows < 0 || n_rows > m->cap) return set_error(PLO_ERR_INVALID_ARG, "n_rows exceeds the stored batch");
+    if (n_rows == 0) return PLO_OK;
+    const size_t bytes = (size_t)n_rows * m->geom.in_pad[layer] * 2;
+    cudaError_t e = cudaMemcpyAsync(d_out, m->H[layer], bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    return e == cudaSuccess ? PLO_OK : cuda_error(e, "activation copy");
+}
+
+extern "C" plo_status plo_mlp_quad(plo_mlp* m, const float* d_rays, const float* d_raw, const float* d_delta,
+                                   const float* d_rgb_gt, const float* d_alpha_gt, int32_t n_rays, int32_t n_samples,
+                                   float* d_ray_out, float* d_draw, void* stream) {
+    if (!m) return set_error(PLO_ERR_INVALID_ARG, "mlp is NULL");
+    if (!d_rays || !d_raw || !d_delta || !d_rgb_gt || !d_alpha_gt || !d_ray_out)
+        return set_error(PLO_ERR_INVALID_ARG, "a buffer is NULL");
+    if (n_rays <= 0) return set_error(PLO_ERR_INVALID_ARG, "n_rays must be > 0");
+    if (n_samples != 32 && n_samples != 64 && n_samples != 96 && n_samples != 128 && n_samples != 192 &&
+        n_samples != 256)
+        return set_error(PLO_ERR_UNSUPPORTED, "n_samples must be 32, 64, 96, 128, 192 or 256");
+    const int64_t M = (int64_t)n_rays * n_samples;
+    if (M > ((int64_t)1 << 28)) return set_error(PLO_ERR_INVALID_ARG, "batch too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    plo_status st = ensure_workspace(m, M, n_rays);
+    if (st != PLO_OK) return st;
+    cudaError_t e = cudaMemcpy2DAsync(m->raw, OUT_PAD * 4, d_raw, (size_t)m->n_out * 4, (size_t)m->n_out * 4,
+                                      (size_t)M, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->delta, d_delta, (size_t)M * 4, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "quadrature input copy");
+    e = launch_quad(m, n_samples, d_rays, d_rgb_gt, d_alpha_gt, n_rays, m->desc.loss, nullptr, s, d_ray_out);
+    if (e != cudaSuccess) return cuda_error(e, "quadrature kernel launch");
+    if (d_draw) {
+        const __nv_bfloat16* dsig = m->arch == PLO_ARCH_PAPER ? m->dZc + FEAT : nullptr;
+        const int64_t total = M * m->n_out;
+        k_widen_grad<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(m->dO, dsig, COMB_PAD, M, m->n_out, d_draw);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_error(e, "gradient copy");
+    }
+    return PLO_OK;
+}
+
 // ---------------------------------------------------------------- raw GEMM entry points
 extern "C" plo_status plo_gemm_bf16(const void* d_A, const void* d_B, int32_t M, int32_t N, int32_t K,
                                     int32_t epilogue, const float* d_bias, const void* d_mask, uint32_t* d_bits,
@@ -1583,5 +1649,319 @@ extern "C" plo_status plo_distill(plo_mlp* m, int32_t depth, int32_t samples, fl
     } catch (const std::bad_alloc&) {
         if (out) *out = nullptr;
         return set_error(PLO_ERR_OOM, "host allocation during distillation failed");
+    }
+}
+
+// ---------------------------------------------------------------- checkpoints
+// File layout (little-endian):
+//   bytes 0..7    magic "PLOMLP01"
+//   bytes 8..15   uint64 length H of the header
+//   bytes 16..    the header: flat JSON object, ASCII, H bytes, with the
+//                 network description (arch, sh_degree, transmittance, loss,
+//                 total_steps, l_max, eps, lr0, lr1, init_radiance: floats
+//                 printed with 9 significant digits, which round-trips FP32;
+//                 seed as a decimal string), the step count and the blob table
+//   then the blobs, each starting at a multiple of 64 bytes from the file
+//   start: "master", "adam_m", "adam_v" (f32, n_params each, the canonical
+//   parameter order of plo_mlp_get_params) and "weights_bf16" (bf16, the
+//   trained weights W of every canonical block, no biases, the copies the
+//   forward pass multiplies with).
+// The jitter of the stratified samples is keyed by (seed, step), so the two
+// restore the sample stream of an interrupted run.
+namespace {
+
+constexpr char kCkptMagic[9] = "PLOMLP01";
+constexpr const char* kBlobNames[4] = {"master", "adam_m", "adam_v", "weights_bf16"};
+
+int64_t weight_count(int arch, int n_out) {
+    Block bl[MAX_LAYERS + 2];
+    const int nb = canonical_blocks(arch, n_out, bl);
+    int64_t c = 0;
+    for (int k = 0; k < nb; ++k) c += (int64_t)bl[k].rows * bl[k].cols;
+    return c;
+}
+
+std::string fmt_float(float v) {
+    char buf[48];
+    std::snprintf(buf, sizeof(buf), "%.9g", (double)v);
+    return buf;
+}
+
+// Value of "key" in the flat JSON header (number or string, without quotes).
+bool json_value(const std::string& h, const char* key, std::string& out) {
+    const std::string pat = std::string("\"") + key + "\":";
+    size_t p = h.find(pat);
+    if (p == std::string::npos) return false;
+    p += pat.size();
+    while (p < h.size() && h[p] == ' ') ++p;
+    if (p >= h.size()) return false;
+    if (h[p] == '"') {
+        size_t q = h.find('"', p + 1);
+        if (q == std::string::npos) return false;
+        out = h.substr(p + 1, q - p - 1);
+        return true;
+    }
+    size_t q = p;
+    while (q < h.size() && h[q] != ',' && h[q] != '}' && h[q] != ' ') ++q;
+    out = h.substr(p, q - p);
+    return !out.empty();
+}
+
+bool json_int(const std::string& h, const char* key, int64_t& v) {
+    std::string s;
+    if (!json_value(h, key, s)) return false;
+    char* end = nullptr;
+    const long long x = std::strtoll(s.c_str(), &end, 10);
+    if (!end || *end) return false;
+    v = x;
+    return true;
+}
+
+bool json_float(const std::string& h, const char* key, float& v) {
+    std::string s;
+    if (!json_value(h, key, s)) return false;
+    char* end = nullptr;
+    const float x = std::strtof(s.c_str(), &end);
+    if (!end || *end) return false;
+    v = x;
+    return true;
+}
+
+struct CkptHeader {
+    plo_mlp_desc desc;
+    int64_t step, n_params, n_weights;
+    int64_t off[4];  // blob offsets from the file start
+    int64_t data_end;
+};
+
+// Reads and checks the header (magic, keys, counts against the arch, blob
+// offsets and the file size); host only.
+plo_status read_ckpt_header(std::FILE* f, CkptHeader* out) {
+    char magic[8];
+    uint64_t hl = 0;
+    if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kCkptMagic, 8) != 0)
+        return set_error(PLO_ERR_INVALID_ARG, "not a plo network checkpoint (bad magic)");
+    if (std::fread(&hl, 8, 1, f) != 1 || hl == 0 || hl > (1u << 20))
+        return set_error(PLO_ERR_INVALID_ARG, "checkpoint header length is missing or out of range");
+    std::string h(hl, '\0');
+    if (std::fread(&h[0], 1, hl, f) != hl) return set_error(PLO_ERR_INVALID_ARG, "checkpoint header is truncated");
+    std::string fmt;
+    int64_t version = 0;
+    if (!json_value(h, "format", fmt) || fmt != "plo-mlp" || !json_int(h, "version", version) || version != 1)
+        return set_error(PLO_ERR_UNSUPPORTED, "unknown checkpoint format or version");
+    plo_mlp_desc d{};
+    int64_t arch, deg, trans, loss, total, step, np;
+    std::string seed;
+    if (!json_int(h, "arch", arch) || !json_int(h, "sh_degree", deg) || !json_int(h, "transmittance", trans) ||
+        !json_int(h, "loss", loss) || !json_int(h, "total_steps", total) || !json_float(h, "l_max", d.l_max) ||
+        !json_float(h, "eps", d.eps) || !json_float(h, "lr0", d.lr0) || !json_float(h, "lr1", d.lr1) ||
+        !json_float(h, "init_radiance", d.init_radiance) || !json_value(h, "seed", seed) ||
+        !json_int(h, "step", step) || !json_int(h, "n_params", np))
+        return set_error(PLO_ERR_INVALID_ARG, "checkpoint header lacks a required key");
+    d.arch = (int32_t)arch;
+    d.sh_degree = (int32_t)deg;
+    d.transmittance = (int32_t)trans;
+    d.loss = (int32_t)loss;
+    d.total_steps = (int32_t)total;
+    char* end = nullptr;
+    d.seed = std::strtoull(seed.c_str(), &end, 10);
+    if (seed.empty() || !end || *end) return set_error(PLO_ERR_INVALID_ARG, "checkpoint seed is not a decimal integer");
+    plo_status st = check_mlp_desc(&d);
+    if (st != PLO_OK) return st;
+    if (step < 0) return set_error(PLO_ERR_INVALID_ARG, "checkpoint step is negative");
+    const int n_out = 1 + 3 * (d.sh_degree + 1) * (d.sh_degree + 1);
+    if (np != canonical_count(d.arch, n_out))
+        return set_error(PLO_ERR_INVALID_ARG, "checkpoint n_params does not match its architecture");
+    const int64_t nw = weight_count(d.arch, n_out);
+    int64_t pos = 16 + (int64_t)hl;
+    for (int b = 0; b < 4; ++b) {
+        const std::string key = std::string(kBlobNames[b]) + "_offset";
+        int64_t o = 0;
+        if (!json_int(h, key.c_str(), o)) return set_error(PLO_ERR_INVALID_ARG, "checkpoint lacks a blob offset");
+        if (o < pos || o % 64 != 0) return set_error(PLO_ERR_INVALID_ARG, "checkpoint blob offsets are out of order");
+        out->off[b] = o;
+        pos = o + (b < 3 ? np * 4 : nw * 2);
+    }
+    if (std::fseek(f, 0, SEEK_END) != 0) return set_error(PLO_ERR_INVALID_ARG, "checkpoint is not seekable");
+    const long size = std::ftell(f);
+    if (size < 0 || (int64_t)size < pos) return set_error(PLO_ERR_INVALID_ARG, "checkpoint file is truncated");
+    out->desc = d;
+    out->step = step;
+    out->n_params = np;
+    out->n_weights = nw;
+    out->data_end = pos;
+    return PLO_OK;
+}
+
+// bf16 weights of the canonical blocks, gathered from the device copies
+plo_status download_bf16_weights(const plo_mlp* m, std::vector<uint16_t>& out) {
+    Block bl[MAX_LAYERS + 2];
+    const int nb = canonical_blocks(m->arch, m->n_out, bl);
+    const LayerGeom& g = m->geom;
+    out.clear();
+    for (int k = 0; k < nb; ++k) {
+        const Block& B = bl[k];
+        std::vector<uint16_t> pad((size_t)g.out_pad[B.layer] * g.in_pad[B.layer]);
+        cudaError_t e = cudaMemcpy(pad.data(), m->W[B.layer], pad.size() * 2, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_error(e, "bf16 weight download");
+        for (int o = 0; o < B.rows; ++o)
+            for (int i = 0; i < B.cols; ++i) out.push_back(pad[(size_t)(B.row0 + o) * g.in_pad[B.layer] + i]);
+    }
+    return PLO_OK;
+}
+
+plo_status save_mlp(const plo_mlp* m, const char* path) {
+    const int64_t np = canonical_count(m->arch, m->n_out);
+    std::vector<float> blobs[3];
+    const float* src[3] = {m->master, m->adam_m, m->adam_v};
+    for (int b = 0; b < 3; ++b) {
+        blobs[b].resize(np);
+        plo_status st = download_canonical(m, src[b], blobs[b].data(), np);
+        if (st != PLO_OK) return st;
+    }
+    std::vector<uint16_t> wb;
+    plo_status st = download_bf16_weights(m, wb);
+    if (st != PLO_OK) return st;
+    const plo_mlp_desc& d = m->desc;
+    // the header's length depends on the offsets it lists: fix the offsets
+    // for a header of at most 1 KiB of padding, then pad to that length
+    std::string h;
+    int64_t off[4];
+    for (int pass = 0; pass < 2; ++pass) {
+        int64_t pos = pass == 0 ? 0 : (int64_t)(16 + h.size() + 63) / 64 * 64;
+        for (int b = 0; b < 4; ++b) {
+            off[b] = pos;
+            pos = (pos + (b < 3 ? np * 4 : (int64_t)wb.size() * 2) + 63) / 64 * 64;
+        }
+        h = "{\"format\": \"plo-mlp\", \"version\": 1, \"arch\": " + std::to_string(d.arch) +
+            ", \"sh_degree\": " + std::to_string(d.sh_degree) + ", \"transmittance\": " +
+            std::to_string(d.transmittance) + ", \"loss\": " + std::to_string(d.loss) + ", \"total_steps\": " +
+            std::to_string(d.total_steps) + ", \"l_max\": " + fmt_float(d.l_max) + ", \"eps\": " + fmt_float(d.eps) +
+            ", \"lr0\": " + fmt_float(d.lr0) + ", \"lr1\": " + fmt_float(d.lr1) + ", \"init_radiance\": " +
+            fmt_float(d.init_radiance) + ", \"seed\": \"" + std::to_string((unsigned long long)d.seed) +
+            "\", \"step\": " + std::to_string(m->step) + ", \"n_params\": " + std::to_string(np);
+        for (int b = 0; b < 4; ++b)
+            h += std::string(", \"") + kBlobNames[b] + "_offset\": " + std::to_string(off[b] + (pass ? 0 : 100000000000LL));
+        h += "}";
+    }
+    // pass 0 used wide placeholder offsets, so the real header is no longer
+    const int64_t data0 = (int64_t)(16 + h.size() + 63) / 64 * 64;
+    if (off[0] < data0) return set_error(PLO_ERR_CUDA, "checkpoint header layout");  // cannot happen
+    std::FILE* f = std::fopen(path, "wb");
+    if (!f) return set_error(PLO_ERR_INVALID_ARG, std::string("cannot open checkpoint for writing: ") + path);
+    const uint64_t hl = h.size();
+    bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(&hl, 8, 1, f) == 1 &&
+              std::fwrite(h.data(), 1, h.size(), f) == h.size();
+    int64_t pos = 16 + (int64_t)h.size();
+    static const char zeros[64] = {};
+    for (int b = 0; b < 4 && ok; ++b) {
+        for (int64_t gap = off[b] - pos; gap > 0 && ok; gap -= 64) {
+            const size_t z = (size_t)(gap < 64 ? gap : 64);
+            ok = std::fwrite(zeros, 1, z, f) == z;
+        }
+        const size_t n = b < 3 ? (size_t)np : wb.size();
+        const size_t es = b < 3 ? 4 : 2;
+        const void* p = b < 3 ? (const void*)blobs[b].data() : (const void*)wb.data();
+        ok = ok && std::fwrite(p, es, n, f) == n;
+        pos = off[b] + (int64_t)(n * es);
+    }
+    ok = std::fclose(f) == 0 && ok;
+    return ok ? PLO_OK : set_error(PLO_ERR_INVALID_ARG, std::string("writing the checkpoint failed: ") + path);
+}
+
+}  // namespace
+
+extern "C" plo_status plo_mlp_save(const plo_mlp* m, const char* path) {
+    if (!m || !path) return set_error(PLO_ERR_INVALID_ARG, "mlp or path is NULL");
+    try {
+        return save_mlp(m, path);
+    } catch (const std::bad_alloc&) {
+        return set_error(PLO_ERR_OOM, "host allocation while saving the network failed");
+    }
+}
+
+extern "C" plo_status plo_mlp_checkpoint_info(const char* path, plo_mlp_desc* desc, int64_t* step) {
+    if (!path) return set_error(PLO_ERR_INVALID_ARG, "path is NULL");
+    std::FILE* f = std::fopen(path, "rb");
+    if (!f) return set_error(PLO_ERR_INVALID_ARG, std::string("cannot open checkpoint: ") + path);
+    CkptHeader hd{};
+    plo_status st;
+    try {
+        st = read_ckpt_header(f, &hd);
+    } catch (const std::bad_alloc&) {
+        st = set_error(PLO_ERR_OOM, "host allocation while reading the checkpoint failed");
+    }
+    std::fclose(f);
+    if (st != PLO_OK) return st;
+    if (desc) *desc = hd.desc;
+    if (step) *step = hd.step;
+    return PLO_OK;
+}
+
+namespace {
+plo_status load_mlp(const char* path, plo_mlp** out) {
+    std::FILE* f = std::fopen(path, "rb");
+    if (!f) return set_error(PLO_ERR_INVALID_ARG, std::string("cannot open checkpoint: ") + path);
+    CkptHeader hd{};
+    plo_status st = read_ckpt_header(f, &hd);
+    std::vector<float> blobs[3];
+    std::vector<uint16_t> wb;
+    for (int b = 0; b < 4 && st == PLO_OK; ++b) {
+        const size_t n = b < 3 ? (size_t)hd.n_params : (size_t)hd.n_weights;
+        void* p;
+        size_t es;
+        if (b < 3) {
+            blobs[b].resize(n);
+            p = blobs[b].data();
+            es = 4;
+        } else {
+            wb.resize(n);
+            p = wb.data();
+            es = 2;
+        }
+        if (std::fseek(f, (long)hd.off[b], SEEK_SET) != 0 || std::fread(p, es, n, f) != n)
+            st = set_error(PLO_ERR_INVALID_ARG, "checkpoint blob is truncated");
+    }
+    std::fclose(f);
+    if (st != PLO_OK) return st;
+    plo_mlp* m = nullptr;
+    st = plo_mlp_create(&hd.desc, 0, &m);
+    if (st != PLO_OK) return st;
+    std::vector<float> pad;
+    float* dst[3] = {m->master, m->adam_m, m->adam_v};
+    for (int b = 0; b < 3 && st == PLO_OK; ++b) {
+        canonical_to_padded(m, blobs[b].data(), pad);
+        cudaError_t e = cudaMemcpy(dst[b], pad.data(), pad.size() * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_error(e, "checkpoint upload");
+    }
+    if (st == PLO_OK) st = refresh_bf16(m, nullptr);
+    if (st == PLO_OK) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = cuda_error(e, "checkpoint upload");
+    }
+    // the bf16 copies are the rounding of the masters: a mismatch means the
+    // file's blobs do not belong together
+    std::vector<uint16_t> now;
+    if (st == PLO_OK) st = download_bf16_weights(m, now);
+    if (st == PLO_OK && now != wb)
+        st = set_error(PLO_ERR_INVALID_ARG, "checkpoint's bf16 weights are not the rounding of its FP32 masters");
+    if (st != PLO_OK) {
+        plo_mlp_free(m);
+        return st;
+    }
+    m->step = hd.step;
+    *out = m;
+    return PLO_OK;
+}
+}  // namespace
+
+extern "C" plo_status plo_mlp_load(const char* path, plo_mlp** out) {
+    if (!out) return set_error(PLO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!path) return set_error(PLO_ERR_INVALID_ARG, "path is NULL");
+    try {
+        return load_mlp(path, out);
+    } catch (const std::bad_alloc&) {
+        return set_error(PLO_ERR_OOM, "host allocation while loading the network failed");
     }
 }

@@ -29,6 +29,8 @@
 //           up to 16 (K=9: 64 B, K=16: 96 B).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <string>
 
@@ -52,9 +54,11 @@ inline int sh_stride_bytes(int K, int precision) {
 plo_status set_error(plo_status s, const std::string& msg);
 plo_status cuda_error(int err, const char* what);
 
-// Every device allocation of the library goes through here, so that tests
-// can make the n-th one fail (plo_debug_fail_alloc_after).
+// Every device allocation of the library goes through one of these two
+// (cudaMalloc, and cudaMallocAsync on a stream), so that tests can make the
+// n-th one fail (plo_debug_fail_alloc_after).
 int dev_malloc(void** p, size_t bytes);
+int dev_malloc_async(void** p, size_t bytes, cudaStream_t s);
 
 }  // namespace plo
 

@@ -269,8 +269,8 @@ extern "C" plo_status plo_pt_render(const plo_tree* lum, const plo_render_params
     const size_t per = 6 + 3 + 3 + 6 + 3 + 3 + 1 + 3 + 1;
     float* ws = nullptr;
     float* own_samples = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&ws, (size_t)chunk * per * 4, s);
-    if (e == cudaSuccess && !d_samples) e = cudaMallocAsync((void**)&own_samples, (size_t)total * 12, s);
+    cudaError_t e = (cudaError_t)dev_malloc_async((void**)&ws, (size_t)chunk * per * 4, s);
+    if (e == cudaSuccess && !d_samples) e = (cudaError_t)dev_malloc_async((void**)&own_samples, (size_t)total * 12, s);
     if (e != cudaSuccess) {
         if (ws) cudaFreeAsync(ws, s);
         return cuda_error(e, "path tracer workspace");

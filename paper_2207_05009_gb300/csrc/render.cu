@@ -123,9 +123,34 @@ __device__ __forceinline__ DF df_sub(DF a, DF b) {
     DF s = two_sum(a.hi, -b.hi);
     return fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo)));
 }
-__device__ __forceinline__ DF df_from_double(double x) {
-    const float hi = __double2float_rn(x);
-    return {hi, __double2float_rn(x - (double)hi)};
+// a * b exactly, as a double-float
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_mul_df(DF a, DF b) {
+    DF p = two_prod(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.lo, p.lo);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+// a / b (b.hi != 0): quotient of the high parts plus one correction step
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const DF r = df_sub(a, df_mul_df(b, DF{q1, 0.0f}));
+    return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+// sqrt(a) for a >= 0: one Newton correction of the FP32 root
+__device__ __forceinline__ DF df_sqrt(DF a) {
+    const float s = __fsqrt_rn(a.hi);
+    if (s == 0.0f) return {0.0f, 0.0f};
+    const float e = __fadd_rn(__fmaf_rn(-s, s, a.hi), a.lo);
+    return fast_two_sum(s, __fdiv_rn(e, __fmul_rn(2.0f, s)));
 }
 // (P - p) for an exact float plane P
 __device__ __forceinline__ DF df_from_plane(float P, DF p) {
@@ -380,23 +405,32 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
     }
     if (SPHERE) {
         // sphere proxy (Sec. 5): keep the part of [tn, tf] inside the ball
-        // |o + t d - c| <= r, solved once per ray in FP64 in world space
-        double a2 = 0.0, b = 0.0, q = 0.0;
+        // |o + t d - c| <= r, solved once per ray in world space with
+        // double-float arithmetic (about 44 significant bits; no FP64 on the
+        // device).  With oc = o - c: a t^2 + 2 b t + q = 0, a = d.d,
+        // b = oc.d, q = oc.oc - r^2; the root away from -b comes from
+        // m = -(b + sign(b) sqrt(b^2 - a q)) as m / a, the other as q / m, so
+        // neither subtracts nearly equal numbers.
+        DF a2 = {0.0f, 0.0f}, b = {0.0f, 0.0f}, q = {0.0f, 0.0f};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double oc = (double)o[a] - (double)kp.sphere[a], dd = (double)dw[a];
-            a2 += dd * dd;
-            b += oc * dd;
-            q += oc * oc;
+            const DF oc = two_sum(o[a], -kp.sphere[a]);
+            const DF dd = {dw[a], 0.0f};
+            a2 = df_add(a2, two_prod(dw[a], dw[a]));
+            b = df_add(b, df_mul_df(oc, dd));
+            q = df_add(q, df_mul_df(oc, oc));
         }
-        const double r = (double)kp.sphere[3];
-        const double disc = b * b - a2 * (q - r * r);
-        if (!(disc > 0.0)) {
+        q = df_sub(q, two_prod(kp.sphere[3], kp.sphere[3]));
+        const DF disc = df_sub(df_mul_df(b, b), df_mul_df(a2, q));
+        if (!(disc.hi > 0.0f || (disc.hi == 0.0f && disc.lo > 0.0f))) {
             ray_store(kp, i, R);
             return;
         }
-        const double sq = sqrt(disc);
-        const DF s0 = df_from_double((-b - sq) / a2), s1 = df_from_double((-b + sq) / a2);
+        const DF sq = df_sqrt(disc);
+        const DF m = df_neg(b.hi >= 0.0f ? df_add(b, sq) : df_sub(b, sq));
+        const DF r_far = df_div(m, a2), r_near = df_div(q, m);
+        const bool mneg = m.hi < 0.0f;
+        const DF s0 = mneg ? r_far : r_near, s1 = mneg ? r_near : r_far;
         if (df_less(tn, s0)) tn = s0;
         if (df_less(s1, tf)) tf = s1;
         if (!df_less(tn, tf) || !(tf.hi > 0.0f || (tf.hi == 0.0f && tf.lo > 0.0f))) {
@@ -907,7 +941,7 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     cudaStream_t cs = (cudaStream_t)stream;
     unsigned long long* cursor = nullptr;
     if (!TRACE && n >= DYNAMIC_MIN_RAYS) {
-        e = cudaMallocAsync((void**)&cursor, sizeof(unsigned long long), cs);
+        e = (cudaError_t)dev_malloc_async((void**)&cursor, sizeof(unsigned long long), cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), cs);
         if (e != cudaSuccess) {
             if (cursor) cudaFreeAsync(cursor, cs);
@@ -947,7 +981,7 @@ extern "C" plo_status plo_trace_rays(const plo_tree* tree, const float* d_rays, 
     if (n < 0) return set_error(PLO_ERR_INVALID_ARG, "n must be >= 0");
     if (n == 0) return PLO_OK;
     float* rgbT = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&rgbT, (size_t)n * 4 * sizeof(float), (cudaStream_t)stream);
+    cudaError_t e = (cudaError_t)dev_malloc_async((void**)&rgbT, (size_t)n * 4 * sizeof(float), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_error(e, "trace scratch allocation");
     plo_status st = render_common<true>(tree, d_rays, n, params, rgbT, rgbT + 3 * n, nullptr, max_cells, d_leaf,
                                         d_t, d_count, stream);
@@ -977,26 +1011,61 @@ extern "C" plo_status plo_lookup_points(const plo_tree* t, const float* d_points
 namespace {
 
 constexpr int64_t kNoAllocMaxRays = 262144;  // 10 floats per ray: 10 MiB in all
+// plo_render_rays takes a stream-ordered work counter from DYNAMIC_MIN_RAYS
+// rays up; every call of this path stays below that, so it never allocates.
+static_assert(kNoAllocMaxRays < DYNAMIC_MIN_RAYS,
+              "the allocation-free path must stay below the ray count at which plo_render_rays allocates");
 // rays [max][6], then rgb [max][3], then T [max].  Every GPU that loads the
 // library holds this array until the process exits.  All calls share it.
 __device__ __align__(256) float g_noalloc_stage[kNoAllocMaxRays * 10];
 
-constexpr int kNoAllocMaxDevices = 64;
+// Device addresses of the staging array, one per CUDA context seen: a new
+// primary context (after cudaDeviceReset, say) gets its own lookup instead
+// of a stale address.
+constexpr int kNoAllocMaxContexts = 64;
 std::mutex g_noalloc_mu;
-float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+void* g_noalloc_ctx[kNoAllocMaxContexts] = {};
+float* g_noalloc_ptr[kNoAllocMaxContexts] = {};
+int g_noalloc_used = 0;
 
-// Device address of the staging array on the current device (`dev`),
-// looked up once per device.  In host code g_noalloc_stage names a host-side
-// stand-in, never the device memory, so only this address may be used.
-plo_status noalloc_stage(int dev, float** out) {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+using CtxGetCurrentFn = int (*)(void**);  // cuCtxGetCurrent(CUcontext*)
+
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_stage);
-        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress of the no-allocation staging array");
-        g_noalloc_ptr[dev] = static_cast<float*>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    });
+    return fn;
+}
+
+// Device address of the staging array in the current context.  In host
+// code g_noalloc_stage names a host-side stand-in, never the device memory,
+// so only this address may be used.
+plo_status noalloc_stage(float** out) {
+    CtxGetCurrentFn get = ctx_get_current();
+    if (!get) return set_error(PLO_ERR_CUDA, "cuCtxGetCurrent is not available from the driver");
+    void* ctx = nullptr;
+    if (get(&ctx) != 0 || !ctx) return set_error(PLO_ERR_CUDA, "no current CUDA context");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    for (int k = 0; k < g_noalloc_used; ++k)
+        if (g_noalloc_ctx[k] == ctx) {
+            *out = g_noalloc_ptr[k];
+            return PLO_OK;
+        }
+    if (g_noalloc_used == kNoAllocMaxContexts)
+        return set_error(PLO_ERR_UNSUPPORTED, "too many CUDA contexts for the allocation-free path's table");
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_stage);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress of the no-allocation staging array");
+    g_noalloc_ctx[g_noalloc_used] = ctx;
+    g_noalloc_ptr[g_noalloc_used] = static_cast<float*>(p);
+    ++g_noalloc_used;
+    *out = static_cast<float*>(p);
     return PLO_OK;
 }
 
@@ -1016,12 +1085,10 @@ extern "C" plo_status plo_render_rays_host_noalloc(const plo_tree* tree, const f
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kNoAllocMaxDevices)
-        return set_error(PLO_ERR_UNSUPPORTED, "device index beyond the allocation-free path's table");
     if (dev != tree->device)
         return set_error(PLO_ERR_INVALID_ARG, "the tree lives on another device than the current one");
     float* base = nullptr;
-    plo_status st = noalloc_stage(dev, &base);
+    plo_status st = noalloc_stage(&base);
     if (st != PLO_OK) return st;
     float* d_rays = base;
     float* d_rgb = base + 6 * kNoAllocMaxRays;

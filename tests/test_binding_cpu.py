@@ -37,3 +37,62 @@ def test_host_render_checks_its_buffers_before_the_library():
 def test_device_render_rejects_host_rays():
     with pytest.raises(ValueError, match="CUDA"):
         plo.render(None, torch.zeros(8, 6))
+
+
+def test_device_render_rejects_rays_of_the_wrong_rank():
+    with pytest.raises(ValueError, match=r"\[n, 6\]"):
+        plo.render(None, torch.zeros(8, 2, 6))
+
+
+def test_batch_checks_its_buffers_against_the_ray_count():
+    b = plo.Batch.__new__(plo.Batch)  # no library handle: the checks run first
+    b.n_rays = 16
+    rays, rgb, T = torch.zeros(16, 6), torch.zeros(16, 3), torch.zeros(16)
+    with pytest.raises(ValueError, match="rays"):
+        b.render(torch.zeros(15, 6), rgb, T)
+    with pytest.raises(ValueError, match="rgb"):
+        b.capture(rays, torch.zeros(16, 4), T)
+    with pytest.raises(ValueError, match="T"):
+        b.autotune(rays, rgb, torch.zeros(16, dtype=torch.float64))
+    with pytest.raises(ValueError, match="status"):
+        b.render(rays, rgb, T, status=torch.zeros(16, dtype=torch.int64))
+    with pytest.raises(ValueError, match="CUDA"):  # right shapes, host memory
+        b.render(rays, rgb, T)
+
+
+def test_network_calls_check_their_buffers():
+    net = plo.Mlp.__new__(plo.Mlp)
+    rays, rgb, alpha = torch.zeros(64, 6), torch.zeros(64, 3), torch.zeros(64)
+    with pytest.raises(ValueError, match="points"):
+        net.forward(torch.zeros(10, 4))
+    with pytest.raises(ValueError, match="rgb_gt"):
+        net.train_step(rays, torch.zeros(63, 3), alpha)
+    with pytest.raises(ValueError, match="alpha_gt"):
+        net.train_step(rays, rgb, torch.zeros(64, 1))
+    with pytest.raises(ValueError, match="jitter"):
+        net.train_step(rays, rgb, alpha, n_samples=32, jitter=torch.zeros(64, 16))
+    with pytest.raises(ValueError, match="xi"):
+        plo.Mlp.train_step_hier(net, net, rays, rgb, alpha, n_coarse=64, n_fine=128, xi=torch.zeros(64, 64))
+
+
+def test_tensor_core_entry_points_check_their_buffers():
+    bf = torch.bfloat16
+    A, B = torch.zeros(128, 64, dtype=bf), torch.zeros(256, 64, dtype=bf)
+    with pytest.raises(ValueError, match="B"):
+        plo.gemm_bf16(A, torch.zeros(256, 32, dtype=bf), 1)
+    with pytest.raises(ValueError, match="bias"):
+        plo.gemm_bf16(A, B, 1, bias=torch.zeros(255))
+    with pytest.raises(ValueError, match="mask"):
+        plo.gemm_bf16(A, B, 2, mask=torch.zeros(128, 256))
+    with pytest.raises(ValueError, match="bits"):
+        plo.gemm_bf16(A, B, 0, bits=torch.zeros(128, 7, dtype=torch.int32))
+    with pytest.raises(ValueError, match="out"):
+        plo.gemm_bf16(A, B, 1, out=torch.zeros(128, 256, dtype=bf))
+    with pytest.raises(ValueError, match="dW"):
+        plo.wgrad_bf16(torch.zeros(64, 256, dtype=bf), torch.zeros(64, 64, dtype=bf), torch.zeros(64, 256))
+    with pytest.raises(ValueError, match="db"):
+        plo.wgrad_bf16(torch.zeros(64, 256, dtype=bf), torch.zeros(64, 64, dtype=bf), torch.zeros(256, 64),
+                       db=torch.zeros(64))
+    with pytest.raises(ValueError, match="delta"):
+        plo.hier_samples(torch.zeros(8, 6), torch.zeros(8, 64), torch.zeros(8, 63), torch.zeros(8, 64),
+                         torch.zeros(8, 128))

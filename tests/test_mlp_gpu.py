@@ -51,26 +51,109 @@ def cosine(a, b):
     return float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
 
 
-def test_forward_matches_oracle(torch_cuda):
+U32 = 2.0 ** -24  # unit roundoff of FP32
+
+
+def to_np(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def test_forward_layers_match_oracle_elementwise(torch_cuda):
+    """Every tensor-core layer of the forward pass, element by element: the
+    GPU's own bf16 input of layer l, times the bf16 weights, plus the FP32
+    bias, then ReLU, in FP64, against the GPU's bf16 output of that layer.
+    Bound: one bf16 rounding (2^-8 relative) plus FP32 accumulation over K
+    terms (K 2^-24 sum |w h|).  The encoded input is the bf16 rounding of the
+    FP32 sin / cos of the encoding (2^-8 relative plus 2^-23)."""
     torch = torch_cuda
     flat = random_params(1)
     net = plo.Mlp(l_max=8.0)
     net.set_params(flat)
     np.testing.assert_array_equal(net.get_params(), flat)
-    pts = np.random.default_rng(2).random((10_000, 3)).astype(np.float32)
+    n = 4096
+    pts = np.random.default_rng(2).random((n, 3)).astype(np.float32)
     raw = net.forward(torch.from_numpy(pts).cuda())
+    H = [to_np(net.activation(l, n)) for l in range(omlp.DEPTH + 1)]
     torch.cuda.synchronize()
     net.check()
-    raw = raw.cpu().numpy().astype(np.float64)
+    raw = to_np(raw)
     Ws, bs = unflatten(flat)
-    ref, _ = omlp.forward([bf16(w) for w in Ws], bs, omlp.positional_encoding(pts.astype(np.float64)))
-    assert cosine(raw.ravel(), ref.ravel()) > 0.999
-    assert np.linalg.norm(raw - ref) / np.linalg.norm(ref) < 3e-2
+    Wb = [bf16(w) for w in Ws]
+    pe = omlp.positional_encoding(pts.astype(np.float64))
+    assert np.all(H[0][:, 63] == 0)
+    assert np.all(np.abs(H[0][:, :63] - pe) <= 2.0 ** -8 * np.abs(pe) + 2 * U32)
+    for l in range(omlp.DEPTH):
+        h_in = H[l][:, :Wb[l].shape[1]]
+        ref = np.maximum(h_in @ Wb[l].T + bs[l], 0.0)
+        acc = Wb[l].shape[1] * U32 * (np.abs(h_in) @ np.abs(Wb[l]).T + np.abs(bs[l]))
+        err = np.abs(H[l + 1] - ref)
+        assert np.all(err <= 2.0 ** -8 * np.abs(ref) + acc * (1 + 2.0 ** -8)), (l, float((err - acc).max()))
+    ref = H[omlp.DEPTH] @ Wb[-1].T + bs[-1]
+    acc = 256 * U32 * (np.abs(H[omlp.DEPTH]) @ np.abs(Wb[-1]).T + np.abs(bs[-1]))
+    assert np.all(np.abs(raw - ref) <= acc + 1e-30)
+    # and end to end against the FP64 oracle that rounds what the network
+    # stores to bf16 (same precision decisions, independent of the GPU's
+    # intermediate values)
+    ref_b, _ = omlp.forward(Wb, bs, pe, storage="bf16")
+    assert cosine(raw.ravel(), ref_b.ravel()) > 0.9999
+    assert np.linalg.norm(raw - ref_b) / np.linalg.norm(ref_b) < 1e-2
+
+
+def quad_inputs(R, N, seed):
+    rng = np.random.default_rng(seed)
+    rays = plogen.rays_sphere(R, seed=seed)
+    raw = rng.normal(0.0, 1.0, (R * N, 49))
+    # sigma_raw, ReLU clipping the negative ones; a per-ray scale spreads the
+    # optical depth over ~0.02 .. 20, so rays range from clear to opaque
+    raw[:, 0] = rng.uniform(-2.0, 30.0, R * N) * np.repeat(10.0 ** rng.uniform(-3, 0, R), N)
+    delta = rng.uniform(0.2, 1.8, (R * N)) * (1.7 / N)
+    C_gt = rng.uniform(0.0, 5.0, (R, 3))
+    a_gt = rng.uniform(0.0, 1.0, R)
+    return rays, raw.astype(np.float32), delta.astype(np.float32), C_gt.astype(np.float32), a_gt.astype(np.float32)
+
+
+@pytest.mark.parametrize("loss,trans,N", [(plo.LOSS_PAPER, plo.TRANS_EXP, 64), (plo.LOSS_MSE, plo.TRANS_EXP, 128),
+                                          (plo.LOSS_PAPER, plo.TRANS_LINEAR, 32),
+                                          (plo.LOSS_REG, plo.TRANS_EXP, 256)])
+def test_quadrature_matches_oracle_per_ray(torch_cuda, loss, trans, N):
+    """The quadrature render and loss stage (k_quad) per ray and channel: C^
+    and alpha^ within 1e-4 relative, the loss within 1e-4 relative, and
+    d loss / d raw per element within one bf16 rounding (2^-8) plus 1e-4 of
+    the largest gradient of that ray and column, against the oracle's
+    composite / loss_terms / composite_backward on the same raw outputs and
+    segment lengths."""
+    torch = torch_cuda
+    R, l_max = 96, 6.0
+    rays, raw, delta, C_gt, a_gt = quad_inputs(R, N, seed=11 + N)
+    net = plo.Mlp(l_max=l_max, loss=loss, transmittance=trans)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ray_out, draw = net.quad(dev(rays), dev(raw), dev(delta), dev(C_gt), dev(a_gt), N)
+    torch.cuda.synchronize()
+    ray_out, draw = to_np(ray_out), to_np(draw)
+    kind = {plo.LOSS_PAPER: "paper", plo.LOSS_MSE: "mse", plo.LOSS_REG: "reg"}[loss]
+    tname = "exp" if trans == plo.TRANS_EXP else "linear"
+    Y = omlp.sh_matrix(rays[:, 3:].astype(np.float64), 3)
+    C, alpha, cache = omlp.composite(raw.astype(np.float64).reshape(R, N, 49), delta.astype(np.float64).reshape(R, N),
+                                     Y, l_max, tname)
+    per_ray, dC, dA = omlp.loss_terms(C, alpha, C_gt.astype(np.float64), a_gt.astype(np.float64), l_max, kind)
+    ref = omlp.composite_backward(cache, dC / R, dA / R).reshape(R * N, 49)
+    np.testing.assert_allclose(ray_out[:, :3], C, rtol=1e-4, atol=0)
+    np.testing.assert_allclose(ray_out[:, 3], alpha, rtol=1e-4, atol=1e-7)
+    np.testing.assert_allclose(ray_out[:, 4], per_ray, rtol=1e-4, atol=1e-7)
+    assert 0.05 < float(alpha.mean()) < 0.95  # both opaque and clear rays in the batch
+    scale = np.abs(ref.reshape(R, N, 49)).max(axis=1, keepdims=True)
+    tol = 2.0 ** -8 * np.abs(ref.reshape(R, N, 49)) + 1e-4 * scale
+    err = np.abs(draw.reshape(R, N, 49) - ref.reshape(R, N, 49))
+    assert np.all(err <= tol), float((err / np.maximum(tol, 1e-300)).max())
 
 
 @pytest.mark.parametrize("loss,trans", [(plo.LOSS_PAPER, plo.TRANS_EXP), (plo.LOSS_MSE, plo.TRANS_EXP),
                                         (plo.LOSS_PAPER, plo.TRANS_LINEAR)])
 def test_gradients_match_oracle(torch_cuda, loss, trans):
+    """A training step's gradients against the FP64 oracle that stores
+    activations and gradients in bf16 where the network does, on the GPU's
+    own encoded samples: per layer (weights and biases) within 1e-2 of the
+    layer's gradient norm, and the loss within 1e-3 relative."""
     torch = torch_cuda
     R, N = 64, 32
     flat = random_params(3, scale=0.5)
@@ -83,6 +166,7 @@ def test_gradients_match_oracle(torch_cuda, loss, trans):
     a_gt = rng.uniform(0, 1, R).astype(np.float32)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     loss_gpu = net.train_step(dev(rays), dev(C_gt), dev(a_gt), n_samples=N, jitter=dev(jit))
+    X = to_np(net.activation(0, R * N))[:, :63]
     torch.cuda.synchronize()
     net.check()
     g = net.get_grads().astype(np.float64)
@@ -91,21 +175,49 @@ def test_gradients_match_oracle(torch_cuda, loss, trans):
     tname = "exp" if trans == plo.TRANS_EXP else "linear"
     L, dWs, dbs, _ = omlp.train_loss_and_grads([bf16(w) for w in Ws], bs, rays, jit.astype(np.float64),
                                                C_gt.astype(np.float64), a_gt.astype(np.float64), 6.0, kind=kind,
-                                               transmittance=tname)
+                                               transmittance=tname, storage="bf16", X=X)
     ref = flatten(dWs, dbs)
-    assert float(loss_gpu.item()) == pytest.approx(L, rel=2e-2)
-    assert cosine(g, ref) > 0.999
-    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 1e-2 * 3
-    # every layer's gradient points the same way
+    # the oracle's activations are its own (bf16 roundings may fall on the
+    # other side of a boundary), so the loss agrees to ~1e-4, not to FP32
+    assert float(loss_gpu.item()) == pytest.approx(L, rel=1e-3)
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 1e-2
     i = 0
     for w, b in zip(dWs, dbs):
         n = w.size + b.size
-        assert cosine(g[i:i + n], ref[i:i + n]) > 0.99
+        assert np.linalg.norm(g[i:i + n] - ref[i:i + n]) <= 1e-2 * np.linalg.norm(ref[i:i + n]), i
         i += n
-    # the step moved the parameters by Adam's first update, ~lr * sign(g)
-    p1 = net.get_params()
-    moved = np.abs(p1 - flat)
-    assert moved.max() <= 5e-4 * 1.01 and moved.max() > 1e-4
+
+
+def test_adam_matches_oracle_over_steps(torch_cuda):
+    """Six training steps with the learning rate decaying over four (so the
+    last steps run at lr1): after each step the FP32 masters equal the
+    oracle's Adam (adam_update with lr_at) replayed on the gradients the GPU
+    used, element by element, within 2e-6 relative plus 2e-6 lr0 (FP32
+    moments and parameters against FP64)."""
+    torch = torch_cuda
+    R, N, total, lr0, lr1 = 64, 32, 4, 5e-4, 5e-6
+    flat = random_params(13, scale=0.5)
+    net = plo.Mlp(l_max=6.0, total_steps=total, lr0=lr0, lr1=lr1)
+    net.set_params(flat)
+    rng = np.random.default_rng(14)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    p = flat.astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for step in range(1, 7):
+        rays = plogen.rays_sphere(R, seed=40 + step)
+        jit = rng.random((R, N)).astype(np.float32)
+        C_gt = rng.uniform(0, 5, (R, 3)).astype(np.float32)
+        a_gt = rng.uniform(0, 1, R).astype(np.float32)
+        net.train_step(dev(rays), dev(C_gt), dev(a_gt), n_samples=N, jitter=dev(jit))
+        torch.cuda.synchronize()
+        g = net.get_grads().astype(np.float64)
+        p, m, v = omlp.adam_update(p, g, m, v, step, omlp.lr_at(step - 1, total, lr0, lr1))
+        got = net.get_params().astype(np.float64)
+        err = np.abs(got - p)
+        assert np.all(err <= 2e-6 * np.abs(p) + 2e-6 * lr0), (step, float(err.max()))
+    assert net.step == 6
+    assert omlp.lr_at(5, total, lr0, lr1) == pytest.approx(lr1)
 
 
 def gt_batches(torch, n_batches, R=4096, seed0=100):

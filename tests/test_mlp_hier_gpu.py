@@ -55,6 +55,26 @@ def dev(torch, a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+U32 = 2.0 ** -24  # unit roundoff of FP32
+
+
+def to_np(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def layer_ok(h_out, h_in, W, b, relu=True, rounded=True):
+    """One tensor-core layer element by element: FP64 product of the GPU's
+    own bf16 input and the bf16 weights plus the FP32 bias (ReLU'd), against
+    the GPU's output; bound one bf16 rounding (if stored in bf16) plus FP32
+    accumulation over K terms."""
+    ref = h_in @ W.T + b
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    acc = W.shape[1] * U32 * (np.abs(h_in) @ np.abs(W).T + np.abs(b))
+    tol = (2.0 ** -8 * np.abs(ref) + acc * (1 + 2.0 ** -8)) if rounded else acc + 1e-30
+    return bool(np.all(np.abs(h_out - ref) <= tol))
+
+
 def test_paper_arch_param_layout_and_forward(torch_cuda):
     torch = torch_cuda
     flat = paper_params(1)
@@ -62,17 +82,29 @@ def test_paper_arch_param_layout_and_forward(torch_cuda):
     assert net.n_params == flat.size
     net.set_params(flat)
     np.testing.assert_array_equal(net.get_params(), flat)
-    pts = np.random.default_rng(2).random((10_000, 3)).astype(np.float32)
+    n = 4096
+    pts = np.random.default_rng(2).random((n, 3)).astype(np.float32)
     raw = net.forward(dev(torch, pts))
+    H = [to_np(net.activation(l, n)) for l in range(omlp.DEPTH + 2)]
     torch.cuda.synchronize()
     net.check()
-    raw = raw.cpu().numpy().astype(np.float64)
+    raw = to_np(raw)
     Ws, bs = unflatten(flat)
-    ref, _ = omlp.forward_paper([bf16(w) for w in Ws], bs, omlp.positional_encoding(pts.astype(np.float64)))
+    Wb = [bf16(w) for w in Ws]
+    D = omlp.DEPTH
+    # every layer element by element on the GPU's own inputs: the trunk,
+    # sigma (FP32, from h8), the 128-wide layer (bf16, ReLU), the SH layer
+    for l in range(D):
+        assert layer_ok(H[l + 1], H[l][:, :Wb[l].shape[1]], Wb[l], bs[l]), l
+    assert layer_ok(raw[:, :1], H[D], Wb[D], bs[D], relu=False, rounded=False)
+    assert layer_ok(H[D + 1], H[D], Wb[D + 1], bs[D + 1])
+    assert layer_ok(raw[:, 1:], H[D + 1], Wb[D + 2], bs[D + 2], relu=False, rounded=False)
+    # end to end against the oracle that stores activations in bf16
+    ref, _ = omlp.forward_paper(Wb, bs, omlp.positional_encoding(pts.astype(np.float64)), storage="bf16")
     for cols in (slice(0, 1), slice(1, 49)):  # sigma, then the SH coefficients
         a, b = raw[:, cols].ravel(), ref[:, cols].ravel()
-        assert cosine(a, b) > 0.999
-        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 3e-2
+        assert cosine(a, b) > 0.9999
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-2
 
 
 @pytest.mark.parametrize("loss,trans", [(plo.LOSS_PAPER, plo.TRANS_EXP), (plo.LOSS_PAPER, plo.TRANS_LINEAR)])
@@ -89,6 +121,7 @@ def test_paper_arch_gradients_match_oracle(torch_cuda, loss, trans):
     a_gt = rng.uniform(0, 1, R).astype(np.float32)
     loss_gpu = net.train_step(dev(torch, rays), dev(torch, C_gt), dev(torch, a_gt), n_samples=N,
                               jitter=dev(torch, jit))
+    X = to_np(net.activation(0, R * N))[:, :63]
     torch.cuda.synchronize()
     net.check()
     g = net.get_grads().astype(np.float64)
@@ -96,15 +129,14 @@ def test_paper_arch_gradients_match_oracle(torch_cuda, loss, trans):
     tname = "exp" if trans == plo.TRANS_EXP else "linear"
     L, dWs, dbs, _ = omlp.train_loss_and_grads([bf16(w) for w in Ws], bs, rays, jit.astype(np.float64),
                                                C_gt.astype(np.float64), a_gt.astype(np.float64), 6.0,
-                                               transmittance=tname, arch="paper")
+                                               transmittance=tname, arch="paper", storage="bf16", X=X)
     ref = flatten(dWs, dbs)
-    assert float(loss_gpu.item()) == pytest.approx(L, rel=2e-2)
-    assert cosine(g, ref) > 0.999
-    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 3e-2
+    assert float(loss_gpu.item()) == pytest.approx(L, rel=1e-3)
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 1e-2
     i = 0
     for w, b in zip(dWs, dbs):  # every block, including sigma, the 128 layer and the SH layer
         n = w.size + b.size
-        assert cosine(g[i:i + n], ref[i:i + n]) > 0.99
+        assert np.linalg.norm(g[i:i + n] - ref[i:i + n]) <= 1e-2 * np.linalg.norm(ref[i:i + n]), i
         i += n
 
 
@@ -170,6 +202,8 @@ def test_coarse_fine_step_matches_oracle(torch_cuda, trans):
     a_gt = rng.uniform(0, 1, R).astype(np.float32)
     loss_gpu = plo.Mlp.train_step_hier(coarse, fine, dev(torch, rays), dev(torch, C_gt), dev(torch, a_gt),
                                        n_coarse=NC, n_fine=NF, jitter=dev(torch, jit), xi=dev(torch, xi))
+    Xc = to_np(coarse.activation(0, R * NC))[:, :63]
+    Xf = to_np(fine.activation(0, R * (NC + NF)))[:, :63]
     torch.cuda.synchronize()
     coarse.check()
     fine.check()
@@ -177,15 +211,22 @@ def test_coarse_fine_step_matches_oracle(torch_cuda, trans):
     Wc, bc = unflatten(fc)
     Wf, bf = unflatten(ff)
     tname = "exp" if trans == plo.TRANS_EXP else "linear"
+    # both passes on the GPU's own encoded samples (the fine ones follow the
+    # GPU's coarse weights), activations stored in bf16 as the network does
     L, (dWc, dbc), (dWf, dbf), ex = omlp.train_loss_and_grads_hier(
         [bf16(w) for w in Wc], bc, [bf16(w) for w in Wf], bf, rays, jit.astype(np.float64), xi.astype(np.float64),
-        C_gt.astype(np.float64), a_gt.astype(np.float64), 6.0, transmittance=tname)
-    assert float(loss_gpu.item()) == pytest.approx(L, rel=3e-2)
-    rc, rf = flatten(dWc, dbc), flatten(dWf, dbf)
-    assert cosine(gc, rc) > 0.999
-    # the fine samples follow the coarse weights of the bf16 network, so the
-    # fine network sees slightly moved samples
-    assert cosine(gf, rf) > 0.99
+        C_gt.astype(np.float64), a_gt.astype(np.float64), 6.0, transmittance=tname, storage="bf16", X_coarse=Xc,
+        X_fine=Xf)
+    # the oracle's fine segment lengths follow its own coarse weights, which
+    # differ from the GPU's by bf16 roundings: the loss agrees to ~1e-3
+    assert float(loss_gpu.item()) == pytest.approx(L, rel=3e-3)
+    for g, (dWs, dbs) in ((gc, (dWc, dbc)), (gf, (dWf, dbf))):
+        ref = flatten(dWs, dbs)
+        i = 0
+        for w, b in zip(dWs, dbs):
+            n = w.size + b.size
+            assert np.linalg.norm(g[i:i + n] - ref[i:i + n]) <= 1e-2 * np.linalg.norm(ref[i:i + n]), i
+            i += n
     assert coarse.step == 1 and fine.step == 1
 
 

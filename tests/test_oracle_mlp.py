@@ -353,3 +353,72 @@ def test_hier_gradients_match_central_differences(seed, trans):
                 done += 1
                 checks += 1
     assert checks == 20
+
+
+def test_adam_accumulates_moments_over_steps():
+    """Closed forms of Adam's moments (Kingma & Ba, Algorithm 1) over several
+    steps: with a constant gradient g the bias-corrected moments are g and
+    g^2 at every step, so each step moves lr g / (|g| + eps); with a gradient
+    of alternating sign (-1)^t g the first moment is the geometric sum
+    (1 - b1) g (-1)^t (1 - (-b1)^t) / (1 + b1)."""
+    b1, b2, eps = 0.9, 0.999, 1e-8
+    g = np.array([0.3, -2.0, 1e-3, 5e-9])
+    p, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    for t in range(1, 8):
+        lr = mlp.lr_at(t - 1, 4)
+        p_new, m, v = mlp.adam_update(p, g, m, v, t, lr)
+        np.testing.assert_allclose(p - p_new, lr * g / (np.abs(g) + eps), rtol=1e-9)
+        np.testing.assert_allclose(m, g * (1 - b1 ** t), rtol=1e-12)
+        np.testing.assert_allclose(v, g * g * (1 - b2 ** t), rtol=1e-12)
+        p = p_new
+    m, v = np.zeros(4), np.zeros(4)
+    p = np.zeros(4)
+    for t in range(1, 9):
+        gt = (-1.0) ** t * g
+        p_new, m, v = mlp.adam_update(p, gt, m, v, t, 1e-3)
+        m_ref = (1 - b1) * g * (-1.0) ** t * (1 - (-b1) ** t) / (1 + b1)
+        np.testing.assert_allclose(m, m_ref, rtol=1e-12)
+        mh, vh = m_ref / (1 - b1 ** t), g * g
+        np.testing.assert_allclose(p - p_new, 1e-3 * mh / (np.sqrt(vh) + eps), rtol=1e-9)
+        p = p_new
+    # the schedule reaches lr1 at total_steps and stays there
+    assert mlp.lr_at(4, 4) == pytest.approx(5e-6) and mlp.lr_at(9, 4) == pytest.approx(5e-6)
+
+
+def test_bf16_rounding_pins():
+    """round_bf16: 8 significant bits, nearest with ties to even; values
+    already in bf16 are unchanged; the error is at most half a unit in the
+    last place (2^-8 relative)."""
+    exact = np.array([1.0, 1.5, -3.0, 2.0 ** -100, 0.0, 1.0 + 2 ** -7, 65280.0])
+    np.testing.assert_array_equal(mlp.round_bf16(exact), exact)
+    u = 2.0 ** -7  # spacing of bf16 in [1, 2)
+    cases = {1 + u / 2: 1.0, 1 + 1.5 * u: 1 + 2 * u, 1 + u / 2 + 2 ** -20: 1 + u, -(1 + u / 2): -1.0,
+             1 + 0.49 * u: 1.0, 2 + u: 2.0, 2 + 3 * u: 2 + 4 * u}
+    for x, want in cases.items():
+        assert mlp.round_bf16(np.array([x]))[0] == want, x
+    x = np.random.default_rng(0).normal(0, 10, 100_000)
+    r = mlp.round_bf16(x)
+    assert np.all(np.abs(r - x) <= 2.0 ** -8 * np.abs(x) * (1 + 1e-6))
+    bits = r.astype(np.float32).view(np.uint32)
+    assert np.all(bits & 0xFFFF == 0)
+
+
+def test_bf16_storage_rounds_only_what_the_network_stores():
+    """Under storage='bf16' every stored activation is a bf16 value, the raw
+    outputs are not rounded, the masks are the signs of the unrounded
+    pre-activations, and the result stays within bf16 error of FP64."""
+    rng = np.random.default_rng(3)
+    Ws, bs = mlp.init_params(rng)
+    X = mlp.positional_encoding(rng.random((64, 3)))
+    masks = []
+    raw_b, H_b = mlp.forward(Ws, bs, X, storage="bf16", masks=masks)
+    raw_f, H_f = mlp.forward(Ws, bs, X)
+    for h in H_b:
+        np.testing.assert_array_equal(h, mlp.round_bf16(h))
+    h = mlp.round_bf16(X)
+    for l in range(mlp.DEPTH):
+        z = h @ Ws[l].T + bs[l]
+        np.testing.assert_array_equal(masks[l], z > 0)
+        h = mlp.round_bf16(np.maximum(z, 0))
+    np.testing.assert_array_equal(raw_b, h @ Ws[-1].T + bs[-1])
+    assert np.linalg.norm(raw_b - raw_f) / np.linalg.norm(raw_f) < 2e-2
