@@ -281,7 +281,8 @@ def run_variants(plo, torch, tree32, rays, rgb, T, timed, rays_total):
     cases = {"exp": P(), "linear": P(transmittance=plo.TRANS_LINEAR),
              "exp_heuristics": P.paper_heuristics(),
              "linear_heuristics": P.paper_heuristics(transmittance=plo.TRANS_LINEAR),
-             "exp_sphere_r0.5": P(sphere=(0.5, 0.5, 0.5, 0.5))}
+             "exp_sphere_r0.5": P(sphere=(0.5, 0.5, 0.5, 0.5)),
+             "exp_tstop_1e-4": P(t_stop=1e-4)}
     exact = {"exp": outputs(cases["exp"]), "linear": outputs(cases["linear"])}
     out = {}
     for name, p in cases.items():
@@ -504,6 +505,8 @@ def main():
     out32 = (rgb[: args.cpu_sample].cpu().numpy(), T[: args.cpu_sample].cpu().numpy())
     plo.render(trees["fp16"], rays, params, rgb=rgb, T=T)
     out16 = (rgb[: args.cpu_sample].cpu().numpy(), T[: args.cpu_sample].cpu().numpy())
+    plo.render(trees["bf16"], rays, params, rgb=rgb, T=T)
+    outb16 = (rgb[: args.cpu_sample].cpu().numpy(), T[: args.cpu_sample].cpu().numpy())
     torch.cuda.synchronize()
 
     if rank != 0:
@@ -525,11 +528,27 @@ def main():
         cpu_s = time.perf_counter() - tc
         cpu = {"value": sample / cpu_s / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {sample} rays of the {n}-ray wavefront ({cpu_s:.1f} s)"}
+        # the same oracle on one thread, and on the 65,536-ray depth-6 set
+        one = min(sample, 1 << 14)
+        tc = time.perf_counter()
+        oracle.render(tree, rays_np[:one], n_threads=1)
+        cpu["one_thread"] = {"value": one / (time.perf_counter() - tc) / 1e6, "unit": UNIT, "cores": 1,
+                             "sample": f"first {one} rays of the wavefront"}
+        import plogen
+        tree6, rays6 = plogen.luminaire_tree(plogen.LUMINAIRE_D6), plogen.rays_sphere(65536, seed=1)
+        tc = time.perf_counter()
+        oracle.render(tree6, rays6, n_threads=cores)
+        cpu["depth6_65536_rays"] = {"value": 65536 / (time.perf_counter() - tc) / 1e6, "unit": UNIT,
+                                    "cores": cores, "sample": "all 65,536 rays of the depth-6 (SH degree 2) set"}
         leaf_visits = float(ref["n_leaf"].mean())
         sh_visits = float(ref["n_sh"].mean())
         cells = float(ref["n_cell"].mean())
+        # [radiance, T] max errors against the FP64 oracle on FP32 leaves
         parity = {"sample_rays": sample, "fp32_max_rel_err": rel_errors(*out32, ref),
-                  "fp16_max_rel_err": rel_errors(*out16, ref)}
+                  "fp16_max_rel_err": rel_errors(*out16, ref),
+                  "bf16_max_rel_err": rel_errors(*outb16, ref),
+                  "metric": "[radiance, T]: |g - o| / sum_i w_i sum_k |c_k Y_k| per channel, "
+                            "|T_g - T_o| / max(T_o, 1e-3)"}
     else:
         leaf_visits = sh_visits = cells = float("nan")
         parity = None

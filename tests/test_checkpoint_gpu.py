@@ -1,0 +1,83 @@
+"""Checkpoint and resume of a training run (plo_mlp_save / plo_mlp_load):
+ten steps, save, load into a fresh network, ten more steps, against twenty
+uninterrupted steps.  The sample jitter is drawn from (seed, step) in both
+runs, so the resumed run also checks that the random stream is restored."""
+import numpy as np
+import pytest
+
+import paper_2207_05009_gb300 as plo
+import plogen
+from tests import ckpt_format
+
+pytestmark = pytest.mark.gpu
+
+LR0 = 5e-4
+
+
+def batches(torch, n, R=64, seed=70):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        rays = torch.from_numpy(plogen.rays_sphere(R, seed=seed + k)).cuda()
+        C = torch.from_numpy(rng.uniform(0, 5, (R, 3)).astype(np.float32)).cuda()
+        a = torch.from_numpy(rng.uniform(0, 1, R).astype(np.float32)).cuda()
+        out.append((rays, C, a))
+    return out
+
+
+@pytest.mark.parametrize("arch", [plo.ARCH_LINEAR_HEAD, plo.ARCH_PAPER])
+def test_resume_matches_uninterrupted_training(cuda_available, tmp_path, arch):
+    import torch
+    data = batches(torch, 20)
+    kw = dict(l_max=6.0, total_steps=15, seed=3, jitter_seed=9, init_radiance=1.5, arch=arch, lr0=LR0)
+    straight = plo.Mlp(**kw)
+    for rays, C, a in data:
+        straight.train_step(rays, C, a, n_samples=32)
+    first = plo.Mlp(**kw)
+    for rays, C, a in data[:10]:
+        first.train_step(rays, C, a, n_samples=32)
+    path10 = str(tmp_path / "step10.plomlp")
+    first.save(path10)
+    desc, step = plo.checkpoint_info(path10)
+    assert step == 10 and desc["arch"] == arch and desc["seed"] == 9
+    first.free()
+    resumed = plo.Mlp.load(path10)
+    assert resumed.step == 10
+    for rays, C, a in data[10:]:
+        resumed.train_step(rays, C, a, n_samples=32)
+    torch.cuda.synchronize()
+    straight.check()
+    resumed.check()
+    assert resumed.step == 20
+    p_s, p_r = straight.get_params(), resumed.get_params()
+    # weight gradients are summed with float atomics, so the two runs may
+    # differ in the last bits; a lost Adam moment, step count or jitter
+    # stream moves parameters by ~lr0 instead
+    assert np.abs(p_s - p_r).max() <= 1e-3 * LR0
+    a_path, b_path = str(tmp_path / "a.plomlp"), str(tmp_path / "b.plomlp")
+    straight.save(a_path)
+    resumed.save(b_path)
+    (ha, ba), (hb, bb) = ckpt_format.read(a_path), ckpt_format.read(b_path)
+    assert ha["step"] == hb["step"] == 20
+    for name in ("adam_m", "adam_v"):
+        np.testing.assert_allclose(bb[name], ba[name], rtol=1e-4, atol=1e-6 * np.abs(ba[name]).max())
+    np.testing.assert_array_equal(bb["master"], p_r)
+
+
+def test_load_rejects_weights_that_do_not_match_the_masters(cuda_available, tmp_path):
+    import torch
+    net = plo.Mlp(l_max=6.0, init_radiance=1.5)
+    rays, C, a = batches(torch, 1)[0]
+    net.train_step(rays, C, a, n_samples=32)
+    good = str(tmp_path / "good.plomlp")
+    net.save(good)
+    head, blobs = ckpt_format.read(good)
+    data = bytearray(open(good, "rb").read())
+    o = head["weights_bf16_offset"] + 2 * 1000
+    data[o] ^= 0x40  # flip a bit of one bf16 weight
+    bad = str(tmp_path / "bad.plomlp")
+    open(bad, "wb").write(bytes(data))
+    with pytest.raises(plo.PloError, match="bf16"):
+        plo.Mlp.load(bad)
+    again = plo.Mlp.load(good)
+    np.testing.assert_array_equal(again.get_params(), net.get_params())

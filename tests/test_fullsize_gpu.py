@@ -21,7 +21,7 @@ import bench
 import oracle
 import paper_2207_05009_gb300 as plo
 import plogen
-from tests.parity import RTOL_FP16, RTOL_FP32, assert_radiance_close, quantise_tree
+from tests.parity import RTOL_BF16, RTOL_FP16, RTOL_FP32, assert_radiance_close, quantise_tree
 
 pytestmark = pytest.mark.gpu
 
@@ -79,8 +79,8 @@ def test_16bit_leaves_depth6_on_16m_rays(room_rays):
         g_rgb, g_T = rgb[sel].cpu().numpy(), T[sel].cpu().numpy()
         ref_q = oracle.render(quantise_tree(tree, name), rays_np[idx], n_threads=CORES)
         assert_radiance_close(g_rgb, g_T, ref_q, RTOL_FP32, what=f"{name} leaves vs dequantised oracle")
-        if name == "fp16":
-            assert_radiance_close(g_rgb, g_T, ref, RTOL_FP16, what="fp16 leaves vs FP32-leaf oracle")
+        rtol = RTOL_FP16 if name == "fp16" else RTOL_BF16
+        assert_radiance_close(g_rgb, g_T, ref, rtol, what=f"{name} leaves vs FP32-leaf oracle")
 
 
 def test_batch_of_8_luminaires_full_size(cuda_available):

@@ -7,7 +7,7 @@ import oracle
 import paper_2207_05009_gb300 as plo
 import plogen
 from plogen import HostTree
-from tests.parity import COND_ETA_LINEAR, RTOL_FP16, RTOL_FP32, assert_radiance_close, quantise_tree
+from tests.parity import COND_ETA_LINEAR, RTOL_BF16, RTOL_FP16, RTOL_FP32, assert_radiance_close, quantise_tree
 from tests.trees import random_tree, uniform_tree
 
 pytestmark = pytest.mark.gpu
@@ -195,8 +195,8 @@ def test_16bit_leaves(torch_cuda, d6, prec, name):
     assert_radiance_close(g_rgb, g_T, ref_q, RTOL_FP32, what=f"{name} vs dequantised oracle")
     # storage error: the oracle on the original FP32 leaves
     ref = oracle.render(d6, rays)
-    if name == "fp16":
-        assert_radiance_close(g_rgb, g_T, ref, RTOL_FP16, what="fp16 vs FP32-leaf oracle")
+    rtol = RTOL_FP16 if name == "fp16" else RTOL_BF16
+    assert_radiance_close(g_rgb, g_T, ref, rtol, what=f"{name} vs FP32-leaf oracle")
 
 
 def test_lookup_bit_exact(torch_cuda, d6):
