@@ -514,15 +514,6 @@ class Mlp:
         return ray_out, draw
 
 
-def checkpoint_info(path: str) -> tuple[dict, int]:
-    """plo_mlp_checkpoint_info: (network description, step) of a checkpoint
-    file, read on the host without a GPU."""
-    lib = mlp_lib()
-    desc = MlpDesc()
-    step = ctypes.c_int64()
-    _check(lib.plo_mlp_checkpoint_info(os.fsencode(path), ctypes.byref(desc), ctypes.byref(step)))
-    return {k: getattr(desc, k) for k, _ in MlpDesc._fields_}, int(step.value)
-
     def free(self):
         if getattr(self, "_h", None) and self._h.value:
             mlp_lib().plo_mlp_free(self._h)
@@ -533,6 +524,16 @@ def checkpoint_info(path: str) -> tuple[dict, int]:
             self.free()
         except Exception:
             pass
+
+
+def checkpoint_info(path: str) -> tuple[dict, int]:
+    """plo_mlp_checkpoint_info: (network description, step) of a checkpoint
+    file, read on the host without a GPU."""
+    lib = mlp_lib()
+    desc = MlpDesc()
+    step = ctypes.c_int64()
+    _check(lib.plo_mlp_checkpoint_info(os.fsencode(path), ctypes.byref(desc), ctypes.byref(step)))
+    return {k: getattr(desc, k) for k, _ in MlpDesc._fields_}, int(step.value)
 
 
 def gemm_bf16(A, B, epilogue: int, bias=None, mask=None, out=None, err=None, bits=None, stream=None):

@@ -414,7 +414,9 @@ __global__ void k_quad(const float* raw, const float* delta, const float* rays, 
     for (int s = 0; s < S; ++s) {
         cum += a[s];
         T[s + 1] = lin ? fmaxf(0.0f, 1.0f - cum) : expf(-cum);
-        w[s] = T[s] - T[s + 1];
+        // w = T_j - T_{j+1} in a form that does not cancel when sigma delta
+        // is small: T_j (1 - e^{-a_j}) (exponential), min(T_j, a_j) (linear)
+        w[s] = lin ? fminf(T[s], a[s]) : T[s] * -expm1f(-a[s]);
     }
     float C[3] = {0.0f, 0.0f, 0.0f}, alpha = 0.0f;
 #pragma unroll

@@ -96,3 +96,11 @@ def test_tensor_core_entry_points_check_their_buffers():
     with pytest.raises(ValueError, match="delta"):
         plo.hier_samples(torch.zeros(8, 6), torch.zeros(8, 64), torch.zeros(8, 63), torch.zeros(8, 64),
                          torch.zeros(8, 128))
+
+
+def test_network_handle_class_keeps_its_methods():
+    # the class must keep free / __del__ (a module-level function defined in
+    # the middle of the class once swallowed them)
+    for name in ("free", "__del__", "save", "load", "quad", "activation", "train_step", "distill"):
+        assert callable(getattr(plo.Mlp, name)), name
+    assert callable(plo.checkpoint_info)

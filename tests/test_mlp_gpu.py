@@ -141,10 +141,23 @@ def test_quadrature_matches_oracle_per_ray(torch_cuda, loss, trans, N):
     np.testing.assert_allclose(ray_out[:, 3], alpha, rtol=1e-4, atol=1e-7)
     np.testing.assert_allclose(ray_out[:, 4], per_ray, rtol=1e-4, atol=1e-7)
     assert 0.05 < float(alpha.mean()) < 0.95  # both opaque and clear rays in the batch
-    scale = np.abs(ref.reshape(R, N, 49)).max(axis=1, keepdims=True)
-    tol = 2.0 ** -8 * np.abs(ref.reshape(R, N, 49)) + 1e-4 * scale
-    err = np.abs(draw.reshape(R, N, 49) - ref.reshape(R, N, 49))
-    assert np.all(err <= tol), float((err / np.maximum(tol, 1e-300)).max())
+    ref3 = ref.reshape(R, N, 49)
+    tol = 2.0 ** -8 * np.abs(ref3) + 1e-5 * np.abs(ref3).max(axis=1, keepdims=True)
+    # d loss / d sigma_j is a difference of FP32 prefix / suffix sums (exp:
+    # T_{j+1} g_j - sum_{k>j} w_k g_k; linear: sums of g_k over the samples
+    # where T is positive): its FP32 error scales with the sums' magnitude
+    g_w = np.einsum("rnc,rc->rn", cache["c"], dC / R) + (dA / R)[:, None]
+    wg = np.abs(cache["w"] * g_w)
+    suffix = np.flip(np.cumsum(np.flip(wg, 1), 1), 1) - wg
+    if tname == "exp":
+        cancel = cache["T"][:, 1:] * np.abs(g_w) + suffix
+    else:
+        cancel = np.flip(np.cumsum(np.flip(np.abs(g_w), 1), 1), 1)
+    tol[..., 0] += 1e-5 * cancel * delta.astype(np.float64).reshape(R, N)
+    err = np.abs(draw.reshape(R, N, 49) - ref3)
+    bad = np.argwhere(err > tol)
+    assert bad.size == 0, (len(bad), [tuple(int(x) for x in b) for b in bad[:5]],
+                           float((err / np.maximum(tol, 1e-300)).max()))
 
 
 @pytest.mark.parametrize("loss,trans", [(plo.LOSS_PAPER, plo.TRANS_EXP), (plo.LOSS_MSE, plo.TRANS_EXP),
@@ -192,8 +205,11 @@ def test_adam_matches_oracle_over_steps(torch_cuda):
     """Six training steps with the learning rate decaying over four (so the
     last steps run at lr1): after each step the FP32 masters equal the
     oracle's Adam (adam_update with lr_at) replayed on the gradients the GPU
-    used, element by element, within 2e-6 relative plus 2e-6 lr0 (FP32
-    moments and parameters against FP64)."""
+    used, element by element.  Bound after k steps: k 1e-6 |p| for the FP32
+    parameter roundings (2^-24 relative each, with margin) plus 1e-5 of the
+    learning rates summed so far, for the FP32 constants of the GPU's
+    update (0.9f, 0.999f and the FP32 bias corrections move an update by
+    about 7e-6 of lr)."""
     torch = torch_cuda
     R, N, total, lr0, lr1 = 64, 32, 4, 5e-4, 5e-6
     flat = random_params(13, scale=0.5)
@@ -204,6 +220,7 @@ def test_adam_matches_oracle_over_steps(torch_cuda):
     p = flat.astype(np.float64)
     m = np.zeros_like(p)
     v = np.zeros_like(p)
+    lr_sum = 0.0
     for step in range(1, 7):
         rays = plogen.rays_sphere(R, seed=40 + step)
         jit = rng.random((R, N)).astype(np.float32)
@@ -212,10 +229,17 @@ def test_adam_matches_oracle_over_steps(torch_cuda):
         net.train_step(dev(rays), dev(C_gt), dev(a_gt), n_samples=N, jitter=dev(jit))
         torch.cuda.synchronize()
         g = net.get_grads().astype(np.float64)
-        p, m, v = omlp.adam_update(p, g, m, v, step, omlp.lr_at(step - 1, total, lr0, lr1))
+        lr = omlp.lr_at(step - 1, total, lr0, lr1)
+        lr_sum += lr
+        p0 = p
+        p, m, v = omlp.adam_update(p, g, m, v, step, lr)
         got = net.get_params().astype(np.float64)
         err = np.abs(got - p)
-        assert np.all(err <= 2e-6 * np.abs(p) + 2e-6 * lr0), (step, float(err.max()))
+        tol = 1e-6 * step * np.abs(p) + 1e-5 * lr_sum
+        i = int(np.argmax(err / tol))
+        assert err[i] <= tol[i], dict(step=step, index=i, p_before=p0[i], g=g[i], gpu=got[i], oracle=p[i],
+                                      err=err[i], tol=tol[i])
+        assert np.abs(got - p0).max() > 0.5 * lr  # the step moved the parameters
     assert net.step == 6
     assert omlp.lr_at(5, total, lr0, lr1) == pytest.approx(lr1)
 
