@@ -116,6 +116,28 @@ typedef struct {
     float sphere[4];
 } plo_render_params;
 
+/* Device layout of a packed tree (plo_build_tree_ex).
+ *   PLO_LAYOUT_OCTREE  the octree itself: 8-byte child entries, a leaf's
+ *                      density in its parent's entry; the render walks it
+ *                      cell by cell with a descent per cell.
+ *   PLO_LAYOUT_BRICKS  the octree above level depth - s, and below it dense
+ *                      bricks of (2^s)^3 finest cells holding the entry of
+ *                      the leaf that covers each cell; the render walks the
+ *                      bricks with a per-axis digital differential analyser
+ *                      (one integer step per finest cell, no descent).
+ * Both give the same integral (a leaf crossed in several finest cells is
+ * the sum of its parts); lookup and trace always use the octree. */
+enum { PLO_LAYOUT_OCTREE = 0, PLO_LAYOUT_BRICKS = 1, PLO_LAYOUT_DEFAULT = PLO_LAYOUT_BRICKS };
+
+/* Options of plo_build_tree_ex: precision PLO_PREC_*, layout PLO_LAYOUT_*,
+ * brick_log the brick side's log2 (1..3; 0 = 3, 8^3 cells), capped at
+ * depth - 1 so that the root is always a node. */
+typedef struct {
+    int32_t precision;
+    int32_t layout;
+    int32_t brick_log;
+} plo_build_options;
+
 typedef struct {
     int32_t depth, sh_degree, precision;
     int32_t top_levels;        /* levels staged in shared memory by the render kernel */
@@ -125,6 +147,11 @@ typedef struct {
     int64_t sh_bytes;          /* device bytes of the SH record table                */
     int32_t sh_record_stride;  /* bytes between SH records                           */
     int32_t device;            /* CUDA device that holds the tree                    */
+    int32_t layout;            /* PLO_LAYOUT_*                                       */
+    int32_t brick_log;         /* brick side log2 (0 for the octree layout)         */
+    int64_t n_bricks;          /* bricks of the brick layout                         */
+    int64_t brick_bytes;       /* device bytes of the bricks                         */
+    int64_t top_nodes;         /* nodes of the brick layout's top tree               */
 } plo_tree_info;
 
 /* Checks a canonical tree on the host without touching a GPU: index ranges,
@@ -144,6 +171,12 @@ plo_status plo_validate_tree(const plo_tree_desc* desc);
  * PLO_ERR_INVALID_ARG for a bad precision; PLO_ERR_OOM when a host or device
  * allocation fails (nothing of the tree is left allocated); PLO_ERR_CUDA. */
 plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out);
+
+/* plo_build_tree with a chosen layout (plo_build_tree uses PLO_LAYOUT_DEFAULT
+ * with 8^3 bricks).  Same errors, plus PLO_ERR_INVALID_ARG for an unknown
+ * layout or brick_log.  The brick layout keeps the octree node table too
+ * (for lookup and trace), so it takes node_bytes + brick_bytes. */
+plo_status plo_build_tree_ex(const plo_tree_desc* desc, const plo_build_options* options, plo_tree** out);
 
 /* Frees a tree (NULL is a no-op).  Synchronises the device first. */
 void plo_tree_free(plo_tree* tree);

@@ -16,10 +16,12 @@ import numpy as np
 from . import _build
 
 __all__ = ["PloError", "Tree", "RenderParams", "load", "render", "render_host", "lookup", "trace",
-           "PREC_FP32", "PREC_FP16", "PREC_BF16", "TRANS_EXP", "TRANS_LINEAR", "TRANS_LINEAR_LITERAL",
+           "PREC_FP32", "PREC_FP16", "PREC_BF16", "LAYOUT_OCTREE", "LAYOUT_BRICKS", "LAYOUT_DEFAULT", "TRANS_EXP", "TRANS_LINEAR", "TRANS_LINEAR_LITERAL",
            "ACT_RELU", "ACT_SIGMOID", "PROXY_BOX", "PROXY_SPHERE"]
 
 PREC_FP32, PREC_FP16, PREC_BF16 = 0, 1, 2
+LAYOUT_OCTREE, LAYOUT_BRICKS = 0, 1
+LAYOUT_DEFAULT = LAYOUT_BRICKS
 TRANS_EXP, TRANS_LINEAR, TRANS_LINEAR_LITERAL = 0, 1, 2
 ACT_RELU, ACT_SIGMOID = 0, 1
 PROXY_BOX, PROXY_SPHERE = 0, 1
@@ -54,7 +56,13 @@ class TreeInfo(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("top_levels", ctypes.c_int32), ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
                 ("n_sh_records", ctypes.c_int64), ("node_bytes", ctypes.c_int64), ("sh_bytes", ctypes.c_int64),
-                ("sh_record_stride", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("sh_record_stride", ctypes.c_int32), ("device", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("brick_log", ctypes.c_int32), ("n_bricks", ctypes.c_int64), ("brick_bytes", ctypes.c_int64),
+                ("top_nodes", ctypes.c_int64)]
+
+
+class BuildOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("layout", ctypes.c_int32), ("brick_log", ctypes.c_int32)]
 
 
 @dataclass
@@ -104,6 +112,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     sigs = {
         "plo_validate_tree": (I32, [P]),
         "plo_build_tree": (I32, [P, I32, P]),
+        "plo_build_tree_ex": (I32, [P, P, P]),
         "plo_tree_free": (None, [P]),
         "plo_tree_get_info": (I32, [P, P]),
         "plo_render_rays": (I32, [P, P, I64, P, P, P, P, P]),
@@ -203,13 +212,15 @@ def _require_np(a, name: str, shape, dtype):
 class Tree:
     """A packed plenoctree on the current CUDA device (plo_build_tree)."""
 
-    def __init__(self, host_tree, precision: int = PREC_FP32):
+    def __init__(self, host_tree, precision: int = PREC_FP32, layout: int = LAYOUT_DEFAULT, brick_log: int = 0):
         lib = load()
         d, keep = _desc(host_tree)
         h = ctypes.c_void_p()
-        _check(lib.plo_build_tree(ctypes.byref(d), precision, ctypes.byref(h)))
+        opt = BuildOptions(precision, layout, brick_log)
+        _check(lib.plo_build_tree_ex(ctypes.byref(d), ctypes.byref(opt), ctypes.byref(h)))
         self._h = h
         self.precision = precision
+        self.layout = layout
 
     @property
     def handle(self):

@@ -21,6 +21,15 @@
 //           non-emissive leaf costs no load beyond the descent itself.
 //           Nodes of the top `top_levels` levels come first (breadth-first),
 //           the rest follow in depth-first (Morton) order.
+//   Brick layout (PLO_LAYOUT_BRICKS) adds, for the render kernels:
+//   top     uint2 [n_top_nodes][8]  the nodes of levels < B = depth - s in
+//           the same order and encoding, except that a child at level B
+//           that has children is a brick id;
+//   bricks  uint2 [n_bricks][2^3s]  per brick a dense array of the entries
+//           of its (2^s)^3 finest cells, index = Morton interleave of the
+//           brick-local coordinates (x lowest): the entry of the leaf that
+//           covers the cell (a leaf above the finest level repeats over its
+//           cells), or ENTRY_EMPTY.
 //   leaf_ids int32 [n_nodes][8]  canonical leaf id per entry (-1 otherwise);
 //           read only by the lookup and trace diagnostics.
 //   sh      records of 3*K coefficients, channel-major, one per emissive
@@ -77,4 +86,14 @@ struct plo_tree {
     unsigned int* d_flags;  // device error flags (bit 0: step limit)
     int64_t node_bytes, sh_bytes;
     int32_t sm_count;
+    // brick layout (PLO_LAYOUT_BRICKS): the octree above brick_level with
+    // brick ids at that level, and the dense bricks below it
+    int32_t layout;
+    int32_t brick_log;     // brick side 2^brick_log finest cells
+    int32_t brick_level;   // level of the brick cells (= depth for the octree layout)
+    int32_t n_top_staged;  // top-tree nodes of levels < min(4, brick_level)
+    int64_t n_top_nodes, n_bricks;
+    int64_t top_bytes, brick_bytes;
+    void* d_top = nullptr;     // uint2 [n_top_nodes][8]
+    void* d_bricks = nullptr;  // uint2 [n_bricks][2^(3 brick_log)], Morton order
 };

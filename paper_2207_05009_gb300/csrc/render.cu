@@ -47,10 +47,13 @@ constexpr int64_t RENDER_CLAIM = 64;  // rays a warp claims at a time from the s
 
 // One packed tree as the kernels see it.
 struct TreeParams {
-    const uint2* nodes;
+    const uint2* nodes;   // node table walked by the descent (the brick layout's top tree)
     const int32_t* leaf_ids;
     const uint8_t* sh;
     unsigned int* flags;
+    const uint2* bricks;  // brick layout: dense bricks below top_depth (NULL: octree layout)
+    int32_t brick_log;    // brick side 2^brick_log finest cells
+    int32_t top_depth;    // level of the brick cells (= depth for the octree layout)
     int32_t sh_stride;
     int32_t depth;
     int32_t n_top;   // nodes staged in shared memory (ids 0 .. n_top-1)
@@ -257,8 +260,8 @@ __device__ __forceinline__ float act_fn(float s, int act, float l_max) {
 
 // ---------------------------------------------------------------- per-ray state
 // Lane states: idle (no ray), descending to the cell at its current point,
-// or at a leaf cell waiting to composite it.
-enum : int { ST_IDLE = 0, ST_DESCEND = 1, ST_LEAF = 2 };
+// at a leaf cell waiting to composite it, or walking a brick cell by cell.
+enum : int { ST_IDLE = 0, ST_DESCEND = 1, ST_LEAF = 2, ST_BRICK = 3 };
 
 struct Ray {
     DF p[3];
@@ -269,7 +272,12 @@ struct Ray {
     DF t;               // ray parameter at the current cell entry (trace only)
     DF rem;             // ray parameter left inside the sphere proxy (sphere only)
     uint32_t q[3];      // integer coordinates of the current point on the finest (depth-D) grid
-    uint32_t node;      // node whose child is looked up next (ST_DESCEND)
+                        // (ST_BRICK: of the point where the ray entered the brick)
+    uint32_t node;      // node whose child is looked up next (ST_DESCEND); the brick (ST_BRICK)
+    DF tn[3];           // ST_BRICK: ray parameter, from the brick entry point, of the next
+                        // finest-grid plane crossed on each axis
+    DF tb;              // ST_BRICK: the same parameter at the current cell's entry
+    uint32_t loc;       // ST_BRICK: brick-local finest coordinates x | y << 4 | z << 8
     uint32_t entry_x, entry_y;
     int level;
     int steps;
@@ -294,18 +302,59 @@ __device__ __forceinline__ uint2 load_entry(const TreeParams& tp, const uint2* s
     return __ldg(tp.nodes + (size_t)node * 8 + slot);
 }
 
+// Brick-local cell index: Morton interleave of the local coordinates
+// (loc = x | y << 4 | z << 8, each < 8), x lowest.
+__device__ __forceinline__ uint32_t spread3(uint32_t x) { return (x & 1u) | ((x & 2u) << 2) | ((x & 4u) << 4); }
+__device__ __forceinline__ uint2 brick_entry(const TreeParams& tp, uint32_t brick, uint32_t loc) {
+    const uint32_t m = spread3(loc & 15u) | (spread3((loc >> 4) & 15u) << 1) | (spread3(loc >> 8) << 2);
+    return __ldg(tp.bricks + ((size_t)brick << (3 * tp.brick_log)) + m);
+}
+
+// Enters brick `brick`, the level-top_depth cell that holds the current
+// point: the brick-local coordinates of the finest cell R.q, and per axis the
+// parameter of the next finest plane from the current point,
+// (P - p) / d in double-float (as the octree step computes its exits).  The
+// first cell's entry is loaded here, for the next iteration.
+__device__ __forceinline__ void brick_enter(const TreeParams& tp, Ray& R, uint32_t brick) {
+    const uint32_t smask = (1u << tp.brick_log) - 1u;
+    R.node = brick;
+    R.loc = (R.q[0] & smask) | ((R.q[1] & smask) << 4) | ((R.q[2] & smask) << 8);
+    const float cell = pow2i(-tp.depth);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        DF v = {INFINITY, 0.0f};
+        if (R.d[a] != 0.0f) {
+            const float P = (float)(R.q[a] + (R.d[a] > 0.0f ? 1u : 0u)) * cell;  // exact
+            v = df_mul(df_from_plane(P, R.p[a]), low_parts()[(6 + a) * BLOCK], low_parts()[(3 + a) * BLOCK]);
+            if (v.hi < 0.0f) v = {0.0f, 0.0f};
+        }
+        R.tn[a] = v;
+    }
+    R.tb = {0.0f, 0.0f};
+    const uint2 e = brick_entry(tp, brick, R.loc);
+    R.entry_x = e.x;
+    R.entry_y = e.y;
+    R.state = ST_BRICK;
+}
+
 // Descends from R.node (level R.level) to the leaf or empty octant that holds
 // the point, taking the child bits from the finest-grid coordinates R.q, and
-// ends in ST_LEAF.  The whole descent runs in one step: stopping after each
+// ends in ST_LEAF (or, in the brick layout, in ST_BRICK when it reaches a
+// brick).  The whole descent runs in one step: stopping after each
 // dependent global load, so that lanes with shorter descents could go on,
 // was measured slower (304 vs 320 Mrays/s).
+template <bool BRICKS>
 __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* s_nodes, Ray& R, uint32_t* stack) {
     for (int guard = 0; guard <= MAX_DEPTH; ++guard) {
         const int sh = tp.depth - 1 - R.level;
         R.slot = (int)(((R.q[0] >> sh) & 1u) | (((R.q[1] >> sh) & 1u) << 1) | (((R.q[2] >> sh) & 1u) << 2));
         uint2 e = load_entry(tp, s_nodes, R.node, R.slot);
         ++R.level;
-        if ((e.x & LEAF_BIT) || R.level >= tp.depth) {  // leaf, empty octant (or a malformed table)
+        if ((e.x & LEAF_BIT) || R.level >= tp.top_depth) {  // leaf, empty octant, brick (or a malformed table)
+            if (BRICKS && tp.bricks && !(e.x & LEAF_BIT) && R.level == tp.top_depth) {
+                brick_enter(tp, R, e.x);
+                return;
+            }
             if (!(e.x & LEAF_BIT)) e = make_uint2(ENTRY_EMPTY, 0u);
             R.entry_x = e.x;
             R.entry_y = e.y;
@@ -458,6 +507,48 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
     R.state = ST_DESCEND;
 }
 
+// Composites the current cell's entry over a segment of length `seg` (Eq.
+// 3-5): optical depth as a compensated sum, weight T_in (1 - e^{-sigma seg})
+// or the linear model's, SH emission of emitting leaves.  Returns true when
+// the ray is finished (T below t_stop) and its outputs are written.
+template <int K, int PREC>
+__device__ __forceinline__ bool composite(const KParams& kp, const TreeParams& tp, int64_t i, Ray& R, float seg,
+                                          const float* sY) {
+    if (R.entry_x == ENTRY_EMPTY) return false;
+    float sigma = decode_sigma<PREC>(R.entry_y, tp.prec);
+    if (sigma < kp.sigma_min) sigma = 0.0f;
+    if (!(sigma > 0.0f)) return false;
+    const float a = sigma * seg;
+    const float Tin = R.T;
+    const DF s = two_sum(R.od.hi, a);
+    R.od = fast_two_sum(s.hi, __fadd_rn(s.lo, R.od.lo));
+    float w, Tout;
+    if (kp.transmittance == PLO_TRANS_EXP) {
+        w = Tin * (-expm1f(-a));
+        Tout = expf(-(R.od.hi + R.od.lo));
+    } else {
+        Tout = fmaxf(0.0f, __fsub_rn(__fsub_rn(1.0f, R.od.hi), R.od.lo));
+        const float dT = fminf(Tin, a);
+        w = kp.transmittance == PLO_TRANS_LINEAR ? dT : 0.5f * dT * (Tin + Tout);
+    }
+    const uint32_t rec = R.entry_x & ~LEAF_BIT;
+    float cr = 0.0f, cg = 0.0f, cb = 0.0f;
+    const bool emits = rec != NO_SH_RECORD;
+    if (emits) sh_emission<K, PREC>(tp, rec, R.entry_y, R.dirn, cr, cg, cb, sY);
+    if (emits || kp.activation != PLO_ACT_RELU) {
+        R.r = __fmaf_rn(w, act_fn(cr, kp.activation, kp.l_max), R.r);
+        R.g = __fmaf_rn(w, act_fn(cg, kp.activation, kp.l_max), R.g);
+        R.b = __fmaf_rn(w, act_fn(cb, kp.activation, kp.l_max), R.b);
+    }
+    R.T = Tout;
+    if (R.T < kp.t_stop || R.T <= 0.0f) {
+        ray_store(kp, i, R);
+        R.state = ST_IDLE;
+        return true;
+    }
+    return false;
+}
+
 // One cell: segment length, compositing, advance.  Leaves the lane in
 // ST_DESCEND (next cell) or ST_IDLE (ray finished, outputs written).
 template <int K, int PREC, bool TRACE, bool SPHERE>
@@ -548,40 +639,7 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
     }
 
     // composite the leaf (Eq. 3-5)
-    if (R.entry_x != ENTRY_EMPTY) {
-        float sigma = decode_sigma<PREC>(R.entry_y, tp.prec);
-        if (sigma < kp.sigma_min) sigma = 0.0f;
-        if (sigma > 0.0f) {
-            float a = sigma * seg;
-            float Tin = R.T;
-            DF s = two_sum(R.od.hi, a);
-            R.od = fast_two_sum(s.hi, __fadd_rn(s.lo, R.od.lo));
-            float w, Tout;
-            if (kp.transmittance == PLO_TRANS_EXP) {
-                w = Tin * (-expm1f(-a));
-                Tout = expf(-(R.od.hi + R.od.lo));
-            } else {
-                Tout = fmaxf(0.0f, __fsub_rn(__fsub_rn(1.0f, R.od.hi), R.od.lo));
-                float dT = fminf(Tin, a);
-                w = kp.transmittance == PLO_TRANS_LINEAR ? dT : 0.5f * dT * (Tin + Tout);
-            }
-            uint32_t rec = R.entry_x & ~LEAF_BIT;
-            float cr = 0.0f, cg = 0.0f, cb = 0.0f;
-            bool emits = rec != NO_SH_RECORD;
-            if (emits) sh_emission<K, PREC>(tp, rec, R.entry_y, R.dirn, cr, cg, cb, sY);
-            if (emits || kp.activation != PLO_ACT_RELU) {
-                R.r = __fmaf_rn(w, act_fn(cr, kp.activation, kp.l_max), R.r);
-                R.g = __fmaf_rn(w, act_fn(cg, kp.activation, kp.l_max), R.g);
-                R.b = __fmaf_rn(w, act_fn(cb, kp.activation, kp.l_max), R.b);
-            }
-            R.T = Tout;
-            if (R.T < kp.t_stop || R.T <= 0.0f) {
-                ray_store(kp, i, R);
-                R.state = ST_IDLE;
-                return;
-            }
-        }
-    }
+    if (composite<K, PREC>(kp, tp, i, R, seg, sY)) return;
     if (last) {
         ray_store(kp, i, R);
         R.state = ST_IDLE;
@@ -629,9 +687,120 @@ __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ra
     R.state = ST_DESCEND;
 }
 
+// Leaves a brick across the face of axis `ax` at parameter tx (from the
+// brick entry point R.p): the exit point, snapped onto the planes it lies on
+// (the face, and any other axis whose next plane is crossed within 2^-36
+// of tx, so that a ray through an edge steps diagonally), its finest-grid
+// cell from the walk's own coordinates (no rounding: the walk counted every
+// plane crossed), then a descent from the deepest common ancestor of the
+// brick and that cell.
+__device__ __forceinline__ void brick_exit(const KParams& kp, const TreeParams& tp, int64_t i, Ray& R,
+                                           uint32_t* stack, int ax, DF tx) {
+    const int s = tp.brick_log;
+    const uint32_t S = 1u << s;
+    const int Bl = tp.top_depth;
+    const float cell = pow2i(-tp.depth);
+    const float tie = __fmaf_rn(tx.hi, 1.4551915228366852e-11f, tx.hi);
+    bool left = false;
+    int l_anc = Bl;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const uint32_t base = R.q[a] & ~(S - 1u);  // the brick's corner on this axis
+        const uint32_t l = (R.loc >> (4 * a)) & 15u;
+        if (R.d[a] != 0.0f && (a == ax || R.tn[a].hi <= tie)) {
+            const bool up = R.d[a] > 0.0f;
+            const uint32_t qn = up ? base + l + 1u : base + l - 1u;  // wraps below 0: outside the cube
+            R.p[a] = {(float)(up ? qn : qn + 1u) * cell, 0.0f};
+            const uint32_t cb = base >> s, cn = qn >> s;
+            left |= (cn >> Bl) != 0u;
+            if (cn != cb) {
+                const int diff = 32 - __clz(cn ^ cb);
+                if (Bl - diff < l_anc) l_anc = Bl - diff;
+            }
+            R.q[a] = qn;
+        } else {
+            R.p[a] = df_axpy(R.p[a], tx, R.d[a], low_parts()[a * BLOCK]);
+            R.q[a] = base + l;
+        }
+    }
+    if (left || l_anc < 0) {
+        ray_store(kp, i, R);
+        R.state = ST_IDLE;
+        return;
+    }
+    R.level = l_anc;
+    R.node = stack[l_anc * BLOCK];
+    R.state = ST_DESCEND;
+}
+
+// One finest cell of a brick: the exit parameter is the smallest of the
+// three next-plane parameters (a digital differential analyser); composite
+// the cell over [tb, exit], then step one cell along the exit axis and load
+// that cell's entry for the next iteration.
+template <int K, int PREC, bool SPHERE>
+__device__ void brick_step(const KParams& kp, const TreeParams& tp, int64_t i, Ray& R, uint32_t* stack,
+                           const float* sY = nullptr) {
+    int ax = 0;
+    DF tx = R.tn[0];
+    if (df_less(R.tn[1], tx)) {
+        ax = 1;
+        tx = R.tn[1];
+    }
+    if (df_less(R.tn[2], tx)) {
+        ax = 2;
+        tx = R.tn[2];
+    }
+    DF dt = df_sub(tx, R.tb);
+    if (dt.hi < 0.0f) dt = {0.0f, 0.0f};
+    bool last = false;  // the sphere proxy ends inside this cell
+    if (SPHERE) {
+        if (df_less(dt, R.rem)) {
+            R.rem = df_sub(R.rem, dt);
+        } else {
+            dt = R.rem;
+            last = true;
+        }
+    }
+    ++R.steps;
+    if (composite<K, PREC>(kp, tp, i, R, dt.hi, sY)) return;
+    if (last) {
+        ray_store(kp, i, R);
+        R.state = ST_IDLE;
+        return;
+    }
+    if (R.steps >= tp.max_steps) {
+        R.status = PLO_RAY_STEP_LIMIT;
+        atomicOr(tp.flags, 1u);
+        ray_store(kp, i, R);
+        R.state = ST_IDLE;
+        return;
+    }
+    // the next plane on the exit axis is one finest cell further: add
+    // 2^-D |1/d| (a power-of-two scaling of the double-float 1/d, exact)
+    const float sc = pow2i(-tp.depth);
+    const float rh = low_parts()[(6 + ax) * BLOCK], rl = low_parts()[(3 + ax) * BLOCK];
+    const DF step = rh > 0.0f ? DF{rh * sc, rl * sc} : DF{-rh * sc, -rl * sc};
+    const DF tnew = df_add(tx, step);
+    const bool up = ax == 0 ? R.d[0] > 0.0f : (ax == 1 ? R.d[1] > 0.0f : R.d[2] > 0.0f);
+    const int sh = 4 * ax;
+    const uint32_t l = (R.loc >> sh) & 15u;
+    if (up ? l + 1u < (1u << tp.brick_log) : l > 0u) {
+        R.tb = tx;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (a == ax) R.tn[a] = tnew;
+        R.loc = up ? R.loc + (1u << sh) : R.loc - (1u << sh);
+        const uint2 e = brick_entry(tp, R.node, R.loc);
+        R.entry_x = e.x;
+        R.entry_y = e.y;
+        return;
+    }
+    brick_exit(kp, tp, i, R, stack, ax, tx);
+}
+
 // The trace and sphere-proxy kernels keep more per-ray state: 3 blocks per
 // SM (80 registers) beats 4 with spills for them (measured).
-template <int K, int PREC, bool TRACE, bool SPHERE>
+template <int K, int PREC, bool TRACE, bool SPHERE, bool BRICKS>
 __global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : PLO_RENDER_MIN_BLOCKS) k_render(KParams kp) {
     // nodes of the top levels, staged once per (persistent) block
     extern __shared__ uint2 s_nodes[];
@@ -693,9 +862,11 @@ __global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : PLO_RENDER_MIN_
         }
         const unsigned live = __ballot_sync(0xffffffffu, R.state != ST_IDLE);
         if (live == 0u) break;
-        // every live lane is at a leaf here (descents run to the leaf)
+        // every live lane is at a leaf or in a brick here (descents run to
+        // the leaf or brick)
+        if (BRICKS && R.state == ST_BRICK) brick_step<K, PREC, SPHERE>(kp, tp, my, R, stack, sY);
         if (R.state == ST_LEAF) leaf_step<K, PREC, TRACE, SPHERE>(kp, tp, my, R, stack, sY);
-        if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
+        if (R.state == ST_DESCEND) descend_step<BRICKS>(tp, s_nodes, R, stack);
     }
 }
 
@@ -771,8 +942,9 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(B
         const unsigned live = __ballot_sync(0xffffffffu, R.state != ST_IDLE);
         if (live == 0u) break;
         const TreeParams& tp = s_tp[R.tree];
+        if (R.state == ST_BRICK) brick_step<0, -1, false>(kp, tp, my, R, stack);
         if (R.state == ST_LEAF) leaf_step<0, -1, false, false>(kp, tp, my, R, stack);
-        if (R.state == ST_DESCEND) descend_step(tp, s_nodes, R, stack);
+        if (R.state == ST_DESCEND) descend_step<true>(tp, s_nodes, R, stack);
     }
 }
 
@@ -820,9 +992,9 @@ __global__ void k_lookup(const uint2* nodes, const int32_t* leaf_ids, int depth,
 
 // Persistent grid: as many blocks as fit on the device at once (occupancy
 // API), each warp owning a contiguous chunk of the rays.
-template <int K, int PREC, bool TRACE, bool SPHERE>
+template <int K, int PREC, bool TRACE, bool SPHERE, bool BRICKS>
 cudaError_t launch_k(KParams kp, int sm_count, size_t smem, cudaStream_t s) {
-    auto fn = k_render<K, PREC, TRACE, SPHERE>;
+    auto fn = k_render<K, PREC, TRACE, SPHERE, BRICKS>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -839,10 +1011,10 @@ cudaError_t launch_k(KParams kp, int sm_count, size_t smem, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <bool TRACE, bool SPHERE>
+template <bool TRACE, bool SPHERE, bool BRICKS>
 cudaError_t dispatch(const plo_tree* t, const KParams& kp, size_t smem, cudaStream_t s) {
 #define PLO_CASE(KK, PP)                                                   \
-    if (t->K == KK && t->precision == PP) return launch_k<KK, PP, TRACE, SPHERE>(kp, t->sm_count, smem, s);
+    if (t->K == KK && t->precision == PP) return launch_k<KK, PP, TRACE, SPHERE, BRICKS>(kp, t->sm_count, smem, s);
     PLO_CASE(1, PLO_PREC_FP32) PLO_CASE(4, PLO_PREC_FP32) PLO_CASE(9, PLO_PREC_FP32) PLO_CASE(16, PLO_PREC_FP32)
     PLO_CASE(1, PLO_PREC_FP16) PLO_CASE(4, PLO_PREC_FP16) PLO_CASE(9, PLO_PREC_FP16) PLO_CASE(16, PLO_PREC_FP16)
     PLO_CASE(1, PLO_PREC_BF16) PLO_CASE(4, PLO_PREC_BF16) PLO_CASE(9, PLO_PREC_BF16) PLO_CASE(16, PLO_PREC_BF16)
@@ -850,14 +1022,21 @@ cudaError_t dispatch(const plo_tree* t, const KParams& kp, size_t smem, cudaStre
     return cudaErrorInvalidValue;
 }
 
-void fill_tree_params(const plo_tree* t, const plo_render_params* p, TreeParams* tp) {
-    tp->nodes = static_cast<const uint2*>(t->d_nodes);
+// Kernel view of a tree.  `walk_bricks`: the brick layout's top tree and
+// bricks (render kernels); otherwise the octree node table (trace, and
+// trees packed with the octree layout).
+void fill_tree_params(const plo_tree* t, const plo_render_params* p, TreeParams* tp, bool walk_bricks = true) {
+    const bool bricks = walk_bricks && t->layout == PLO_LAYOUT_BRICKS;
+    tp->nodes = static_cast<const uint2*>(bricks ? t->d_top : t->d_nodes);
+    tp->bricks = bricks ? static_cast<const uint2*>(t->d_bricks) : nullptr;
+    tp->brick_log = bricks ? t->brick_log : 0;
+    tp->top_depth = bricks ? t->brick_level : t->depth;
     tp->leaf_ids = t->d_leaf_ids;
     tp->sh = static_cast<const uint8_t*>(t->d_sh);
     tp->flags = t->d_flags;
     tp->sh_stride = t->sh_stride;
     tp->depth = t->depth;
-    tp->n_top = t->n_top;
+    tp->n_top = bricks ? t->n_top_staged : t->n_top;
     tp->s_off = 0;
     tp->K = t->K;
     tp->prec = t->precision;
@@ -915,7 +1094,7 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     if (TRACE && p->proxy != PLO_PROXY_BOX)
         return set_error(PLO_ERR_UNSUPPORTED, "plo_trace_rays follows the box proxy only");
     KParams kp{};
-    fill_tree_params(t, p, &kp.tree);
+    fill_tree_params(t, p, &kp.tree, !TRACE);
     kp.transmittance = p->transmittance;
     kp.activation = p->activation;
     kp.l_max = p->l_max;
@@ -949,12 +1128,15 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
         }
         kp.cursor = cursor;
     }
+    const bool bricks = !TRACE && t->layout == PLO_LAYOUT_BRICKS;
     if (TRACE)
-        e = dispatch<TRACE, false>(t, kp, smem, (cudaStream_t)stream);
+        e = dispatch<TRACE, false, false>(t, kp, smem, (cudaStream_t)stream);
     else if (kp.proxy == PLO_PROXY_SPHERE)
-        e = dispatch<false, true>(t, kp, smem, (cudaStream_t)stream);
+        e = bricks ? dispatch<false, true, true>(t, kp, smem, (cudaStream_t)stream)
+                   : dispatch<false, true, false>(t, kp, smem, (cudaStream_t)stream);
     else
-        e = dispatch<false, false>(t, kp, smem, (cudaStream_t)stream);
+        e = bricks ? dispatch<false, false, true>(t, kp, smem, (cudaStream_t)stream)
+                   : dispatch<false, false, false>(t, kp, smem, (cudaStream_t)stream);
     if (cursor) cudaFreeAsync(cursor, cs);
     if (e != cudaSuccess) return cuda_error(e, "render kernel launch");
     return PLO_OK;
@@ -1202,7 +1384,7 @@ extern "C" plo_status plo_batch_create(const plo_tree* const* trees, int32_t n_t
     kp.n = b->n_rays;
     for (int t = 0; t < n_trees; ++t) {
         fill_tree_params(trees[t], params, &b->bp.trees[t]);
-        b->full_top[t] = std::min<int32_t>(trees[t]->n_top, BATCH_TOP_NODES);
+        b->full_top[t] = std::min<int32_t>(b->bp.trees[t].n_top, BATCH_TOP_NODES);
     }
     for (int t = 0; t <= n_trees; ++t) b->bp.off[t] = ray_offsets[t];
     b->bp.n_trees = n_trees;

@@ -163,11 +163,21 @@ extern "C" plo_status plo_validate_tree(const plo_tree_desc* desc) {
 }
 
 namespace {
-plo_status build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out) {
+// Bit i of x goes to bit 3 i (x < 8): the Morton interleave of brick-local
+// coordinates, x lowest.
+inline uint32_t spread3(uint32_t x) { return (x & 1u) | ((x & 2u) << 2) | ((x & 4u) << 4); }
+
+plo_status build_tree(const plo_tree_desc* desc, const plo_build_options* opt, plo_tree** out) {
     if (!out) return set_error(PLO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
+    if (!opt) return set_error(PLO_ERR_INVALID_ARG, "options are NULL");
+    const int32_t precision = opt->precision;
     if (precision < PLO_PREC_FP32 || precision > PLO_PREC_BF16)
         return set_error(PLO_ERR_INVALID_ARG, "precision must be PLO_PREC_FP32, _FP16 or _BF16");
+    if (opt->layout != PLO_LAYOUT_OCTREE && opt->layout != PLO_LAYOUT_BRICKS)
+        return set_error(PLO_ERR_INVALID_ARG, "layout must be PLO_LAYOUT_OCTREE or PLO_LAYOUT_BRICKS");
+    if (opt->brick_log != 0 && (opt->brick_log < 1 || opt->brick_log > 3))
+        return set_error(PLO_ERR_INVALID_ARG, "brick_log must be 0 (default), 1, 2 or 3");
     plo_status st = validate(desc);
     if (st != PLO_OK) return st;
     const int K = sh_K(desc->sh_degree);
@@ -333,8 +343,96 @@ plo_status build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** o
         }
     }
 
+    // Brick layout: the octree above level B = depth - s (top nodes keep the
+    // packed order; a child at level B that has children is a brick), and
+    // below it one dense (2^s)^3 array of cell entries per brick, in Morton
+    // order, each finest cell holding the entry of the leaf that covers it.
+    const bool bricks = opt->layout == PLO_LAYOUT_BRICKS;
+    const int blog = bricks ? std::min(opt->brick_log > 0 ? opt->brick_log : 3, depth - 1) : 0;
+    const int B = depth - blog;
+    std::vector<uint32_t> top_tab;
+    std::vector<uint32_t> brick_cells;
+    int64_t n_top_nodes = 0, n_bricks = 0;
+    int32_t n_top_staged = 0;
+    if (bricks) {
+        std::vector<int32_t> top_id(n_nodes, -1), brick_id(n_nodes, -1), top_order, brick_nodes;
+        for (int32_t v : order) {
+            if (level[v] < B) {
+                top_id[v] = (int32_t)top_order.size();
+                top_order.push_back(v);
+                if (level[v] < std::min(top, B)) ++n_top_staged;
+            } else if (level[v] == B) {
+                brick_id[v] = (int32_t)brick_nodes.size();
+                brick_nodes.push_back(v);
+            }
+        }
+        n_top_nodes = (int64_t)top_order.size();
+        n_bricks = (int64_t)brick_nodes.size();
+        top_tab.assign(n_top_nodes * 16, 0);
+        for (int64_t i = 0; i < n_top_nodes; ++i) {
+            const int32_t v = top_order[i];
+            const int64_t src = (int64_t)new_id[v] * 16;
+            for (int sl = 0; sl < 8; ++sl) {
+                const int32_t e = child[(int64_t)v * 8 + sl];
+                uint32_t x = nodes[src + 2 * sl], y = nodes[src + 2 * sl + 1];
+                if (e >= 0) x = (uint32_t)(level[e] < B ? top_id[e] : brick_id[e]), y = 0;
+                top_tab[i * 16 + 2 * sl] = x;
+                top_tab[i * 16 + 2 * sl + 1] = y;
+            }
+        }
+        const int S = 1 << blog;
+        const int64_t cells = (int64_t)S * S * S;
+        brick_cells.assign(n_bricks * cells * 2, 0);
+        parallel_ranges(n_bricks, [&](int64_t b0, int64_t b1) {
+            struct Item {
+                int32_t v;
+                int lev;
+                uint32_t x, y, z;  // brick-local finest coordinates of the node's corner
+            };
+            std::vector<Item> st;
+            for (int64_t b = b0; b < b1; ++b) {
+                uint32_t* dst = brick_cells.data() + b * cells * 2;
+                for (int64_t c = 0; c < cells; ++c) dst[2 * c] = ENTRY_EMPTY;
+                st.clear();
+                st.push_back({brick_nodes[b], B, 0, 0, 0});
+                while (!st.empty()) {
+                    Item it = st.back();
+                    st.pop_back();
+                    const uint32_t half = 1u << (depth - it.lev - 1);  // child size in finest cells
+                    const int64_t src = (int64_t)new_id[it.v] * 16;
+                    for (int sl = 0; sl < 8; ++sl) {
+                        const int32_t e = child[(int64_t)it.v * 8 + sl];
+                        const uint32_t cx = it.x + (sl & 1) * half, cy = it.y + ((sl >> 1) & 1) * half,
+                                       cz = it.z + ((sl >> 2) & 1) * half;
+                        if (e >= 0) {
+                            st.push_back({e, it.lev + 1, cx, cy, cz});
+                        } else if (e <= -2) {
+                            const uint32_t ex = nodes[src + 2 * sl], ey = nodes[src + 2 * sl + 1];
+                            for (uint32_t k = 0; k < half; ++k)
+                                for (uint32_t j = 0; j < half; ++j)
+                                    for (uint32_t i = 0; i < half; ++i) {
+                                        const uint32_t m = spread3(cx + i) | (spread3(cy + j) << 1) |
+                                                           (spread3(cz + k) << 2);
+                                        dst[2 * m] = ex;
+                                        dst[2 * m + 1] = ey;
+                                    }
+                        }
+                    }
+                }
+            }
+        });
+    }
+
     plo_tree* t = new (std::nothrow) plo_tree();
     if (!t) return set_error(PLO_ERR_OOM, "host allocation failed");
+    t->layout = bricks ? PLO_LAYOUT_BRICKS : PLO_LAYOUT_OCTREE;
+    t->brick_log = blog;
+    t->brick_level = bricks ? B : depth;
+    t->n_top_nodes = n_top_nodes;
+    t->n_top_staged = n_top_staged;
+    t->n_bricks = n_bricks;
+    t->top_bytes = n_top_nodes * 64;
+    t->brick_bytes = (int64_t)brick_cells.size() * 4;
     t->depth = depth;
     t->sh_degree = desc->sh_degree;
     t->K = K;
@@ -364,7 +462,10 @@ plo_status build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** o
         (err = (cudaError_t)dev_malloc((void**)&t->d_leaf_ids, (size_t)n_packed * 8 * sizeof(int32_t))) !=
             cudaSuccess ||
         (err = (cudaError_t)dev_malloc(&t->d_sh, sh_alloc)) != cudaSuccess ||
-        (err = (cudaError_t)dev_malloc((void**)&t->d_flags, 256)) != cudaSuccess) {
+        (err = (cudaError_t)dev_malloc((void**)&t->d_flags, 256)) != cudaSuccess ||
+        (bricks && (err = (cudaError_t)dev_malloc(&t->d_top, (size_t)t->top_bytes)) != cudaSuccess) ||
+        (bricks && (err = (cudaError_t)dev_malloc(&t->d_bricks, (size_t)std::max<int64_t>(t->brick_bytes, 256))) !=
+                       cudaSuccess)) {
         plo_tree_free(t);
         cudaGetLastError();
         return err == cudaErrorMemoryAllocation ? set_error(PLO_ERR_OOM, "device allocation for the tree failed")
@@ -374,7 +475,12 @@ plo_status build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** o
         (err = cudaMemcpy(t->d_leaf_ids, leaf_ids.data(), (size_t)n_packed * 8 * sizeof(int32_t),
                           cudaMemcpyHostToDevice)) != cudaSuccess ||
         (err = cudaMemcpy(t->d_sh, sh.get(), sh_alloc, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (err = cudaMemset(t->d_flags, 0, 256)) != cudaSuccess) {
+        (err = cudaMemset(t->d_flags, 0, 256)) != cudaSuccess ||
+        (bricks && (err = cudaMemcpy(t->d_top, top_tab.data(), (size_t)t->top_bytes, cudaMemcpyHostToDevice)) !=
+                       cudaSuccess) ||
+        (bricks && t->brick_bytes > 0 &&
+         (err = cudaMemcpy(t->d_bricks, brick_cells.data(), (size_t)t->brick_bytes, cudaMemcpyHostToDevice)) !=
+             cudaSuccess)) {
         plo_tree_free(t);
         return cuda_error(err, "upload of the packed tree");
     }
@@ -386,13 +492,18 @@ plo_status build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** o
 
 // Host allocations are large (the packed records alone are n_sh x stride
 // bytes); none of them may escape the C ABI as an exception.
-extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out) {
+extern "C" plo_status plo_build_tree_ex(const plo_tree_desc* desc, const plo_build_options* options, plo_tree** out) {
     try {
-        return build_tree(desc, precision, out);
+        return build_tree(desc, options, out);
     } catch (const std::bad_alloc&) {
         if (out) *out = nullptr;
         return set_error(PLO_ERR_OOM, "host allocation while packing the tree failed");
     }
+}
+
+extern "C" plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out) {
+    const plo_build_options opt = {precision, PLO_LAYOUT_DEFAULT, 0};
+    return plo_build_tree_ex(desc, &opt, out);
 }
 
 extern "C" void plo_tree_free(plo_tree* t) {
@@ -405,6 +516,8 @@ extern "C" void plo_tree_free(plo_tree* t) {
     cudaFree(t->d_leaf_ids);
     cudaFree(t->d_sh);
     cudaFree(t->d_flags);
+    cudaFree(t->d_top);
+    cudaFree(t->d_bricks);
     if (prev >= 0) cudaSetDevice(prev);
     delete t;
 }
@@ -422,6 +535,11 @@ extern "C" plo_status plo_tree_get_info(const plo_tree* t, plo_tree_info* out) {
     out->sh_bytes = t->sh_bytes;
     out->sh_record_stride = t->sh_stride;
     out->device = t->device;
+    out->layout = t->layout;
+    out->brick_log = t->brick_log;
+    out->n_bricks = t->n_bricks;
+    out->brick_bytes = t->brick_bytes;
+    out->top_nodes = t->n_top_nodes;
     return PLO_OK;
 }
 

@@ -41,12 +41,12 @@ def room_rays(cuda_available):
     return rays_np, torch.from_numpy(rays_np).cuda()
 
 
-def render_all(torch, tree, rays, precision):
+def render_all(torch, tree, rays, precision, layout=plo.LAYOUT_DEFAULT):
     n = rays.shape[0]
     rgb = torch.empty((n, 3), device="cuda")
     T = torch.empty(n, device="cuda")
     st = torch.full((n,), -7, dtype=torch.int32, device="cuda")
-    t = plo.Tree(tree, precision)
+    t = plo.Tree(tree, precision, layout)
     plo.render(t, rays, plo.RenderParams(), rgb=rgb, T=T, status=st)
     torch.cuda.synchronize()
     t.check()
@@ -61,10 +61,13 @@ def test_full_size_workload_sampled_parity(room_rays):
     idx = spread(N_FULL, 1 << 18)
     ref = oracle.render(tree, rays_np[idx], n_threads=CORES)
     sel = torch.from_numpy(idx).cuda()
-    for prec, rtol, name in ((plo.PREC_FP32, RTOL_FP32, "fp32"), (plo.PREC_FP16, RTOL_FP16, "fp16")):
-        rgb, T = render_all(torch, tree, rays, prec)
+    for prec, rtol, name, layout in ((plo.PREC_FP32, RTOL_FP32, "fp32", plo.LAYOUT_DEFAULT),
+                                     (plo.PREC_FP16, RTOL_FP16, "fp16", plo.LAYOUT_DEFAULT),
+                                     (plo.PREC_FP32, RTOL_FP32, "fp32 octree layout", plo.LAYOUT_OCTREE)):
+        rgb, T = render_all(torch, tree, rays, prec, layout)
         assert_radiance_close(rgb[sel].cpu().numpy(), T[sel].cpu().numpy(), ref, rtol,
                               what=f"full-size {name} launch vs oracle")
+        del rgb, T
 
 
 def test_16bit_leaves_depth6_on_16m_rays(room_rays):

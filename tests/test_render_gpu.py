@@ -27,8 +27,15 @@ def d6():
     return plogen.luminaire_tree(plogen.LUMINAIRE_D6)
 
 
-def gpu_render(torch, tree, rays, precision=plo.PREC_FP32, **kw):
-    t = plo.Tree(tree, precision)
+# device layouts: the octree, and bricks of side 8, 4 and 2 finest cells
+LAYOUTS = {"octree": (plo.LAYOUT_OCTREE, 0), "bricks8": (plo.LAYOUT_BRICKS, 3), "bricks4": (plo.LAYOUT_BRICKS, 2),
+           "bricks2": (plo.LAYOUT_BRICKS, 1)}
+ALL_LAYOUTS = pytest.mark.parametrize("layout", list(LAYOUTS))
+TWO_LAYOUTS = pytest.mark.parametrize("layout", ["octree", "bricks8"])
+
+
+def gpu_render(torch, tree, rays, precision=plo.PREC_FP32, layout="bricks8", **kw):
+    t = plo.Tree(tree, precision, *LAYOUTS[layout])
     r = torch.from_numpy(np.ascontiguousarray(rays)).cuda()
     st = torch.full((len(rays),), -7, dtype=torch.int32, device="cuda")
     rgb, T, _ = plo.render(t, r, plo.RenderParams(**kw), status=st)
@@ -37,10 +44,11 @@ def gpu_render(torch, tree, rays, precision=plo.PREC_FP32, **kw):
     return rgb.cpu().numpy(), T.cpu().numpy(), st.cpu().numpy()
 
 
+@TWO_LAYOUTS
 @pytest.mark.parametrize("model", ["exp", "lin", "lit"])
-def test_d6_luminaire_fp32_parity(torch_cuda, d6, model):
+def test_d6_luminaire_fp32_parity(torch_cuda, d6, model, layout):
     rays = plogen.rays_sphere(65536, seed=1)
-    g_rgb, g_T, st = gpu_render(torch_cuda, d6, rays, transmittance=TRANS[model][0])
+    g_rgb, g_T, st = gpu_render(torch_cuda, d6, rays, transmittance=TRANS[model][0], layout=layout)
     ref = oracle.render(d6, rays, transmittance=TRANS[model][1])
     assert np.all(st == 0)
     eta = 0.0 if model == "exp" else COND_ETA_LINEAR
@@ -55,25 +63,27 @@ def test_sigmoid_activation_parity(torch_cuda, d6):
     assert_radiance_close(g_rgb, g_T, ref, RTOL_FP32, what="sigmoid")
 
 
+@ALL_LAYOUTS
 @pytest.mark.parametrize("seed", range(8))
-def test_random_trees_all_degrees_ragged(torch_cuda, seed):
+def test_random_trees_all_degrees_ragged(torch_cuda, seed, layout):
     rng = np.random.default_rng(seed)
     deg = seed % 4
     tree = random_tree(1 + seed % 5, rng, sh_degree=deg)
     n = 1000 + 37 * seed  # not a multiple of the warp or block size
     rays = plogen.rays_sphere(n, seed=100 + seed, radius=1.5 + seed)
-    g_rgb, g_T, st = gpu_render(torch_cuda, tree, rays)
+    g_rgb, g_T, st = gpu_render(torch_cuda, tree, rays, layout=layout)
     ref = oracle.render(tree, rays)
     assert np.all(st == 0)
     assert_radiance_close(g_rgb, g_T, ref, RTOL_FP32, what=f"random tree {seed}")
 
 
-def test_degenerate_trees(torch_cuda):
+@ALL_LAYOUTS
+def test_degenerate_trees(torch_cuda, layout):
     c = np.random.default_rng(0).normal(size=(3, 9)).astype(np.float32) + 2
     rays = plogen.rays_sphere(2000, seed=5)
     for tree in (uniform_tree(0, 2.0, c), uniform_tree(1, 0.7, c),
                  HostTree(0, 2, np.zeros((0, 8), np.int32), np.zeros(0, np.float32), np.zeros((0, 3, 9), np.float32))):
-        g_rgb, g_T, st = gpu_render(torch_cuda, tree, rays)
+        g_rgb, g_T, st = gpu_render(torch_cuda, tree, rays, layout=layout)
         ref = oracle.render(tree, rays)
         assert_radiance_close(g_rgb, g_T, ref, RTOL_FP32, what=f"degenerate depth {tree.depth}")
 
@@ -95,16 +105,18 @@ def deep_chain_tree(depth, rng):
     return HostTree(depth, 2, np.array(child, np.int32), np.array(sig, np.float32), np.array(sh, np.float32))
 
 
-def test_max_depth_16(torch_cuda):
+@ALL_LAYOUTS
+def test_max_depth_16(torch_cuda, layout):
     tree = deep_chain_tree(16, np.random.default_rng(3))
     rays = plogen.rays_sphere(4000, seed=6, radius=2.0, center=(0.0, 0.0, 0.0))
-    g_rgb, g_T, st = gpu_render(torch_cuda, tree, rays)
+    g_rgb, g_T, st = gpu_render(torch_cuda, tree, rays, layout=layout)
     ref = oracle.render(tree, rays)
     assert np.all(st == 0)
     assert_radiance_close(g_rgb, g_T, ref, RTOL_FP32, what="depth 16")
 
 
-def test_edge_rays(torch_cuda, d6):
+@ALL_LAYOUTS
+def test_edge_rays(torch_cuda, d6, layout):
     rng = np.random.default_rng(7)
     rays = []
     g = np.arange(65) / 64.0
@@ -125,16 +137,17 @@ def test_edge_rays(torch_cuda, d6):
     rays.append([1.0, 0.3, 0.3, 1.0, 0.0, 0.0])     # starts on a face, leaves at once
     rays.append([0.0, 0.2, 0.2, 0.0, 1.0, 0.0])     # slides along the x = 0 face
     rays = np.array(rays, np.float32)
-    g_rgb, g_T, st = gpu_render(torch_cuda, d6, rays)
+    g_rgb, g_T, st = gpu_render(torch_cuda, d6, rays, layout=layout)
     ref = oracle.render(d6, rays)
     assert np.all(st == 0)
     assert_radiance_close(g_rgb, g_T, ref, RTOL_FP32, what="edge rays")
 
 
-def test_invalid_and_missing_rays(torch_cuda, d6):
+@TWO_LAYOUTS
+def test_invalid_and_missing_rays(torch_cuda, d6, layout):
     rays = np.array([[np.nan, 0, 0, 0, 0, 1], [0, 0, -1, 0, 0, 0], [0.5, 0.5, -1, 0, 0, np.inf],
                      [5, 5, 5, 1, 0, 0], [0.5, 0.5, -1, 0, 0, -1]], np.float32)
-    g_rgb, g_T, st = gpu_render(torch_cuda, d6, rays)
+    g_rgb, g_T, st = gpu_render(torch_cuda, d6, rays, layout=layout)
     ref = oracle.render(d6, rays)
     assert list(st) == [plo.RAY_INVALID] * 3 + [0, 0]
     assert np.all(np.isnan(g_rgb[:3])) and np.all(np.isnan(g_T[:3]))
@@ -152,9 +165,10 @@ def test_empty_input_is_a_noop(torch_cuda, d6):
     assert rgb.shape == (0, 3) and T.shape == (0,)
 
 
-def test_early_stop_within_tail_bound(torch_cuda, d6):
+@TWO_LAYOUTS
+def test_early_stop_within_tail_bound(torch_cuda, d6, layout):
     rays = plogen.rays_sphere(65536, seed=9)
-    g_rgb, g_T, _ = gpu_render(torch_cuda, d6, rays, t_stop=1e-4)
+    g_rgb, g_T, _ = gpu_render(torch_cuda, d6, rays, t_stop=1e-4, layout=layout)
     full = oracle.render(d6, rays)
     stop = oracle.render(d6, rays, t_stop=1e-4)
     # same stop rule as the oracle: compare with the oracle's early-stopped
@@ -186,10 +200,11 @@ def test_world_bbox(torch_cuda, d6):
     assert_radiance_close(g_rgb, g_T, ref, RTOL_FP32, what="world bbox")
 
 
+@TWO_LAYOUTS
 @pytest.mark.parametrize("prec,name", [(plo.PREC_FP16, "fp16"), (plo.PREC_BF16, "bf16")])
-def test_16bit_leaves(torch_cuda, d6, prec, name):
+def test_16bit_leaves(torch_cuda, d6, prec, name, layout):
     rays = plogen.rays_sphere(65536, seed=12)
-    g_rgb, g_T, _ = gpu_render(torch_cuda, d6, rays, precision=prec)
+    g_rgb, g_T, _ = gpu_render(torch_cuda, d6, rays, precision=prec, layout=layout)
     # arithmetic parity: the oracle on the exactly dequantised tree
     ref_q = oracle.render(quantise_tree(d6, name), rays)
     assert_radiance_close(g_rgb, g_T, ref_q, RTOL_FP32, what=f"{name} vs dequantised oracle")
@@ -268,9 +283,10 @@ def cube_rays(n, seed):
 
 @pytest.mark.parametrize("model", ["exp", "lin"])
 @pytest.mark.parametrize("sphere", [(0.5, 0.5, 0.5, 0.4), (0.62, 0.45, 0.5, 0.55), (0.5, 0.5, 0.5, 0.9)])
-def test_sphere_proxy_parity(torch_cuda, d6, model, sphere):
+@TWO_LAYOUTS
+def test_sphere_proxy_parity(torch_cuda, d6, model, sphere, layout):
     rays = np.concatenate([plogen.rays_sphere(32768, seed=31), cube_rays(4096, 33)])
-    g_rgb, g_T, st = gpu_render(torch_cuda, d6, rays, transmittance=TRANS[model][0], sphere=sphere)
+    g_rgb, g_T, st = gpu_render(torch_cuda, d6, rays, transmittance=TRANS[model][0], sphere=sphere, layout=layout)
     # the API takes the sphere in FP32: give the oracle the same values
     sphere = tuple(float(np.float32(v)) for v in sphere)
     ref = oracle.render(d6, rays, transmittance=TRANS[model][1], sphere=sphere)
@@ -285,10 +301,11 @@ def test_sphere_proxy_parity(torch_cuda, d6, model, sphere):
         assert not clipped.any()
 
 
-def test_paper_heuristics_parity(torch_cuda, d6):
+@TWO_LAYOUTS
+def test_paper_heuristics_parity(torch_cuda, d6, layout):
     rays = plogen.rays_sphere(65536, seed=32)
     hp = dict(sigma_min=0.1, saturate=True)
-    g_rgb, g_T, _ = gpu_render(torch_cuda, d6, rays, t_stop=0.1, **hp)
+    g_rgb, g_T, _ = gpu_render(torch_cuda, d6, rays, t_stop=0.1, layout=layout, **hp)
     ref = oracle.render(d6, rays, t_stop=0.1, **hp)
     # rays whose running T passes within FP32 rounding of t_stop may stop one
     # leaf apart: find them by moving the threshold by 1e-5 either way
