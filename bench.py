@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--no-pt", action="store_true", help="skip the path-tracer emitter timing")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the linear / sigma_min-alpha_max / sphere-proxy timings")
+    ap.add_argument("--no-layouts", action="store_true",
+                    help="skip the device-layout comparison (octree vs bricks of 4^3 and 8^3 cells)")
     ap.add_argument("--learned", action="store_true",
                     help="run the learned-part experiment (train, distill, error vs ground truth) instead")
     ap.add_argument("--train-steps", type=int, default=3000)
@@ -160,7 +162,7 @@ def measured_peak():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for fn in ("render.cu", "plo_internal.h"):
+    for fn in ("render.cu", "tree.cu", "plo_internal.h"):
         with open(os.path.join(ROOT, "paper_2207_05009_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -477,6 +479,23 @@ def main():
     res = {}
     for name in ("fp32", "fp16", "bf16"):
         res[name] = timed(trees[name])
+    layouts = None
+    if not args.no_layouts:
+        # the same rays on the other device layouts (plo_build_tree_ex), FP32
+        # and FP16 leaves; the default layout's numbers are the lines above
+        layouts = {}
+        for lname, lay, blog in (("octree", plo.LAYOUT_OCTREE, 0), ("bricks4", plo.LAYOUT_BRICKS, 2),
+                                 ("bricks8", plo.LAYOUT_BRICKS, 3)):
+            layouts[lname] = {}
+            for pname, prec in (("fp32", plo.PREC_FP32), ("fp16", plo.PREC_FP16)):
+                tr = plo.Tree(tree, prec, lay, blog)
+                total, per_launch = timed(tr)
+                inf = tr.info()
+                layouts[lname][pname] = {"value": job_rate(world, n, K, total / 1e3), "kernel_ms": per_launch,
+                                         "structure_bytes": int(inf["node_bytes"] if lay == plo.LAYOUT_OCTREE
+                                                                else inf["brick_bytes"] + 64 * inf["top_nodes"])}
+                tr.free()
+            layouts[lname]["fp16_speedup_vs_fp32"] = layouts[lname]["fp16"]["value"] / layouts[lname]["fp32"]["value"]
     variants = None if args.no_variants else run_variants(plo, torch, trees["fp32"], rays, rgb, T, timed,
                                                           world * n * K)
     pt = None if args.no_pt else run_pt(plo, torch, trees["fp32"], W, K)
@@ -590,6 +609,10 @@ def main():
         "fp16": {k: v for k, v in lines["fp16"].items()},
         "bf16": {k: v for k, v in lines["bf16"].items()},
         "fp16_speedup_vs_fp32": lines["fp16"]["value"] / lines["fp32"]["value"],
+        "layout": {"default": "bricks8" if info["layout"] == plo.LAYOUT_BRICKS and info["brick_log"] == 3
+                   else ("octree" if info["layout"] == plo.LAYOUT_OCTREE else f"bricks{1 << info['brick_log']}"),
+                   "n_bricks": int(info["n_bricks"]), "brick_bytes": int(info["brick_bytes"]),
+                   "compared": layouts},
         "parity": parity,
         "batch": batch,
         "variants": variants,
