@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--no-pt", action="store_true", help="skip the path-tracer emitter timing")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the linear / sigma_min-alpha_max / sphere-proxy timings")
+    ap.add_argument("--no-train", action="store_true", help="skip the training-step timing")
+    ap.add_argument("--train-timed-steps", type=int, default=60)
     ap.add_argument("--no-layouts", action="store_true",
                     help="skip the device-layout comparison (octree vs bricks of 4^3 and 8^3 cells)")
     ap.add_argument("--learned", action="store_true",
@@ -330,6 +332,86 @@ def run_pt(plo, torch, tree32, W, K):
     return out
 
 
+def measured_tflops():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), float(d["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, 1900.0, "fallback"
+
+
+def run_train(plo, torch, steps: int, W: int):
+    """The training step of the learned part (Sec. 4.4): 4096 rays x 128
+    samples per step on targets rendered from the depth-6 luminaire by the
+    plain renderer, the paper's loss, linear-head network; `steps` timed
+    steps after W warm-up steps (CUDA events), plus the tensor-core layers
+    alone on the same shapes (524,288 rows): forward 256 -> 256 with the
+    ReLU bits, data gradient through the mask, weight gradient with the bias
+    sums."""
+    import plogen
+    from paper_2207_05009_gb300 import learned
+    gt = plo.Tree(plogen.luminaire_tree(plogen.LUMINAIRE_D6))
+    batches = learned.target_batches(gt, [plogen.rays_sphere(4096, seed=200 + k) for k in range(8)])
+    l_max, c0 = learned.emission_scale(batches)
+    net = plo.Mlp(l_max=l_max, total_steps=steps + W, init_radiance=c0)
+    loss = torch.empty(1, device="cuda")
+    stream = torch.cuda.current_stream()
+    for k in range(W):
+        rays, rgb, alpha = batches[k % 8]
+        net.train_step(rays, rgb, alpha, n_samples=128, loss_out=loss)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(steps):
+        rays, rgb, alpha = batches[k % 8]
+        net.train_step(rays, rgb, alpha, n_samples=128, loss_out=loss)
+    b.record(stream)
+    torch.cuda.synchronize()
+    net.check()
+    ms = a.elapsed_time(b) / steps
+    M = 4096 * 128
+    trunk = 63 * 256 + 7 * 256 * 256
+    flops = M * 2 * 3 * (trunk + 256 * 49)
+    sustained, burst, src = measured_tflops()
+
+    def time_op(fn, reps=10):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    g = torch.Generator(device="cuda").manual_seed(5)
+    H = (torch.rand(M, 256, device="cuda", generator=g) - 0.3).to(torch.bfloat16)
+    Wt = (torch.randn(256, 256, device="cuda", generator=g) * 0.06).to(torch.bfloat16)
+    bias = torch.zeros(256, device="cuda")
+    bits = torch.empty((M, 8), device="cuda", dtype=torch.int32)
+    out = torch.empty((M, 256), device="cuda", dtype=torch.bfloat16)
+    dW = torch.zeros(256, 256, device="cuda")
+    db = torch.zeros(256, device="cuda")
+    layer_flops = 2 * M * 256 * 256
+    layers = {}
+    for name, fn in (("forward_relu_bits", lambda: plo.gemm_bf16(H, Wt, 0, bias=bias, bits=bits, out=out)),
+                     ("data_gradient_mask", lambda: plo.gemm_bf16(H, Wt, 3, bits=bits, out=out)),
+                     ("weight_gradient_bias", lambda: plo.wgrad_bf16(H, H, dW, db=db))):
+        t = time_op(fn)
+        layers[name] = {"ms": t, "tflops": layer_flops / (t / 1e3) / 1e12}
+    del H, out
+    return {"workload": "4096 rays x 128 samples per step (524,288 network evaluations), paper loss, "
+                        "8 x 256 trunk + linear head, targets from the depth-6 luminaire",
+            "steps_timed": steps, "ms_per_step": ms, "tflops": flops / (ms / 1e3) / 1e12,
+            "flops_per_step": flops, "peak_tflops_sustained": sustained,
+            "frac_of_sustained": flops / (ms / 1e3) / 1e12 / sustained, "peak_source": f"{src} (MEASURED_PEAKS.json)",
+            "final_loss": float(loss.item()), "layer_256x256_M524288": layers}
+
+
 def run_learned(args):
     """Train the NeRF-SH network on targets rendered from the depth-6
     luminaire (4096 rays x 128 samples per step, the paper's loss), distil it
@@ -499,6 +581,7 @@ def main():
     variants = None if args.no_variants else run_variants(plo, torch, trees["fp32"], rays, rgb, T, timed,
                                                           world * n * K)
     pt = None if args.no_pt else run_pt(plo, torch, trees["fp32"], W, K)
+    train = None if args.no_train else run_train(plo, torch, args.train_timed_steps, W)
     e2e = None
     if not args.no_e2e:
         rays_h = torch.from_numpy(rays_np).pin_memory()
@@ -617,6 +700,7 @@ def main():
         "batch": batch,
         "variants": variants,
         "path_tracer": pt,
+        "train": train,
     }
     line["fp16"]["roofline"]["frac"] = line["fp16"]["roofline"]["achieved"] / peak
     print(json.dumps(line), flush=True)
