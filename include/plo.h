@@ -68,7 +68,7 @@ typedef struct plo_tree plo_tree;
 
 /* Canonical host tree (Sec. 5 plenoctree), read-only during the call.
  *   depth      maximum leaf level, 0..16 (level 0 = the root cell).
- *   sh_degree  l_max, 0..3; K = (l_max + 1)^2 coefficients per channel.
+ *   sh_degree  l_max, 0..4; K = (l_max + 1)^2 coefficients per channel.
  *   child      int32 [n_nodes][8]: >= 0 internal node id, -1 empty octant,
  *              <= -2 leaf with id -c-2.  Node 0 is the root; the child slot is
  *              bx | by << 1 | bz << 2 with b = 1 for the upper half.

@@ -108,7 +108,7 @@ def max_threads() -> int:
 def sh_basis(degree: int, d) -> np.ndarray:
     """Y_k(d), k = l(l+1)+m, FP64, for one direction d."""
     lib = _load()
-    out = np.zeros(16, np.float64)
+    out = np.zeros(25, np.float64)
     lib.oracle_sh_basis(degree, float(d[0]), float(d[1]), float(d[2]), out.ctypes.data)
     return out[: (degree + 1) ** 2]
 

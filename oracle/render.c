@@ -248,7 +248,7 @@ static void render_one(const oracle_tree* t, const oracle_params* prm, const flo
         if (!(tn < tf) || !(tf > 0.0)) return;
     }
 
-    double Y[16];
+    double Y[25];
     oracle_sh_basis(t->sh_degree, dw[0], dw[1], dw[2], Y);
 
     double tcur = tn > 0.0 ? tn : 0.0;

@@ -41,6 +41,9 @@ constexpr int BLOCK = 256;
 #ifndef PLO_RENDER_MIN_BLOCKS
 #define PLO_RENDER_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for (measured best)
 #endif
+#ifndef PLO_BRICK_MIN_BLOCKS
+#define PLO_BRICK_MIN_BLOCKS 3  // the same for the brick-layout kernels
+#endif
 constexpr int WARPS = BLOCK / 32;
 constexpr int STACK = MAX_DEPTH + 1;
 constexpr int64_t RENDER_CLAIM = 64;  // rays a warp claims at a time from the shared cursor
@@ -242,10 +245,14 @@ __device__ __forceinline__ void sh_emission(const TreeParams& tp, uint32_t rec, 
         sh_eval<(K > 0 ? K : 1), PREC>(p, yword, Y, r, g, b);
         return;
     }
-    float Y[16];
-    sh_basis<16>(dirn[0], dirn[1], dirn[2], Y);
+    float Y[25];
+    if (tp.K == 25)
+        sh_basis<25>(dirn[0], dirn[1], dirn[2], Y);
+    else
+        sh_basis<16>(dirn[0], dirn[1], dirn[2], Y);
 #define PLO_SH_CASE(KK, PP) \
     if (tp.K == KK && tp.prec == PP) return sh_eval<KK, PP>(p, yword, Y, r, g, b);
+    PLO_SH_CASE(25, PLO_PREC_FP32) PLO_SH_CASE(25, PLO_PREC_FP16) PLO_SH_CASE(25, PLO_PREC_BF16)
     PLO_SH_CASE(16, PLO_PREC_FP32) PLO_SH_CASE(9, PLO_PREC_FP32) PLO_SH_CASE(16, PLO_PREC_FP16)
     PLO_SH_CASE(9, PLO_PREC_FP16) PLO_SH_CASE(16, PLO_PREC_BF16) PLO_SH_CASE(9, PLO_PREC_BF16)
     PLO_SH_CASE(4, PLO_PREC_FP32) PLO_SH_CASE(4, PLO_PREC_FP16) PLO_SH_CASE(4, PLO_PREC_BF16)
@@ -801,7 +808,8 @@ __device__ void brick_step(const KParams& kp, const TreeParams& tp, int64_t i, R
 // The trace and sphere-proxy kernels keep more per-ray state: 3 blocks per
 // SM (80 registers) beats 4 with spills for them (measured).
 template <int K, int PREC, bool TRACE, bool SPHERE, bool BRICKS>
-__global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : PLO_RENDER_MIN_BLOCKS) k_render(KParams kp) {
+__global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : (BRICKS ? PLO_BRICK_MIN_BLOCKS : PLO_RENDER_MIN_BLOCKS))
+    k_render(KParams kp) {
     // nodes of the top levels, staged once per (persistent) block
     extern __shared__ uint2 s_nodes[];
     const TreeParams& tp = kp.tree;
@@ -811,7 +819,7 @@ __global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : PLO_RENDER_MIN_
     // node id per level of the current cell's path, one column per thread
     __shared__ uint32_t s_stack[STACK * BLOCK];
     uint32_t* stack = s_stack + threadIdx.x;
-    __shared__ float s_Y[16 * BLOCK];
+    __shared__ float s_Y[K * BLOCK];
     float* sY = s_Y + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
@@ -1018,6 +1026,7 @@ cudaError_t dispatch(const plo_tree* t, const KParams& kp, size_t smem, cudaStre
     PLO_CASE(1, PLO_PREC_FP32) PLO_CASE(4, PLO_PREC_FP32) PLO_CASE(9, PLO_PREC_FP32) PLO_CASE(16, PLO_PREC_FP32)
     PLO_CASE(1, PLO_PREC_FP16) PLO_CASE(4, PLO_PREC_FP16) PLO_CASE(9, PLO_PREC_FP16) PLO_CASE(16, PLO_PREC_FP16)
     PLO_CASE(1, PLO_PREC_BF16) PLO_CASE(4, PLO_PREC_BF16) PLO_CASE(9, PLO_PREC_BF16) PLO_CASE(16, PLO_PREC_BF16)
+    PLO_CASE(25, PLO_PREC_FP32) PLO_CASE(25, PLO_PREC_FP16) PLO_CASE(25, PLO_PREC_BF16)
 #undef PLO_CASE
     return cudaErrorInvalidValue;
 }

@@ -45,8 +45,8 @@ plo_status validate(const plo_tree_desc* t) {
     if (!t) return set_error(PLO_ERR_INVALID_ARG, "tree descriptor is NULL");
     if (t->depth < 0 || t->depth > MAX_DEPTH)
         return set_error(PLO_ERR_INVALID_ARG, "depth must be in [0, 16], got " + std::to_string(t->depth));
-    if (t->sh_degree < 0 || t->sh_degree > 3)
-        return set_error(PLO_ERR_INVALID_ARG, "sh_degree must be in [0, 3], got " + std::to_string(t->sh_degree));
+    if (t->sh_degree < 0 || t->sh_degree > 4)
+        return set_error(PLO_ERR_INVALID_ARG, "sh_degree must be in [0, 4], got " + std::to_string(t->sh_degree));
     if (t->n_nodes < 0 || t->n_leaves < 0) return set_error(PLO_ERR_INVALID_ARG, "negative node or leaf count");
     if (t->n_nodes >= (int64_t)LEAF_BIT - 1) return set_error(PLO_ERR_INVALID_ARG, "too many nodes (>= 2^31 - 1)");
     if (t->n_leaves >= (int64_t)NO_SH_RECORD) return set_error(PLO_ERR_INVALID_ARG, "too many leaves");

@@ -68,7 +68,7 @@ enum { STREAM_EMISSIVE = 1, STREAM_SIGMA = 2, STREAM_SH = 3, STREAM_RAY = 4 };
 /* ------------------------------------------------------------------ */
 typedef struct {
     int32_t depth;          /* 1..16 */
-    int32_t sh_degree;      /* 0..3 */
+    int32_t sh_degree;      /* 0..4 */
     uint64_t seed;
     double shell_center[3];
     double shell_radius;
@@ -202,7 +202,7 @@ void plogen_free(plogen_tree* t) {
 /* Pass 1: structure.  Returns NULL on invalid parameters or allocation
  * failure. */
 plogen_tree* plogen_build(const plogen_params* p, int64_t* n_nodes, int64_t* n_leaves) {
-    if (!p || p->depth < 1 || p->depth > 16 || p->sh_degree < 0 || p->sh_degree > 3) return NULL;
+    if (!p || p->depth < 1 || p->depth > 16 || p->sh_degree < 0 || p->sh_degree > 4) return NULL;
     plogen_tree* t = (plogen_tree*)calloc(1, sizeof(plogen_tree));
     if (!t) return NULL;
     t->p = *p;

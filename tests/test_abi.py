@@ -86,7 +86,8 @@ def test_validator_rejects_malformed_trees():
         _expect(t, BAD)
     # parameter errors
     _expect(HostTree(17, 2, base.child, base.sigma, base.sh), ARG)
-    _expect(HostTree(base.depth, 4, base.child, base.sigma, np.zeros((base.n_leaves, 3, 25), np.float32)), ARG)
+    _expect(HostTree(base.depth, 5, base.child, base.sigma, np.zeros((base.n_leaves, 3, 36), np.float32)), ARG)
+    plo.validate(HostTree(base.depth, 4, base.child, base.sigma, np.zeros((base.n_leaves, 3, 25), np.float32)))
     t = HostTree(base.depth, 2, base.child, base.sigma, base.sh)
     t.bbox_min, t.bbox_max = (0, 0, 0), (1, 0, 1)
     _expect(t, ARG)

@@ -22,8 +22,9 @@ def test_matches_cartesian_table():
     for _ in range(200):
         v = rng.normal(size=3)
         v /= np.linalg.norm(v)
-        got = oracle.sh_basis(3, v)
-        np.testing.assert_allclose(got, cartesian_table(*v), rtol=0, atol=2e-15)
+        got = oracle.sh_basis(4, v)
+        np.testing.assert_allclose(got, cartesian_table(*v), rtol=0, atol=4e-15)
+        np.testing.assert_array_equal(oracle.sh_basis(3, v), got[:16])
 
 
 def test_signs_and_index_order():
@@ -32,19 +33,19 @@ def test_signs_and_index_order():
     assert oracle.sh_basis(1, (0, 1, 0))[1] == pytest.approx(c1)   # m=-1 ~ y
     assert oracle.sh_basis(1, (0, 0, 1))[2] == pytest.approx(c1)   # m=0 ~ z
     # m < 0 terms are sin(|m| phi): they vanish on the xz half-plane phi = 0
-    Y = oracle.sh_basis(3, (0.6, 0.0, 0.8))
-    for l in range(1, 4):
+    Y = oracle.sh_basis(4, (0.6, 0.0, 0.8))
+    for l in range(1, 5):
         for m in range(-l, 0):
             assert abs(Y[l * (l + 1) + m]) < 1e-15
 
 
 def test_orthonormal_under_exact_quadrature():
     # Gauss-Legendre in cos(theta) x uniform phi is exact for the products
-    # Y_i Y_j of degree <= 6.
-    deg = 3
+    # Y_i Y_j of degree <= 8.
+    deg = 4
     K = (deg + 1) ** 2
     xs, ws = np.polynomial.legendre.leggauss(8)
-    nphi = 16
+    nphi = 20
     G = np.zeros((K, K))
     for z, w in zip(xs, ws):
         s = math.sqrt(1 - z * z)
@@ -61,8 +62,8 @@ def test_addition_theorem():
         a, b = rng.normal(size=3), rng.normal(size=3)
         a /= np.linalg.norm(a)
         b /= np.linalg.norm(b)
-        Ya, Yb = oracle.sh_basis(3, a), oracle.sh_basis(3, b)
-        for l in range(4):
+        Ya, Yb = oracle.sh_basis(4, a), oracle.sh_basis(4, b)
+        for l in range(5):
             sl = slice(l * l, (l + 1) ** 2)
             lhs = float(np.dot(Ya[sl], Yb[sl]))
             rhs = (2 * l + 1) / (4 * math.pi) * np.polynomial.legendre.Legendre.basis(l)(float(np.dot(a, b)))

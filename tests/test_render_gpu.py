@@ -67,7 +67,7 @@ def test_sigmoid_activation_parity(torch_cuda, d6):
 @pytest.mark.parametrize("seed", range(8))
 def test_random_trees_all_degrees_ragged(torch_cuda, seed, layout):
     rng = np.random.default_rng(seed)
-    deg = seed % 4
+    deg = seed % 5
     tree = random_tree(1 + seed % 5, rng, sh_degree=deg)
     n = 1000 + 37 * seed  # not a multiple of the warp or block size
     rays = plogen.rays_sphere(n, seed=100 + seed, radius=1.5 + seed)
@@ -212,6 +212,21 @@ def test_16bit_leaves(torch_cuda, d6, prec, name, layout):
     ref = oracle.render(d6, rays)
     rtol = RTOL_FP16 if name == "fp16" else RTOL_BF16
     assert_radiance_close(g_rgb, g_T, ref, rtol, what=f"{name} vs FP32-leaf oracle")
+
+
+@TWO_LAYOUTS
+@pytest.mark.parametrize("prec,name", [(plo.PREC_FP32, "fp32"), (plo.PREC_FP16, "fp16"), (plo.PREC_BF16, "bf16")])
+def test_sh_degree_4_leaves(torch_cuda, prec, name, layout):
+    """l_max = 4 (K = 25, the largest degree of the paper's ablation, Sec.
+    6.2) on the depth-6 luminaire's geometry: FP32 leaves against the FP64
+    oracle, 16-bit leaves against the oracle on the dequantised tree."""
+    tree = plogen.luminaire_tree(plogen.LUMINAIRE_D6.with_(sh_degree=4))
+    assert tree.K == 25
+    rays = plogen.rays_sphere(32768, seed=21)
+    g_rgb, g_T, st = gpu_render(torch_cuda, tree, rays, precision=prec, layout=layout)
+    assert np.all(st == 0)
+    ref = oracle.render(tree if name == "fp32" else quantise_tree(tree, name), rays)
+    assert_radiance_close(g_rgb, g_T, ref, RTOL_FP32, what=f"l_max 4 {name} {layout}")
 
 
 def test_lookup_bit_exact(torch_cuda, d6):

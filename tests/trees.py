@@ -157,8 +157,9 @@ def chord(o, d, lo=(0, 0, 0), hi=(1, 1, 1)):
 
 
 def cartesian_table(x, y, z):
-    """Real orthonormal SH, l <= 3, no Condon-Shortley phase, k = l(l+1)+m
-    (standard Cartesian table)."""
+    """Real orthonormal SH, l <= 4, no Condon-Shortley phase, k = l(l+1)+m
+    (standard Cartesian table; degree 4 from the associated Legendre
+    functions P_4^m and cos / sin(m phi) written as polynomials of x, y, z)."""
     pi = math.pi
     return np.array([
         0.5 * math.sqrt(1 / pi),
@@ -177,6 +178,15 @@ def cartesian_table(x, y, z):
         0.25 * math.sqrt(21 / (2 * pi)) * x * (5 * z * z - 1),
         0.25 * math.sqrt(105 / pi) * z * (x * x - y * y),
         0.25 * math.sqrt(35 / (2 * pi)) * x * (x * x - 3 * y * y),
+        0.75 * math.sqrt(35 / pi) * x * y * (x * x - y * y),
+        0.75 * math.sqrt(35 / (2 * pi)) * y * z * (3 * x * x - y * y),
+        0.75 * math.sqrt(5 / pi) * x * y * (7 * z * z - 1),
+        0.75 * math.sqrt(5 / (2 * pi)) * y * z * (7 * z * z - 3),
+        3 / 16 * math.sqrt(1 / pi) * (35 * z ** 4 - 30 * z * z + 3),
+        0.75 * math.sqrt(5 / (2 * pi)) * x * z * (7 * z * z - 3),
+        3 / 8 * math.sqrt(5 / pi) * (x * x - y * y) * (7 * z * z - 1),
+        0.75 * math.sqrt(35 / (2 * pi)) * x * z * (x * x - 3 * y * y),
+        3 / 16 * math.sqrt(35 / pi) * (x ** 4 - 6 * x * x * y * y + y ** 4),
     ])
 
 
