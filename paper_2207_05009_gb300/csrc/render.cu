@@ -45,7 +45,6 @@ constexpr int BLOCK = 256;
 #define PLO_BRICK_MIN_BLOCKS 3  // the same for the brick-layout kernels
 #endif
 constexpr int WARPS = BLOCK / 32;
-constexpr int STACK = MAX_DEPTH + 1;
 constexpr int64_t RENDER_CLAIM = 64;  // rays a warp claims at a time from the shared cursor
 
 // One packed tree as the kernels see it.
@@ -245,18 +244,19 @@ __device__ __forceinline__ void sh_emission(const TreeParams& tp, uint32_t rec, 
         sh_eval<(K > 0 ? K : 1), PREC>(p, yword, Y, r, g, b);
         return;
     }
-    float Y[25];
-    if (tp.K == 25)
-        sh_basis<25>(dirn[0], dirn[1], dirn[2], Y);
-    else
-        sh_basis<16>(dirn[0], dirn[1], dirn[2], Y);
-#define PLO_SH_CASE(KK, PP) \
-    if (tp.K == KK && tp.prec == PP) return sh_eval<KK, PP>(p, yword, Y, r, g, b);
-    PLO_SH_CASE(25, PLO_PREC_FP32) PLO_SH_CASE(25, PLO_PREC_FP16) PLO_SH_CASE(25, PLO_PREC_BF16)
+    // each degree builds only its own basis, so that the registers of the
+    // larger bases are taken only in their branches
+#define PLO_SH_CASE(KK, PP)                                  \
+    if (tp.K == KK && tp.prec == PP) {                       \
+        float Y[KK];                                         \
+        sh_basis<KK>(dirn[0], dirn[1], dirn[2], Y);          \
+        return sh_eval<KK, PP>(p, yword, Y, r, g, b);        \
+    }
     PLO_SH_CASE(16, PLO_PREC_FP32) PLO_SH_CASE(9, PLO_PREC_FP32) PLO_SH_CASE(16, PLO_PREC_FP16)
     PLO_SH_CASE(9, PLO_PREC_FP16) PLO_SH_CASE(16, PLO_PREC_BF16) PLO_SH_CASE(9, PLO_PREC_BF16)
     PLO_SH_CASE(4, PLO_PREC_FP32) PLO_SH_CASE(4, PLO_PREC_FP16) PLO_SH_CASE(4, PLO_PREC_BF16)
     PLO_SH_CASE(1, PLO_PREC_FP32) PLO_SH_CASE(1, PLO_PREC_FP16) PLO_SH_CASE(1, PLO_PREC_BF16)
+    PLO_SH_CASE(25, PLO_PREC_FP32) PLO_SH_CASE(25, PLO_PREC_FP16) PLO_SH_CASE(25, PLO_PREC_BF16)
 #undef PLO_SH_CASE
     r = g = b = 0.0f;
 }
@@ -810,15 +810,15 @@ __device__ void brick_step(const KParams& kp, const TreeParams& tp, int64_t i, R
 template <int K, int PREC, bool TRACE, bool SPHERE, bool BRICKS>
 __global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : (BRICKS ? PLO_BRICK_MIN_BLOCKS : PLO_RENDER_MIN_BLOCKS))
     k_render(KParams kp) {
-    // nodes of the top levels, staged once per (persistent) block
+    // nodes of the top levels, staged once per (persistent) block, then the
+    // node id per level of the current cell's path (top_depth + 1 rows, one
+    // column per thread): dynamic shared memory sized by the tree, so that a
+    // shallow tree leaves more of the SM's memory to L1
     extern __shared__ uint2 s_nodes[];
     const TreeParams& tp = kp.tree;
     for (int j = threadIdx.x; j < tp.n_top * 8; j += BLOCK) s_nodes[j] = tp.nodes[j];
     __syncthreads();
-
-    // node id per level of the current cell's path, one column per thread
-    __shared__ uint32_t s_stack[STACK * BLOCK];
-    uint32_t* stack = s_stack + threadIdx.x;
+    uint32_t* stack = reinterpret_cast<uint32_t*>(s_nodes + tp.n_top * 8) + threadIdx.x;
     __shared__ float s_Y[K * BLOCK];
     float* sY = s_Y + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -893,10 +893,13 @@ struct BatchParams {
     int64_t off[MAX_BATCH + 1];
     int32_t n_trees;
     int32_t claim;
+    int32_t stack_off;           // entries (uint2) of staged nodes before the node stack
     unsigned long long* cursor;  // zeroed before each launch
 };
 
-__global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(BatchParams bp) {
+template <bool BRICKS>
+__global__ void __launch_bounds__(BLOCK, BRICKS ? PLO_BRICK_MIN_BLOCKS : PLO_RENDER_MIN_BLOCKS)
+    k_render_batch(BatchParams bp) {
     extern __shared__ uint2 s_nodes[];
     __shared__ TreeParams s_tp[MAX_BATCH];
     __shared__ long long s_off[MAX_BATCH + 1];
@@ -909,8 +912,8 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(B
     __syncthreads();
     const KParams& kp = bp.base;
     const long long total = s_off[bp.n_trees];
-    __shared__ uint32_t s_stack[STACK * BLOCK];
-    uint32_t* stack = s_stack + threadIdx.x;
+    // per-thread node stack after the staged nodes (bp.stack_rows rows)
+    uint32_t* stack = reinterpret_cast<uint32_t*>(s_nodes + bp.stack_off) + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
 
@@ -950,9 +953,9 @@ __global__ void __launch_bounds__(BLOCK, PLO_RENDER_MIN_BLOCKS) k_render_batch(B
         const unsigned live = __ballot_sync(0xffffffffu, R.state != ST_IDLE);
         if (live == 0u) break;
         const TreeParams& tp = s_tp[R.tree];
-        if (R.state == ST_BRICK) brick_step<0, -1, false>(kp, tp, my, R, stack);
+        if (BRICKS && R.state == ST_BRICK) brick_step<0, -1, false>(kp, tp, my, R, stack);
         if (R.state == ST_LEAF) leaf_step<0, -1, false, false>(kp, tp, my, R, stack);
-        if (R.state == ST_DESCEND) descend_step<true>(tp, s_nodes, R, stack);
+        if (R.state == ST_DESCEND) descend_step<BRICKS>(tp, s_nodes, R, stack);
     }
 }
 
@@ -1124,7 +1127,7 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     // stage only the nodes of levels 0..2 (measured: the shared memory left
     // over goes to L1, which serves the deeper node loads better)
     if (kp.tree.n_top > BATCH_TOP_NODES) kp.tree.n_top = BATCH_TOP_NODES;
-    size_t smem = (size_t)kp.tree.n_top * 8 * sizeof(uint2);
+    size_t smem = (size_t)kp.tree.n_top * 8 * sizeof(uint2) + (size_t)(kp.tree.top_depth + 1) * BLOCK * 4;
     cudaError_t e = cudaSuccess;
     cudaStream_t cs = (cudaStream_t)stream;
     unsigned long long* cursor = nullptr;
@@ -1306,6 +1309,7 @@ struct plo_batch {
     int device;
     plo_batch_config cfg;
     int32_t full_top[MAX_BATCH];  // stageable top nodes per tree (<= BATCH_TOP_NODES)
+    bool bricks;                  // some tree uses the brick layout
     unsigned long long* d_cursor;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -1321,15 +1325,23 @@ void apply_config(plo_batch* b) {
         b->bp.trees[t].s_off = off;
         off += n * 8;
     }
-    b->smem = (size_t)off * sizeof(uint2);
+    int rows = 1;
+    for (int t = 0; t < b->n_trees; ++t) rows = std::max(rows, b->bp.trees[t].top_depth + 1);
+    b->bp.stack_off = off;
+    b->smem = (size_t)off * sizeof(uint2) + (size_t)rows * BLOCK * 4;
     b->bp.claim = b->cfg.claim_rays;
 }
 
+void (*batch_kernel(const plo_batch* b))(BatchParams) {
+    return b->bricks ? k_render_batch<true> : k_render_batch<false>;
+}
+
 cudaError_t launch_batch(plo_batch* b, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_render_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    auto fn = batch_kernel(b);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_batch, BLOCK, b->smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BLOCK, b->smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     const int bps = b->cfg.blocks_per_sm > 0 && b->cfg.blocks_per_sm < per_sm ? b->cfg.blocks_per_sm : per_sm;
@@ -1338,7 +1350,7 @@ cudaError_t launch_batch(plo_batch* b, cudaStream_t s) {
     if (grid < 1) return cudaSuccess;
     e = cudaMemsetAsync(b->d_cursor, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    k_render_batch<<<(unsigned)grid, BLOCK, b->smem, s>>>(b->bp);
+    fn<<<(unsigned)grid, BLOCK, b->smem, s>>>(b->bp);
     return cudaGetLastError();
 }
 
@@ -1393,6 +1405,7 @@ extern "C" plo_status plo_batch_create(const plo_tree* const* trees, int32_t n_t
     kp.n = b->n_rays;
     for (int t = 0; t < n_trees; ++t) {
         fill_tree_params(trees[t], params, &b->bp.trees[t]);
+        b->bricks |= trees[t]->layout == PLO_LAYOUT_BRICKS;
         b->full_top[t] = std::min<int32_t>(b->bp.trees[t].n_top, BATCH_TOP_NODES);
     }
     for (int t = 0; t <= n_trees; ++t) b->bp.off[t] = ray_offsets[t];
@@ -1455,7 +1468,7 @@ extern "C" plo_status plo_batch_capture(plo_batch* b, const float* d_rays, float
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_error(e, "capture stream");
     // the occupancy query and attribute set happen outside the capture
-    e = cudaFuncSetAttribute(k_render_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    e = cudaFuncSetAttribute(batch_kernel(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t le = launch_batch(b, cs);

@@ -34,7 +34,7 @@ ALL_LAYOUTS = pytest.mark.parametrize("layout", list(LAYOUTS))
 TWO_LAYOUTS = pytest.mark.parametrize("layout", ["octree", "bricks8"])
 
 
-def gpu_render(torch, tree, rays, precision=plo.PREC_FP32, layout="bricks8", **kw):
+def gpu_render(torch, tree, rays, precision=plo.PREC_FP32, layout="octree", **kw):
     t = plo.Tree(tree, precision, *LAYOUTS[layout])
     r = torch.from_numpy(np.ascontiguousarray(rays)).cuda()
     st = torch.full((len(rays),), -7, dtype=torch.int32, device="cuda")
