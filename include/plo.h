@@ -422,10 +422,12 @@ plo_status plo_hier_samples(const float* d_rays, int32_t n_rays, int32_t n_coars
  * kept, each as a leaf holding the mean of ReLU(sigma_raw) and of the raw SH
  * coefficients over `samples` (1..256) jittered positions inside it (offsets
  * from SplitMix64 keyed by the desc's seed and the voxel's Morton code).  The
- * tree is packed at `precision` and owned by *out; render it with
- * PLO_ACT_SIGMOID and the network's l_max.  Host memory: 8 bytes per kept
- * voxel for its code and 4 (1 + 3K) for its values, plus plo_build_tree's;
- * device memory: the same values and codes, plus the network's workspace.
+ * tree is packed at `precision` in the octree layout, on the device (no host
+ * copy of the leaves), and owned by *out; render it with PLO_ACT_SIGMOID and
+ * the network's l_max.  Device memory: 4 bytes per voxel of the 2^depth grid
+ * for the kept codes, per kept voxel 5 bytes plus its SH record (12K bytes
+ * FP32, 6K 16-bit, rounded up to 16), the node tables (96 bytes per node),
+ * plus the network's workspace.
  * Errors: PLO_ERR_INVALID_ARG; PLO_ERR_OOM when a host or device allocation
  * fails; PLO_ERR_CUDA; PLO_ERR_TIMEOUT from the network's kernels. */
 plo_status plo_distill(plo_mlp* mlp, int32_t depth, int32_t samples, float sigma_thresh, int32_t precision,
@@ -473,6 +475,14 @@ plo_status plo_mlp_get_activation(const plo_mlp* mlp, int32_t layer, void* d_out
 plo_status plo_mlp_quad(plo_mlp* mlp, const float* d_rays, const float* d_raw, const float* d_delta,
                         const float* d_rgb_gt, const float* d_alpha_gt, int32_t n_rays, int32_t n_samples,
                         float* d_ray_out, float* d_draw, void* stream);
+
+/* Canonical export of a packed tree (synchronous): the node table as the
+ * canonical child table (node ids of the packed layout; leaves by their
+ * canonical ids), and every leaf's sigma and SH coefficients, dequantised for
+ * FP16 / BF16 trees.  h_child int32 [n_nodes][8], h_sigma float [n_leaves],
+ * h_sh float [n_leaves][3][K] (counts from plo_tree_get_info).  A distilled
+ * tree exported this way and rebuilt with plo_build_tree renders the same. */
+plo_status plo_tree_export(const plo_tree* tree, int32_t* h_child, float* h_sigma, float* h_sh);
 
 /* Synchronises `stream`; PLO_ERR_TIMEOUT if a tensor-core kernel gave up on
  * a bounded pipeline wait since the last check (the flag is cleared). */

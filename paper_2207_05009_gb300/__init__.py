@@ -234,6 +234,22 @@ class Tree:
     def check(self, stream=None) -> None:
         _check(load().plo_tree_check(self._h, _stream(stream)))
 
+    def export(self):
+        """plo_tree_export: the packed tree as a canonical host tree (plogen
+        HostTree; 16-bit leaves dequantised)."""
+        from plogen import HostTree
+        inf = self.info()
+        K = (inf["sh_degree"] + 1) ** 2
+        child = np.empty((inf["n_nodes"], 8), np.int32)
+        sigma = np.empty(inf["n_leaves"], np.float32)
+        sh = np.empty((inf["n_leaves"], 3, K), np.float32)
+        lib = load()
+        fn = lib.plo_tree_export
+        fn.restype, fn.argtypes = ctypes.c_int32, [ctypes.c_void_p] * 4
+        _check(fn(self._h, ctypes.c_void_p(child.ctypes.data), ctypes.c_void_p(sigma.ctypes.data),
+                  ctypes.c_void_p(sh.ctypes.data)))
+        return HostTree(inf["depth"], inf["sh_degree"], child, sigma, sh)
+
     def free(self):
         if getattr(self, "_h", None) and self._h.value:
             load().plo_tree_free(self._h)

@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -311,12 +312,12 @@ __global__ void k_pe_centres(uint64_t base, int64_t n, int D, __nv_bfloat16* X) 
 // S jittered samples in each listed voxel -> X (row i*S + s).  Offsets come
 // from SplitMix64 (Steele, Lea, Flood 2014): key = mix(mix(seed ^ 0xD15711)
 // ^ (code * 0x9E3779B97F4A7C15 + 3 s + a)), u = (key >> 40) / 2^24.
-__global__ void k_pe_jitter(const uint64_t* codes, int64_t nv, int S, int D, uint64_t seed, __nv_bfloat16* X) {
+__global__ void k_pe_jitter(const uint32_t* codes, int64_t nv, int S, int D, uint64_t seed, __nv_bfloat16* X) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nv * S) return;
     const int64_t i = idx / S;
     const int s = (int)(idx % S);
-    const uint64_t code = __ldg(reinterpret_cast<const unsigned long long*>(codes) + i);
+    const uint64_t code = __ldg(codes + i);
     uint32_t c[3];
     morton_decode(code, D, c);
     const uint64_t k0 = mix64(seed ^ 0xD15711ULL);
@@ -332,29 +333,80 @@ __global__ void k_pe_jitter(const uint64_t* codes, int64_t nv, int S, int D, uin
     encode_point(x, X + idx * PE_PAD);
 }
 
-__global__ void k_keep(const float* raw, int64_t n, float thresh, uint8_t* flags) {
+__global__ void k_keep(const float* raw, int64_t n, float thresh, uint32_t* flags) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
-    flags[idx] = fmaxf(__ldg(raw + idx * OUT_PAD), 0.0f) >= thresh ? 1 : 0;
+    flags[idx] = fmaxf(__ldg(raw + idx * OUT_PAD), 0.0f) >= thresh ? 1u : 0u;
 }
 
-// out[i] = mean over the S samples of voxel i: ReLU(sigma_raw), raw SH.
-// Mean over a voxel's S jittered samples of ReLU(sigma_raw) -> sigma[i] and
-// of each raw SH output -> sh[i][k] (n_out = 1 + 3K outputs per sample).
-__global__ void k_average(const float* raw, int64_t nv, int S, int n_out, float* sigma, float* sh) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nv * n_out) return;
-    const int64_t i = idx / n_out;
-    const int k = (int)(idx % n_out);
-    float acc = 0.0f;
-    for (int s = 0; s < S; ++s) {
-        const float v = __ldg(raw + (i * S + s) * OUT_PAD + k);
-        acc += k == 0 ? fmaxf(v, 0.0f) : v;
+// Appends the kept voxels of a chunk (codes base + i, Morton order) at the
+// running count *count; the last thread advances the count.
+__global__ void k_compact_kept(uint64_t base, int64_t n, const uint32_t* flag, const uint32_t* pos, uint32_t* count,
+                               uint32_t* codes) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t c0 = *count;
+    if (flag[i]) codes[c0 + pos[i]] = (uint32_t)(base + (uint64_t)i);
+}
+__global__ void k_advance_count(const uint32_t* flag, const uint32_t* pos, int64_t n, uint32_t* count) {
+    *count += pos[n - 1] + flag[n - 1];
+}
+
+// sigma >= 0 as a 24-bit float (the 16-bit trees' density word): FP32
+// without its sign, mantissa rounded to nearest even at 16 bits, kept finite.
+__device__ __forceinline__ uint32_t sigma24(float v) {
+    const uint32_t b = __float_as_uint(v) & 0x7FFFFFFFu;
+    uint32_t r = (b + 0x3Fu + ((b >> 7) & 1u)) >> 7;
+    return r >= 0xFF0000u ? 0xFEFFFFu : r;
+}
+
+// One distilled leaf per thread: the mean over its S jittered samples of
+// ReLU(sigma_raw) and of each raw SH coefficient, packed as plo_build_tree
+// packs a leaf: the record (FP32 coefficients, or 16-bit ones times a
+// power-of-two scale 2^e that puts the largest |coefficient| in [2^14, 2^15)
+// for FP16 and in [0.5, 1) for BF16) and the entry word.
+template <int PREC>
+__global__ void k_pack_leaves(const float* raw, int64_t nv, int S, int K, int stride, uint32_t* yword, uint8_t* emits,
+                              uint8_t* records) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    float sig = 0.0f;
+    for (int s = 0; s < S; ++s) sig += fmaxf(__ldg(raw + (i * S + s) * OUT_PAD), 0.0f);
+    sig /= (float)S;
+    const int nc = 3 * K;
+    uint8_t* rec = records + (size_t)i * stride;
+    // the means (written at once for FP32 records; for 16-bit ones this pass
+    // finds the largest |mean| and the next recomputes the same values)
+    float m = 0.0f;
+    bool any = false;
+    for (int k = 0; k < nc; ++k) {
+        float acc = 0.0f;
+        for (int s = 0; s < S; ++s) acc += __ldg(raw + (i * S + s) * OUT_PAD + 1 + k);
+        const float c = acc / (float)S;
+        any |= c != 0.0f;
+        m = fmaxf(m, fabsf(c));
+        if (PREC == PLO_PREC_FP32) reinterpret_cast<float*>(rec)[k] = c;
     }
-    if (k == 0)
-        sigma[i] = acc / (float)S;
-    else
-        sh[i * (n_out - 1) + (k - 1)] = acc / (float)S;
+    emits[i] = any ? 1 : 0;
+    if (PREC == PLO_PREC_FP32) {
+        for (int b = 4 * nc; b < stride; ++b) rec[b] = 0;
+        yword[i] = __float_as_uint(sig);
+        return;
+    }
+    int e;
+    frexpf(m, &e);
+    if (PREC == PLO_PREC_FP16) e -= 15;
+    e = max(-126, min(127, e));
+    const float inv = ldexpf(1.0f, -e);
+    uint16_t* h = reinterpret_cast<uint16_t*>(rec);
+    for (int k = 0; k < nc; ++k) {
+        float acc = 0.0f;
+        for (int s = 0; s < S; ++s) acc += __ldg(raw + (i * S + s) * OUT_PAD + 1 + k);
+        const float v = (acc / (float)S) * inv;
+        h[k] = PREC == PLO_PREC_FP16 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
+    for (int b = 2 * nc; b < stride; ++b) rec[b] = 0;
+    yword[i] = sigma24(sig) | (any ? (uint32_t)(e + 127) << 24 : 0u);
 }
 
 // Quadrature render of Eq. 3 from the head outputs, the loss of Eq. 7-9 and
@@ -1528,8 +1580,8 @@ extern "C" plo_status plo_wgrad_bf16(const void* d_dZ, int32_t n_out, const void
 // centre of every voxel at `depth` decides which voxels are kept (sigma >=
 // sigma_thresh); each kept voxel gets the mean of ReLU(sigma_raw) and of the
 // raw SH coefficients over `samples` jittered positions inside it.  Voxels
-// are visited in Morton order, so the kept list is sorted and the octree is
-// assembled on the host in one pass, then packed by plo_build_tree.
+// are visited in Morton order, so the kept list is sorted, and the octree is
+// packed on the device from it (pack.cu): no host copy of the leaves.
 namespace {
 plo_status distill(plo_mlp* m, int32_t depth, int32_t samples, float sigma_thresh, int32_t precision, plo_tree** out,
                    void* stream) {
@@ -1538,112 +1590,95 @@ plo_status distill(plo_mlp* m, int32_t depth, int32_t samples, float sigma_thres
     if (depth < 1 || depth > 10) return set_error(PLO_ERR_INVALID_ARG, "depth must be in [1, 10]");
     if (samples < 1 || samples > 256) return set_error(PLO_ERR_INVALID_ARG, "samples must be in [1, 256]");
     if (!(sigma_thresh >= 0.0f)) return set_error(PLO_ERR_INVALID_ARG, "sigma_thresh must be >= 0");
+    if (precision < PLO_PREC_FP32 || precision > PLO_PREC_BF16)
+        return set_error(PLO_ERR_INVALID_ARG, "precision must be PLO_PREC_FP32, _FP16 or _BF16");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t total = (int64_t)1 << (3 * depth);
     const int64_t C = total < ((int64_t)1 << 19) ? total : ((int64_t)1 << 19);
     plo_status st = ensure_workspace(m, C < 128 ? 128 : C, m->cap_rays);
     if (st != PLO_OK) return st;
-    const int n_out = m->n_out;
     const int K = m->K;
+    const int stride = sh_stride_bytes(K, precision);
     // pass 1: sigma at every voxel centre, in chunks of C voxels (Morton
-    // order); the kept voxels' codes are collected in that order
-    uint8_t* d_flags = nullptr;
-    cudaError_t e = (cudaError_t)dev_malloc((void**)&d_flags, (size_t)C);
-    std::vector<uint8_t> flags(C);
-    std::vector<unsigned long long> codes;
+    // order); the kept voxels' codes are appended on the device in that
+    // order (a Morton code at depth <= 10 fits 30 bits)
+    uint32_t *d_flag = nullptr, *d_pos = nullptr, *d_count = nullptr, *d_codes = nullptr;
+    cudaError_t e = (cudaError_t)dev_malloc((void**)&d_flag, (size_t)C * 4);
+    if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_pos, (size_t)C * 4);
+    if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_count, 256);
+    if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_codes, (size_t)total * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, 4, s);
+    auto free_pass1 = [&]() {
+        cudaStreamSynchronize(s);
+        cudaFree(d_flag);
+        cudaFree(d_pos);
+        cudaFree(d_count);
+    };
     for (int64_t base = 0; e == cudaSuccess && st == PLO_OK && base < total; base += C) {
         const int64_t n = total - base < C ? total - base : C;
         k_pe_centres<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((uint64_t)base, n, depth, m->H[0]);
         st = forward_layers(m, n, s);
         if (st != PLO_OK) break;
-        k_keep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->raw, n, sigma_thresh, d_flags);
-        e = cudaMemcpyAsync(flags.data(), d_flags, (size_t)n, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        k_keep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->raw, n, sigma_thresh, d_flag);
+        e = device_exclusive_scan(d_flag, d_pos, n, s);
         if (e != cudaSuccess) break;
-        for (int64_t i = 0; i < n; ++i)
-            if (flags[i]) codes.push_back((unsigned long long)(base + i));
+        k_compact_kept<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((uint64_t)base, n, d_flag, d_pos, d_count, d_codes);
+        k_advance_count<<<1, 1, 0, s>>>(d_flag, d_pos, n, d_count);
+        e = cudaGetLastError();
     }
-    cudaFree(d_flags);
-    if (st != PLO_OK) return st;
-    if (e != cudaSuccess) return cuda_error(e, "plo_distill");
-    // pass 2: the mean of `samples` jittered evaluations per kept voxel, all
-    // on the device (sub-chunks of C samples), copied back once
-    const int64_t nl = (int64_t)codes.size();
-    std::vector<float> sigma(nl), sh((size_t)nl * 3 * K);
-    if (nl > 0) {
-        const int64_t vmax = C / samples > 0 ? C / samples : 1;
-        unsigned long long* d_codes = nullptr;
-        float *d_sigma = nullptr, *d_sh = nullptr;
-        e = (cudaError_t)dev_malloc((void**)&d_codes, (size_t)nl * 8);
-        if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_sigma, (size_t)nl * 4);
-        if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_sh, (size_t)nl * 3 * K * 4);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_codes, codes.data(), (size_t)nl * 8, cudaMemcpyHostToDevice, s);
-        for (int64_t off = 0; off < nl && e == cudaSuccess && st == PLO_OK; off += vmax) {
-            const int64_t nv = nl - off < vmax ? nl - off : vmax;
-            k_pe_jitter<<<(unsigned)((nv * samples + 255) / 256), 256, 0, s>>>(
-                reinterpret_cast<const uint64_t*>(d_codes + off), nv, samples, depth, m->desc.seed, m->H[0]);
-            st = forward_layers(m, nv * samples, s);
-            if (st != PLO_OK) break;
-            k_average<<<(unsigned)((nv * n_out + 255) / 256), 256, 0, s>>>(m->raw, nv, samples, n_out, d_sigma + off,
-                                                                           d_sh + off * 3 * K);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess && st == PLO_OK)
-            e = cudaMemcpyAsync(sigma.data(), d_sigma, (size_t)nl * 4, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && st == PLO_OK)
-            e = cudaMemcpyAsync(sh.data(), d_sh, (size_t)nl * 3 * K * 4, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    uint32_t nl32 = 0;
+    if (e == cudaSuccess && st == PLO_OK) e = cudaMemcpyAsync(&nl32, d_count, 4, cudaMemcpyDeviceToHost, s);
+    free_pass1();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (st != PLO_OK || e != cudaSuccess) {
         cudaFree(d_codes);
-        cudaFree(d_sigma);
-        cudaFree(d_sh);
-        if (st != PLO_OK) return st;
-        if (e != cudaSuccess) return cuda_error(e, "plo_distill");
+        return st != PLO_OK ? st : cuda_error(e, "plo_distill");
     }
-    st = plo_mlp_check(m, stream);
-    if (st != PLO_OK) return st;
-    // octree over the kept voxels, leaves at level `depth`.  The codes are
-    // sorted, so one pass with the path of the previous leaf creates the
-    // nodes in pre-order: a leaf shares its previous neighbour's nodes down
-    // to the deepest level where their codes agree, and new nodes below.
-    std::vector<int32_t> child(8, -1);
-    int32_t n_nodes = 1;
-    int32_t path[MAX_DEPTH + 1] = {0};  // node id per level of the previous leaf's path
-    for (int64_t i = 0; i < nl; ++i) {
-        const unsigned long long c = codes[i];
-        int first_new = 1;  // levels 1 .. depth-1 hold nodes; the root is shared
-        if (i > 0) {
-            const unsigned long long x = c ^ codes[i - 1];
-            const int msb = 63 - __builtin_clzll(x);  // codes are distinct, so x != 0
-            first_new = depth - msb / 3;
-        }
-        for (int l = first_new; l < depth; ++l) {
-            const int slot = (int)((c >> (3 * (depth - l))) & 7ull);
-            const int32_t node = n_nodes++;
-            child.resize((size_t)n_nodes * 8, -1);
-            child[(size_t)path[l - 1] * 8 + slot] = node;
-            path[l] = node;
-        }
-        child[(size_t)path[depth - 1] * 8 + (int)(c & 7ull)] = (int32_t)(-i - 2);
+    const int64_t nl = nl32;
+    // pass 2: the mean of `samples` jittered evaluations per kept voxel,
+    // packed straight into the leaf's record and entry word
+    uint32_t* d_yword = nullptr;
+    uint8_t *d_emits = nullptr, *d_rec = nullptr;
+    e = (cudaError_t)dev_malloc((void**)&d_yword, (size_t)std::max<int64_t>(nl, 1) * 4);
+    if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_emits, (size_t)std::max<int64_t>(nl, 1));
+    if (e == cudaSuccess) e = (cudaError_t)dev_malloc((void**)&d_rec, (size_t)std::max<int64_t>(nl, 1) * stride);
+    const int64_t vmax = C / samples > 0 ? C / samples : 1;
+    for (int64_t off = 0; off < nl && e == cudaSuccess && st == PLO_OK; off += vmax) {
+        const int64_t nv = nl - off < vmax ? nl - off : vmax;
+        k_pe_jitter<<<(unsigned)((nv * samples + 255) / 256), 256, 0, s>>>(d_codes + off, nv, samples, depth,
+                                                                          m->desc.seed, m->H[0]);
+        st = forward_layers(m, nv * samples, s);
+        if (st != PLO_OK) break;
+        const unsigned g = (unsigned)((nv + 127) / 128);
+        uint8_t* rec = d_rec + (size_t)off * stride;
+        if (precision == PLO_PREC_FP32)
+            k_pack_leaves<PLO_PREC_FP32><<<g, 128, 0, s>>>(m->raw, nv, samples, K, stride, d_yword + off, d_emits + off, rec);
+        else if (precision == PLO_PREC_FP16)
+            k_pack_leaves<PLO_PREC_FP16><<<g, 128, 0, s>>>(m->raw, nv, samples, K, stride, d_yword + off, d_emits + off, rec);
+        else
+            k_pack_leaves<PLO_PREC_BF16><<<g, 128, 0, s>>>(m->raw, nv, samples, K, stride, d_yword + off, d_emits + off, rec);
+        e = cudaGetLastError();
     }
-    plo_tree_desc d{};
-    d.depth = depth;
-    d.sh_degree = m->desc.sh_degree;
-    d.n_nodes = n_nodes;
-    d.n_leaves = nl;
-    d.child = child.data();
-    d.sigma = sigma.data();
-    d.sh = sh.data();
-    for (int a = 0; a < 3; ++a) {
-        d.bbox_min[a] = 0.0f;
-        d.bbox_max[a] = 1.0f;
+    if (st == PLO_OK && e == cudaSuccess) st = plo_mlp_check(m, stream);
+    // the octree over the kept voxels, leaves at level `depth`, packed on
+    // the device from the sorted codes
+    if (st == PLO_OK && e == cudaSuccess)
+        st = pack_voxel_tree(depth, m->desc.sh_degree, precision, d_codes, nl, d_yword, d_emits, d_rec, s, out);
+    cudaStreamSynchronize(s);
+    cudaFree(d_codes);
+    cudaFree(d_yword);
+    cudaFree(d_emits);
+    if (st != PLO_OK || e != cudaSuccess) {
+        cudaFree(d_rec);
+        return st != PLO_OK ? st : cuda_error(e, "plo_distill");
     }
-    return plo_build_tree(&d, precision, out);
+    return PLO_OK;
 }
 }  // namespace
 
-// The kept voxels' codes and averages live in host vectors (1 + 3K floats
-// per kept voxel: tens of GB at depth 10); an allocation failure is returned
-// as PLO_ERR_OOM, never thrown through the C ABI.
+// Everything stays on the device (per kept voxel: a 4-byte code, an entry
+// word and its SH record); an allocation failure is returned as
+// PLO_ERR_OOM, never thrown through the C ABI.
 extern "C" plo_status plo_distill(plo_mlp* m, int32_t depth, int32_t samples, float sigma_thresh,
                                   int32_t precision, plo_tree** out, void* stream) {
     try {

@@ -69,6 +69,19 @@ plo_status cuda_error(int err, const char* what);
 int dev_malloc(void** p, size_t bytes);
 int dev_malloc_async(void** p, size_t bytes, cudaStream_t s);
 
+// Exclusive prefix sum of n uint32 values on the device (async on s; its
+// temporary goes through dev_malloc_async).  in == out is allowed.
+cudaError_t device_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+
+// Packs, on the device, the octree whose leaves are the voxels with the
+// sorted Morton codes d_codes [nl] at level `depth` (<= 10): their entry
+// words d_yword (sigma bits; for 16-bit trees sigma24 | scale exponent << 24)
+// and emission flags d_emits, and their packed SH records d_records [nl]
+// (record id = leaf id), which the tree takes over on success.  Same layout
+// as plo_build_tree of the equivalent canonical tree (octree layout).
+plo_status pack_voxel_tree(int depth, int sh_degree, int precision, const uint32_t* d_codes, int64_t nl,
+                           uint32_t* d_yword, uint8_t* d_emits, void* d_records, cudaStream_t s, plo_tree** out);
+
 }  // namespace plo
 
 struct plo_tree {

@@ -53,11 +53,13 @@ def test_resume_matches_uninterrupted_training(cuda_available, tmp_path, arch):
     # Weight gradients are summed with float atomics, so two runs differ in
     # the last bits of every gradient; where a gradient is itself at the
     # rounding level (near zero), Adam's m / sqrt(v) turns that noise into
-    # a step of up to ~lr, so a few parameters may differ by that much.  A
-    # lost Adam moment, step count or jitter stream moves nearly every
-    # parameter by ~lr: the median and the 99th percentile catch it.
+    # a step of up to ~lr, so a few parameters may differ by that much, and
+    # ten more steps let the two trajectories drift apart by ~1e-4 lr
+    # (measured median for the paper architecture: 2.6e-4 lr).  A lost Adam
+    # moment or jitter stream changes every update by O(lr), a lost step
+    # count the learning rate 20x: either moves the median past 1e-2 lr.
     d = np.abs(p_s.astype(np.float64) - p_r)
-    assert np.median(d) <= 1e-6 * LR0 and np.percentile(d, 99) <= 1e-3 * LR0, (np.median(d),
+    assert np.median(d) <= 1e-3 * LR0 and np.percentile(d, 99) <= 3e-2 * LR0, (np.median(d),
                                                                                np.percentile(d, 99), d.max())
     assert d.max() <= 20 * LR0
     a_path, b_path = str(tmp_path / "a.plomlp"), str(tmp_path / "b.plomlp")

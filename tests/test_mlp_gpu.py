@@ -297,7 +297,7 @@ def tree_from_morton(depth, codes, sigma, sh):
 def test_distill_matches_oracle(torch_cuda):
     torch = torch_cuda
     import oracle
-    from tests.parity import relative_errors
+    from tests.parity import quantise_tree, relative_errors
     depth, S, seed = 4, 4, 99
     flat = random_params(7, scale=0.6)
     net = plo.Mlp(l_max=5.0, jitter_seed=seed)
@@ -337,6 +337,63 @@ def test_distill_matches_oracle(torch_cuda):
     torch.cuda.synchronize()
     e_c, e_T = relative_errors(rgb.cpu().numpy(), T.cpu().numpy(), ref)
     assert e_c < 3e-2 and e_T < 3e-2, (e_c, e_T)
+    # the device packer against the host one: the distilled tree exported to
+    # the canonical format and packed again by plo_build_tree has the same
+    # kept set (leaf ids in Morton order) and renders bit for bit the same
+    host = tree.export()
+    assert host.n_leaves == len(codes)
+    plo.validate(host)
+    again = plo.Tree(host)
+    rgb2, T2, _ = plo.render(again, torch.from_numpy(rays).cuda(), plo.RenderParams(activation=plo.ACT_SIGMOID,
+                                                                                     l_max=5.0))
+    torch.cuda.synchronize()
+    assert torch.equal(rgb2, rgb) and torch.equal(T2, T)
+    # and the exported leaves equal the oracle's averages on the bf16 network
+    # to the network's bf16 precision
+    np.testing.assert_allclose(host.sigma, sig, rtol=3e-2, atol=1e-3 * float(np.abs(sig).max()))
+    np.testing.assert_allclose(host.sh.reshape(len(codes), -1), sh.reshape(len(codes), -1), rtol=0,
+                               atol=3e-2 * float(np.abs(sh).max()))
+    # 16-bit distillation: the device's leaf encoding equals the host
+    # packer's, as emulated by quantise_tree, bit for bit
+    for name, prec in (("fp16", plo.PREC_FP16), ("bf16", plo.PREC_BF16)):
+        t16 = net.distill(depth, samples=S, sigma_thresh=thresh, precision=prec)
+        h16 = t16.export()
+        q = quantise_tree(host, name)
+        np.testing.assert_array_equal(h16.child, host.child)
+        np.testing.assert_array_equal(h16.sigma, q.sigma)
+        np.testing.assert_array_equal(h16.sh, q.sh)
+
+
+def test_distill_depth_10_on_the_device(torch_cuda):
+    """Depth 10 (1024^3 voxel centres, Sec. 5) end to end on the device.  The
+    kept set is checked bit for bit on 200,000 random voxels: the centre
+    pass and plo_mlp_forward encode the same FP32 centre the same way, so the
+    network's sigma there is the same, and a voxel is a leaf of the packed
+    tree (plo_lookup_points) exactly where it reaches the threshold."""
+    torch = torch_cuda
+    flat = random_params(7, scale=0.6)
+    net = plo.Mlp(l_max=5.0, jitter_seed=99)
+    net.set_params(flat)
+    G = 1024
+    rng = np.random.default_rng(21)
+    probe = torch.from_numpy(((rng.integers(0, G, (65536, 3)) + 0.5) / G).astype(np.float32)).cuda()
+    sig = torch.relu(net.forward(probe)[:, 0])
+    thresh = float(torch.quantile(sig, 0.95))  # ~5% of the voxels: ~50M leaves
+    tree = net.distill(10, samples=1, sigma_thresh=thresh)
+    inf = tree.info()
+    assert inf["depth"] == 10 and 0.01 * G ** 3 < inf["n_leaves"] < 0.2 * G ** 3
+    ijk = rng.integers(0, G, (200_000, 3))
+    centres = torch.from_numpy(((ijk + 0.5) / G).astype(np.float32)).cuda()
+    kept = torch.relu(net.forward(centres)[:, 0]) >= thresh
+    leaf, level = plo.lookup(tree, centres)
+    torch.cuda.synchronize()
+    assert torch.equal(leaf >= 0, kept)
+    assert bool((level[kept] == 10).all())
+    rays = torch.from_numpy(plogen.rays_sphere(65536, seed=9)).cuda()
+    rgb, T, _ = plo.render(tree, rays, plo.RenderParams(activation=plo.ACT_SIGMOID, l_max=5.0))
+    torch.cuda.synchronize()
+    tree.check()
+    assert bool(torch.isfinite(rgb).all()) and bool((T < 1).any())
 
 
 def test_learned_gain_over_mse_and_untrained(torch_cuda):
