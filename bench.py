@@ -51,6 +51,9 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the linear / sigma_min-alpha_max / sphere-proxy timings")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step timing")
+    ap.add_argument("--no-distill", action="store_true",
+                    help="skip the trained network's depth-10 distillation and its error")
+    ap.add_argument("--distill-train-steps", type=int, default=2000)
     ap.add_argument("--train-timed-steps", type=int, default=60)
     ap.add_argument("--no-layouts", action="store_true",
                     help="skip the device-layout comparison (octree vs bricks of 4^3 and 8^3 cells)")
@@ -412,6 +415,31 @@ def run_train(plo, torch, steps: int, W: int):
             "final_loss": float(loss.item()), "layer_256x256_M524288": layers}
 
 
+def run_distill(plo, torch, steps: int):
+    """The learned part's end product (Sec. 5): a network trained `steps`
+    steps with the paper's loss on targets rendered from the depth-6
+    luminaire, distilled into a depth-10 octree (1024^3 voxel centres, 8
+    jittered samples per kept voxel, sigma >= 0.01) on the device, and the
+    distilled octree's render error against the ground-truth renders on
+    65,536 test rays; depth 8 beside it."""
+    import plogen
+    from paper_2207_05009_gb300 import learned
+    gt = plo.Tree(plogen.luminaire_tree(plogen.LUMINAIRE_D6))
+    train_b = learned.target_batches(gt, [plogen.rays_sphere(4096, seed=200 + k) for k in range(64)])
+    test_b = learned.target_batches(gt, [plogen.rays_sphere(65536, seed=900)])
+    l_max, _ = learned.emission_scale(train_b)
+    net, losses, dt = learned.train(train_b, steps, plo.LOSS_PAPER, l_max=l_max)
+    out = {"workload": f"paper loss, {steps} steps of 4096 rays x 128 samples on the depth-6 luminaire's "
+                       "renders; distilled with 8 samples per kept voxel, sigma >= 0.01; error on 65,536 test rays",
+           "train_s": dt, "final_loss": float(np.mean(losses[-32:]))}
+    for depth in (8, 10):
+        e = learned.distilled_error(net, l_max, test_b, depth=depth)
+        out[f"depth{depth}"] = e.__dict__
+    del net
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_learned(args):
     """Train the NeRF-SH network on targets rendered from the depth-6
     luminaire (4096 rays x 128 samples per step, the paper's loss), distil it
@@ -453,10 +481,10 @@ def run_learned(args):
         e7 = learned.distilled_error(net, l_max, test_b, depth=7)
         res["depth7"] = e7.__dict__
         # the deepest distillation whose leaf count (predicted from depth 7,
-        # 8x per level) fits comfortably in memory: <= 80M leaves
+        # 8x per level) fits comfortably in device memory: <= 400M leaves
         frac = e7.leaves / 8 ** 7
         depth = args.distill_depth
-        while depth > 7 and frac * 8 ** depth > 80e6:
+        while depth > 7 and frac * 8 ** depth > 400e6:
             depth -= 1
         if depth > 7:
             res[f"depth{depth}"] = learned.distilled_error(net, l_max, test_b, depth=depth).__dict__
@@ -582,6 +610,7 @@ def main():
                                                           world * n * K)
     pt = None if args.no_pt else run_pt(plo, torch, trees["fp32"], W, K)
     train = None if args.no_train else run_train(plo, torch, args.train_timed_steps, W)
+    distill = None if args.no_distill else run_distill(plo, torch, args.distill_train_steps)
     e2e = None
     if not args.no_e2e:
         rays_h = torch.from_numpy(rays_np).pin_memory()
@@ -701,6 +730,7 @@ def main():
         "variants": variants,
         "path_tracer": pt,
         "train": train,
+        "distill": distill,
     }
     line["fp16"]["roofline"]["frac"] = line["fp16"]["roofline"]["achieved"] / peak
     print(json.dumps(line), flush=True)
