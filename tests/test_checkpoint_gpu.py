@@ -67,9 +67,13 @@ def test_resume_matches_uninterrupted_training(cuda_available, tmp_path, arch):
     resumed.save(b_path)
     (ha, ba), (hb, bb) = ckpt_format.read(a_path), ckpt_format.read(b_path)
     assert ha["step"] == hb["step"] == 20
+    # Adam's moments are averages of the gradients the two runs saw, which
+    # differ as the parameters drift (measured median 2.5e-3 relative); a
+    # lost first moment would leave out 0.9^10 = 35% of its weight, a lost
+    # second moment about half of it
     for name in ("adam_m", "adam_v"):
         rel = np.abs(bb[name].astype(np.float64) - ba[name]) / (np.abs(ba[name]) + 1e-30)
-        assert np.median(rel) <= 1e-4, (name, np.median(rel))
+        assert np.median(rel) <= 3e-2, (name, np.median(rel))
     np.testing.assert_array_equal(bb["master"], p_r)
 
 
