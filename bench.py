@@ -55,6 +55,8 @@ def parse_args():
                     help="skip the trained network's depth-10 distillation and its error")
     ap.add_argument("--distill-train-steps", type=int, default=2000)
     ap.add_argument("--train-timed-steps", type=int, default=60)
+    ap.add_argument("--layout", choices=["octree", "bricks4", "bricks8"], default="octree",
+                    help="device layout of the timed trees (plo_build_tree_ex)")
     ap.add_argument("--no-layouts", action="store_true",
                     help="skip the device-layout comparison (octree vs bricks of 4^3 and 8^3 cells)")
     ap.add_argument("--learned", action="store_true",
@@ -552,8 +554,10 @@ def main():
     n = len(rays_np)
     stream = torch.cuda.current_stream()
     t0 = time.time()
-    trees = {"fp32": plo.Tree(tree, plo.PREC_FP32), "fp16": plo.Tree(tree, plo.PREC_FP16),
-             "bf16": plo.Tree(tree, plo.PREC_BF16)}
+    lay = {"octree": (plo.LAYOUT_OCTREE, 0), "bricks4": (plo.LAYOUT_BRICKS, 2),
+           "bricks8": (plo.LAYOUT_BRICKS, 3)}[args.layout]
+    trees = {"fp32": plo.Tree(tree, plo.PREC_FP32, *lay), "fp16": plo.Tree(tree, plo.PREC_FP16, *lay),
+             "bf16": plo.Tree(tree, plo.PREC_BF16, *lay)}
     build_s = time.time() - t0
     rays = torch.from_numpy(rays_np).cuda()
     rgb = torch.empty((n, 3), device="cuda")
@@ -721,8 +725,7 @@ def main():
         "fp16": {k: v for k, v in lines["fp16"].items()},
         "bf16": {k: v for k, v in lines["bf16"].items()},
         "fp16_speedup_vs_fp32": lines["fp16"]["value"] / lines["fp32"]["value"],
-        "layout": {"default": "bricks8" if info["layout"] == plo.LAYOUT_BRICKS and info["brick_log"] == 3
-                   else ("octree" if info["layout"] == plo.LAYOUT_OCTREE else f"bricks{1 << info['brick_log']}"),
+        "layout": {"timed": args.layout,
                    "n_bricks": int(info["n_bricks"]), "brick_bytes": int(info["brick_bytes"]),
                    "compared": layouts},
         "parity": parity,

@@ -39,7 +39,7 @@
  *     whose final T is below t_stop counts as opaque (T = 0): the sigma_min /
  *     alpha_max heuristics of Sec. 6 ("Performance vs Quality"), with
  *     t_stop = 1 - alpha_max;
- *   - proxy geometry (Sec. 5, "a sphere or a box"): the box is the tree's
+ *   - proxy geometry (Sec. 5, a spherical or a box proxy): the box is the tree's
  *     bounding box; a sphere proxy restricts the integral to the part of the
  *     ray inside both the box and the ball.
  */
