@@ -35,10 +35,15 @@ def luminaire():
                     bbox_max=(2.0, 2.0, 2.0))
 
 
-def run(torch, host, sc, spp, seed=3):
+def uniforms(sc, spp, seed):
     rng = np.random.default_rng(seed)
     n = spp * sc["width"] * sc["height"]
-    u = rng.random((n, 2 + 5 * sc["max_bounces"])).astype(np.float32)
+    return rng.random((n, 2 + 5 * sc["max_bounces"])).astype(np.float32)
+
+
+def run(torch, host, sc, spp, seed=3):
+    n = spp * sc["width"] * sc["height"]
+    u = uniforms(sc, spp, seed)
     t = plo.Tree(host)
     img, smp = plo.pt_render(t, sc, spp, uniforms=torch.from_numpy(u).cuda(), samples=True)
     torch.cuda.synchronize()
@@ -63,12 +68,29 @@ def test_octree_luminaire_matches_oracle(torch_cuda, bounces):
     img, g, ref = run(torch_cuda, luminaire(), sc, spp=2, seed=4 + bounces)
     scale = np.abs(ref).max(axis=1) + 1e-3 * np.abs(ref).mean()
     err = np.abs(g - ref).max(axis=1) / scale
-    # the luminaire query is exact to 1e-4 of its error scale; a next-event
-    # ray aimed in FP32 instead of FP64 may graze a cell boundary
-    # differently, so a few samples may differ more
+    # the luminaire query is exact to 1e-4 of its error scale; the path's own
+    # arithmetic (camera ray, wall hit, next-event ray, bounce) runs in FP32,
+    # which acts like moving the sample's uniforms by a few FP32 units, so
+    # samples whose exact value is that sensitive (a vertex at a room edge
+    # flips walls, a ray grazing a cell face) may differ more: at most 0.5%
     assert np.mean(err < 1e-3) > 0.995, np.sort(err)[-10:]
     assert abs(g.mean() - ref.mean()) <= 1e-3 * ref.mean()
     assert (ref.sum(1) > 0).mean() > 0.1
+    # every such sample must be one: the oracle itself, with the uniforms
+    # moved by 4e-6 (64 FP32 units at 1), changes by at least half the
+    # GPU's difference
+    out = np.nonzero(err >= 1e-3)[0]
+    if out.size:
+        host, u = luminaire(), uniforms(sc, 2, 4 + bounces)
+        rng = np.random.default_rng(17)
+        spread = np.zeros(out.size)
+        for _ in range(8):
+            up = u.astype(np.float64)
+            up[out] += rng.choice([-4e-6, 4e-6], size=(out.size, u.shape[1]))
+            ref_p = oracle.pt_render(host, sc, np.clip(up, 0.0, 1.0 - 1e-12))
+            spread = np.maximum(spread, np.abs(ref_p[out] - ref[out]).max(axis=1))
+        diff = np.abs(g[out] - ref[out]).max(axis=1)
+        assert np.all(diff <= 2.0 * spread + 1e-3 * scale[out]), (diff / scale[out], spread / scale[out])
 
 
 def test_seeded_render_is_deterministic(torch_cuda):
