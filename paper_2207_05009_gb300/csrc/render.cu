@@ -389,6 +389,28 @@ __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* 
     }
 }
 
+// Staging of a ray's listed records: four (record, weight) pairs and their
+// scale bytes per thread (column layout), written to the ray's list one
+// 32-byte sector at a time.
+__device__ __forceinline__ uint2* stage_slots() {
+    __shared__ uint2 s_stage[4 * BLOCK];
+    return s_stage + threadIdx.x;
+}
+__device__ __forceinline__ uint32_t* stage_exps() {
+    __shared__ uint32_t s_stage_e[BLOCK];
+    return s_stage_e + threadIdx.x;
+}
+// Writes the staged records as list entries k0 .. k0+3 of ray i (k0 a
+// multiple of 4; entries past the ray's count are never read).
+__device__ __forceinline__ void flush_stage(const KParams& kp, int64_t i, int k0, bool bits16) {
+    const uint2* st = stage_slots();
+    const uint2 a = st[0], b = st[BLOCK], c = st[2 * BLOCK], d = st[3 * BLOCK];
+    uint4* dst = reinterpret_cast<uint4*>(kp.list + (size_t)i * kp.list_cap + k0);
+    dst[0] = make_uint4(a.x, a.y, b.x, b.y);
+    dst[1] = make_uint4(c.x, c.y, d.x, d.y);
+    if (bits16) *reinterpret_cast<uint32_t*>(kp.list_e + (size_t)i * kp.list_cap + k0) = stage_exps()[0];
+}
+
 __device__ __forceinline__ void ray_store(const KParams& kp, int64_t i, const Ray& R) {
     kp.rgb[3 * i + 0] = R.r;
     kp.rgb[3 * i + 1] = R.g;
@@ -396,7 +418,11 @@ __device__ __forceinline__ void ray_store(const KParams& kp, int64_t i, const Ra
     kp.T[i] = kp.saturate && R.T < kp.t_stop ? 0.0f : R.T;  // a saturated ray is opaque (Sec. 6.2)
     if (kp.status) kp.status[i] = R.status;
     if (kp.tr_count) kp.tr_count[i] = R.steps;
-    if (kp.counts) kp.counts[i] = R.nrec;
+    if (kp.counts) {
+        const int listed = R.nrec < kp.list_cap ? R.nrec : kp.list_cap;
+        if (listed & 3) flush_stage(kp, i, listed & ~3, kp.list_e != nullptr);
+        kp.counts[i] = R.nrec;
+    }
 }
 
 // Proxy clip.  On a hit the lane enters ST_DESCEND at the root; on a miss or
@@ -554,14 +580,21 @@ __device__ __forceinline__ bool composite(const KParams& kp, const TreeParams& t
     bool emits = rec != NO_SH_RECORD;
     if (emits && kp.list && R.nrec < kp.list_cap) {
         // listed for the shading kernel, which accumulates the ray's records
-        // in this order with the same arithmetic
-        const size_t slot = (size_t)i * kp.list_cap + R.nrec;
-        kp.list[slot] = make_uint2(rec, __float_as_uint(w));
-        if (PREC != PLO_PREC_FP32 && (PREC > 0 || tp.prec != PLO_PREC_FP32)) kp.list_e[slot] = (uint8_t)(R.entry_y >> 24);
+        // in this order with the same arithmetic; four records (a 32-byte
+        // sector) are staged in shared memory and written together
+        const bool bits16 = PREC != PLO_PREC_FP32 && (PREC > 0 || tp.prec != PLO_PREC_FP32);
+        const int k = R.nrec & 3;
+        stage_slots()[k * BLOCK] = make_uint2(rec, __float_as_uint(w));
+        if (bits16) {
+            uint32_t& e8 = stage_exps()[0];
+            e8 = (e8 & ~(0xFFu << (8 * k))) | ((R.entry_y >> 24) << (8 * k));
+        }
         ++R.nrec;
+        if (k == 3) flush_stage(kp, i, R.nrec - 4, bits16);
         emits = false;
     } else if (emits) {
         sh_emission<K, PREC>(tp, rec, R.entry_y, R.dirn, cr, cg, cb, sY);
+        if (kp.list) ++R.nrec;  // counted, so that the shading kernel adds the walk's part
     }
     if (emits || (!kp.list && kp.activation != PLO_ACT_RELU)) {
         R.r = __fmaf_rn(w, act_fn(cr, kp.activation, kp.l_max), R.r);
