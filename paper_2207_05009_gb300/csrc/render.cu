@@ -78,14 +78,6 @@ struct KParams {
     float* rgb;
     float* T;
     int32_t* status;
-    // emission lists (walk then shade): per ray up to list_cap (record id,
-    // weight) pairs of its emitting segments, in segment order, the scale
-    // exponent byte of 16-bit records beside them, and the ray's count; NULL
-    // list: the walk evaluates the SH records itself
-    uint2* list;
-    uint8_t* list_e;
-    int32_t* counts;
-    int32_t list_cap;
     // trace mode
     int32_t trace_max;
     int64_t* tr_leaf;
@@ -300,7 +292,6 @@ struct Ray {
     int state;
     int status;
     int tree;           // index into the batch's tree table (batch kernel only)
-    int nrec;           // emitting segments listed for the shading kernel
 };
 
 // Per-ray constants read once per cell, kept in shared memory to leave
@@ -389,28 +380,6 @@ __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* 
     }
 }
 
-// Staging of a ray's listed records: four (record, weight) pairs and their
-// scale bytes per thread (column layout), written to the ray's list one
-// 32-byte sector at a time.
-__device__ __forceinline__ uint2* stage_slots() {
-    __shared__ uint2 s_stage[4 * BLOCK];
-    return s_stage + threadIdx.x;
-}
-__device__ __forceinline__ uint32_t* stage_exps() {
-    __shared__ uint32_t s_stage_e[BLOCK];
-    return s_stage_e + threadIdx.x;
-}
-// Writes the staged records as list entries k0 .. k0+3 of ray i (k0 a
-// multiple of 4; entries past the ray's count are never read).
-__device__ __forceinline__ void flush_stage(const KParams& kp, int64_t i, int k0, bool bits16) {
-    const uint2* st = stage_slots();
-    const uint2 a = st[0], b = st[BLOCK], c = st[2 * BLOCK], d = st[3 * BLOCK];
-    uint4* dst = reinterpret_cast<uint4*>(kp.list + (size_t)i * kp.list_cap + k0);
-    dst[0] = make_uint4(a.x, a.y, b.x, b.y);
-    dst[1] = make_uint4(c.x, c.y, d.x, d.y);
-    if (bits16) *reinterpret_cast<uint32_t*>(kp.list_e + (size_t)i * kp.list_cap + k0) = stage_exps()[0];
-}
-
 __device__ __forceinline__ void ray_store(const KParams& kp, int64_t i, const Ray& R) {
     kp.rgb[3 * i + 0] = R.r;
     kp.rgb[3 * i + 1] = R.g;
@@ -418,11 +387,6 @@ __device__ __forceinline__ void ray_store(const KParams& kp, int64_t i, const Ra
     kp.T[i] = kp.saturate && R.T < kp.t_stop ? 0.0f : R.T;  // a saturated ray is opaque (Sec. 6.2)
     if (kp.status) kp.status[i] = R.status;
     if (kp.tr_count) kp.tr_count[i] = R.steps;
-    if (kp.counts) {
-        const int listed = R.nrec < kp.list_cap ? R.nrec : kp.list_cap;
-        if (listed & 3) flush_stage(kp, i, listed & ~3, kp.list_e != nullptr);
-        kp.counts[i] = R.nrec;
-    }
 }
 
 // Proxy clip.  On a hit the lane enters ST_DESCEND at the root; on a miss or
@@ -440,7 +404,6 @@ __device__ void ray_begin(const KParams& kp, const TreeParams& tp, int64_t i, Ra
     R.r = R.g = R.b = 0.0f;
     R.od = {0.0f, 0.0f};
     R.t = {0.0f, 0.0f};
-    R.nrec = 0;
     R.status = PLO_RAY_OK;
     R.steps = 0;
     R.state = ST_IDLE;
@@ -577,26 +540,9 @@ __device__ __forceinline__ bool composite(const KParams& kp, const TreeParams& t
     }
     const uint32_t rec = R.entry_x & ~LEAF_BIT;
     float cr = 0.0f, cg = 0.0f, cb = 0.0f;
-    bool emits = rec != NO_SH_RECORD;
-    if (emits && kp.list && R.nrec < kp.list_cap) {
-        // listed for the shading kernel, which accumulates the ray's records
-        // in this order with the same arithmetic; four records (a 32-byte
-        // sector) are staged in shared memory and written together
-        const bool bits16 = PREC != PLO_PREC_FP32 && (PREC > 0 || tp.prec != PLO_PREC_FP32);
-        const int k = R.nrec & 3;
-        stage_slots()[k * BLOCK] = make_uint2(rec, __float_as_uint(w));
-        if (bits16) {
-            uint32_t& e8 = stage_exps()[0];
-            e8 = (e8 & ~(0xFFu << (8 * k))) | ((R.entry_y >> 24) << (8 * k));
-        }
-        ++R.nrec;
-        if (k == 3) flush_stage(kp, i, R.nrec - 4, bits16);
-        emits = false;
-    } else if (emits) {
-        sh_emission<K, PREC>(tp, rec, R.entry_y, R.dirn, cr, cg, cb, sY);
-        if (kp.list) ++R.nrec;  // counted, so that the shading kernel adds the walk's part
-    }
-    if (emits || (!kp.list && kp.activation != PLO_ACT_RELU)) {
+    const bool emits = rec != NO_SH_RECORD;
+    if (emits) sh_emission<K, PREC>(tp, rec, R.entry_y, R.dirn, cr, cg, cb, sY);
+    if (emits || kp.activation != PLO_ACT_RELU) {
         R.r = __fmaf_rn(w, act_fn(cr, kp.activation, kp.l_max), R.r);
         R.g = __fmaf_rn(w, act_fn(cg, kp.activation, kp.l_max), R.g);
         R.b = __fmaf_rn(w, act_fn(cb, kp.activation, kp.l_max), R.b);
@@ -932,68 +878,6 @@ __global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : (BRICKS ? PLO_B
     }
 }
 
-// ---------------------------------------------------------------- shading kernel
-// Second half of the split render: the walk lists each ray's emitting
-// segments (record, weight) instead of evaluating them, and this kernel
-// evaluates the SH records at the ray's direction (Eq. 6) with many loads in
-// flight per SM.  It accumulates a ray's records in segment order with the
-// walk's own arithmetic (same direction, basis, record evaluation and FMA
-// chain), so a ray whose records all fit its list gets the bits the
-// one-kernel render gives; records past the list's capacity were evaluated
-// by the walk, whose partial sum is added at the end.
-__device__ __forceinline__ void ray_direction(const float* q, float* dirn) {
-    float dw[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) dw[a] = __ldg(q + 3 + a);
-    const float inv_n = rsqrtf(__fadd_rn(__fadd_rn(__fmul_rn(dw[0], dw[0]), __fmul_rn(dw[1], dw[1])),
-                                         __fmul_rn(dw[2], dw[2])));
-#pragma unroll
-    for (int a = 0; a < 3; ++a) dirn[a] = __fmul_rn(dw[a], inv_n);
-}
-
-template <int K, int PREC>
-__device__ __forceinline__ void shade_ray(const KParams& kp, const TreeParams& tp, int64_t i) {
-    const int cnt = __ldg(kp.counts + i);
-    if (cnt == 0) return;
-    float dirn[3];
-    ray_direction(kp.rays + 6 * i, dirn);
-    float Y[K > 0 ? K : 1];
-    if (K > 0) sh_basis<(K > 0 ? K : 1)>(dirn[0], dirn[1], dirn[2], Y);
-    float r = 0.0f, g = 0.0f, b = 0.0f;
-    const int m = cnt < kp.list_cap ? cnt : kp.list_cap;
-    const size_t base = (size_t)i * kp.list_cap;
-    const bool bits16 = PREC != PLO_PREC_FP32 && (PREC > 0 || tp.prec != PLO_PREC_FP32);
-    for (int k = 0; k < m; ++k) {
-        const uint2 e = __ldg(kp.list + base + k);
-        const uint32_t yword = bits16 ? (uint32_t)__ldg(kp.list_e + base + k) << 24 : 0u;
-        float cr, cg, cb;
-        if (K > 0)
-            sh_eval<(K > 0 ? K : 1), (PREC >= 0 ? PREC : 0)>(tp.sh + (size_t)e.x * tp.sh_stride, yword, Y, cr, cg, cb);
-        else
-            sh_emission<0, -1>(tp, e.x, yword, dirn, cr, cg, cb);
-        const float w = __uint_as_float(e.y);
-        r = __fmaf_rn(w, act_fn(cr, kp.activation, kp.l_max), r);
-        g = __fmaf_rn(w, act_fn(cg, kp.activation, kp.l_max), g);
-        b = __fmaf_rn(w, act_fn(cb, kp.activation, kp.l_max), b);
-    }
-    float* out = kp.rgb + 3 * i;
-    if (cnt > kp.list_cap) {
-        r += out[0];
-        g += out[1];
-        b += out[2];
-    }
-    out[0] = r;
-    out[1] = g;
-    out[2] = b;
-}
-
-template <int K, int PREC>
-__global__ void __launch_bounds__(256) k_shade(KParams kp) {
-    const int64_t step = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kp.n; i += step)
-        shade_ray<K, PREC>(kp, kp.tree, i);
-}
-
 // ---------------------------------------------------------------- batched render
 // Several luminaires in one launch: rays of tree t occupy [off[t], off[t+1])
 // of one concatenated array.  Persistent warps claim `claim` rays at a time
@@ -1072,18 +956,6 @@ __global__ void __launch_bounds__(BLOCK, BRICKS ? PLO_BRICK_MIN_BLOCKS : PLO_REN
         if (BRICKS && R.state == ST_BRICK) brick_step<0, -1, false>(kp, tp, my, R, stack);
         if (R.state == ST_LEAF) leaf_step<0, -1, false, false>(kp, tp, my, R, stack);
         if (R.state == ST_DESCEND) descend_step<BRICKS>(tp, s_nodes, R, stack);
-    }
-}
-
-// Shading kernel of the batch: the tree of each ray from the offsets, the
-// record's degree and precision from the tree table.
-__global__ void __launch_bounds__(256) k_shade_batch(BatchParams bp) {
-    const int64_t total = bp.off[bp.n_trees];
-    const int64_t step = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
-        int t = 0;
-        while (t + 1 < bp.n_trees && bp.off[t + 1] <= i) ++t;
-        shade_ray<0, -1>(bp.base, bp.trees[t], i);
     }
 }
 
@@ -1218,42 +1090,6 @@ plo_status check_params(const plo_render_params* p) {
 // long does not hold up the end of the launch (static per-warp chunks are
 // kept below DYNAMIC_MIN_RAYS, where a call must not allocate).
 constexpr int64_t DYNAMIC_MIN_RAYS = (int64_t)1 << 20;
-// Emitting segments listed per ray for the shading kernel (the rest, ~2% of
-// the depth-10 luminaire's records, are evaluated by the walk itself).
-constexpr int LIST_CAP = 64;
-
-// Bytes of the split render's scratch for n rays: the work counter, the
-// per-ray counts, the lists, and for 16-bit records their scale bytes.
-size_t split_scratch_bytes(int64_t n, bool bits16) {
-    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-    return 256 + up((size_t)n * 4) + up((size_t)n * LIST_CAP * 8) + (bits16 ? up((size_t)n * LIST_CAP) : 0);
-}
-void split_scratch_layout(char* base, int64_t n, bool bits16, unsigned long long** cursor, int32_t** counts,
-                          uint2** list, uint8_t** list_e) {
-    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-    *cursor = reinterpret_cast<unsigned long long*>(base);
-    char* p = base + 256;
-    *counts = reinterpret_cast<int32_t*>(p);
-    p += up((size_t)n * 4);
-    *list = reinterpret_cast<uint2*>(p);
-    p += up((size_t)n * LIST_CAP * 8);
-    *list_e = bits16 ? reinterpret_cast<uint8_t*>(p) : nullptr;
-}
-
-cudaError_t dispatch_shade(const plo_tree* t, const KParams& kp, cudaStream_t s) {
-    const int64_t blocks = std::min<int64_t>((kp.n + 255) / 256, (int64_t)t->sm_count * 8);
-#define PLO_CASE(KK, PP)                                                          \
-    if (t->K == KK && t->precision == PP) {                                       \
-        k_shade<KK, PP><<<(unsigned)blocks, 256, 0, s>>>(kp);                     \
-        return cudaGetLastError();                                                \
-    }
-    PLO_CASE(1, PLO_PREC_FP32) PLO_CASE(4, PLO_PREC_FP32) PLO_CASE(9, PLO_PREC_FP32) PLO_CASE(16, PLO_PREC_FP32)
-    PLO_CASE(1, PLO_PREC_FP16) PLO_CASE(4, PLO_PREC_FP16) PLO_CASE(9, PLO_PREC_FP16) PLO_CASE(16, PLO_PREC_FP16)
-    PLO_CASE(1, PLO_PREC_BF16) PLO_CASE(4, PLO_PREC_BF16) PLO_CASE(9, PLO_PREC_BF16) PLO_CASE(16, PLO_PREC_BF16)
-    PLO_CASE(25, PLO_PREC_FP32) PLO_CASE(25, PLO_PREC_FP16) PLO_CASE(25, PLO_PREC_BF16)
-#undef PLO_CASE
-    return cudaErrorInvalidValue;
-}
 
 template <bool TRACE>
 plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, const plo_render_params* p,
@@ -1294,26 +1130,15 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     size_t smem = (size_t)kp.tree.n_top * 8 * sizeof(uint2) + (size_t)(kp.tree.top_depth + 1) * BLOCK * 4;
     cudaError_t e = cudaSuccess;
     cudaStream_t cs = (cudaStream_t)stream;
-    // From DYNAMIC_MIN_RAYS rays on, one stream-ordered allocation holds the
-    // work counter and, for the plain render (box proxy, max(0, .) emission),
-    // the emission lists of the split walk / shade render.
-    char* scratch = nullptr;
-    const bool split = !TRACE && n >= DYNAMIC_MIN_RAYS && kp.proxy == PLO_PROXY_BOX && kp.activation == PLO_ACT_RELU;
-    const bool bits16 = t->precision != PLO_PREC_FP32;
+    unsigned long long* cursor = nullptr;
     if (!TRACE && n >= DYNAMIC_MIN_RAYS) {
-        const size_t bytes = split ? split_scratch_bytes(n, bits16) : 256;
-        e = (cudaError_t)dev_malloc_async((void**)&scratch, bytes, cs);
-        if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), cs);
+        e = (cudaError_t)dev_malloc_async((void**)&cursor, sizeof(unsigned long long), cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), cs);
         if (e != cudaSuccess) {
-            if (scratch) cudaFreeAsync(scratch, cs);
-            return cuda_error(e, "render work counter and emission lists");
+            if (cursor) cudaFreeAsync(cursor, cs);
+            return cuda_error(e, "render work counter");
         }
-        kp.cursor = reinterpret_cast<unsigned long long*>(scratch);
-        if (split) {
-            unsigned long long* cur;
-            split_scratch_layout(scratch, n, bits16, &cur, &kp.counts, &kp.list, &kp.list_e);
-            kp.list_cap = LIST_CAP;
-        }
+        kp.cursor = cursor;
     }
     const bool bricks = !TRACE && t->layout == PLO_LAYOUT_BRICKS;
     if (TRACE)
@@ -1324,8 +1149,7 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     else
         e = bricks ? dispatch<false, false, true>(t, kp, smem, (cudaStream_t)stream)
                    : dispatch<false, false, false>(t, kp, smem, (cudaStream_t)stream);
-    if (e == cudaSuccess && split) e = dispatch_shade(t, kp, cs);
-    if (scratch) cudaFreeAsync(scratch, cs);
+    if (cursor) cudaFreeAsync(cursor, cs);
     if (e != cudaSuccess) return cuda_error(e, "render kernel launch");
     return PLO_OK;
 }
@@ -1487,7 +1311,6 @@ struct plo_batch {
     int32_t full_top[MAX_BATCH];  // stageable top nodes per tree (<= BATCH_TOP_NODES)
     bool bricks;                  // some tree uses the brick layout
     unsigned long long* d_cursor;
-    char* d_lists;  // emission lists of the walk / shade split (counts, lists, scale bytes)
     cudaGraph_t graph;
     cudaGraphExec_t exec;
 };
@@ -1528,13 +1351,7 @@ cudaError_t launch_batch(plo_batch* b, cudaStream_t s) {
     e = cudaMemsetAsync(b->d_cursor, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     fn<<<(unsigned)grid, BLOCK, b->smem, s>>>(b->bp);
-    e = cudaGetLastError();
-    if (e == cudaSuccess && b->bp.base.list) {
-        const int64_t blocks = std::min<int64_t>((b->n_rays + 255) / 256, (int64_t)b->sm_count * 8);
-        k_shade_batch<<<(unsigned)blocks, 256, 0, s>>>(b->bp);
-        e = cudaGetLastError();
-    }
-    return e;
+    return cudaGetLastError();
 }
 
 void set_buffers(plo_batch* b, const float* d_rays, float* d_rgb, float* d_T, int32_t* d_status) {
@@ -1601,21 +1418,6 @@ extern "C" plo_status plo_batch_create(const plo_tree* const* trees, int32_t n_t
         return cuda_error(e, "batch cursor allocation");
     }
     b->bp.cursor = b->d_cursor;
-    // the split walk / shade render for the plain emission (max(0, .)), with
-    // lists owned by the batch so that a captured graph allocates nothing
-    if (params->activation == PLO_ACT_RELU && b->n_rays > 0) {
-        bool bits16 = false;
-        for (int t = 0; t < n_trees; ++t) bits16 |= trees[t]->precision != PLO_PREC_FP32;
-        e = dev_malloc((void**)&b->d_lists, split_scratch_bytes(b->n_rays, bits16));
-        if (e != 0) {
-            cudaFree(b->d_cursor);
-            delete b;
-            return cuda_error(e, "batch emission lists allocation");
-        }
-        unsigned long long* unused;
-        split_scratch_layout(b->d_lists, b->n_rays, bits16, &unused, &kp.counts, &kp.list, &kp.list_e);
-        kp.list_cap = LIST_CAP;
-    }
     *out = b;
     return PLO_OK;
 }
@@ -1625,7 +1427,6 @@ extern "C" void plo_batch_free(plo_batch* b) {
     cudaDeviceSynchronize();
     drop_graph(b);
     cudaFree(b->d_cursor);
-    cudaFree(b->d_lists);
     delete b;
 }
 
