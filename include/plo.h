@@ -492,7 +492,8 @@ plo_status plo_mlp_check(const plo_mlp* mlp, void* stream);
 int64_t plo_mlp_step(const plo_mlp* mlp);
 
 /* The tensor-core building blocks (async), exposed for testing.
- * plo_gemm_bf16: C[M][N] = A[M][K] B[N][K]^T, A and B bf16 row-major,
+ * plo_gemm_bf16: C[M][N] = A[M][K] B[N][K]^T, A and B bf16 row-major, bias
+ *   16-byte aligned,
  *   (N, K) in {(256, 64), (256, 256), (64, 256)}; epilogue 0: bf16
  *   ReLU(C + bias), and if d_bits is not NULL where C + bias > 0 (fp32,
  *   before rounding) as bits (uint32 [M][N / 32], bit j of word c for

@@ -13,9 +13,11 @@
 //          (both operands MN-major, read straight from the row-major
 //          activations), split over CTAs and reduced with vector atomics.
 //
-// Warp roles (192 threads): warp 0 lane 0 issues TMA, warp 1 owns TMEM and
-// lane 0 issues MMAs, warps 2-5 run the epilogue (warp w reads TMEM lanes
-// 32*(w%4) .. +31).  All mbarrier waits are bounded; a wait that gives up
+// Warp roles: warp 0 lane 0 issues TMA, warp 1 owns TMEM and lane 0 issues
+// MMAs, the rest run the epilogue (warp w reads TMEM lanes 32*(w%4) .. +31).
+// k_gemm has two epilogue warpgroups (320 threads): the two warps of a lane
+// quadrant take half of the tile's 32-column chunks each, so every
+// sub-partition interleaves two epilogue warps; k_wgrad has one (192).  All mbarrier waits are bounded; a wait that gives up
 // raises an abort flag in shared memory and a bit in the caller's error word,
 // every role then drains what it has in flight and the CTA frees its TMEM.
 #pragma once
@@ -30,7 +32,9 @@
 namespace plo {
 namespace gemm {
 
-constexpr int THREADS = 192;
+constexpr int THREADS = 192;       // k_wgrad
+constexpr int EPI_GROUPS = 2;      // k_gemm epilogue warpgroups
+constexpr int GEMM_THREADS = 64 + 128 * EPI_GROUPS;
 constexpr int BM = 128;
 constexpr int BK = 64;  // one 128-byte swizzle row of bf16
 constexpr int STAGES = 4;
@@ -64,8 +68,8 @@ __host__ __device__ constexpr int tmem_cols_for(int n) {
 }
 constexpr int OUT_STAGE_BYTES = 32 * 32 * 2;  // one 32 x 32 bf16 box, per epilogue warp and buffer
 __host__ __device__ constexpr size_t gemm_smem_bytes(int N, int K) {
-    return 1024 /*align*/ + (size_t)N * K * 2 + (size_t)STAGES * A_STAGE_BYTES + 8 * OUT_STAGE_BYTES +
-           256 /*barriers*/;
+    return 1024 /*align*/ + (size_t)N * K * 2 + (size_t)STAGES * A_STAGE_BYTES +
+           8 * EPI_GROUPS * OUT_STAGE_BYTES + 256 /*barriers*/;
 }
 
 struct Ctl {
@@ -116,10 +120,19 @@ __device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int r
     uint32_t packed[16];
     if (epi == EPI_RELU_BF16 || epi == EPI_SPLIT) {
         uint32_t pos = 0u;  // bit j: pre-activation j is > 0 (the ReLU derivative)
+        float bv[32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 b4 = __ldg(reinterpret_cast<const float4*>(ep.bias + col) + j);
+            bv[4 * j] = b4.x;
+            bv[4 * j + 1] = b4.y;
+            bv[4 * j + 2] = b4.z;
+            bv[4 * j + 3] = b4.w;
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const float x0 = v[2 * j] + __ldg(ep.bias + col + 2 * j);
-            const float x1 = v[2 * j + 1] + __ldg(ep.bias + col + 2 * j + 1);
+            const float x0 = v[2 * j] + bv[2 * j];
+            const float x1 = v[2 * j + 1] + bv[2 * j + 1];
             __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(x0, 0.0f), fmaxf(x1, 0.0f));
             packed[j] = *reinterpret_cast<uint32_t*>(&h);
             pos |= (x0 > 0.0f ? 1u : 0u) << (2 * j);
@@ -158,7 +171,7 @@ __device__ __forceinline__ void epilogue_chunk(const EpiArgs& ep, int epi, int r
 }
 
 template <int N, int K>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            const __grid_constant__ CUtensorMap tmO, EpiArgs ep, int epi, int M) {
     static_assert(K % BK == 0 && N % 32 == 0 && N <= 256, "tile shape");
@@ -169,8 +182,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* sB = smem;                    // KB blocks of [N rows][128 B]
     uint8_t* sA = sB + (size_t)N * K * 2;  // STAGES x [128 rows][128 B]
-    uint8_t* sO = sA + STAGES * A_STAGE_BYTES;  // 4 epilogue warps x 2 output boxes
-    Ctl* ctl = reinterpret_cast<Ctl*>(sO + 8 * OUT_STAGE_BYTES);
+    uint8_t* sO = sA + STAGES * A_STAGE_BYTES;  // epilogue warps x 2 output boxes
+    Ctl* ctl = reinterpret_cast<Ctl*>(sO + 8 * EPI_GROUPS * OUT_STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -181,7 +194,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         sm100::mbar_init(&ctl->bfull, 1);
         for (int j = 0; j < 2; ++j) {
             sm100::mbar_init(&ctl->tfull[j], 1);
-            sm100::mbar_init(&ctl->tempty[j], 128);
+            sm100::mbar_init(&ctl->tempty[j], 128 * EPI_GROUPS);
         }
         sm100::mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
@@ -273,7 +286,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else if (warp >= 2) {
         // ---------------- epilogue
-        const int q = warp & 3;
+        const int q = warp & 3;                 // TMEM lane quadrant (rows q*32 .. +31 of the tile)
+        const int grp = (warp - 2) >> 2;        // which half of the column chunks
+        constexpr int CH = N / 32 / EPI_GROUPS;  // chunks per warp
+        static_assert((N / 32) % EPI_GROUPS == 0, "chunks split evenly between the epilogue warpgroups");
+        const int c_beg = grp * CH, c_end = c_beg + CH;
+        uint8_t* sOw = sO + (size_t)(warp - 2) * 2 * OUT_STAGE_BYTES;  // this warp's two output boxes
         int acc = 0, sbuf = 0;
         uint32_t aph = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -286,25 +304,25 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint32_t* brow = bitmask ? ep.bits + (size_t)row * ep.ldb : nullptr;
             uint4 mk[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) mk[j] = masked ? __ldg(mrow + j) : make_uint4(0u, 0u, 0u, 0u);
-            if (bitmask) mk[0].x = __ldg(brow);
+            for (int j = 0; j < 4; ++j) mk[j] = masked ? __ldg(mrow + 4 * c_beg + j) : make_uint4(0u, 0u, 0u, 0u);
+            if (bitmask) mk[0].x = __ldg(brow + c_beg);
             if (!wait_or_abort(&ctl->tfull[acc], aph, ctl, ep.err)) break;
             sm100::tc_fence_after();
 #pragma unroll 1
-            for (int c = 0; c < N / 32; ++c) {
+            for (int c = c_beg; c < c_end; ++c) {
                 float v[32];
                 sm100::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * N + c * 32), v);
                 uint4 nx[4];
-                const bool more = masked && c + 1 < N / 32;
+                const bool more = masked && c + 1 < c_end;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) nx[j] = more ? __ldg(mrow + 4 * (c + 1) + j) : make_uint4(0u, 0u, 0u, 0u);
-                if (bitmask && c + 1 < N / 32) nx[0].x = __ldg(brow + c + 1);
+                if (bitmask && c + 1 < c_end) nx[0].x = __ldg(brow + c + 1);
                 const bool tma = ep.tma_out && epi != EPI_BIAS_F32 && !(epi == EPI_SPLIT && c * 32 >= ep.split);
                 if (tma) {
                     // stage the warp's 32 x 32 box, then one thread stores it;
                     // a buffer is refilled once the store issued from it two
                     // chunks ago has read it (rows past M are clipped)
-                    uint8_t* st = sO + (size_t)(q * 2 + sbuf) * OUT_STAGE_BYTES;
+                    uint8_t* st = sOw + (size_t)sbuf * OUT_STAGE_BYTES;
                     if (lane == 0) sm100::bulk_wait_read_1();
                     __syncwarp();
                     epilogue_chunk<N>(ep, epi, row, M, c * 32, v, mk, reinterpret_cast<uint4*>(st + lane * 64));

@@ -127,7 +127,7 @@ cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, const CUtens
     int tiles = (M + gemm::BM - 1) / gemm::BM;
     int grid = tiles < sms ? tiles : sms;
     if (grid < 1) return cudaSuccess;
-    gemm::k_gemm<N, K><<<grid, gemm::THREADS, smem, s>>>(A, B, O ? *O : A, ep, epi, M);
+    gemm::k_gemm<N, K><<<grid, gemm::GEMM_THREADS, smem, s>>>(A, B, O ? *O : A, ep, epi, M);
     return cudaGetLastError();
 }
 
@@ -1507,6 +1507,8 @@ extern "C" plo_status plo_gemm_bf16(const void* d_A, const void* d_B, int32_t M,
     if (epilogue < 0 || epilogue > 3) return set_error(PLO_ERR_INVALID_ARG, "unknown epilogue");
     if ((epilogue <= 1 && !d_bias) || (epilogue == 2 && !d_mask) || (epilogue == 3 && !d_bits))
         return set_error(PLO_ERR_INVALID_ARG, "bias (epilogues 0, 1), mask (2) or bits (3) is NULL");
+    if (d_bias && reinterpret_cast<uintptr_t>(d_bias) % 16 != 0)
+        return set_error(PLO_ERR_INVALID_ARG, "bias must be 16-byte aligned (the epilogue reads it as float4)");
     const int epi = epilogue == 3 ? (int)gemm::EPI_MASKBITS_BF16 : epilogue;
     CUtensorMap mA, mB, mO;
     plo_status st = make_map(&mA, d_A, (uint64_t)M, (uint64_t)K, 128);
