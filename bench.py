@@ -304,6 +304,22 @@ def run_variants(plo, torch, tree32, rays, rgb, T, timed, rays_total):
     return out
 
 
+def run_sh_degrees(plo, torch, depth, rays, rgb, T, timed, rays_total):
+    """Render speed against the SH degree (Sec. 6.2's comparison of l_max 2,
+    3 and 4): the same luminaire geometry and leaf densities with l_max = 2,
+    3, 4 (9, 16, 25 coefficients per channel), FP32 leaves, the same rays."""
+    import plogen
+    out = {}
+    for deg in (2, 3, 4):
+        t = plo.Tree(plogen.luminaire_tree(plogen.LUMINAIRE_D10.with_(depth=depth, sh_degree=deg)))
+        total, per_launch = timed(t)
+        out[f"l_max_{deg}"] = {"value": rays_total / (total / 1e3) / 1e6, "unit": UNIT, "kernel_ms": per_launch,
+                               "record_bytes_fp32": int(t.info()["sh_record_stride"])}
+        t.free()
+    out["l_max_4_vs_2"] = out["l_max_4"]["value"] / out["l_max_2"]["value"]
+    return out
+
+
 def run_pt(plo, torch, tree32, W, K):
     """The luminaire as an emitter in a path tracer (Sec. 3 Eq. 2, Sec. 5):
     paths per second with the octree luminaire, and with an opaque box of
@@ -613,6 +629,8 @@ def main():
     variants = None if args.no_variants else run_variants(plo, torch, trees["fp32"], rays, rgb, T, timed,
                                                           world * n * K)
     pt = None if args.no_pt else run_pt(plo, torch, trees["fp32"], W, K)
+    sh_degrees = None if args.no_variants else run_sh_degrees(plo, torch, args.depth, rays, rgb, T, timed,
+                                                              world * n * K)
     train = None if args.no_train else run_train(plo, torch, args.train_timed_steps, W)
     distill = None if args.no_distill else run_distill(plo, torch, args.distill_train_steps)
     e2e = None
@@ -732,6 +750,7 @@ def main():
         "batch": batch,
         "variants": variants,
         "path_tracer": pt,
+        "sh_degrees": sh_degrees,
         "train": train,
         "distill": distill,
     }
