@@ -350,7 +350,7 @@ __device__ __forceinline__ void brick_enter(const TreeParams& tp, Ray& R, uint32
 // brick).  The whole descent runs in one step: stopping after each
 // dependent global load, so that lanes with shorter descents could go on,
 // was measured slower (304 vs 320 Mrays/s).
-template <bool BRICKS>
+template <bool BRICKS, int PREC>
 __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* s_nodes, Ray& R, uint32_t* stack) {
     for (int guard = 0; guard <= MAX_DEPTH; ++guard) {
         const int sh = tp.depth - 1 - R.level;
@@ -369,9 +369,11 @@ __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* 
             // the SH record is read in the next iteration: start pulling it
             // into L2 now (16-bit records; measured on the depth-10 workload:
             // FP16 347 -> 388 Mrays/s with it, FP32 339 -> 330, so FP32
-            // records are left to the load itself)
+            // records are left to the load itself).  The choice is made at
+            // compile time: as a run-time test it cost the FP16 kernel 9%.
             const uint32_t rec = e.x & ~LEAF_BIT;
-            if (tp.prec != PLO_PREC_FP32 && e.x != ENTRY_EMPTY && rec != NO_SH_RECORD) {
+            constexpr bool always = PREC > 0, never = PREC == PLO_PREC_FP32;
+            if (!never && (always || tp.prec != PLO_PREC_FP32) && e.x != ENTRY_EMPTY && rec != NO_SH_RECORD) {
                 const char* a = reinterpret_cast<const char*>(tp.sh) + (size_t)rec * tp.sh_stride;
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(a + tp.sh_stride - 1));
@@ -877,7 +879,7 @@ __global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : (BRICKS ? PLO_B
         // the leaf or brick)
         if (BRICKS && R.state == ST_BRICK) brick_step<K, PREC, SPHERE>(kp, tp, my, R, stack, sY);
         if (R.state == ST_LEAF) leaf_step<K, PREC, TRACE, SPHERE>(kp, tp, my, R, stack, sY);
-        if (R.state == ST_DESCEND) descend_step<BRICKS>(tp, s_nodes, R, stack);
+        if (R.state == ST_DESCEND) descend_step<BRICKS, PREC>(tp, s_nodes, R, stack);
     }
 }
 
@@ -958,7 +960,7 @@ __global__ void __launch_bounds__(BLOCK, BRICKS ? PLO_BRICK_MIN_BLOCKS : PLO_REN
         const TreeParams& tp = s_tp[R.tree];
         if (BRICKS && R.state == ST_BRICK) brick_step<0, -1, false>(kp, tp, my, R, stack);
         if (R.state == ST_LEAF) leaf_step<0, -1, false, false>(kp, tp, my, R, stack);
-        if (R.state == ST_DESCEND) descend_step<BRICKS>(tp, s_nodes, R, stack);
+        if (R.state == ST_DESCEND) descend_step<BRICKS, -1>(tp, s_nodes, R, stack);
     }
 }
 
