@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the linear / sigma_min-alpha_max / sphere-proxy timings")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step timing")
+    ap.add_argument("--no-octopt", action="store_true", help="skip the direct leaf optimisation section")
+    ap.add_argument("--octopt-fit-steps", type=int, default=400)
     ap.add_argument("--no-distill", action="store_true",
                     help="skip the trained network's depth-10 distillation and its error")
     ap.add_argument("--distill-train-steps", type=int, default=2000)
@@ -458,6 +460,62 @@ def run_distill(plo, torch, steps: int):
     return out
 
 
+def run_octopt(plo, torch, steps: int, W: int, fit_steps: int):
+    """Direct optimisation of the octree's leaves (Sec. 7's alternative to
+    the network): the structure of the depth-8 luminaire (SH degree 3),
+    every leaf starting at sigma = 1 with zero SH, fitted with the paper's
+    loss, small TV weights and Adam to the plain renderer's images of the
+    luminaire (the network's targets), 65,536 rays per step.  `steps` timed
+    steps after W warm-up steps (CUDA events); then the fit continues to
+    `fit_steps` steps and the packed result is scored on 65,536 test rays
+    like the distilled network."""
+    import plogen
+    from paper_2207_05009_gb300 import learned
+    gt_host = plogen.luminaire_tree(plogen.LUMINAIRE_D10.with_(depth=8))
+    gt = plo.Tree(gt_host)
+    n = 65536
+    batches = learned.target_batches(gt, [plogen.rays_sphere(n, seed=300 + k) for k in range(16)])
+    test_b = learned.target_batches(gt, [plogen.rays_sphere(n, seed=900)])
+    gt.free()
+    l_max, _ = learned.emission_scale(batches)
+    init = plogen.HostTree(gt_host.depth, gt_host.sh_degree, gt_host.child,
+                           np.ones(gt_host.n_leaves, np.float32), np.zeros_like(gt_host.sh))
+    total = max(fit_steps, steps + W)
+    opt = plo.OctOpt(init, l_max, max_rays=n, lr_sigma=2.0, lr_sh=0.05, lr_decay=0.1, total_steps=total,
+                     tv_sigma=1e-3, tv_sh=1e-4)
+    loss = torch.empty(3, device="cuda")
+    stream = torch.cuda.current_stream()
+    first = None
+    for k in range(W):
+        opt.step(*batches[k % 16], loss_out=loss)
+        if first is None:
+            first = float(loss[0].item())
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(steps):
+        opt.step(*batches[(W + k) % 16], loss_out=loss)
+    b.record(stream)
+    torch.cuda.synchronize()
+    opt.check()
+    ms = a.elapsed_time(b) / steps
+    for k in range(W + steps, total):
+        opt.step(*batches[k % 16], loss_out=loss)
+    torch.cuda.synchronize()
+    opt.check()
+    fit = opt.build_tree()
+    rel, psnr, a_rmse = learned.tree_error(fit, l_max, test_b)
+    fit.free()
+    out = {"workload": f"depth-8 luminaire structure ({gt_host.n_leaves} leaves, SH degree 3) fitted from sigma = 1, "
+                       "SH = 0 to the plain renderer's images; paper loss, TV 1e-3 / 1e-4, Adam; 65,536 rays per step",
+           "rays_per_step": n, "steps_timed": steps, "ms_per_step": ms, "mrays_per_s": n / (ms / 1e3) / 1e6,
+           "fit_steps": total, "first_loss": first, "final_loss": float(loss[0].item()),
+           "error": {"rel_l2_radiance": rel, "psnr": psnr, "alpha_rmse": a_rmse}}
+    opt.free()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_learned(args):
     """Train the NeRF-SH network on targets rendered from the depth-6
     luminaire (4096 rays x 128 samples per step, the paper's loss), distil it
@@ -633,6 +691,7 @@ def main():
                                                               world * n * K)
     train = None if args.no_train else run_train(plo, torch, args.train_timed_steps, W)
     distill = None if args.no_distill else run_distill(plo, torch, args.distill_train_steps)
+    octopt = None if args.no_octopt else run_octopt(plo, torch, 20, W, args.octopt_fit_steps)
     e2e = None
     if not args.no_e2e:
         rays_h = torch.from_numpy(rays_np).pin_memory()
@@ -753,6 +812,7 @@ def main():
         "sh_degrees": sh_degrees,
         "train": train,
         "distill": distill,
+        "octopt": octopt,
     }
     line["fp16"]["roofline"]["frac"] = line["fp16"]["roofline"]["achieved"] / peak
     print(json.dumps(line), flush=True)

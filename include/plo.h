@@ -564,6 +564,94 @@ plo_status plo_pt_render(const plo_tree* lum, const plo_render_params* params, c
                          void* stream);
 
 /* ------------------------------------------------------------------------
+ * Direct optimisation of the octree's leaves (Sec. 7, "Limitations --
+ * Precomputation cost": fitting the SH octree itself, with a total-variation
+ * regulariser against aliasing, instead of training a network and projecting
+ * it).  The tree's structure is fixed; per leaf i the parameters are a raw
+ * density s_i (sigma_i = max(0, s_i)) and the 3K SH coefficients
+ * (channel-major), emitting L_max sigmoid(sum_k k_k Y_k(d)) as the network
+ * does (Eq. 6).  Each ray is rendered over the exact leaf segments of the
+ * octree walk (plo_trace_rays of the structure, Eq. 3-5), so the forward pass
+ * equals plo_render_rays of the exported tree with PLO_ACT_SIGMOID.
+ * Objective: the paper's loss (Sec. 4.3, as plo_mlp_desc.loss, on values
+ * divided by l_max) averaged over the batch's rays, plus
+ * tv_sigma TV(s) + tv_sh TV(k), where per leaf and channel the TV term is
+ * sqrt(1e-8 + sum_a (x_{n_a(i)} - x_i)^2) over the axes a, n_a(i) being the
+ * leaf that holds the point just across i's upper face a at the face's
+ * centre (none: outside the cube or an empty octant, the difference is 0),
+ * averaged over the leaves.  Adam (beta 0.9, 0.999, eps 1e-8) with step
+ * sizes lr * lr_decay^(min(t - 1, total_steps) / total_steps) at update t. */
+typedef struct plo_octopt plo_octopt;
+
+typedef struct {
+    int32_t transmittance;  /* PLO_TRANS_EXP or PLO_TRANS_LINEAR               */
+    int32_t loss;           /* PLO_LOSS_*                                      */
+    float l_max;            /* emission scale L_max and loss unit (> 0)        */
+    float eps;              /* loss regulariser (0.01 in the paper)            */
+    float lr_sigma, lr_sh;  /* Adam step sizes of the densities and the SH     */
+    float lr_decay;         /* factor the step sizes fall by over total_steps,
+                               in (0, 1]                                       */
+    int32_t total_steps;    /* decay horizon (>= 1)                            */
+    float tv_sigma, tv_sh;  /* weights of the TV terms (>= 0)                  */
+    int64_t max_rays;       /* rays per step the scratch is sized for (>= 1)   */
+    int32_t max_cells;      /* cells per ray the trace holds; 0 = 3 * 2^depth
+                               + 2 (no ray crosses more)                       */
+} plo_octopt_config;
+
+/* What plo_octopt_read / _write move. */
+enum {
+    PLO_OCTOPT_SIGMA = 0,      /* float [n_leaves]: raw densities s          */
+    PLO_OCTOPT_SH = 1,         /* float [n_leaves][3][K]                      */
+    PLO_OCTOPT_GRAD_SIGMA = 2, /* float [n_leaves]: d objective / d s of the
+                                  last plo_octopt_grad or _step (read only)   */
+    PLO_OCTOPT_GRAD_SH = 3,    /* float [n_leaves][3][K] (read only)          */
+    PLO_OCTOPT_NEIGHBOURS = 4  /* int32 [n_leaves][3]: n_a(i), -1 for none
+                                  (read only)                                 */
+};
+
+/* Creates an optimiser on the current device for the structure of `init`
+ * (validated as for plo_build_tree; depth <= 10, n_leaves < 2^31), starting
+ * from its sigma (as raw densities) and SH coefficients.  Builds the
+ * structure's walk tree and the face-neighbour table, and allocates the
+ * parameters, gradients, Adam moments and the trace scratch (max_rays *
+ * cells * 16 bytes).  Synchronous.  Errors: those of plo_build_tree;
+ * PLO_ERR_INVALID_ARG for a bad config; PLO_ERR_UNSUPPORTED for depth > 10
+ * or 2^31 leaves or more; PLO_ERR_OOM. */
+plo_status plo_octopt_create(const plo_tree_desc* init, const plo_octopt_config* config, plo_octopt** out);
+void plo_octopt_free(plo_octopt* opt);
+
+/* The objective's gradient on n rays (async on `stream`), into the
+ * optimiser's gradient buffers (no update).
+ *   d_rays      float [n][6] world-space origin and direction
+ *   d_rgb_gt    float [n][3] target L_e;  d_alpha_gt float [n] target alpha
+ *   d_ray_out   float [n][5] (C^ rgb, alpha^, the ray's loss), or NULL
+ *   d_loss_out  float [3] (mean loss, TV(s), TV(k)), or NULL
+ * n <= max_rays.  A ray that crosses more than max_cells cells is left out
+ * and flagged (plo_octopt_check). */
+plo_status plo_octopt_grad(plo_octopt* opt, const float* d_rays, const float* d_rgb_gt, const float* d_alpha_gt,
+                           int64_t n, float* d_ray_out, float* d_loss_out, void* stream);
+
+/* plo_octopt_grad followed by one Adam update of every parameter (async).
+ * n == 0 is a no-op. */
+plo_status plo_octopt_step(plo_octopt* opt, const float* d_rays, const float* d_rgb_gt, const float* d_alpha_gt,
+                           int64_t n, float* d_ray_out, float* d_loss_out, void* stream);
+
+/* Copies one of the PLO_OCTOPT_* arrays to `dst` / from `src` (host or
+ * device memory; async on `stream`, so a host buffer must outlive the
+ * copy).  Writing resets nothing else (Adam's moments stay). */
+plo_status plo_octopt_read(const plo_octopt* opt, int32_t what, void* dst, void* stream);
+plo_status plo_octopt_write(plo_octopt* opt, int32_t what, const void* src, void* stream);
+
+/* Synchronises `stream`; PLO_ERR_TRAVERSAL_LIMIT if a ray of an earlier
+ * step crossed more than max_cells cells (the flag is cleared). */
+plo_status plo_octopt_check(plo_octopt* opt, void* stream);
+
+/* Packs the current parameters into a renderable tree (synchronous):
+ * sigma = max(0, s) and the coefficients, on the structure of `init`.
+ * Render it with PLO_ACT_SIGMOID and the optimiser's l_max. */
+plo_status plo_octopt_build_tree(const plo_octopt* opt, const plo_build_options* options, plo_tree** out);
+
+/* ------------------------------------------------------------------------
  * Test hooks for failure detection (nothing here faults or hangs a GPU).
  * plo_debug_fail_alloc_after(n): the n-th following device allocation made
  *   by the library fails as out-of-memory (n < 0 turns the hook off).

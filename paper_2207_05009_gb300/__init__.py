@@ -623,6 +623,132 @@ def wgrad_bf16(dZ, H, dW, db=None, err=None, stream=None):
 PT_OCTREE, PT_CONSTANT_BOX = 0, 1
 
 
+OCTOPT_SIGMA, OCTOPT_SH, OCTOPT_GRAD_SIGMA, OCTOPT_GRAD_SH, OCTOPT_NEIGHBOURS = 0, 1, 2, 3, 4
+
+
+class OctOptConfig(ctypes.Structure):
+    _fields_ = [("transmittance", ctypes.c_int32), ("loss", ctypes.c_int32), ("l_max", ctypes.c_float),
+                ("eps", ctypes.c_float), ("lr_sigma", ctypes.c_float), ("lr_sh", ctypes.c_float),
+                ("lr_decay", ctypes.c_float), ("total_steps", ctypes.c_int32), ("tv_sigma", ctypes.c_float),
+                ("tv_sh", ctypes.c_float), ("max_rays", ctypes.c_int64), ("max_cells", ctypes.c_int32)]
+
+
+def _octopt_lib():
+    lib = load()
+    if not getattr(lib, "_octopt_sigs", False):
+        P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        sigs = {
+            "plo_octopt_create": (I32, [P, P, P]),
+            "plo_octopt_free": (None, [P]),
+            "plo_octopt_grad": (I32, [P, P, P, P, I64, P, P, P]),
+            "plo_octopt_step": (I32, [P, P, P, P, I64, P, P, P]),
+            "plo_octopt_read": (I32, [P, I32, P, P]),
+            "plo_octopt_write": (I32, [P, I32, P, P]),
+            "plo_octopt_check": (I32, [P, P]),
+            "plo_octopt_build_tree": (I32, [P, P, P]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype, fn.argtypes = res, args
+        lib._octopt_sigs = True
+    return lib
+
+
+class OctOpt:
+    """Direct optimisation of an octree's leaves (plo_octopt_*): raw
+    densities and SH coefficients fitted to rendered targets with the
+    paper's loss, TV regularisers and Adam, on the structure of `init`."""
+
+    def __init__(self, init, l_max: float, max_rays: int, loss: int = LOSS_PAPER, transmittance: int = TRANS_EXP,
+                 eps: float = 0.01, lr_sigma: float = 0.1, lr_sh: float = 0.05, lr_decay: float = 0.1,
+                 total_steps: int = 1000, tv_sigma: float = 0.0, tv_sh: float = 0.0, max_cells: int = 0):
+        lib = _octopt_lib()
+        d, keep = _desc(init)
+        c = OctOptConfig(transmittance, loss, l_max, eps, lr_sigma, lr_sh, lr_decay, total_steps, tv_sigma, tv_sh,
+                         max_rays, max_cells)
+        h = ctypes.c_void_p()
+        _check(lib.plo_octopt_create(ctypes.byref(d), ctypes.byref(c), ctypes.byref(h)))
+        self._h = h
+        self.n_leaves = int(init.sigma.shape[0])
+        self.K = (int(init.sh_degree) + 1) ** 2
+        self.max_rays = int(max_rays)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _run(self, fn, rays, rgb_gt, alpha_gt, ray_out, loss_out, stream):
+        import torch
+        R = rays.shape[0] if rays.ndim == 2 else -1
+        _require_all((ray_out, "ray_out", (R, 5), torch.float32), (loss_out, "loss_out", (3,), torch.float32))
+        _require_rays_targets(rays, rgb_gt, alpha_gt)
+        if R > self.max_rays:
+            raise ValueError(f"{R} rays exceed max_rays = {self.max_rays}")
+        loss_out = loss_out if loss_out is not None else torch.empty(3, device=rays.device, dtype=torch.float32)
+        _check(fn(self._h, _ptr(rays), _ptr(rgb_gt), _ptr(alpha_gt), R, _ptr(ray_out), _ptr(loss_out),
+                  _stream(stream)))
+        return loss_out
+
+    def grad(self, rays, rgb_gt, alpha_gt, ray_out=None, loss_out=None, stream=None):
+        """plo_octopt_grad; returns the device tensor (mean loss, TV(s), TV(k))."""
+        return self._run(_octopt_lib().plo_octopt_grad, rays, rgb_gt, alpha_gt, ray_out, loss_out, stream)
+
+    def step(self, rays, rgb_gt, alpha_gt, ray_out=None, loss_out=None, stream=None):
+        """plo_octopt_step (gradient and one Adam update)."""
+        return self._run(_octopt_lib().plo_octopt_step, rays, rgb_gt, alpha_gt, ray_out, loss_out, stream)
+
+    def _shape(self, what):
+        if what in (OCTOPT_SIGMA, OCTOPT_GRAD_SIGMA):
+            return (self.n_leaves,), np.float32
+        if what in (OCTOPT_SH, OCTOPT_GRAD_SH):
+            return (self.n_leaves, 3, self.K), np.float32
+        if what == OCTOPT_NEIGHBOURS:
+            return (self.n_leaves, 3), np.int32
+        raise ValueError(f"unknown array {what}")
+
+    def read(self, what: int) -> np.ndarray:
+        """One PLO_OCTOPT_* array, copied to the host (synchronous)."""
+        import torch
+        shape, dt = self._shape(what)
+        out = np.empty(shape, dt)
+        lib = _octopt_lib()
+        _check(lib.plo_octopt_read(self._h, what, ctypes.c_void_p(out.ctypes.data), _stream(None)))
+        torch.cuda.current_stream().synchronize()
+        return out
+
+    def write(self, what: int, values: np.ndarray) -> None:
+        import torch
+        shape, dt = self._shape(what)
+        values = np.ascontiguousarray(values, dt)
+        _require_np(values, "values", shape, dt)
+        _check(_octopt_lib().plo_octopt_write(self._h, what, ctypes.c_void_p(values.ctypes.data), _stream(None)))
+        torch.cuda.current_stream().synchronize()
+
+    def check(self, stream=None) -> None:
+        _check(_octopt_lib().plo_octopt_check(self._h, _stream(stream)))
+
+    def build_tree(self, precision: int = PREC_FP32, layout: int = LAYOUT_DEFAULT, brick_log: int = 0) -> "Tree":
+        """plo_octopt_build_tree: the current parameters as a renderable Tree
+        (render it with ACT_SIGMOID and this optimiser's l_max)."""
+        t = Tree.__new__(Tree)
+        h = ctypes.c_void_p()
+        opt = BuildOptions(precision, layout, brick_log)
+        _check(_octopt_lib().plo_octopt_build_tree(self._h, ctypes.byref(opt), ctypes.byref(h)))
+        t._h, t.precision, t.layout = h, precision, layout
+        return t
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _octopt_lib().plo_octopt_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 class PtScene(ctypes.Structure):
     _fields_ = [("room_min", ctypes.c_float * 3), ("room_max", ctypes.c_float * 3),
                 ("albedo", (ctypes.c_float * 3) * 6), ("cam_pos", ctypes.c_float * 3),

@@ -92,14 +92,10 @@ class DistillError:
     distill_s: float
 
 
-def distilled_error(net: Mlp, l_max: float, test_batches, depth: int, samples: int = 8,
-                    sigma_thresh: float = 0.01, precision: int = PREC_FP32) -> DistillError:
+def tree_error(tree: Tree, l_max: float, test_batches):
+    """(rel_l2_radiance, psnr, alpha_rmse) of a tree rendered with the
+    sigmoid emission of scale l_max against the ground-truth batches."""
     import torch
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    tree = net.distill(depth, samples=samples, sigma_thresh=sigma_thresh, precision=precision)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
     params = RenderParams(activation=ACT_SIGMOID, l_max=l_max)
     se_c = ss_c = se_n = se_a = 0.0
     n = 0
@@ -115,9 +111,20 @@ def distilled_error(net: Mlp, l_max: float, test_batches, depth: int, samples: i
         se_a += float((da * da).sum())
         n += rays.shape[0]
     torch.cuda.synchronize()
+    mse_n = se_n / (3 * n)
+    return (float(np.sqrt(se_c / max(ss_c, 1e-300))), float(10 * np.log10(1.0 / max(mse_n, 1e-30))),
+            float(np.sqrt(se_a / n)))
+
+
+def distilled_error(net: Mlp, l_max: float, test_batches, depth: int, samples: int = 8,
+                    sigma_thresh: float = 0.01, precision: int = PREC_FP32) -> DistillError:
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tree = net.distill(depth, samples=samples, sigma_thresh=sigma_thresh, precision=precision)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rel, psnr, a_rmse = tree_error(tree, l_max, test_batches)
     leaves = tree.info()["n_leaves"]
     tree.free()
-    mse_n = se_n / (3 * n)
-    return DistillError(rel_l2_radiance=float(np.sqrt(se_c / max(ss_c, 1e-300))),
-                        psnr=float(10 * np.log10(1.0 / max(mse_n, 1e-30))), alpha_rmse=float(np.sqrt(se_a / n)),
-                        leaves=int(leaves), distill_s=dt)
+    return DistillError(rel_l2_radiance=rel, psnr=psnr, alpha_rmse=a_rmse, leaves=int(leaves), distill_s=dt)
