@@ -52,7 +52,7 @@ def parse_args():
                     help="skip the linear / sigma_min-alpha_max / sphere-proxy timings")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step timing")
     ap.add_argument("--no-octopt", action="store_true", help="skip the direct leaf optimisation section")
-    ap.add_argument("--octopt-fit-steps", type=int, default=400)
+    ap.add_argument("--octopt-fit-steps", type=int, default=1000)
     ap.add_argument("--no-distill", action="store_true",
                     help="skip the trained network's depth-10 distillation and its error")
     ap.add_argument("--distill-train-steps", type=int, default=2000)
@@ -441,7 +441,8 @@ def run_distill(plo, torch, steps: int):
     luminaire, distilled into a depth-10 octree (1024^3 voxel centres, 8
     jittered samples per kept voxel, sigma >= 0.01) on the device, and the
     distilled octree's render error against the ground-truth renders on
-    65,536 test rays; depth 8 beside it."""
+    65,536 test rays; depth 8 beside it, with 8 and with the paper's 256
+    samples per kept voxel."""
     import plogen
     from paper_2207_05009_gb300 import learned
     gt = plo.Tree(plogen.luminaire_tree(plogen.LUMINAIRE_D6))
@@ -450,11 +451,15 @@ def run_distill(plo, torch, steps: int):
     l_max, _ = learned.emission_scale(train_b)
     net, losses, dt = learned.train(train_b, steps, plo.LOSS_PAPER, l_max=l_max)
     out = {"workload": f"paper loss, {steps} steps of 4096 rays x 128 samples on the depth-6 luminaire's "
-                       "renders; distilled with 8 samples per kept voxel, sigma >= 0.01; error on 65,536 test rays",
+                       "renders; distilled with 8 samples per kept voxel (depth 8 also with the paper's 256), "
+                       "sigma >= 0.01; error on 65,536 test rays",
            "train_s": dt, "final_loss": float(np.mean(losses[-32:]))}
-    for depth in (8, 10):
-        e = learned.distilled_error(net, l_max, test_b, depth=depth)
-        out[f"depth{depth}"] = e.__dict__
+    for depth, samples in ((8, 8), (8, 256), (10, 8)):
+        e = learned.distilled_error(net, l_max, test_b, depth=depth, samples=samples)
+        d = e.__dict__
+        d["samples_per_voxel"] = samples
+        d["network_samples_per_s"] = e.leaves * samples / max(e.distill_s, 1e-9)
+        out[f"depth{depth}" + ("" if samples == 8 else f"_samples{samples}")] = d
     del net
     torch.cuda.empty_cache()
     return out
@@ -463,8 +468,9 @@ def run_distill(plo, torch, steps: int):
 def run_octopt(plo, torch, steps: int, W: int, fit_steps: int):
     """Direct optimisation of the octree's leaves (Sec. 7's alternative to
     the network): the structure of the depth-8 luminaire (SH degree 3),
-    every leaf starting at sigma = 1 with zero SH, fitted with the paper's
-    loss, small TV weights and Adam to the plain renderer's images of the
+    every leaf starting at sigma = 1 with the DC coefficient of the mean
+    emission (the network's starting level), fitted with the paper's loss,
+    small TV weights and Adam to the plain renderer's images of the
     luminaire (the network's targets), 65,536 rays per step.  `steps` timed
     steps after W warm-up steps (CUDA events); then the fit continues to
     `fit_steps` steps and the packed result is scored on 65,536 test rays
@@ -477,12 +483,15 @@ def run_octopt(plo, torch, steps: int, W: int, fit_steps: int):
     batches = learned.target_batches(gt, [plogen.rays_sphere(n, seed=300 + k) for k in range(16)])
     test_b = learned.target_batches(gt, [plogen.rays_sphere(n, seed=900)])
     gt.free()
-    l_max, _ = learned.emission_scale(batches)
+    l_max, c0 = learned.emission_scale(batches)
+    sh0 = np.zeros_like(gt_host.sh)
+    u = min(max(c0 / l_max, 1e-6), 1 - 1e-6)
+    sh0[:, :, 0] = np.log(u / (1 - u)) / 0.28209479177387814  # emission c0 in every direction
     init = plogen.HostTree(gt_host.depth, gt_host.sh_degree, gt_host.child,
-                           np.ones(gt_host.n_leaves, np.float32), np.zeros_like(gt_host.sh))
+                           np.ones(gt_host.n_leaves, np.float32), sh0)
     total = max(fit_steps, steps + W)
-    opt = plo.OctOpt(init, l_max, max_rays=n, lr_sigma=2.0, lr_sh=0.05, lr_decay=0.1, total_steps=total,
-                     tv_sigma=1e-3, tv_sh=1e-4)
+    opt = plo.OctOpt(init, l_max, max_rays=n, lr_sigma=5.0, lr_sh=0.1, lr_decay=0.1, total_steps=total,
+                     tv_sigma=1e-4, tv_sh=1e-5)
     loss = torch.empty(3, device="cuda")
     stream = torch.cuda.current_stream()
     first = None
@@ -506,8 +515,9 @@ def run_octopt(plo, torch, steps: int, W: int, fit_steps: int):
     fit = opt.build_tree()
     rel, psnr, a_rmse = learned.tree_error(fit, l_max, test_b)
     fit.free()
-    out = {"workload": f"depth-8 luminaire structure ({gt_host.n_leaves} leaves, SH degree 3) fitted from sigma = 1, "
-                       "SH = 0 to the plain renderer's images; paper loss, TV 1e-3 / 1e-4, Adam; 65,536 rays per step",
+    out = {"workload": f"depth-8 luminaire structure ({gt_host.n_leaves} leaves, SH degree 3) fitted from sigma = 1 "
+                       "and the mean emission to the plain renderer's images; paper loss, TV 1e-4 / 1e-5, Adam "
+                       "(5.0 / 0.1 decaying to a tenth); 65,536 rays per step",
            "rays_per_step": n, "steps_timed": steps, "ms_per_step": ms, "mrays_per_s": n / (ms / 1e3) / 1e6,
            "fit_steps": total, "first_loss": first, "final_loss": float(loss[0].item()),
            "error": {"rel_l2_radiance": rel, "psnr": psnr, "alpha_rmse": a_rmse}}

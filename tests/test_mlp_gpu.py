@@ -294,11 +294,13 @@ def tree_from_morton(depth, codes, sigma, sh):
                     np.asarray(sh, np.float32).reshape(len(codes), 3, 16))
 
 
-def test_distill_matches_oracle(torch_cuda):
+@pytest.mark.parametrize("S", [4, 256])
+def test_distill_matches_oracle(torch_cuda, S):
+    """S = 256 is the paper's sample count per kept voxel (Sec. 5)."""
     torch = torch_cuda
     import oracle
     from tests.parity import quantise_tree, relative_errors
-    depth, S, seed = 4, 4, 99
+    depth, seed = 4, 99
     flat = random_params(7, scale=0.6)
     net = plo.Mlp(l_max=5.0, jitter_seed=seed)
     net.set_params(flat)
