@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "gemm.cuh"
+#include "trunk.cuh"
 #include "plo_internal.h"
 #include "sh.cuh"
 
@@ -976,21 +977,38 @@ void padded_to_canonical(const plo_mlp* m, const std::vector<float>& p, float* c
 // writes fp32 raw outputs.  For training (`masks`), each ReLU layer also
 // writes which of its outputs are positive as bits (HB), the backward pass's
 // ReLU masks at 1/16 of the bytes of the activations.
-plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s, bool masks = false) {
+// The trunk (layers 0..7) runs as one layer-fused kernel (k_trunk): each
+// 128-row tile stays in shared memory from the encoding to H[8]; the layers'
+// outputs H[1..8] are stored for the backward pass and the activation hook
+// (`keep` false: only H[8], which the head reads).
+cudaError_t launch_trunk(plo_mlp* m, int64_t samples, bool masks, bool keep, cudaStream_t s) {
+    static_assert(gemm::TR_LAYERS == DEPTH && gemm::TR_N == WIDTH, "trunk shape");
+    gemm::TrunkMaps maps;
+    maps.x = m->mapA_H[0];
+    gemm::TrunkArgs a{};
+    for (int l = 0; l < DEPTH; ++l) {
+        maps.w[l] = m->mapW[l];
+        maps.h[l] = m->mapA_H[l + 1];
+        a.bias[l] = bias_ptr(m, m->master, l);
+        a.bits[l] = masks ? m->HB[l + 1] : nullptr;
+    }
+    a.store = keep ? 0xFFu : 0x80u;
+    a.err = m->d_err;
+    a.M = (int)samples;
+    const size_t smem = gemm::trunk_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(gemm::k_trunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = (int)((samples + gemm::BM - 1) / gemm::BM);
+    const int grid = tiles < m->sms ? tiles : m->sms;
+    if (grid < 1) return cudaSuccess;
+    gemm::k_trunk<<<grid, gemm::TR_THREADS, smem, s>>>(maps, a);
+    return cudaGetLastError();
+}
+
+plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s, bool masks = false, bool keep = true) {
     gemm::EpiArgs ep{};
     ep.err = m->d_err;
-    cudaError_t e = cudaSuccess;
-    for (int l = 0; l < DEPTH && e == cudaSuccess; ++l) {
-        ep.bias = bias_ptr(m, m->master, l);
-        ep.out_bf16 = m->H[l + 1];
-        ep.ldo = WIDTH;
-        ep.bits_out = masks ? m->HB[l + 1] : nullptr;
-        ep.ldb = WIDTH / 32;
-        if (l == 0)
-            e = launch_gemm<WIDTH, PE_PAD>(m->mapA_H[0], m->mapW[0], &m->mapO_H[1], ep, gemm::EPI_RELU_BF16, (int)samples, m->sms, s);
-        else
-            e = launch_gemm<WIDTH, WIDTH>(m->mapA_H[l], m->mapW[l], &m->mapO_H[l + 1], ep, gemm::EPI_RELU_BF16, (int)samples, m->sms, s);
-    }
+    cudaError_t e = launch_trunk(m, samples, masks, keep, s);
     ep.bits_out = nullptr;  // no ReLU after the head
     if (e == cudaSuccess && m->arch == PLO_ARCH_LINEAR_HEAD) {
         ep.bias = bias_ptr(m, m->master, DEPTH);
@@ -1619,7 +1637,7 @@ plo_status distill(plo_mlp* m, int32_t depth, int32_t samples, float sigma_thres
     for (int64_t base = 0; e == cudaSuccess && st == PLO_OK && base < total; base += C) {
         const int64_t n = total - base < C ? total - base : C;
         k_pe_centres<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((uint64_t)base, n, depth, m->H[0]);
-        st = forward_layers(m, n, s);
+        st = forward_layers(m, n, s, false, false);  // only H[8] is read (by the head)
         if (st != PLO_OK) break;
         k_keep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->raw, n, sigma_thresh, d_flag);
         e = device_exclusive_scan(d_flag, d_pos, n, s);
@@ -1649,7 +1667,7 @@ plo_status distill(plo_mlp* m, int32_t depth, int32_t samples, float sigma_thres
         const int64_t nv = nl - off < vmax ? nl - off : vmax;
         k_pe_jitter<<<(unsigned)((nv * samples + 255) / 256), 256, 0, s>>>(d_codes + off, nv, samples, depth,
                                                                           m->desc.seed, m->H[0]);
-        st = forward_layers(m, nv * samples, s);
+        st = forward_layers(m, nv * samples, s, false, false);
         if (st != PLO_OK) break;
         const unsigned g = (unsigned)((nv + 127) / 128);
         uint8_t* rec = d_rec + (size_t)off * stride;

@@ -58,6 +58,32 @@ def to_np(t):
     return t.float().cpu().numpy().astype(np.float64)
 
 
+def test_fused_trunk_equals_layer_by_layer_gemm(torch_cuda):
+    """The layer-fused trunk (one kernel for layers 1-8, the tile kept in
+    shared memory) against the single-layer tensor-core GEMM applied to each
+    of its own stored inputs: bit for bit, on a ragged sample count whose
+    tiles give the CTAs both full pairs and a lone tile."""
+    torch = torch_cuda
+    flat = random_params(3)
+    net = plo.Mlp(l_max=8.0)
+    net.set_params(flat)
+    n = 152 * 128 * 3 + 77
+    pts = np.random.default_rng(4).random((n, 3)).astype(np.float32)
+    net.forward(torch.from_numpy(pts).cuda())
+    H = [net.activation(l, n) for l in range(omlp.DEPTH + 1)]
+    Ws, bs = unflatten(flat)
+    for l in range(omlp.DEPTH):
+        W = np.zeros((256, H[l].shape[1]), np.float32)
+        W[:, :Ws[l].shape[1]] = Ws[l]
+        Wd = torch.from_numpy(W).cuda().to(torch.bfloat16)
+        bias = torch.from_numpy(bs[l].astype(np.float32)).cuda()
+        out, err = plo.gemm_bf16(H[l].contiguous(), Wd, 0, bias=bias)
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        assert torch.equal(out, H[l + 1]), (l, int((out != H[l + 1]).sum()))
+    net.check()
+
+
 def test_forward_layers_match_oracle_elementwise(torch_cuda):
     """Every tensor-core layer of the forward pass, element by element: the
     GPU's own bf16 input of layer l, times the bf16 weights, plus the FP32
