@@ -14,8 +14,9 @@
 //
 // Warp roles: 0 lane 0 TMA loads (input tiles, weights), 1 TMEM owner and
 // MMA issuer (lane 0), 2 lane 0 TMA stores of the finished activation
-// tiles, 4..11 the epilogue (warp w reads TMEM lanes 32 (w % 4) .. +31 and
-// half of the 32-column chunks).  The epilogue writes its bf16 results into
+// tiles, 4..19 the epilogue (warp w reads TMEM lanes 32 (w % 4) .. +31 and
+// a quarter of the 32-column chunks; 16 warps measured 2.60 -> 2.54 ms per
+// training step against 8).  The epilogue writes its bf16 results into
 // the activation buffer in the layout a 128-byte-swizzled TMA load would
 // produce (row r's 16-byte chunk c at r * 128 + ((c ^ (r & 7)) * 16) of
 // its 64-column block), so the next layer's MMA and the TMA store read it
@@ -35,8 +36,10 @@ constexpr int TR_WSTAGES = 3;
 constexpr int TR_WBYTES = TR_N * 128;          // one K-block of a weight matrix: 256 rows x 128 B
 constexpr int TR_KBYTES = BM * 128;            // one K-block of an activation tile: 128 rows x 128 B
 constexpr int TR_ABYTES = 4 * TR_KBYTES;       // a 128 x 256 bf16 activation tile
-constexpr int TR_THREADS = 384;
 constexpr int TR_EPI_WARP0 = 4;
+constexpr int TR_EPI_GROUPS = 4;                      // epilogue warps per TMEM lane quadrant
+constexpr int TR_CHUNKS = TR_N / 32 / TR_EPI_GROUPS;  // 32-column chunks per epilogue warp
+constexpr int TR_THREADS = 32 * TR_EPI_WARP0 + 128 * TR_EPI_GROUPS;
 __host__ __device__ constexpr size_t trunk_smem_bytes() {
     return 1024 + 2 * (size_t)TR_ABYTES + (size_t)TR_WSTAGES * TR_WBYTES + 256;
 }
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_trunk(const __grid_constant__
                     uint32_t* bits = a.bits[l];
                     uint8_t* A = act[p];
 #pragma unroll 1
-                    for (int c = grp * 4; c < grp * 4 + 4; ++c) {
+                    for (int c = grp * TR_CHUNKS; c < (grp + 1) * TR_CHUNKS; ++c) {
                         float v[32];
                         sm100::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(p * TR_N + c * 32), v);
                         uint32_t packed[16], pos = 0u;
