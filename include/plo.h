@@ -462,7 +462,9 @@ plo_status plo_mlp_checkpoint_info(const char* path, plo_mlp_desc* desc, int64_t
  *   network layer `layer` as the last forward or training step left it:
  *   layer 0 is the positional encoding (64 columns, column 63 zero),
  *   1..8 the outputs of the eight trunk layers (256 columns), and for
- *   PLO_ARCH_PAPER 9 the 128-wide layer's output.  d_out bf16 [n_rows][cols].
+ *   PLO_ARCH_PAPER 9 the 128-wide layer's output; PLO_MLP_DZ_BASE + l (l =
+ *   0..7) the last training step's d loss / d Z_l, the gradient at the
+ *   pre-activation of trunk layer l (256 columns).  d_out bf16 [n_rows][cols].
  * plo_mlp_quad: the quadrature render and loss stage of plo_mlp_train_step
  *   alone (Eq. 3-9, the network's l_max, eps, transmittance and loss) on
  *   given raw outputs d_raw float [n_rays * n_samples][1 + 3K] (row
@@ -471,6 +473,7 @@ plo_status plo_mlp_checkpoint_info(const char* path, plo_mlp_desc* desc, int64_t
  *   ray's loss) and, if d_draw is not NULL, d (mean loss) / d raw float
  *   [n_rays * n_samples][1 + 3K] as the backward pass receives it (rounded
  *   to bf16).  n_samples in {32, 64, 96, 128, 192, 256}. */
+enum { PLO_MLP_DZ_BASE = 16 };
 plo_status plo_mlp_get_activation(const plo_mlp* mlp, int32_t layer, void* d_out, int64_t n_rows, void* stream);
 plo_status plo_mlp_quad(plo_mlp* mlp, const float* d_rays, const float* d_raw, const float* d_delta,
                         const float* d_rgb_gt, const float* d_alpha_gt, int32_t n_rays, int32_t n_samples,

@@ -364,6 +364,7 @@ def trace(tree: Tree, rays, max_cells: int, params: RenderParams | None = None, 
 
 # ---------------------------------------------------------------- learned part
 LOSS_PAPER, LOSS_REG, LOSS_MSE = 0, 1, 2
+MLP_DZ_BASE = 16
 ARCH_LINEAR_HEAD, ARCH_PAPER = 0, 1
 
 
@@ -521,7 +522,7 @@ class Mlp:
         """plo_mlp_get_activation: bf16 input of `layer` for the first n_rows
         samples of the last forward or training step."""
         import torch
-        cols = 64 if layer == 0 else (128 if layer == 9 else 256)
+        cols = 64 if layer == 0 else (128 if layer == 9 else 256)  # MLP_DZ_BASE + l: d loss / d Z_l
         out = torch.empty((n_rows, cols), device="cuda", dtype=torch.bfloat16)
         _check(mlp_lib().plo_mlp_get_activation(self._h, layer, _ptr(out), n_rows, _stream(stream)))
         return out

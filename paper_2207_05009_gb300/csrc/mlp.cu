@@ -790,15 +790,15 @@ struct plo_mlp {
     float* raw = nullptr;               // [cap][64]
     float* sraw = nullptr;              // [cap][64] fp32 half of the paper combined layer (column 0: sigma)
     __nv_bfloat16* dO = nullptr;        // [cap][64]
-    __nv_bfloat16* dZ[2] = {};          // [cap][256]
+    __nv_bfloat16* dZ[DEPTH] = {};      // [cap][256]: d loss / d Z_l (pre-activation of trunk layer l)
     __nv_bfloat16* dZc = nullptr;       // [cap][192] gradient of the paper combined layer's output
     float* delta = nullptr;
     float* tsamp = nullptr;             // [cap] sample parameters (coarse pass)
     float* wts = nullptr;               // [cap] quadrature weights (coarse pass)
     float* ray_loss = nullptr;
-    CUtensorMap mapA_H[MAX_LAYERS], mapA_dO, mapA_dZ[2], mapA_dZc;  // A operand boxes (128 rows)
-    CUtensorMap mapW_H[MAX_LAYERS], mapW_dO, mapW_dZ[2], mapW_dZc;  // wgrad boxes (64 rows)
-    CUtensorMap mapO_H[MAX_LAYERS], mapO_dZ[2], mapO_dZc;           // TMA-store boxes (32 x 32)
+    CUtensorMap mapA_H[MAX_LAYERS], mapA_dO, mapA_dZ[DEPTH], mapA_dZc;  // A operand boxes (128 rows)
+    CUtensorMap mapW_H[MAX_LAYERS], mapW_dO, mapW_dZ[DEPTH], mapW_dZc;  // wgrad boxes (64 rows)
+    CUtensorMap mapO_H[MAX_LAYERS], mapO_dZ7, mapO_dZc;           // TMA-store boxes (32 x 32)
 };
 
 namespace {
@@ -809,15 +809,14 @@ void free_workspace(plo_mlp* m) {
     cudaFree(m->raw);
     cudaFree(m->sraw);
     cudaFree(m->dO);
-    cudaFree(m->dZ[0]);
-    cudaFree(m->dZ[1]);
+    for (int l = 0; l < DEPTH; ++l) cudaFree(m->dZ[l]), m->dZ[l] = nullptr;
     cudaFree(m->dZc);
     cudaFree(m->delta);
     cudaFree(m->tsamp);
     cudaFree(m->wts);
     cudaFree(m->ray_loss);
     m->raw = m->sraw = m->delta = m->tsamp = m->wts = m->ray_loss = nullptr;
-    m->dO = m->dZ[0] = m->dZ[1] = m->dZc = nullptr;
+    m->dO = m->dZc = nullptr;
     m->cap = 0;
     m->cap_rays = 0;
 }
@@ -839,8 +838,7 @@ plo_status ensure_workspace(plo_mlp* m, int64_t samples, int rays) {
     alloc((void**)&m->raw, (size_t)samples * OUT_PAD * 4);
     if (paper) alloc((void**)&m->sraw, (size_t)samples * OUT_PAD * 4);
     alloc((void**)&m->dO, (size_t)samples * OUT_PAD * 2);
-    alloc((void**)&m->dZ[0], (size_t)samples * WIDTH * 2);
-    alloc((void**)&m->dZ[1], (size_t)samples * WIDTH * 2);
+    for (int l = 0; l < DEPTH; ++l) alloc((void**)&m->dZ[l], (size_t)samples * WIDTH * 2);
     if (paper) alloc((void**)&m->dZc, (size_t)samples * COMB_PAD * 2);
     alloc((void**)&m->delta, (size_t)samples * 4);
     alloc((void**)&m->tsamp, (size_t)samples * 4);
@@ -866,10 +864,10 @@ plo_status ensure_workspace(plo_mlp* m, int64_t samples, int rays) {
     if (st == PLO_OK && paper) st = make_store_map(&m->mapO_dZc, m->dZc, samples, COMB_PAD);
     for (int l = 1; l < m->n_layers && st == PLO_OK; ++l)
         st = make_store_map(&m->mapO_H[l], m->H[l], samples, m->geom.in_pad[l]);
-    for (int k = 0; k < 2 && st == PLO_OK; ++k) st = make_store_map(&m->mapO_dZ[k], m->dZ[k], samples, WIDTH);
+    if (st == PLO_OK) st = make_store_map(&m->mapO_dZ7, m->dZ[DEPTH - 1], samples, WIDTH);
     if (st == PLO_OK) st = make_map(&m->mapA_dO, m->dO, samples, OUT_PAD, 128);
     if (st == PLO_OK) st = make_map(&m->mapW_dO, m->dO, samples, OUT_PAD, 64);
-    for (int k = 0; k < 2 && st == PLO_OK; ++k) {
+    for (int k = 0; k < DEPTH && st == PLO_OK; ++k) {
         st = make_map(&m->mapA_dZ[k], m->dZ[k], samples, WIDTH, 128);
         if (st == PLO_OK) st = make_map(&m->mapW_dZ[k], m->dZ[k], samples, WIDTH, 64);
     }
@@ -981,6 +979,18 @@ void padded_to_canonical(const plo_mlp* m, const std::vector<float>& p, float* c
 // 128-row tile stays in shared memory from the encoding to H[8]; the layers'
 // outputs H[1..8] are stored for the backward pass and the activation hook
 // (`keep` false: only H[8], which the head reads).
+template <bool BWD>
+cudaError_t launch_trunk_kernel(const gemm::TrunkMaps& maps, const gemm::TrunkArgs& a, int sms, cudaStream_t s) {
+    const size_t smem = gemm::trunk_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(gemm::k_trunk<BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = (a.M + gemm::BM - 1) / gemm::BM;
+    const int grid = tiles < sms ? tiles : sms;
+    if (grid < 1) return cudaSuccess;
+    gemm::k_trunk<BWD><<<grid, gemm::TR_THREADS, smem, s>>>(maps, a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_trunk(plo_mlp* m, int64_t samples, bool masks, bool keep, cudaStream_t s) {
     static_assert(gemm::TR_LAYERS == DEPTH && gemm::TR_N == WIDTH, "trunk shape");
     gemm::TrunkMaps maps;
@@ -995,14 +1005,25 @@ cudaError_t launch_trunk(plo_mlp* m, int64_t samples, bool masks, bool keep, cud
     a.store = keep ? 0xFFu : 0x80u;
     a.err = m->d_err;
     a.M = (int)samples;
-    const size_t smem = gemm::trunk_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(gemm::k_trunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int tiles = (int)((samples + gemm::BM - 1) / gemm::BM);
-    const int grid = tiles < m->sms ? tiles : m->sms;
-    if (grid < 1) return cudaSuccess;
-    gemm::k_trunk<<<grid, gemm::TR_THREADS, smem, s>>>(maps, a);
-    return cudaGetLastError();
+    return launch_trunk_kernel<false>(maps, a, m->sms, s);
+}
+
+// The trunk's data-gradient chain (job j: layer l = 7 - j): dZ[l-1] =
+// (dZ[l] W_l) masked by the forward's ReLU bits of H[l], from dZ[7].
+cudaError_t launch_trunk_bwd(plo_mlp* m, int64_t samples, cudaStream_t s) {
+    gemm::TrunkMaps maps;
+    maps.x = m->mapA_dZ[DEPTH - 1];
+    gemm::TrunkArgs a{};
+    for (int j = 0; j < DEPTH - 1; ++j) {
+        const int l = DEPTH - 1 - j;
+        maps.w[j] = m->mapWT[l];
+        maps.h[j] = m->mapA_dZ[l - 1];
+        a.bits[j] = m->HB[l];
+    }
+    a.store = (1u << (DEPTH - 1)) - 1u;
+    a.err = m->d_err;
+    a.M = (int)samples;
+    return launch_trunk_kernel<true>(maps, a, m->sms, s);
 }
 
 plo_status forward_layers(plo_mlp* m, int64_t samples, cudaStream_t s, bool masks = false, bool keep = true) {
@@ -1079,12 +1100,12 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
     if (m->arch == PLO_ARCH_LINEAR_HEAD) {
         e = launch_wgrad<WIDTH>(m->mapW_dO, m->mapW_H[DEPTH], m->grad + m->geom.off[DEPTH], OUT_PAD, (int)M, m->sms,
                                 m->d_err, s, bias_ptr(m, m->grad, DEPTH));
-        ep.out_bf16 = m->dZ[0];
+        ep.out_bf16 = m->dZ[DEPTH - 1];
         ep.ldo = WIDTH;
         ep.bits = m->HB[DEPTH];
         ep.ldb = WIDTH / 32;
         if (e == cudaSuccess)
-            e = launch_gemm<WIDTH, OUT_PAD>(m->mapA_dO, m->mapWT[DEPTH], &m->mapO_dZ[0], ep, gemm::EPI_MASKBITS_BF16, (int)M, m->sms, s);
+            e = launch_gemm<WIDTH, OUT_PAD>(m->mapA_dO, m->mapWT[DEPTH], &m->mapO_dZ7, ep, gemm::EPI_MASKBITS_BF16, (int)M, m->sms, s);
     } else {
         const int SH = DEPTH + 1;
         // SH layer: dW = dO^T feat, db = column sums; d feat -> dZc[:, 0:128]
@@ -1096,33 +1117,28 @@ plo_status backward_update(plo_mlp* m, int64_t M, cudaStream_t s) {
         ep.ldb = FEAT / 32;
         if (e == cudaSuccess)
             e = launch_gemm<FEAT, OUT_PAD>(m->mapA_dO, m->mapWT[SH], &m->mapO_dZc, ep, gemm::EPI_MASKBITS_BF16, (int)M, m->sms, s);
-        // combined layer [features | sigma]: dW = dZc^T h8; d h8 -> dZ[0]
+        // combined layer [features | sigma]: dW = dZc^T h8; d h8 -> dZ[7]
         if (e == cudaSuccess)
             e = launch_wgrad<WIDTH>(m->mapW_dZc, m->mapW_H[DEPTH], m->grad + m->geom.off[DEPTH], COMB_PAD, (int)M,
                                     m->sms, m->d_err, s, bias_ptr(m, m->grad, DEPTH));
-        ep.out_bf16 = m->dZ[0];
+        ep.out_bf16 = m->dZ[DEPTH - 1];
         ep.ldo = WIDTH;
         ep.bits = m->HB[DEPTH];
         ep.ldb = WIDTH / 32;
         if (e == cudaSuccess)
-            e = launch_gemm<WIDTH, COMB_PAD>(m->mapA_dZc, m->mapWT[DEPTH], &m->mapO_dZ[0], ep, gemm::EPI_MASKBITS_BF16, (int)M, m->sms, s);
+            e = launch_gemm<WIDTH, COMB_PAD>(m->mapA_dZc, m->mapWT[DEPTH], &m->mapO_dZ7, ep, gemm::EPI_MASKBITS_BF16, (int)M, m->sms, s);
     }
-    // hidden layers l = 8 .. 2 (index l-1 = 7 .. 1), then layer 1; each
-    // weight-gradient launch also sums the layer's bias gradient
-    int cur = 0;
+    // the trunk: the data gradients dZ[6] .. dZ[0] in one layer-fused chain
+    // from dZ[7], then every layer's weight gradient (each launch also sums
+    // the layer's bias gradient), reading dZ[l] and the layer's input H[l]
+    if (e == cudaSuccess) e = launch_trunk_bwd(m, M, s);
     for (int l = DEPTH - 1; l >= 0 && e == cudaSuccess; --l) {
-        // dZ[cur] is d loss / d pre-activation of layer l (0-based), input H[l]
         if (l == 0)
-            e = launch_wgrad<PE_PAD>(m->mapW_dZ[cur], m->mapW_H[0], m->grad + m->geom.off[0], WIDTH, (int)M, m->sms,
-                                     m->d_err, s, bias_ptr(m, m->grad, l));
+            e = launch_wgrad<PE_PAD>(m->mapW_dZ[0], m->mapW_H[0], m->grad + m->geom.off[0], WIDTH, (int)M, m->sms,
+                                     m->d_err, s, bias_ptr(m, m->grad, 0));
         else
-            e = launch_wgrad<WIDTH>(m->mapW_dZ[cur], m->mapW_H[l], m->grad + m->geom.off[l], WIDTH, (int)M, m->sms,
+            e = launch_wgrad<WIDTH>(m->mapW_dZ[l], m->mapW_H[l], m->grad + m->geom.off[l], WIDTH, (int)M, m->sms,
                                     m->d_err, s, bias_ptr(m, m->grad, l));
-        if (l == 0 || e != cudaSuccess) break;
-        ep.out_bf16 = m->dZ[cur ^ 1];
-        ep.bits = m->HB[l];
-        e = launch_gemm<WIDTH, WIDTH>(m->mapA_dZ[cur], m->mapWT[l], &m->mapO_dZ[cur ^ 1], ep, gemm::EPI_MASKBITS_BF16, (int)M, m->sms, s);
-        cur ^= 1;
     }
     if (e != cudaSuccess) return cuda_error(e, "MLP backward launch");
     // Adam with exponential decay lr0 -> lr1 over total_steps
@@ -1475,11 +1491,14 @@ __global__ void k_widen_grad(const __nv_bfloat16* dO, const __nv_bfloat16* dsig,
 extern "C" plo_status plo_mlp_get_activation(const plo_mlp* m, int32_t layer, void* d_out, int64_t n_rows,
                                              void* stream) {
     if (!m || !d_out) return set_error(PLO_ERR_INVALID_ARG, "mlp or output is NULL");
-    if (layer < 0 || layer >= m->n_layers) return set_error(PLO_ERR_INVALID_ARG, "layer out of range");
+    const bool grad = layer >= PLO_MLP_DZ_BASE && layer < PLO_MLP_DZ_BASE + DEPTH;
+    if (!grad && (layer < 0 || layer >= m->n_layers)) return set_error(PLO_ERR_INVALID_ARG, "layer out of range");
     if (n_rows < 0 || n_rows > m->cap) return set_error(PLO_ERR_INVALID_ARG, "n_rows exceeds the stored batch");
     if (n_rows == 0) return PLO_OK;
-    const size_t bytes = (size_t)n_rows * m->geom.in_pad[layer] * 2;
-    cudaError_t e = cudaMemcpyAsync(d_out, m->H[layer], bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    const size_t bytes = (size_t)n_rows * (grad ? WIDTH : m->geom.in_pad[layer]) * 2;
+    const void* src = grad ? (const void*)m->dZ[layer - PLO_MLP_DZ_BASE] : (const void*)m->H[layer];
+    if (!src) return set_error(PLO_ERR_INVALID_ARG, "no stored batch");
+    cudaError_t e = cudaMemcpyAsync(d_out, src, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     return e == cudaSuccess ? PLO_OK : cuda_error(e, "activation copy");
 }
 

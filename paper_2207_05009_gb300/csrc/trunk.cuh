@@ -44,16 +44,20 @@ __host__ __device__ constexpr size_t trunk_smem_bytes() {
     return 1024 + 2 * (size_t)TR_ABYTES + (size_t)TR_WSTAGES * TR_WBYTES + 256;
 }
 
+// Indexed by job j of a tile: the forward's layer j (j = 0..7), or in the
+// backward chain the data gradient through layer l = 7 - j (j = 0..6).
 struct TrunkMaps {
-    CUtensorMap x;                 // encoded input [M][64], boxes 64 x 128, 128-byte swizzle
-    CUtensorMap w[TR_LAYERS];      // W_l [256][K_l], boxes 64 x 256
-    CUtensorMap h[TR_LAYERS];      // layer l's output [M][256], boxes 64 x 128 (TMA stores)
+    CUtensorMap x;                 // input tile, boxes 64 x 128, 128-byte swizzle: the encoded
+                                   // samples [M][64] (forward), d loss / d Z_7 [M][256] (backward)
+    CUtensorMap w[TR_LAYERS];      // B operand [256][K], boxes 64 x 256: W_j (forward), W_l^T (backward)
+    CUtensorMap h[TR_LAYERS];      // job j's output [M][256], boxes 64 x 128 (TMA stores)
 };
 
 struct TrunkArgs {
-    const float* bias[TR_LAYERS];
-    uint32_t* bits[TR_LAYERS];  // [M][8] words of layer l's ReLU bits (nullable)
-    uint32_t store;             // bit l: store layer l's output through h[l]
+    const float* bias[TR_LAYERS];  // forward: layer j's bias
+    uint32_t* bits[TR_LAYERS];     // [M][8] words: forward, layer j's ReLU bits (written, nullable);
+                                   // backward, the ReLU bits of H_l (read: the mask of the gradient)
+    uint32_t store;                // bit j: store job j's output through h[j]
     unsigned int* err;          // bit 1: a pipeline wait gave up
     uint32_t wait_limit;        // polls per wait (0: sm100::WAIT_LIMIT)
     int M;
@@ -93,8 +97,14 @@ __device__ __forceinline__ int tr_tile(int pair, int slot, int n_tiles) {
     return t < n_tiles ? t : -1;
 }
 
+// BWD: the data-gradient chain instead of the forward: per job
+// dZ_{l-1} = (dZ_l W_l) masked by the ReLU bits of H_l, l = 7 .. 1, starting
+// from the head's dZ_7 (four input K-blocks) with no bias.
+template <bool BWD>
 __global__ void __launch_bounds__(TR_THREADS, 1) k_trunk(const __grid_constant__ TrunkMaps maps, TrunkArgs a) {
     constexpr uint32_t IDESC = sm100::idesc_bf16(BM, TR_N, 0, 0);
+    constexpr int NJ = BWD ? TR_LAYERS - 1 : TR_LAYERS;  // jobs per tile
+    constexpr int XKB = BWD ? 4 : 1;                      // K-blocks of the input tile
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* act[2] = {smem, smem + TR_ABYTES};
@@ -135,7 +145,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_trunk(const __grid_constant__
         int jobs[2] = {0, 0}, xs[2] = {0, 0};
         bool ok = true;
         for (int pr = 0; ok && pr < n_pairs; ++pr)
-            for (int l = 0; ok && l < TR_LAYERS; ++l)
+            for (int l = 0; ok && l < NJ; ++l)
                 for (int p = 0; ok && p < 2; ++p) {
                     const int tile = tr_tile(pr, p, n_tiles);
                     if (tile < 0) continue;
@@ -145,11 +155,13 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_trunk(const __grid_constant__
                             ok = false;
                             break;
                         }
-                        sm100::mbar_arrive_expect_tx(&ctl->xfull[p], (uint32_t)(BM * 64 * 2));
-                        sm100::tma_load_2d(act[p], &maps.x, 0, tile * BM, &ctl->xfull[p]);
+                        sm100::mbar_arrive_expect_tx(&ctl->xfull[p], (uint32_t)(XKB * TR_KBYTES));
+                        for (int kb = 0; kb < XKB; ++kb)
+                            sm100::tma_load_2d(act[p] + (size_t)kb * TR_KBYTES, &maps.x, kb * 64, tile * BM,
+                                               &ctl->xfull[p]);
                         ++xs[p];
                     }
-                    const int nkb = l == 0 ? 1 : 4;
+                    const int nkb = (!BWD && l == 0) ? 1 : 4;
                     for (int kb = 0; kb < nkb; ++kb) {
                         if (!tr_wait(&ctl->wempty[ws], wph ^ 1u, ctl, a.err)) {
                             ok = false;
@@ -179,7 +191,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_trunk(const __grid_constant__
         int jobs[2] = {0, 0}, xs[2] = {0, 0};
         bool ok = true, issued = false;
         for (int pr = 0; ok && pr < n_pairs; ++pr)
-            for (int l = 0; ok && l < TR_LAYERS; ++l)
+            for (int l = 0; ok && l < NJ; ++l)
                 for (int p = 0; ok && p < 2; ++p) {
                     const int tile = tr_tile(pr, p, n_tiles);
                     if (tile < 0) continue;
@@ -192,7 +204,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_trunk(const __grid_constant__
                     }
                     sm100::tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(p * TR_N);
-                    const int nkb = l == 0 ? 1 : 4;
+                    const int nkb = (!BWD && l == 0) ? 1 : 4;
                     for (int kb = 0; kb < nkb; ++kb) {
                         if (!tr_wait(&ctl->wfull[ws], wph, ctl, a.err)) {
                             ok = false;
@@ -227,7 +239,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_trunk(const __grid_constant__
         int jobs[2] = {0, 0};
         bool ok = true;
         for (int pr = 0; ok && pr < n_pairs; ++pr)
-            for (int l = 0; ok && l < TR_LAYERS; ++l)
+            for (int l = 0; ok && l < NJ; ++l)
                 for (int p = 0; ok && p < 2; ++p) {
                     const int tile = tr_tile(pr, p, n_tiles);
                     if (tile < 0) continue;
@@ -253,7 +265,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_trunk(const __grid_constant__
         int jobs[2] = {0, 0};
         bool ok = true;
         for (int pr = 0; ok && pr < n_pairs; ++pr)
-            for (int l = 0; ok && l < TR_LAYERS; ++l)
+            for (int l = 0; ok && l < NJ; ++l)
                 for (int p = 0; ok && p < 2; ++p) {
                     const int tile = tr_tile(pr, p, n_tiles);
                     if (tile < 0) continue;
@@ -272,8 +284,18 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_trunk(const __grid_constant__
                         float v[32];
                         sm100::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(p * TR_N + c * 32), v);
                         uint32_t packed[16], pos = 0u;
+                        if (BWD) {  // keep the gradient where the forward pre-activation was > 0
+                            const uint32_t mw = row < a.M ? __ldg(bits + (size_t)row * 8 + c) : 0u;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
+                            for (int j = 0; j < 16; ++j) {
+                                const float x0 = ((mw >> (2 * j)) & 1u) ? v[2 * j] : 0.0f;
+                                const float x1 = ((mw >> (2 * j + 1)) & 1u) ? v[2 * j + 1] : 0.0f;
+                                __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+                                packed[j] = *reinterpret_cast<uint32_t*>(&h);
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < 8 && !BWD; ++j) {
                             const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + c * 32) + j);
                             const float x0 = v[4 * j] + b4.x, x1 = v[4 * j + 1] + b4.y;
                             const float x2 = v[4 * j + 2] + b4.z, x3 = v[4 * j + 3] + b4.w;
@@ -285,7 +307,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_trunk(const __grid_constant__
                                     (x3 > 0.0f ? 8u : 0u))
                                    << (4 * j);
                         }
-                        if (bits && row < a.M) bits[(size_t)row * 8 + c] = pos;
+                        if (!BWD && bits && row < a.M) bits[(size_t)row * 8 + c] = pos;
                         uint8_t* blk = A + (size_t)(c >> 1) * TR_KBYTES + (size_t)rl * 128;
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {

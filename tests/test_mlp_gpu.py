@@ -84,6 +84,36 @@ def test_fused_trunk_equals_layer_by_layer_gemm(torch_cuda):
     net.check()
 
 
+def test_fused_backward_chain_equals_layer_by_layer_gemm(torch_cuda):
+    """The layer-fused data-gradient chain of a training step (dZ_{l-1} =
+    (dZ_l W_l) masked where H_l > 0, l = 7 .. 1, in one kernel) against the
+    single-layer tensor-core GEMM with the mask epilogue applied to each of
+    its own stored inputs: bit for bit, on 1,142 rays x 64 samples (571
+    tiles: full pairs and lone tiles per CTA)."""
+    torch = torch_cuda
+    flat = random_params(5, scale=0.5)
+    net = plo.Mlp(l_max=6.0)
+    net.set_params(flat)
+    R, N = 1142, 64
+    rays = plogen.rays_sphere(R, seed=6)
+    rng = np.random.default_rng(7)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    net.train_step(dev(rays), dev(rng.uniform(0, 5, (R, 3)).astype(np.float32)),
+                   dev(rng.uniform(0, 1, R).astype(np.float32)), n_samples=N)
+    M = R * N
+    H = [net.activation(l, M) for l in range(omlp.DEPTH + 1)]
+    dZ = [net.activation(plo.MLP_DZ_BASE + l, M) for l in range(omlp.DEPTH)]
+    Ws, _ = unflatten(flat)  # the weights the step's backward used (before its update)
+    for l in range(omlp.DEPTH - 1, 0, -1):
+        WT = torch.from_numpy(np.ascontiguousarray(Ws[l].T.astype(np.float32))).cuda().to(torch.bfloat16)
+        out, err = plo.gemm_bf16(dZ[l], WT, 2, mask=H[l])
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        assert torch.equal(out, dZ[l - 1]), (l, int((out != dZ[l - 1]).sum()))
+    assert bool(dZ[0].abs().sum() > 0)
+    net.check()
+
+
 def test_forward_layers_match_oracle_elementwise(torch_cuda):
     """Every tensor-core layer of the forward pass, element by element: the
     GPU's own bf16 input of layer l, times the bf16 weights, plus the FP32
