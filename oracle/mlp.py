@@ -258,9 +258,9 @@ def train_loss_and_grads(Ws, bs, rays, jitter, C_gt, alpha_gt, l_max_scale, l_ma
 
 
 # ---------------------------------------------------------------- the paper's full training setup
-# Sec. 4.2 "Network architecture": the 8 x 256 trunk with "an extra output
-# layer of 128 neurons" returning the 3 (l_max+1)^2 SH coefficients; sigma is
-# read linearly from the trunk.  Sec. 4.3 / 4.4: a coarse and a fine network,
+# Sec. 4.2 (network architecture): the 8 x 256 trunk, then a 128-wide hidden
+# layer whose output gives the 3 (l_max+1)^2 SH coefficients; sigma is read
+# linearly from the trunk.  Sec. 4.3 / 4.4: a coarse and a fine network,
 # N_c = 64 stratified samples for the coarse one and N_f = 128 more, placed
 # by the coarse weights, for the fine one; loss L_c + L_f + L_alpha.
 
