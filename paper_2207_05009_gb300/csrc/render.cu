@@ -1089,6 +1089,125 @@ plo_status check_params(const plo_render_params* p) {
 }
 
 
+// ---------------------------------------------------------------- ray order
+// Large wavefronts are rendered in an order that groups rays entering the
+// proxy box near each other: a counting sort by the Morton code of the
+// entry point's cell on a 32^3 grid of the box (rays that miss it or are
+// invalid go to bin 0) moves the rays into a scratch copy, the render
+// kernel runs on the copy unchanged, and its outputs are moved back.
+// Neighbouring rays then walk neighbouring cells, so a warp's lanes share
+// node and record loads in L1 and L2 (measured on the 16M room rays of the
+// depth-10 tree, rays pre-sorted: 336.6 -> 356.6 Mrays/s with FP32 leaves,
+// 386.7 -> 400.8 with FP16; finer keys gained no more).  The sort keeps its
+// histograms in shared memory: one block per SM counts its contiguous chunk
+// of rays, a scan of the (bin, block) table gives every block its slot in
+// every bin, and the block scatters its chunk with shared-memory counters
+// (a sort with global atomics cost 2.5 ms per 16M rays, more than it
+// saved).  Each ray's result does not depend on the order.
+constexpr int ORDER_BITS = 5;                       // cells per axis: 2^5
+constexpr int ORDER_BINS = 1 << (3 * ORDER_BITS);  // 32768
+constexpr int ORDER_THREADS = 1024;
+constexpr size_t ORDER_SMEM = (size_t)ORDER_BINS * 4;  // one counter per bin
+
+__device__ __forceinline__ uint32_t order_spread(uint32_t x) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int b = 0; b < ORDER_BITS; ++b) r |= ((x >> b) & 1u) << (3 * b);
+    return r;
+}
+
+// Bin of a world-space ray: Morton code of the cell where it enters the
+// unit cube of the tree (its origin's cell if it starts inside).
+__device__ __forceinline__ uint32_t order_bin(const float* q, float3 bmin, float3 inv_ext) {
+    const float bm[3] = {bmin.x, bmin.y, bmin.z}, ie[3] = {inv_ext.x, inv_ext.y, inv_ext.z};
+    float u[3], du[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        u[a] = (__ldg(q + a) - bm[a]) * ie[a];
+        du[a] = __ldg(q + 3 + a) * ie[a];
+        ok &= isfinite(u[a]) && isfinite(du[a]);
+    }
+    float tn = 0.0f, tf = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (du[a] == 0.0f) {
+            ok &= u[a] >= 0.0f && u[a] <= 1.0f;
+            continue;
+        }
+        const float t0 = -u[a] / du[a], t1 = (1.0f - u[a]) / du[a];
+        tn = fmaxf(tn, fminf(t0, t1));
+        tf = fminf(tf, fmaxf(t0, t1));
+    }
+    if (!ok || !(tn <= tf)) return 0u;
+    uint32_t c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float e = fminf(fmaxf(__fmaf_rn(tn, du[a], u[a]), 0.0f), 1.0f) * (float)(1 << ORDER_BITS);
+        c[a] = min((uint32_t)e, (1u << ORDER_BITS) - 1u);
+    }
+    return order_spread(c[0]) | (order_spread(c[1]) << 1) | (order_spread(c[2]) << 2);
+}
+
+// Block b counts the bins of rays [b chunk, (b+1) chunk): bins[i], and
+// table[bin * gridDim.x + b] = its count of that bin.
+__global__ void __launch_bounds__(ORDER_THREADS) k_order_count(const float* rays, int64_t n, int64_t chunk,
+                                                               float3 bmin, float3 inv_ext, uint16_t* bins,
+                                                               uint32_t* table) {
+    extern __shared__ uint32_t s_cnt[];
+    for (int j = threadIdx.x; j < ORDER_BINS; j += ORDER_THREADS) s_cnt[j] = 0u;
+    __syncthreads();
+    const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(beg + chunk, n);
+    for (int64_t i = beg + threadIdx.x; i < end; i += ORDER_THREADS) {
+        const uint32_t b = order_bin(rays + 6 * i, bmin, inv_ext);
+        bins[i] = (uint16_t)b;
+        atomicAdd(s_cnt + b, 1u);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < ORDER_BINS; j += ORDER_THREADS) table[(size_t)j * gridDim.x + blockIdx.x] = s_cnt[j];
+}
+
+// After the exclusive scan of the table: block b gives each ray of its chunk
+// the next free position of its bin's slot: order[pos] = i, inv[i] = pos.
+__global__ void __launch_bounds__(ORDER_THREADS) k_order_scatter(int64_t n, int64_t chunk, const uint16_t* bins,
+                                                                 const uint32_t* table, uint32_t* order,
+                                                                 uint32_t* inv) {
+    extern __shared__ uint32_t s_pos[];
+    for (int j = threadIdx.x; j < ORDER_BINS; j += ORDER_THREADS) s_pos[j] = table[(size_t)j * gridDim.x + blockIdx.x];
+    __syncthreads();
+    const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(beg + chunk, n);
+    for (int64_t i = beg + threadIdx.x; i < end; i += ORDER_THREADS) {
+        const uint32_t pos = atomicAdd(s_pos + bins[i], 1u);
+        order[pos] = (uint32_t)i;
+        inv[i] = pos;
+    }
+}
+
+// The rays in order: rays_s[pos] = rays[order[pos]] (writes in order, so
+// only the reads are scattered).
+__global__ void k_order_rays(const float* rays, int64_t n, const uint32_t* order, float* rays_s) {
+    const int64_t pos = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (pos >= n) return;
+    const float* src = rays + 6 * (int64_t)__ldg(order + pos);  // the caller's rays are only 4-byte aligned
+    float* dst = rays_s + 6 * pos;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) dst[k] = __ldg(src + k);
+}
+
+// The outputs back in ray order: ray i's from position inv[i] (writes in
+// ray order, reads scattered).
+__global__ void k_order_outputs(const uint32_t* inv, int64_t n, const float* rgb_s, const float* T_s,
+                                const int32_t* st_s, float* rgb, float* T, int32_t* st) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    const int64_t pos = __ldg(inv + i);
+    rgb[3 * i] = __ldg(rgb_s + 3 * pos);
+    rgb[3 * i + 1] = __ldg(rgb_s + 3 * pos + 1);
+    rgb[3 * i + 2] = __ldg(rgb_s + 3 * pos + 2);
+    T[i] = __ldg(T_s + pos);
+    if (st) st[i] = __ldg(st_s + pos);
+}
+
 // ---------------------------------------------------------------- work distribution
 // Large wavefronts are handed out dynamically: warps claim RENDER_CLAIM rays
 // at a time from a counter allocated for the call, so a warp whose rays are
@@ -1136,12 +1255,55 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     cudaError_t e = cudaSuccess;
     cudaStream_t cs = (cudaStream_t)stream;
     unsigned long long* cursor = nullptr;
+    uint32_t* inv = nullptr;
+    float *rgb_s = nullptr, *T_s = nullptr;
+    int32_t* st_s = nullptr;
     if (!TRACE && n >= DYNAMIC_MIN_RAYS) {
-        e = (cudaError_t)dev_malloc_async((void**)&cursor, sizeof(unsigned long long), cs);
-        if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), cs);
+        // one scratch block: the claim counter, the (bin, block) table, the
+        // order and its inverse, the rays and outputs in that order, each
+        // ray's bin
+        const int nblk = t->sm_count;
+        const int64_t chunk = (n + nblk - 1) / nblk;
+        auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+        const size_t o_table = 256, o_order = o_table + up((size_t)ORDER_BINS * nblk * 4);
+        const size_t o_inv = o_order + up((size_t)n * 4);
+        const size_t o_rays = o_inv + up((size_t)n * 4), o_rgb = o_rays + up((size_t)n * 24);
+        const size_t o_T = o_rgb + up((size_t)n * 12), o_st = o_T + up((size_t)n * 4);
+        const size_t o_bins = o_st + (d_status ? up((size_t)n * 4) : 0), total = o_bins + up((size_t)n * 2);
+        e = (cudaError_t)dev_malloc_async((void**)&cursor, total, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, 256, cs);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_order_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)ORDER_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_order_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)ORDER_SMEM);
+        if (e == cudaSuccess) {
+            uint8_t* base = reinterpret_cast<uint8_t*>(cursor);
+            uint32_t* table = reinterpret_cast<uint32_t*>(base + o_table);
+            uint32_t* order = reinterpret_cast<uint32_t*>(base + o_order);
+            inv = reinterpret_cast<uint32_t*>(base + o_inv);
+            float* rays_s = reinterpret_cast<float*>(base + o_rays);
+            rgb_s = reinterpret_cast<float*>(base + o_rgb);
+            T_s = reinterpret_cast<float*>(base + o_T);
+            st_s = d_status ? reinterpret_cast<int32_t*>(base + o_st) : nullptr;
+            uint16_t* bins = reinterpret_cast<uint16_t*>(base + o_bins);
+            const float3 bmin = make_float3(t->bbox_min[0], t->bbox_min[1], t->bbox_min[2]);
+            const float3 iext = make_float3(t->inv_ext[0], t->inv_ext[1], t->inv_ext[2]);
+            k_order_count<<<nblk, ORDER_THREADS, ORDER_SMEM, cs>>>(d_rays, n, chunk, bmin, iext, bins, table);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = device_exclusive_scan(table, table, (int64_t)ORDER_BINS * nblk, cs);
+            if (e == cudaSuccess) {
+                k_order_scatter<<<nblk, ORDER_THREADS, ORDER_SMEM, cs>>>(n, chunk, bins, table, order, inv);
+                k_order_rays<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(d_rays, n, order, rays_s);
+                e = cudaGetLastError();
+            }
+            kp.rays = rays_s;
+            kp.rgb = rgb_s;
+            kp.T = T_s;
+            kp.status = st_s;
+        }
         if (e != cudaSuccess) {
             if (cursor) cudaFreeAsync(cursor, cs);
-            return cuda_error(e, "render work counter");
+            return cuda_error(e, "render work counter and ray order");
         }
         kp.cursor = cursor;
     }
@@ -1154,6 +1316,10 @@ plo_status render_common(const plo_tree* t, const float* d_rays, int64_t n, cons
     else
         e = bricks ? dispatch<false, false, true>(t, kp, smem, (cudaStream_t)stream)
                    : dispatch<false, false, false>(t, kp, smem, (cudaStream_t)stream);
+    if (e == cudaSuccess && inv) {
+        k_order_outputs<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(inv, n, rgb_s, T_s, st_s, d_rgb, d_T, d_status);
+        e = cudaGetLastError();
+    }
     if (cursor) cudaFreeAsync(cursor, cs);
     if (e != cudaSuccess) return cuda_error(e, "render kernel launch");
     return PLO_OK;
