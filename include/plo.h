@@ -615,9 +615,10 @@ enum {
 /* Creates an optimiser on the current device for the structure of `init`
  * (validated as for plo_build_tree; depth <= 10, n_leaves < 2^31), starting
  * from its sigma (as raw densities) and SH coefficients.  Builds the
- * structure's walk tree and the face-neighbour table, and allocates the
- * parameters, gradients, Adam moments and the trace scratch (max_rays *
- * cells * 16 bytes).  Synchronous.  Errors: those of plo_build_tree;
+ * structure's walk tree, the face-neighbour table and its reverse, and
+ * allocates the parameters, gradients, Adam moments, the TV scratch (8
+ * bytes per coefficient) and the trace scratch (max_rays * cells * 16
+ * bytes).  Synchronous.  Errors: those of plo_build_tree;
  * PLO_ERR_INVALID_ARG for a bad config; PLO_ERR_UNSUPPORTED for depth > 10
  * or 2^31 leaves or more; PLO_ERR_OOM. */
 plo_status plo_octopt_create(const plo_tree_desc* init, const plo_octopt_config* config, plo_octopt** out);

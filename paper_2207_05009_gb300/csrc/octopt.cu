@@ -11,7 +11,8 @@
 //      the ray's trace row as (leaf, delta) and (w, T_out); the loss (Sec.
 //      4.3, Eq. 7-9); then, back to front, d loss / d a_j and the SH
 //      gradients, added to the leaves with atomics;
-//   3. k_tv: the TV terms and their gradients over the face-neighbour table;
+//   3. k_tv_terms, k_tv_grad: the TV terms and their gradients over the
+//      face-neighbour table and its reverse (two gathers, no atomics);
 //   4. k_adam: Adam over the raw densities and the coefficients.
 #include <cuda_runtime.h>
 
@@ -43,6 +44,10 @@ struct plo_octopt {
     float* d_mk = nullptr;
     float* d_vk = nullptr;
     int32_t* d_nb = nullptr;     // face neighbours [n_leaves][3], -1 none
+    int32_t* d_rev_off = nullptr;  // reverse neighbours: leaf i's are d_rev[d_rev_off[i] .. d_rev_off[i+1])
+    int32_t* d_rev = nullptr;      // the leaves j with n_a(j) = i for some axis a
+    float* d_tv_s = nullptr;       // per (leaf, channel): sqrt(eps + sum_a d_a^2) of the last TV pass
+    float* d_tv_own = nullptr;     // per (leaf, channel): -sum_a d_a / s
     int64_t* d_tr_leaf = nullptr;  // trace scratch [max_rays][max_cells]
     float* d_tr_t = nullptr;       // [max_rays][max_cells][2]
     int32_t* d_tr_count = nullptr; // [max_rays]
@@ -238,35 +243,59 @@ __global__ void __launch_bounds__(THREADS) k_grad(GradArgs p) {
     if ((threadIdx.x & 31) == 0 && loss != 0.0f) atomicAdd(p.acc, loss * p.inv_n);
 }
 
-// TV of C channels x [n][C] over the neighbour table: one thread per (leaf,
-// channel).  Adds scale * d TV / d x to g (scale = lambda / n) and TV / n to
-// *val.
-__global__ void __launch_bounds__(THREADS) k_tv(const float* x, int C, const int32_t* nb, int64_t n, float scale,
-                                                 float* g, float* val) {
-    const int64_t idx = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+// TV of C channels x [n][C], pass 1, over every (leaf i, channel c) in a
+// grid-stride loop: d_a = x[n_a(i)] - x[i] (0 without a neighbour), s =
+// sqrt(eps + sum_a d_a^2); stores s and own = -sum_a d_a / s, and adds the
+// sum of s / n to *val once per block (one address: a per-warp atomic cost
+// ~1 ms on 24M elements).
+__global__ void __launch_bounds__(THREADS) k_tv_terms(const float* x, int C, const int32_t* nb, int64_t n,
+                                                       float* s_out, float* own_out, float* val) {
+    __shared__ float s_part[THREADS / 32];
     float v = 0.0f;
-    if (idx < n * C) {
+    for (int64_t idx = (int64_t)blockIdx.x * THREADS + threadIdx.x; idx < n * C;
+         idx += (int64_t)gridDim.x * THREADS) {
         const int64_t i = idx / C;
         const int c = (int)(idx - i * C);
         const float xi = x[idx];
         float d[3], q = TV_EPS;
-        int32_t nbr[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            nbr[a] = nb[3 * i + a];
-            d[a] = nbr[a] >= 0 ? x[(int64_t)nbr[a] * C + c] - xi : 0.0f;
+            const int32_t j = nb[3 * i + a];
+            d[a] = j >= 0 ? x[(int64_t)j * C + c] - xi : 0.0f;
             q = __fmaf_rn(d[a], d[a], q);
         }
-        const float s = sqrtf(q);
-        v = s;
-        const float f = scale / s;
-        atomicAdd(g + idx, -f * (d[0] + d[1] + d[2]));
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (nbr[a] >= 0) atomicAdd(g + (int64_t)nbr[a] * C + c, f * d[a]);
+        const float sv = sqrtf(q);
+        s_out[idx] = sv;
+        own_out[idx] = -(d[0] + d[1] + d[2]) / sv;
+        v += sv;
     }
     v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(val, v / (float)n);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < THREADS / 32; ++w) t += s_part[w];
+        if (t != 0.0f) atomicAdd(val, t / (float)n);
+    }
+}
+
+// Pass 2: d TV / d x[i][c] = (own + sum over the leaves j that have i as a
+// neighbour of (x[i] - x[j]) / s[j]) / n, times lambda: added to g (one
+// writer per element).
+__global__ void __launch_bounds__(THREADS) k_tv_grad(const float* x, int C, const int32_t* rev_off,
+                                                      const int32_t* rev, int64_t n, const float* s_in,
+                                                      const float* own_in, float scale, float* g) {
+    const int64_t idx = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+    if (idx >= n * C) return;
+    const int64_t i = idx / C;
+    const int c = (int)(idx - i * C);
+    const float xi = x[idx];
+    float acc = own_in[idx];
+    for (int32_t r = rev_off[i]; r < rev_off[i + 1]; ++r) {
+        const int64_t jc = (int64_t)rev[r] * C + c;
+        acc += (xi - x[jc]) / s_in[jc];
+    }
+    g[idx] += scale * acc;
 }
 
 // Adam (beta1 0.9, beta2 0.999, eps 1e-8); bc1, bc2 = 1 - beta^t.
@@ -332,6 +361,7 @@ void release(plo_octopt* o) {
     cudaSetDevice(o->device);
     cudaDeviceSynchronize();
     void* bufs[] = {o->d_s, o->d_k, o->d_gs, o->d_gk, o->d_ms, o->d_vs, o->d_mk, o->d_vk, o->d_nb,
+                    o->d_rev_off, o->d_rev, o->d_tv_s, o->d_tv_own,
                     o->d_tr_leaf, o->d_tr_t, o->d_tr_count, o->d_acc, o->d_flags};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -402,6 +432,10 @@ extern "C" plo_status plo_octopt_create(const plo_tree_desc* init, const plo_oct
                     {(void**)&o->d_mk, (size_t)nk * 4},
                     {(void**)&o->d_vk, (size_t)nk * 4},
                     {(void**)&o->d_nb, (size_t)nl * 12},
+                    {(void**)&o->d_rev_off, (size_t)(nl + 1) * 4},
+                    {(void**)&o->d_rev, (size_t)nl * 12},
+                    {(void**)&o->d_tv_s, (size_t)nk * 4},
+                    {(void**)&o->d_tv_own, (size_t)nk * 4},
                     {(void**)&o->d_tr_leaf, (size_t)cells * 8},
                     {(void**)&o->d_tr_t, (size_t)cells * 8},
                     {(void**)&o->d_tr_count, (size_t)config->max_rays * 4},
@@ -478,6 +512,23 @@ extern "C" plo_status plo_octopt_create(const plo_tree_desc* init, const plo_oct
                 k_nb_from_lookup<<<grid_of(nl * 3, 256), 256>>>(d_leaf, nl * 3, o->d_nb);
                 e = cudaDeviceSynchronize();
                 if (e == cudaSuccess) e = cudaGetLastError();
+                // the reverse table (counting sort of the (j, a) pairs by their neighbour)
+                std::vector<int32_t> nbh((size_t)nl * 3), off((size_t)nl + 1, 0), rev;
+                if (e == cudaSuccess) e = cudaMemcpy(nbh.data(), o->d_nb, (size_t)nl * 12, cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess) {
+                    for (int32_t v : nbh)
+                        if (v >= 0) ++off[(size_t)v + 1];
+                    for (int64_t i = 0; i < nl; ++i) off[i + 1] += off[i];
+                    rev.assign((size_t)off[nl] > 0 ? (size_t)off[nl] : 1, 0);
+                    std::vector<int32_t> fill(off.begin(), off.end() - 1);
+                    for (int64_t j = 0; j < nl; ++j)
+                        for (int a2 = 0; a2 < 3; ++a2) {
+                            const int32_t v = nbh[(size_t)j * 3 + a2];
+                            if (v >= 0) rev[(size_t)fill[v]++] = (int32_t)j;
+                        }
+                    e = cudaMemcpy(o->d_rev_off, off.data(), ((size_t)nl + 1) * 4, cudaMemcpyHostToDevice);
+                    if (e == cudaSuccess) e = cudaMemcpy(o->d_rev, rev.data(), (size_t)off[nl] * 4, cudaMemcpyHostToDevice);
+                }
                 if (e != cudaSuccess) st = cuda_error(e, "neighbour table");
             }
         }
@@ -540,13 +591,20 @@ plo_status run_grad(plo_octopt* o, const float* d_rays, const float* d_rgb_gt, c
         e = dispatch_grad(o->K, a, s);
         if (e != cudaSuccess) return cuda_error(e, "gradient kernel launch");
     }
-    if (o->cfg.tv_sigma > 0.0f) {
-        k_tv<<<grid_of(nl, THREADS), THREADS, 0, s>>>(o->d_s, 1, o->d_nb, nl, o->cfg.tv_sigma / (float)nl, o->d_gs,
-                                                      o->d_acc + 1);
-    }
-    if (o->cfg.tv_sh > 0.0f) {
-        k_tv<<<grid_of(nk, THREADS), THREADS, 0, s>>>(o->d_k, 3 * o->K, o->d_nb, nl, o->cfg.tv_sh / (float)nl,
-                                                      o->d_gk, o->d_acc + 2);
+    // the TV terms: densities (1 channel), then coefficients (3K channels);
+    // the two passes share the (s, own) scratch
+    const int chans[2] = {1, 3 * o->K};
+    const float lam[2] = {o->cfg.tv_sigma, o->cfg.tv_sh};
+    const float* xs[2] = {o->d_s, o->d_k};
+    float* gs[2] = {o->d_gs, o->d_gk};
+    for (int q = 0; q < 2; ++q) {
+        if (!(lam[q] > 0.0f)) continue;
+        const unsigned blocks = grid_of(nl * chans[q], THREADS);
+        const unsigned terms_blocks = std::min<unsigned>(blocks, 8u * 152u);
+        k_tv_terms<<<terms_blocks, THREADS, 0, s>>>(xs[q], chans[q], o->d_nb, nl, o->d_tv_s, o->d_tv_own,
+                                                    o->d_acc + 1 + q);
+        k_tv_grad<<<blocks, THREADS, 0, s>>>(xs[q], chans[q], o->d_rev_off, o->d_rev, nl, o->d_tv_s, o->d_tv_own,
+                                             lam[q] / (float)nl, gs[q]);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "TV kernel launch");
