@@ -806,10 +806,10 @@ def main():
                    "mean_sh_reads_per_ray": sh_visits, "host_setup_s": round(gen_s + build_s, 1)},
         "clocks": clocks,
         "e2e": e2e,
-        # per render call of 2^20 rays or more: the ray-order count, a
+        # per render call of 2^23 rays or more: the ray-order count, a
         # three-launch scan of its (bin, block) table, the positions, the
         # rays in order, k_render, the outputs back in ray order
-        "gpu_launches": K * (8 if n >= (1 << 20) else 1),
+        "gpu_launches": K * (8 if n >= (1 << 23) else 1),
         "roofline": lines["fp32"]["roofline"],
         "cpu_baseline": cpu,
         "fp16": {k: v for k, v in lines["fp16"].items()},

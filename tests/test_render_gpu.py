@@ -287,12 +287,12 @@ def test_deterministic_and_host_path(torch_cuda, d6):
 
 @pytest.mark.parametrize("prec", [plo.PREC_FP32, plo.PREC_FP16])
 def test_ray_order_leaves_results_unchanged(torch_cuda, d6, prec):
-    """Wavefronts of 2^20 rays or more are rendered in entry-cell order (a
+    """Wavefronts of 2^23 rays or more are rendered in entry-cell order (a
     sorted scratch copy); the same rays rendered in launches below that size
     (in index order) give bit-identical outputs and statuses, including rays
     that miss the box and rays with non-finite components."""
     import torch
-    rays = plogen.rays_room((1 << 20) + 4097, seed=17).copy()
+    rays = plogen.rays_room((1 << 23) + 4097, seed=17).copy()
     rays[::9973, :3] = (9.0, 9.0, 9.0)  # misses
     rays[5::99991, 3] = np.nan  # invalid
     t = plo.Tree(d6, prec)
