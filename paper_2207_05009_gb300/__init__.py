@@ -681,10 +681,10 @@ class OctOpt:
     def _run(self, fn, rays, rgb_gt, alpha_gt, ray_out, loss_out, stream):
         import torch
         R = rays.shape[0] if rays.ndim == 2 else -1
-        _require_all((ray_out, "ray_out", (R, 5), torch.float32), (loss_out, "loss_out", (3,), torch.float32))
-        _require_rays_targets(rays, rgb_gt, alpha_gt)
         if R > self.max_rays:
             raise ValueError(f"{R} rays exceed max_rays = {self.max_rays}")
+        _require_all((ray_out, "ray_out", (R, 5), torch.float32), (loss_out, "loss_out", (3,), torch.float32))
+        _require_rays_targets(rays, rgb_gt, alpha_gt)
         loss_out = loss_out if loss_out is not None else torch.empty(3, device=rays.device, dtype=torch.float32)
         _check(fn(self._h, _ptr(rays), _ptr(rgb_gt), _ptr(alpha_gt), R, _ptr(ray_out), _ptr(loss_out),
                   _stream(stream)))

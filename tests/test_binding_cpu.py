@@ -104,3 +104,25 @@ def test_network_handle_class_keeps_its_methods():
     for name in ("free", "__del__", "save", "load", "quad", "activation", "train_step", "distill"):
         assert callable(getattr(plo.Mlp, name)), name
     assert callable(plo.checkpoint_info)
+
+
+def test_leaf_optimiser_checks_its_buffers():
+    opt = plo.OctOpt.__new__(plo.OctOpt)  # no library handle: the checks run first
+    opt.n_leaves, opt.K, opt.max_rays = 10, 9, 64
+    rays, rgb, alpha = torch.zeros(64, 6), torch.zeros(64, 3), torch.zeros(64)
+    with pytest.raises(ValueError, match="rgb_gt"):
+        opt.grad(rays, torch.zeros(63, 3), alpha)
+    with pytest.raises(ValueError, match="alpha_gt"):
+        opt.step(rays, rgb, torch.zeros(64, 2))
+    with pytest.raises(ValueError, match="ray_out"):
+        opt.grad(rays, rgb, alpha, ray_out=torch.zeros(64, 4))
+    with pytest.raises(ValueError, match="loss_out"):
+        opt.step(rays, rgb, alpha, loss_out=torch.zeros(2))
+    with pytest.raises(ValueError, match="max_rays"):
+        opt.grad(torch.zeros(65, 6), torch.zeros(65, 3), torch.zeros(65))
+    with pytest.raises(ValueError, match="values"):
+        opt.write(plo.OCTOPT_SH, np.zeros((10, 3, 8), np.float32))
+    with pytest.raises(ValueError, match="unknown array"):
+        opt.read(99)
+    for name in ("free", "__del__", "grad", "step", "read", "write", "check", "build_tree"):
+        assert callable(getattr(plo.OctOpt, name)), name
