@@ -465,16 +465,67 @@ def run_distill(plo, torch, steps: int):
     return out
 
 
+def full_octree_child(depth: int) -> np.ndarray:
+    """Canonical child table of the complete octree of `depth` levels
+    (breadth-first node ids; the 8^depth leaves numbered in the order of
+    their parents)."""
+    rows = []
+    for lev in range(depth):
+        k = np.arange(8 ** lev, dtype=np.int64)[:, None] * 8 + np.arange(8)
+        if lev + 1 < depth:
+            rows.append((8 ** (lev + 1) - 1) // 7 + k)  # the next level's node ids
+        else:
+            rows.append(-k - 2)  # leaves
+    return np.concatenate(rows).astype(np.int32)
+
+
+def fit_octopt(plo, torch, init, l_max, batches, test_b, steps: int, W: int, total: int, **cfg):
+    """Timed steps and a fit of the direct leaf optimisation; returns the
+    step time and the packed result's error on the test rays."""
+    from paper_2207_05009_gb300 import learned
+    n = batches[0][0].shape[0]
+    opt = plo.OctOpt(init, l_max, max_rays=n, total_steps=total, **cfg)
+    loss = torch.empty(3, device="cuda")
+    stream = torch.cuda.current_stream()
+    first = None
+    for k in range(W):
+        opt.step(*batches[k % len(batches)], loss_out=loss)
+        if first is None:
+            first = float(loss[0].item())
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(steps):
+        opt.step(*batches[(W + k) % len(batches)], loss_out=loss)
+    b.record(stream)
+    torch.cuda.synchronize()
+    opt.check()
+    ms = a.elapsed_time(b) / steps
+    for k in range(W + steps, total):
+        opt.step(*batches[k % len(batches)], loss_out=loss)
+    torch.cuda.synchronize()
+    opt.check()
+    fit = opt.build_tree()
+    rel, psnr, a_rmse = learned.tree_error(fit, l_max, test_b)
+    fit.free()
+    opt.free()
+    torch.cuda.empty_cache()
+    return {"leaves": int(init.n_leaves), "rays_per_step": n, "steps_timed": steps, "ms_per_step": ms,
+            "mrays_per_s": n / (ms / 1e3) / 1e6, "fit_steps": total, "first_loss": first,
+            "final_loss": float(loss[0].item()), "error": {"rel_l2_radiance": rel, "psnr": psnr, "alpha_rmse": a_rmse}}
+
+
 def run_octopt(plo, torch, steps: int, W: int, fit_steps: int):
     """Direct optimisation of the octree's leaves (Sec. 7's alternative to
-    the network): the structure of the depth-8 luminaire (SH degree 3),
-    every leaf starting at sigma = 1 with the DC coefficient of the mean
-    emission (the network's starting level), fitted with the paper's loss,
-    small TV weights and Adam to the plain renderer's images of the
-    luminaire (the network's targets), 65,536 rays per step.  `steps` timed
-    steps after W warm-up steps (CUDA events); then the fit continues to
-    `fit_steps` steps and the packed result is scored on 65,536 test rays
-    like the distilled network."""
+    the network), fitted with the paper's loss, small TV weights and Adam to
+    the plain renderer's images of the depth-8 luminaire (the network's
+    targets), 65,536 rays per step, every leaf starting at sigma = 1 with
+    the DC coefficient of the mean emission (the network's starting level):
+    on the luminaire's own structure (497,856 leaves, SH degree 3), and on
+    the complete depth-7 octree (2,097,152 leaves), which knows nothing of
+    it.  `steps` timed steps after W warm-up steps (CUDA events); then each
+    fit continues to `fit_steps` steps and the packed result is scored on
+    65,536 test rays like the distilled network."""
     import plogen
     from paper_2207_05009_gb300 import learned
     gt_host = plogen.luminaire_tree(plogen.LUMINAIRE_D10.with_(depth=8))
@@ -484,45 +535,23 @@ def run_octopt(plo, torch, steps: int, W: int, fit_steps: int):
     test_b = learned.target_batches(gt, [plogen.rays_sphere(n, seed=900)])
     gt.free()
     l_max, c0 = learned.emission_scale(batches)
-    sh0 = np.zeros_like(gt_host.sh)
     u = min(max(c0 / l_max, 1e-6), 1 - 1e-6)
-    sh0[:, :, 0] = np.log(u / (1 - u)) / 0.28209479177387814  # emission c0 in every direction
-    init = plogen.HostTree(gt_host.depth, gt_host.sh_degree, gt_host.child,
-                           np.ones(gt_host.n_leaves, np.float32), sh0)
+    dc = np.log(u / (1 - u)) / 0.28209479177387814  # emission c0 in every direction
     total = max(fit_steps, steps + W)
-    opt = plo.OctOpt(init, l_max, max_rays=n, lr_sigma=5.0, lr_sh=0.1, lr_decay=0.1, total_steps=total,
-                     tv_sigma=1e-4, tv_sh=1e-5)
-    loss = torch.empty(3, device="cuda")
-    stream = torch.cuda.current_stream()
-    first = None
-    for k in range(W):
-        opt.step(*batches[k % 16], loss_out=loss)
-        if first is None:
-            first = float(loss[0].item())
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for k in range(steps):
-        opt.step(*batches[(W + k) % 16], loss_out=loss)
-    b.record(stream)
-    torch.cuda.synchronize()
-    opt.check()
-    ms = a.elapsed_time(b) / steps
-    for k in range(W + steps, total):
-        opt.step(*batches[k % 16], loss_out=loss)
-    torch.cuda.synchronize()
-    opt.check()
-    fit = opt.build_tree()
-    rel, psnr, a_rmse = learned.tree_error(fit, l_max, test_b)
-    fit.free()
-    out = {"workload": f"depth-8 luminaire structure ({gt_host.n_leaves} leaves, SH degree 3) fitted from sigma = 1 "
-                       "and the mean emission to the plain renderer's images; paper loss, TV 1e-4 / 1e-5, Adam "
-                       "(5.0 / 0.1 decaying to a tenth); 65,536 rays per step",
-           "rays_per_step": n, "steps_timed": steps, "ms_per_step": ms, "mrays_per_s": n / (ms / 1e3) / 1e6,
-           "fit_steps": total, "first_loss": first, "final_loss": float(loss[0].item()),
-           "error": {"rel_l2_radiance": rel, "psnr": psnr, "alpha_rmse": a_rmse}}
-    opt.free()
-    torch.cuda.empty_cache()
+    cfg = dict(lr_sigma=5.0, lr_sh=0.1, lr_decay=0.1, tv_sigma=1e-4, tv_sh=1e-5)
+    out = {"workload": "the depth-8 luminaire's images (the network's targets) fitted from sigma = 1 and the mean "
+                       "emission; paper loss, TV 1e-4 / 1e-5, Adam (5.0 / 0.1 decaying to a tenth); 65,536 rays per "
+                       "step; SH degree 3"}
+    for name, depth, child, nl in (("luminaire_structure", gt_host.depth, gt_host.child, gt_host.n_leaves),
+                                   ("complete_depth7", 7, full_octree_child(7), 8 ** 7)):
+        sh0 = np.zeros((nl, 3, gt_host.K), np.float32)
+        sh0[:, :, 0] = dc
+        init = plogen.HostTree(depth, gt_host.sh_degree, child, np.ones(nl, np.float32), sh0)
+        out[name] = fit_octopt(plo, torch, init, l_max, batches, test_b, steps, W, total, **cfg)
+    # the headline fields: the luminaire-structure fit
+    for k in ("ms_per_step", "mrays_per_s", "first_loss", "final_loss", "error", "fit_steps", "rays_per_step",
+              "steps_timed"):
+        out[k] = out["luminaire_structure"][k]
     return out
 
 
