@@ -45,7 +45,10 @@ constexpr int BLOCK = 256;
 #define PLO_BRICK_MIN_BLOCKS 3  // the same for the brick-layout kernels
 #endif
 constexpr int WARPS = BLOCK / 32;
-constexpr int64_t RENDER_CLAIM = 64;  // rays a warp claims at a time from the shared cursor
+constexpr int64_t RENDER_CLAIM = 32;  // rays a warp claims at a time from the shared cursor (32 measured best of 32-128)
+#ifndef PLO_DESCEND_LEVELS
+#define PLO_DESCEND_LEVELS 4  // tree levels a descent goes down per step (measured best of 2, 3, 4, 5, all)
+#endif
 
 // One packed tree as the kernels see it.
 struct TreeParams {
@@ -344,15 +347,18 @@ __device__ __forceinline__ void brick_enter(const TreeParams& tp, Ray& R, uint32
     R.state = ST_BRICK;
 }
 
-// Descends from R.node (level R.level) to the leaf or empty octant that holds
-// the point, taking the child bits from the finest-grid coordinates R.q, and
-// ends in ST_LEAF (or, in the brick layout, in ST_BRICK when it reaches a
-// brick).  The whole descent runs in one step: stopping after each
-// dependent global load, so that lanes with shorter descents could go on,
-// was measured slower (304 vs 320 Mrays/s).
+// Descends from R.node (level R.level) towards the leaf or empty octant that
+// holds the point, taking the child bits from the finest-grid coordinates
+// R.q, and ends in ST_LEAF (or, in the brick layout, in ST_BRICK when it
+// reaches a brick).  A step goes down at most PLO_DESCEND_LEVELS levels; a
+// longer descent goes on in the next step while the other lanes composite.
+// A lane needs 2 levels per step on average but the warp ran the longest
+// descent among its lanes, 5.7 levels (depth-10 luminaire, 16M room rays):
+// 4 levels per step measured 348 -> 365 Mrays/s with FP32 leaves, 390 ->
+// 397 with FP16; 2 levels gained nothing and 1 level lost.
 template <bool BRICKS, int PREC>
 __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* s_nodes, Ray& R, uint32_t* stack) {
-    for (int guard = 0; guard <= MAX_DEPTH; ++guard) {
+    for (int guard = 0; guard < PLO_DESCEND_LEVELS; ++guard) {
         const int sh = tp.depth - 1 - R.level;
         R.slot = (int)(((R.q[0] >> sh) & 1u) | (((R.q[1] >> sh) & 1u) << 1) | (((R.q[2] >> sh) & 1u) << 2));
         uint2 e = load_entry(tp, s_nodes, R.node, R.slot);
@@ -875,8 +881,8 @@ __global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : (BRICKS ? PLO_B
         }
         const unsigned live = __ballot_sync(0xffffffffu, R.state != ST_IDLE);
         if (live == 0u) break;
-        // every live lane is at a leaf or in a brick here (descents run to
-        // the leaf or brick)
+        // every live lane is at a leaf, in a brick, or part-way down a
+        // descent longer than one step allows
         if (BRICKS && R.state == ST_BRICK) brick_step<K, PREC, SPHERE>(kp, tp, my, R, stack, sY);
         if (R.state == ST_LEAF) leaf_step<K, PREC, TRACE, SPHERE>(kp, tp, my, R, stack, sY);
         if (R.state == ST_DESCEND) descend_step<BRICKS, PREC>(tp, s_nodes, R, stack);
