@@ -399,17 +399,22 @@ def run_train(plo, torch, steps: int, W: int):
     flops = M * 2 * 3 * (trunk + 256 * 49)
     sustained, burst, src = measured_tflops()
 
-    def time_op(fn, reps=10):
+    def time_op(fn, reps=10, batches=5):
+        # median over batches of `reps` launches: one late launch (a clock
+        # change, another process on the host) then moves no number
         for _ in range(2):
             fn()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+        per = []
+        for _ in range(batches):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per.append(e0.elapsed_time(e1) / reps)
+        return float(np.median(per))
 
     g = torch.Generator(device="cuda").manual_seed(5)
     H = (torch.rand(M, 256, device="cuda", generator=g) - 0.3).to(torch.bfloat16)
