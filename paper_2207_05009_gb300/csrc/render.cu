@@ -373,13 +373,12 @@ __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* 
             R.entry_y = e.y;
             R.state = ST_LEAF;
             // the SH record is read in the next iteration: start pulling it
-            // into L2 now (16-bit records; measured on the depth-10 workload:
-            // FP16 347 -> 388 Mrays/s with it, FP32 339 -> 330, so FP32
-            // records are left to the load itself).  The choice is made at
-            // compile time: as a run-time test it cost the FP16 kernel 9%.
+            // into L2 now (measured on the depth-10 workload: FP16 347 ->
+            // 388 Mrays/s with it; FP32 records gained only once descents
+            // were limited to 4 levels per step and the rays sorted by entry
+            // cell, 366 -> 379, having cost 339 -> 330 before)
             const uint32_t rec = e.x & ~LEAF_BIT;
-            constexpr bool always = PREC > 0, never = PREC == PLO_PREC_FP32;
-            if (!never && (always || tp.prec != PLO_PREC_FP32) && e.x != ENTRY_EMPTY && rec != NO_SH_RECORD) {
+            if (e.x != ENTRY_EMPTY && rec != NO_SH_RECORD) {
                 const char* a = reinterpret_cast<const char*>(tp.sh) + (size_t)rec * tp.sh_stride;
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(a + tp.sh_stride - 1));
@@ -816,10 +815,14 @@ __device__ void brick_step(const KParams& kp, const TreeParams& tp, int64_t i, R
     brick_exit(kp, tp, i, R, stack, ax, tx);
 }
 
-// The trace and sphere-proxy kernels keep more per-ray state: 3 blocks per
-// SM (80 registers) beats 4 with spills for them (measured).
+// The trace and sphere-proxy kernels keep more per-ray state, and degree-4
+// leaves (K = 25) a larger basis: 3 blocks per SM (80 registers) beats 4
+// with spills for them (measured; K = 25 on the depth-10 luminaire: 217 ->
+// 285 Mrays/s with FP32 leaves, 287 -> 326 with FP16).
 template <int K, int PREC, bool TRACE, bool SPHERE, bool BRICKS>
-__global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE) ? 3 : (BRICKS ? PLO_BRICK_MIN_BLOCKS : PLO_RENDER_MIN_BLOCKS))
+__global__ void __launch_bounds__(BLOCK, (TRACE || SPHERE || K >= 25)
+                                              ? 3
+                                              : (BRICKS ? PLO_BRICK_MIN_BLOCKS : PLO_RENDER_MIN_BLOCKS))
     k_render(KParams kp) {
     // nodes of the top levels, staged once per (persistent) block, then the
     // node id per level of the current cell's path (top_depth + 1 rows, one
