@@ -373,12 +373,15 @@ __device__ __forceinline__ void descend_step(const TreeParams& tp, const uint2* 
             R.entry_y = e.y;
             R.state = ST_LEAF;
             // the SH record is read in the next iteration: start pulling it
-            // into L2 now (measured on the depth-10 workload: FP16 347 ->
-            // 388 Mrays/s with it; FP32 records gained only once descents
-            // were limited to 4 levels per step and the rays sorted by entry
-            // cell, 366 -> 379, having cost 339 -> 330 before)
+            // into L2 now, for 16-bit records (measured on the depth-10
+            // workload: FP16 427 -> 436 Mrays/s with it, FP32 410 -> 404,
+            // so FP32 records are left to the load itself; before the leaf
+            // step advanced ahead of its compositing FP32 gained, 366 ->
+            // 379).  The choice is made at compile time: as a run-time test
+            // it cost the FP16 kernel 9%.
             const uint32_t rec = e.x & ~LEAF_BIT;
-            if (e.x != ENTRY_EMPTY && rec != NO_SH_RECORD) {
+            constexpr bool always = PREC > 0, never = PREC == PLO_PREC_FP32;
+            if (!never && (always || tp.prec != PLO_PREC_FP32) && e.x != ENTRY_EMPTY && rec != NO_SH_RECORD) {
                 const char* a = reinterpret_cast<const char*>(tp.sh) + (size_t)rec * tp.sh_stride;
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(a + tp.sh_stride - 1));
