@@ -538,6 +538,12 @@ __device__ __forceinline__ bool composite(const KParams& kp, const TreeParams& t
     float sigma = decode_sigma<PREC>(R.entry_y, tp.prec);
     if (sigma < kp.sigma_min) sigma = 0.0f;
     if (!(sigma > 0.0f)) return false;
+    // the emission first: its record loads are then in flight during the
+    // transmittance arithmetic (measured +1.5% with FP32 leaves)
+    const uint32_t rec = R.entry_x & ~LEAF_BIT;
+    float cr = 0.0f, cg = 0.0f, cb = 0.0f;
+    const bool emits = rec != NO_SH_RECORD;
+    if (emits) sh_emission<K, PREC>(tp, rec, R.entry_y, R.dirn, cr, cg, cb, sY);
     const float a = sigma * seg;
     const float Tin = R.T;
     const DF s = two_sum(R.od.hi, a);
@@ -551,10 +557,6 @@ __device__ __forceinline__ bool composite(const KParams& kp, const TreeParams& t
         const float dT = fminf(Tin, a);
         w = kp.transmittance == PLO_TRANS_LINEAR ? dT : 0.5f * dT * (Tin + Tout);
     }
-    const uint32_t rec = R.entry_x & ~LEAF_BIT;
-    float cr = 0.0f, cg = 0.0f, cb = 0.0f;
-    const bool emits = rec != NO_SH_RECORD;
-    if (emits) sh_emission<K, PREC>(tp, rec, R.entry_y, R.dirn, cr, cg, cb, sY);
     if (emits || kp.activation != PLO_ACT_RELU) {
         R.r = __fmaf_rn(w, act_fn(cr, kp.activation, kp.l_max), R.r);
         R.g = __fmaf_rn(w, act_fn(cg, kp.activation, kp.l_max), R.g);
