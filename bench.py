@@ -19,6 +19,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -170,10 +171,15 @@ def measured_peak():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the render kernel's code (comments and whitespace left out,
+    so that a comment edit keeps a capture taken on the same code)."""
     h = hashlib.sha256()
     for fn in ("render.cu", "tree.cu", "plo_internal.h"):
-        with open(os.path.join(ROOT, "paper_2207_05009_gb300", "csrc", fn), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2207_05009_gb300", "csrc", fn)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -571,8 +571,9 @@ __device__ __forceinline__ bool composite(const KParams& kp, const TreeParams& t
     return false;
 }
 
-// One cell: segment length, compositing, advance.  Leaves the lane in
-// ST_DESCEND (next cell) or ST_IDLE (ray finished, outputs written).
+// One cell: segment length, advance to the next cell, compositing.  Leaves
+// the lane in ST_DESCEND (next cell) or ST_IDLE (ray finished, outputs
+// written).
 template <int K, int PREC, bool TRACE, bool SPHERE>
 __device__ void leaf_step(const KParams& kp, const TreeParams& tp, int64_t i, Ray& R, uint32_t* stack,
                           const float* sY = nullptr) {
