@@ -54,7 +54,7 @@ constexpr int PE_PAD = 64;
 constexpr int OUT_PAD = 64;
 constexpr int N_LAYERS = DEPTH + 1;      // linear-head architecture
 constexpr int MAX_LAYERS = DEPTH + 2;    // paper architecture: + combined layer, + SH layer
-constexpr int FEAT = 128;                // width of the paper's extra output layer
+constexpr int FEAT = 128;                // width of the layer before the SH outputs (Sec. 4.2)
 constexpr int COMB_PAD = 192;            // combined layer rows: 128 features, sigma, zero padding
 
 // ---------------------------------------------------------------- TMA maps
