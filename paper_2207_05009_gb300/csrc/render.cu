@@ -3,11 +3,12 @@
 // (paper Sec. 4.1, Eq. 3-5; plenoctree of Sec. 4.2 / Sec. 5).
 //
 // One thread renders one ray at a time.  The grid is persistent: warps take
-// rays from a shared counter (64 at a time; small launches give each warp a
+// rays from a shared counter (32 at a time; small launches give each warp a
 // contiguous chunk) and a lane that finishes its ray takes the next one, so
 // a warp does not idle behind its longest ray; each iteration of a warp
-// composites the cell every live lane is in, then descends every lane to its
-// next cell.  Child slots come from the bits of the point's integer
+// moves every live lane past the cell it is in (advance, then composite),
+// then descends every lane towards its next cell, at most 4 levels per
+// iteration.  Child slots come from the bits of the point's integer
 // coordinates on the finest grid.
 //
 // Numerics (all FP32, no FP64 on the device):
